@@ -1,0 +1,129 @@
+"""Physics pins of the oracle's integrator: what the paper fixes about the dynamics.
+
+* thermostat off (gamma = 0): energy conservation, time reversibility and
+  momentum conservation of the Langevin/BAOAB integrator (Eq. 8 without bath,
+  Eq. 4 for the ring polymer);
+* QTB on harmonic oscillators reproduces theta(w0, T) of Eq. 1 up to the
+  friction correction, computed independently by quadrature of the Langevin
+  response with the filter's own spectral density (Eqs. 6-8);
+* PIMD on harmonic oscillators reproduces the finite-P closed form of the
+  primitive estimator (Eqs. 3, 5, 11);
+* QTB-PIMD on harmonic oscillators gives the bead-averaged <x^2> = theta/(m w^2)
+  that Eq. 10 demands, again with the friction correction by quadrature.
+"""
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import spectra as S
+from paper_1905_02521_gb300 import workloads as W
+
+HBAR, KB, MVV2E = 0.6582119569, 8.617333262e-5, 103.64269652680505
+
+
+def _block_sigma(x, nblk=20):
+    b = np.array_split(np.asarray(x), nblk)
+    m = np.array([bb.mean() for bb in b])
+    return m.std(ddof=1) / np.sqrt(nblk)
+
+
+def test_nve_conservation_and_reversibility(oracle):
+    sysd, pot = W.mgo_system(2, T=300.0, gamma=0.0)
+    sim = oracle.Sim(sysd["pos"], sysd["vel"], sysd["types"], pot, sysd["box"], 300.0, 0.0, 1.0, seed=1)
+    rec0 = sim.observe()
+    rec = sim.step(400)
+    E = rec[:, 1] + rec[:, 2]
+    E0 = rec0[1] + rec0[2]
+    assert np.abs(E - E0).max() < 2e-3 * rec0[1]
+    assert np.abs(rec[:, 14:17] - rec0[14:17]).max() < 1e-10
+    # reverse the velocities and integrate back to the start
+    x, v, f, st = sim.state()
+    sim.set_state(x, -v, st)
+    sim.step(400, record=False)
+    xb, vb, _, _ = sim.state()
+    assert np.abs(xb - sysd["pos"]).max() < 1e-7
+    assert np.abs(vb + sysd["vel"]).max() < 1e-9
+
+
+def test_ring_polymer_nve_conserves_effective_hamiltonian(oracle):
+    sysd, pot = W.mgo_system(2, T=300.0, gamma=0.0, n_beads=4)
+    rng = np.random.default_rng(2)
+    pos = sysd["pos"] + rng.normal(0, 0.01, sysd["pos"].shape)
+    sim = oracle.Sim(pos, sysd["vel"], sysd["types"], pot, sysd["box"], 300.0, 0.0, 0.5, seed=1)
+    r0 = sim.observe()
+    rec = sim.step(300)
+    H = rec[:, 1] + rec[:, 3] + rec[:, 2]
+    assert np.abs(H - (r0[1] + r0[3] + r0[2])).max() < 2e-3 * r0[1]
+
+
+def _quad_x2_v2(wgrid_S, w0, gamma, m, wmax):
+    """<x^2>, <v^2> of a Langevin oscillator driven by noise of density 2 m gamma S(w)."""
+    def resp(w):
+        return 2 * gamma / (m * MVV2E * ((w0 ** 2 - w ** 2) ** 2 + (gamma * w) ** 2)) / np.pi
+    pts = [w0]
+    x2 = integrate.quad(lambda w: resp(w) * wgrid_S(w), 0, wmax, points=pts, limit=2000)[0]
+    v2 = integrate.quad(lambda w: resp(w) * w * w * wgrid_S(w), 0, wmax, points=pts, limit=2000)[0]
+    return x2, v2
+
+
+def _filter_density(h, dt):
+    k = np.arange(1, len(h))
+    return lambda w: (h[0] + 2 * np.cos(w * dt * k) @ h[1:]) ** 2
+
+
+@pytest.mark.slow
+def test_qtb_harmonic_oscillator_energy(oracle):
+    w0, T, gamma, dt, L, m = 0.1, 100.0, 0.01, 0.5, 513, 1.008
+    h = S.taps(L, dt, T, 0.5)
+    sysd, pot = W.oscillators(100, T, gamma, mass=m)
+    sim = oracle.Sim(sysd["pos"], sysd["vel"], sysd["types"], pot, None, T, gamma, dt, seed=7, taps=h,
+                     potential=oracle.POT_HARMONIC, ext={"omega": w0})
+    sim.step(2000, record=False)
+    rec = sim.step(20000)
+    E = (rec[:, 1] + rec[:, 2]) / 300.0
+    x2, v2 = _quad_x2_v2(_filter_density(h, dt), w0, gamma, m, np.pi / dt)
+    E_q = 0.5 * m * MVV2E * (v2 + w0 ** 2 * x2)
+    sig = _block_sigma(E)
+    assert abs(E.mean() - E_q) < 4 * sig + 5e-3 * E_q
+    # and the friction-free target of Eq. 1 is close (gamma/w0 = 0.1)
+    assert E_q == pytest.approx(S.theta(w0, T), rel=0.03)
+    # quantum, not classical: theta is ~4x k_B T here
+    assert E.mean() > 3 * KB * T
+
+
+@pytest.mark.slow
+def test_pimd_harmonic_primitive_energy_closed_form(oracle):
+    w0, gamma, dt, m = 0.1, 0.01, 0.5, 1.008
+    T = HBAR * w0 / (3.0 * KB)                       # beta hbar w0 = 3
+    for P in (1, 4):
+        sysd, pot = W.oscillators(100, T, gamma, n_beads=P, mass=m)
+        sim = oracle.Sim(sysd["pos"], sysd["vel"], sysd["types"], pot, None, T, gamma, dt, seed=11,
+                         potential=oracle.POT_HARMONIC, ext={"omega": w0})
+        sim.step(3000, record=False)
+        rec = sim.step(20000)
+        E = rec[:, 4] / 300.0
+        k = np.arange(P)
+        E_P = KB * T * np.sum(1.0 / (1.0 + (2 * P / 3.0) ** 2 * np.sin(k * np.pi / P) ** 2))
+        sig = _block_sigma(E)
+        assert abs(E.mean() - E_P) < 4 * sig + 3e-3 * E_P, (P, E.mean(), E_P, sig)
+
+
+@pytest.mark.slow
+def test_qtb_pimd_harmonic_position_variance(oracle):
+    w0, T, gamma, dt, L, m, P = 0.1, 100.0, 0.01, 0.5, 513, 1.008, 4
+    sol = S.kappa_solve(P)
+    h = S.taps(L, dt, T, 0.5, P=P, sol=sol)
+    sysd, pot = W.oscillators(50, T, gamma, n_beads=P, mass=m)
+    sim = oracle.Sim(sysd["pos"], sysd["vel"], sysd["types"], pot, None, T, gamma, dt, seed=13, taps=h,
+                     potential=oracle.POT_HARMONIC, ext={"omega": w0})
+    sim.step(2000, record=False)
+    rec = sim.step(16000)
+    x2 = rec[:, 17] / 150.0                          # bead-averaged <x^2> per 1-D oscillator
+    dens = _filter_density(h, dt)
+    wk = oracle.nm_freqs(P, T)
+    q2 = [_quad_x2_v2(dens, np.sqrt(w0 ** 2 / P + wk[k] ** 2), gamma, m, np.pi / dt)[0] for k in range(P)]
+    x2_q = np.mean(q2)
+    sig = _block_sigma(x2)
+    assert abs(x2.mean() - x2_q) < 4 * sig + 5e-3 * x2_q
+    # Eq. 10: without friction the bead average is the quantum theta/(m w0^2)
+    assert x2_q == pytest.approx(S.theta(w0, T) / (m * MVV2E * w0 ** 2), rel=0.05)
