@@ -1,0 +1,200 @@
+/*
+ * qtb.h -- C ABI of the GB300 quantum-thermal-bath molecular-dynamics hot path.
+ *
+ * Method: Dammak, Hayoun, Brieuc, Geneste, "Nuclear quantum effects in molecular
+ * dynamics simulations".  The library advances one or many independent systems
+ * (atoms x ring-polymer beads) with a Langevin (BAOAB) integrator whose random
+ * force is coloured so that its power spectral density is 2 m gamma theta(w,T)
+ * (Eqs. 6-8, QTB-MD) or 2 m gamma kappa_P(w,T) applied to the ring-polymer
+ * normal modes (Eqs. 10-12, QTB-PIMD), or white (classical Langevin / PIMD).
+ *
+ * Conventions
+ *   units       A, fs, eV, u (atomic mass), e, K; frequencies in rad/fs.
+ *   errors      every call returns a qtb_status (0 = QTB_OK, negative = error);
+ *               qtb_last_error() gives a one-line message.  No exception or
+ *               longjmp crosses this boundary.
+ *   host arrays are borrowed for the duration of the call only (copied).
+ *   device memory is owned by the library; it is obtained through the
+ *               caller's allocator callbacks when given (e.g. a PyTorch caching
+ *               allocator), else cudaMalloc.
+ *   streams     all device work is issued on the stream given to qtb_init
+ *               (NULL: the library creates and owns a non-blocking stream).  qtb_step_n is asynchronous;
+ *               qtb_observables, qtb_get_* and qtb_sync synchronise the stream
+ *               and report device-side errors (cell overflow, non-finite
+ *               state) raised by earlier steps.
+ *   threads     a context must not be used from two threads at once.
+ */
+#ifndef QTB_H
+#define QTB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qtb_ctx qtb_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    QTB_OK = 0,
+    QTB_ERR_ARG = -1,       /* invalid argument (message says which)           */
+    QTB_ERR_CUDA = -2,      /* a CUDA runtime/driver call failed                */
+    QTB_ERR_OOM = -3,       /* device allocation failed                         */
+    QTB_ERR_TIMEOUT = -4,   /* reserved: a bounded device wait gave up          */
+    QTB_ERR_NONFINITE = -5, /* a force or velocity became NaN/Inf               */
+    QTB_ERR_SOLVE = -6,     /* kappa_P solve failed (non-positive pivot or PSD) */
+    QTB_ERR_OVERFLOW = -7,  /* a cell of the cell list overflowed its capacity  */
+    QTB_ERR_STATE = -8      /* call not valid in the current state              */
+} qtb_status;
+
+/* Arithmetic of the step.  QTB_FP64: every step in FP64.  QTB_MIXED: positions
+ * in 30-bit fixed point per box length, forces/integration in FP32, energies
+ * and virials accumulated in FP64, noise filter per qtb_filter_prec. */
+typedef enum { QTB_FP64 = 0, QTB_MIXED = 1 } qtb_precision;
+
+/* Noise filter arithmetic (QTB_MIXED only; QTB_FP64 always filters in FP64).
+ * FP32: direct FP32 convolution.  BF16: blocked Toeplitz GEMM on the tensor
+ * cores (tcgen05, BF16 operands, FP32 accumulation). */
+typedef enum { QTB_FILTER_FP64 = 0, QTB_FILTER_FP32 = 1, QTB_FILTER_BF16 = 2 } qtb_filter_prec;
+
+/* Random force of the O step.
+ *   WHITE    classical Langevin (PIMD when n_beads > 1): PSD 2 m gamma k_B T.
+ *   QTB      PSD 2 m gamma theta(w,T), Eq. 7 (n_beads must be 1).
+ *   QTB_PIMD PSD 2 m gamma kappa_P(w,T) per normal mode, Eq. 12.
+ *   QTB_PIMD_MLP as QTB_PIMD with kappa_P from the learned model set by
+ *            qtb_set_kappa_model (falls back to the solver where the model's
+ *            error, judged by the solver, exceeds its tolerance). */
+typedef enum { QTB_NOISE_WHITE = 0, QTB_NOISE_QTB = 1, QTB_NOISE_QTB_PIMD = 2, QTB_NOISE_QTB_PIMD_MLP = 3 } qtb_noise;
+
+/* Potential energy surface.  PAIR: Buckingham (energy-shifted at r_cut) plus
+ * damped-shifted-force Coulomb (Fennell & Gezelter 2006) in an orthorhombic
+ * periodic box, all images within r_cut.  HARMONIC / DOUBLEWELL: separable
+ * external potential per Cartesian component, 1/2 m w0^2 x^2 or
+ * V0 (x^2/a^2 - 1)^2 (no box). */
+typedef enum { QTB_POT_PAIR = 0, QTB_POT_HARMONIC = 1, QTB_POT_DOUBLEWELL = 2 } qtb_potential;
+
+typedef struct {
+    int n_atoms;        /* N >= 1                                                  */
+    int n_beads;        /* P in {1..6, 8, 16, 32} (Trotter number of Eq. 2)      */
+    const int *type;    /* [N] type index < n_types                               */
+    const double *pos;  /* [P][N][3] bead positions, A                             */
+    const double *vel;  /* [P][N][3] bead velocities, A/fs; NULL = zero           */
+    double box[3];      /* orthorhombic box edges, A (PAIR only; each >= r_cut)   */
+    double T;           /* temperature, K (> 0)                                    */
+    double gamma;       /* friction coefficient of Eq. 8, 1/fs (>= 0)             */
+} qtb_system;
+
+typedef void *(*qtb_alloc_fn)(size_t bytes, void *user);
+typedef void (*qtb_free_fn)(void *ptr, void *user);
+
+typedef struct {
+    int n_types;
+    const double *mass;    /* [n_types] u                                          */
+    const double *charge;  /* [n_types] e                                          */
+    const double *buck_A;  /* [n_types*n_types] eV   (0 = no Buckingham term)      */
+    const double *buck_rho;/* [n_types*n_types] A                                  */
+    const double *buck_C;  /* [n_types*n_types] eV A^6                              */
+    double dsf_alpha;      /* DSF damping, 1/A                                     */
+    double r_cut;          /* cutoff, A                                            */
+    int potential;         /* qtb_potential                                        */
+    double ext_omega;      /* HARMONIC: w0, rad/fs                                 */
+    double ext_V0, ext_a;  /* DOUBLEWELL: V0 (eV), a (A)                           */
+    double dt;             /* time step, fs                                        */
+    int precision;         /* qtb_precision                                        */
+    int filter_prec;       /* qtb_filter_prec                                      */
+    unsigned long long seed; /* Philox key; system s uses key (lo32(seed), hi32(seed)^s) */
+    int obs_stride;        /* record observables every obs_stride steps (>= 1)     */
+    int max_records;       /* capacity of the per-system observable series (>= 1)  */
+    qtb_alloc_fn dev_alloc;  /* optional device allocator                          */
+    qtb_free_fn dev_free;    /* its matching free                                  */
+    void *alloc_user;        /* passed to both                                     */
+} qtb_params;
+
+/* Observable record (FP64), one per recorded step and system:
+ *   [0] step index after the step   [1] K = sum 1/2 m v^2 over beads (eV)
+ *   [2] V = (1/P) sum_s V(r^(s))    [3] spring = sum_s sum_i 1/2 m w_P^2 (r_s - r_{s+1})^2
+ *   [4] E_prim = K - spring + V (Eq. 5)
+ *   [5..13] virial (1/P) sum_s sum_pairs d (x) F, row-major 3x3 (eV)
+ *   [14..16] total momentum (u A/fs)   [17] (1/P) sum_s sum_i |r_i^(s)|^2 (A^2)
+ *   [18..19] reserved (0) */
+#define QTB_NREC 20
+
+/* Create a context for n_sys independent systems sharing one parameter set.
+ * Copies the host arrays, allocates device state, computes the first forces.
+ * The noise starts WHITE for every system (call qtb_set_filter to change).
+ * Reads: Eqs. 3-4 (ring polymer), Eq. 8 (Langevin).  stream: a cudaStream_t. */
+int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *p, void *stream);
+
+/* Choose the random force of system sys (-1 = all systems).
+ * mode: qtb_noise.  n_taps: odd filter length L = 2K+1 of the zero-phase
+ * time-domain filter (ignored for WHITE).  omega_max: Fermi cutoff of the
+ * spectrum, rad/fs (<= 0: none).  Builds theta(w_j,T) (Eq. 1) or kappa_P
+ * (Eq. 10, solved in FP64 on the GPU) on w_j = 2 pi j/(L dt), then the taps by
+ * an FP64 cosine transform.  Takes effect from the next step; the stochastic
+ * trajectory for a given seed does not depend on when it is called, only on
+ * the filter in force at each step. */
+int qtb_set_filter(qtb_ctx *c, int sys, int mode, int n_taps, double omega_max);
+
+/* Advance every system by n_steps BAOAB steps (asynchronous).  Whole 256-step
+ * noise blocks run as one CUDA-graph launch. */
+int qtb_step_n(qtb_ctx *c, long long n_steps);
+
+/* Wait for the stream; report device-side errors of earlier steps. */
+int qtb_sync(qtb_ctx *c);
+
+/* Latest observable record of system sys (QTB_NREC doubles, host). */
+int qtb_observables(qtb_ctx *c, int sys, double *out);
+
+/* All records kept for system sys, oldest first: out[max][QTB_NREC]; *n_out =
+ * number written (at most max_records of qtb_params). */
+int qtb_get_series(qtb_ctx *c, int sys, double *out, int max, int *n_out);
+
+/* Bead positions/velocities [P][N][3] of system sys (host FP64).  Positions
+ * are wrapped into the box for PAIR systems.  Either pointer may be NULL. */
+int qtb_get_state(qtb_ctx *c, int sys, double *pos, double *vel);
+
+/* Replace positions/velocities of system sys (either may be NULL = keep) and
+ * recompute its forces at the current step index. */
+int qtb_set_state(qtb_ctx *c, int sys, const double *pos, const double *vel);
+
+/* Forces [P][N][3] (eV/A) of system sys at the current positions, including the
+ * 1/P factor of Eq. 4. */
+int qtb_get_forces(qtb_ctx *c, int sys, double *f);
+
+/* Filter taps h_0..h_K (FP64) of system sys; *n_out = K+1. */
+int qtb_get_taps(qtb_ctx *c, int sys, double *h, int max, int *n_out);
+
+/* Coloured noise eta (the O step uses sqrt((1-c1^2)/m) eta) for the 256-step
+ * block containing the current step, system sys: out[256][3 N P] (FP64),
+ * dof = (mode k * 3 + component) * N + atom; *block_out = block index. */
+int qtb_get_noise(qtb_ctx *c, int sys, double *out, long long *block_out);
+
+/* Profiling of whole 256-step blocks: when enabled, the captured block records
+ * a CUDA event pair around every kernel launch (classes: 0 white noise,
+ * 1 filter, 2 integrator, 3 cell list, 4 force, 5 reduction).  Takes effect at
+ * the next block. */
+int qtb_set_profiling(qtb_ctx *c, int enable);
+
+/* Mean device time (ms) and launch count per kernel class over the last
+ * profiled block (synchronises).  mean_ms, counts: [n_classes]. */
+int qtb_kernel_times(qtb_ctx *c, double *mean_ms, int *counts, int n_classes);
+
+/* Current step index (number of steps taken). */
+int qtb_get_step(qtb_ctx *c, long long *step);
+
+/* kappa_P / (k_B T) = F_P(y), y = beta hbar w, solved in FP64 on the GPU on the
+ * collocation grid y_i = y0 sinh(i t), t = asinh(y_max/y0)/(n-1), i < n:
+ * least squares of Eq. 10 imposed at the nodes and midpoints with linear
+ * interpolation and the asymptotic tail f(sqrt(P) y)/P + sqrt(P)/(2y) above
+ * y_max.  F: [n] host output. */
+int qtb_kappa_solve(int P, int n, double y_max, double y0, double *F);
+
+void qtb_destroy(qtb_ctx *c);
+
+/* Message of the last failed call in this thread (never NULL). */
+const char *qtb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QTB_H */

@@ -1,0 +1,1022 @@
+// capi.cu -- host side of the C ABI declared in include/qtb.h.
+//
+// Owns the device layout of every system (bead-major SoA state, noise dofs
+// padded to tensor-core tiles, cell lists per bead replica), the noise
+// pipeline (white blocks in a ring, coloured block per 256 steps) and the
+// CUDA graph that replays one 256-step block.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "qtb_dev.cuh"
+#include "qtb_kernels.cuh"
+
+using namespace qtb;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess) return fail(QTB_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+long long roundup(long long a, long long b) { return (a + b - 1) / b * b; }
+
+struct HSys {
+    int N, P, mode, n_taps;
+    double omega_max, T, gamma, box[3];
+};
+
+}  // namespace
+
+struct qtb_ctx {
+    cudaStream_t st = nullptr;
+    qtb_params p{};
+    std::vector<double> mass, charge, bA, brho, bC;
+    bool mixed = false, pair = true;
+    int fk = FK_FP64;  // ring / filter arithmetic
+    size_t rsz = 8;    // sizeof(R)
+    std::vector<HSys> hs;
+    std::vector<DSys> ds;
+    std::vector<DRep> dr;
+    std::vector<int> cell_rep, icta_sys;
+    Dev d{};
+    MdLaunch ml{};
+    PairTab tab{};
+    long long step = 0;
+    long long dclock = 0;          // host mirror of the device clock
+    long long ring_hi = LLONG_MIN; // highest white block in the ring
+    long long ring_lo = LLONG_MIN; // lowest white block in the ring
+    long long eta_blk = LLONG_MIN; // block whose coloured noise is in eta
+    int Kmax = 0;
+    int max_dofp = 0, max_repN = 0;
+    size_t ring_bytes = 0;
+    std::vector<void *> allocs;
+    std::map<int, double *> kappaF;  // P -> device F grid
+    double *dS = nullptr;            // spectrum scratch
+    DSpec *dspec = nullptr;
+    double *d_taps64 = nullptr;
+    float *d_taps32 = nullptr;
+    int taps_cap = 0;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_dirty = true;
+    bool own_stream = false;
+    // profiling (events recorded inside the captured block)
+    bool profiling = false, capturing = false;
+    std::vector<cudaEvent_t> ev;        // pairs: start, stop
+    std::vector<int> ev_cls;            // class of each pair
+    size_t ev_used = 0, ev_pairs = 0;
+    bool prof_launched = false;
+
+    void *alloc(size_t bytes)
+    {
+        if (bytes == 0) bytes = 16;
+        void *ptr = nullptr;
+        if (p.dev_alloc) {
+            ptr = p.dev_alloc(bytes, p.alloc_user);
+        } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+            ptr = nullptr;
+        }
+        if (ptr) allocs.push_back(ptr);
+        return ptr;
+    }
+    void release(void *ptr)
+    {
+        if (!ptr) return;
+        for (size_t i = 0; i < allocs.size(); ++i)
+            if (allocs[i] == ptr) {
+                allocs.erase(allocs.begin() + i);
+                break;
+            }
+        if (p.dev_free) p.dev_free(ptr, p.alloc_user);
+        else cudaFree(ptr);
+    }
+    ~qtb_ctx()
+    {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (st) cudaStreamSynchronize(st);
+        else cudaDeviceSynchronize();
+        for (void *ptr : allocs) {
+            if (p.dev_free) p.dev_free(ptr, p.alloc_user);
+            else cudaFree(ptr);
+        }
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (own_stream) cudaStreamDestroy(st);
+    }
+};
+
+namespace {
+
+template <class T>
+T *upload(qtb_ctx *c, const std::vector<T> &v)
+{
+    T *ptr = (T *)c->alloc(sizeof(T) * (v.empty() ? 1 : v.size()));
+    if (ptr && !v.empty()) cudaMemcpyAsync(ptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, c->st);
+    return ptr;
+}
+
+// Normal-mode matrix of the cyclic ring polymer (real Fourier basis), C[b][k].
+void nm_matrix(int P, std::vector<double> &C)
+{
+    C.assign((size_t)P * P, 0.0);
+    for (int b = 0; b < P; ++b)
+        for (int k = 0; k < P; ++k) {
+            double v;
+            const double ang = 2.0 * kPi * (double)((b * k) % P) / P;
+            if (k == 0) v = 1.0 / std::sqrt((double)P);
+            else if (2 * k < P) v = std::sqrt(2.0 / P) * std::cos(ang);
+            else if (2 * k == P) v = ((b % 2) ? -1.0 : 1.0) / std::sqrt((double)P);
+            else v = std::sqrt(2.0 / P) * std::sin(ang);
+            C[(size_t)b * P + k] = v;
+        }
+}
+
+int check_err_word(qtb_ctx *c)
+{
+    unsigned e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, c->d.err, sizeof e, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+    if (e & ERR_OVERFLOW) return fail(QTB_ERR_OVERFLOW, "a cell-list cell exceeded its capacity (%d)", c->d.cap);
+    if (e & ERR_NONFINITE) return fail(QTB_ERR_NONFINITE, "non-finite energy: the integration blew up");
+    if (e & ERR_SOLVE) return fail(QTB_ERR_SOLVE, "kappa_P solve: non-positive pivot");
+    return QTB_OK;
+}
+
+// ---- state transfer ------------------------------------------------------
+
+int upload_state(qtb_ctx *c, int s, const double *pos, const double *vel)
+{
+    const HSys &h = c->hs[s];
+    const DSys &S = c->ds[s];
+    const size_t G = (size_t)c->d.G, NP = (size_t)h.N * h.P;
+    for (int comp = 0; comp < 3; ++comp) {
+        if (pos) {
+            if (c->pair && c->mixed) {
+                std::vector<int> buf(NP);
+                const double L = h.box[comp];
+                for (size_t t = 0; t < NP; ++t) {
+                    double u = pos[t * 3 + comp] / L;
+                    u -= std::floor(u);
+                    long long q = std::llround(u * (double)(1 << kFixBits));
+                    buf[t] = (int)(q & ((1LL << kFixBits) - 1));
+                }
+                CUDA_TRY(cudaMemcpyAsync((int *)c->d.x + comp * G + S.g0, buf.data(), NP * 4, cudaMemcpyHostToDevice, c->st));
+                CUDA_TRY(cudaStreamSynchronize(c->st));
+            } else if (c->pair) {
+                std::vector<double> buf(NP);
+                const double L = h.box[comp];
+                for (size_t t = 0; t < NP; ++t) {
+                    double x = pos[t * 3 + comp];
+                    x -= L * std::floor(x / L);
+                    if (x >= L || x < 0) x = 0;
+                    buf[t] = x;
+                }
+                CUDA_TRY(cudaMemcpyAsync((double *)c->d.x + comp * G + S.g0, buf.data(), NP * 8, cudaMemcpyHostToDevice, c->st));
+                CUDA_TRY(cudaStreamSynchronize(c->st));
+            } else if (c->mixed) {
+                std::vector<float> buf(NP);
+                for (size_t t = 0; t < NP; ++t) buf[t] = (float)pos[t * 3 + comp];
+                CUDA_TRY(cudaMemcpyAsync((float *)c->d.x + comp * G + S.g0, buf.data(), NP * 4, cudaMemcpyHostToDevice, c->st));
+                CUDA_TRY(cudaStreamSynchronize(c->st));
+            } else {
+                std::vector<double> buf(NP);
+                for (size_t t = 0; t < NP; ++t) buf[t] = pos[t * 3 + comp];
+                CUDA_TRY(cudaMemcpyAsync((double *)c->d.x + comp * G + S.g0, buf.data(), NP * 8, cudaMemcpyHostToDevice, c->st));
+                CUDA_TRY(cudaStreamSynchronize(c->st));
+            }
+        }
+        if (vel) {
+            if (c->mixed) {
+                std::vector<float> buf(NP);
+                for (size_t t = 0; t < NP; ++t) buf[t] = (float)vel[t * 3 + comp];
+                CUDA_TRY(cudaMemcpyAsync((float *)c->d.v + comp * G + S.g0, buf.data(), NP * 4, cudaMemcpyHostToDevice, c->st));
+                CUDA_TRY(cudaStreamSynchronize(c->st));
+            } else {
+                std::vector<double> buf(NP);
+                for (size_t t = 0; t < NP; ++t) buf[t] = vel[t * 3 + comp];
+                CUDA_TRY(cudaMemcpyAsync((double *)c->d.v + comp * G + S.g0, buf.data(), NP * 8, cudaMemcpyHostToDevice, c->st));
+                CUDA_TRY(cudaStreamSynchronize(c->st));
+            }
+        }
+    }
+    return QTB_OK;
+}
+
+// which: 0 positions, 1 velocities, 2 forces
+int download(qtb_ctx *c, int s, int which, double *out)
+{
+    const HSys &h = c->hs[s];
+    const DSys &S = c->ds[s];
+    const size_t G = (size_t)c->d.G, NP = (size_t)h.N * h.P;
+    for (int comp = 0; comp < 3; ++comp) {
+        if (which == 0 && c->pair && c->mixed) {
+            std::vector<int> buf(NP);
+            CUDA_TRY(cudaMemcpyAsync(buf.data(), (int *)c->d.x + comp * G + S.g0, NP * 4, cudaMemcpyDeviceToHost, c->st));
+            CUDA_TRY(cudaStreamSynchronize(c->st));
+            const double sc = h.box[comp] / (double)(1 << kFixBits);
+            for (size_t t = 0; t < NP; ++t) out[t * 3 + comp] = (double)buf[t] * sc;
+        } else {
+            const void *src = (which == 0) ? c->d.x : (which == 1) ? c->d.v : c->d.f;
+            const bool f32 = c->mixed;  // positions of PAIR+MIXED handled above
+            if (f32) {
+                std::vector<float> buf(NP);
+                CUDA_TRY(cudaMemcpyAsync(buf.data(), (const float *)src + comp * G + S.g0, NP * 4, cudaMemcpyDeviceToHost, c->st));
+                CUDA_TRY(cudaStreamSynchronize(c->st));
+                for (size_t t = 0; t < NP; ++t) out[t * 3 + comp] = buf[t];
+            } else {
+                std::vector<double> buf(NP);
+                CUDA_TRY(cudaMemcpyAsync(buf.data(), (const double *)src + comp * G + S.g0, NP * 8, cudaMemcpyDeviceToHost, c->st));
+                CUDA_TRY(cudaStreamSynchronize(c->st));
+                for (size_t t = 0; t < NP; ++t) out[t * 3 + comp] = buf[t];
+            }
+        }
+    }
+    return QTB_OK;
+}
+
+// ---- pipeline pieces -------------------------------------------------------
+
+void set_clock(qtb_ctx *c, long long b)
+{
+    if (c->dclock != b) {
+        launch_setclock(c->d, b, c->st);
+        c->dclock = b;
+    }
+}
+
+// forces (and energies) at the current positions; no velocity kick
+int refresh_forces(qtb_ctx *c)
+{
+    set_clock(c, floor_div(c->step, kBlockSteps));
+    launch_cells(c->d, c->ml, c->st);
+    launch_force_kick(c->d, c->ml, c->tab, 0, c->st);
+    int j = (int)(c->step - c->dclock * kBlockSteps) - 1;
+    launch_reduce(c->d, c->ml, j, -1, c->st);
+    CUDA_TRY(cudaGetLastError());
+    return QTB_OK;
+}
+
+void gen_white(qtb_ctx *c, long long blk)
+{
+    launch_white(c->d, c->fk, c->max_dofp, c->d.nsys, blk, c->st);
+}
+
+void filter_block(qtb_ctx *c)
+{
+    // the tensor-core form is added with its own translation unit; the SIMT
+    // forms filter in FP64 or FP32
+    launch_filter_simt(c->d, c->fk == FK_BF16 ? FK_FP32 : c->fk, c->max_dofp, c->d.nsys, c->Kmax, c->st);
+}
+
+// make the ring hold white blocks lo .. hi (hi - lo < nslots)
+void ensure_ring(qtb_ctx *c, long long lo, long long hi)
+{
+    long long from = lo;
+    const bool have = (c->ring_hi != LLONG_MIN && c->ring_lo <= lo && c->ring_hi >= lo - 1);
+    if (have) from = c->ring_hi + 1;
+    for (long long blk = from; blk <= hi; ++blk) gen_white(c, blk);
+    if (!have) c->ring_lo = lo;
+    if (!have || hi > c->ring_hi) c->ring_hi = std::max(hi, have ? c->ring_hi : hi);
+    c->ring_lo = std::max(c->ring_lo, c->ring_hi - c->d.nslots + 1);
+}
+
+// make eta hold block b (ring then holds blocks b-Kb .. b+Kb)
+void ensure_eta(qtb_ctx *c, long long b)
+{
+    if (c->eta_blk == b) return;
+    ensure_ring(c, b - c->d.Kb, b + c->d.Kb);
+    set_clock(c, b);
+    filter_block(c);
+    c->eta_blk = b;
+}
+
+// Profiling: event pairs recorded around each kernel class inside the graph
+// (external event-record nodes), so that the per-kernel device time of the
+// last replayed block can be read back.
+enum { KC_WHITE = 0, KC_FILTER = 1, KC_INTEGRATE = 2, KC_CELLS = 3, KC_FORCE = 4, KC_REDUCE = 5, KC_N = 6 };
+
+struct ProfMark {
+    qtb_ctx *c;
+    int cls;
+    bool on;
+    ProfMark(qtb_ctx *c_, int cls_);
+    ~ProfMark();
+};
+
+ProfMark::ProfMark(qtb_ctx *c_, int cls_) : c(c_), cls(cls_), on(c_->profiling && c_->capturing)
+{
+    if (!on) return;
+    const size_t pair = c->ev_used / 2;
+    if (c->ev_used + 2 > c->ev.size()) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        c->ev.push_back(a);
+        c->ev.push_back(b);
+        c->ev_cls.push_back(cls);
+    } else {
+        c->ev_cls[pair] = cls;
+    }
+    cudaEventRecordWithFlags(c->ev[c->ev_used], c->st, cudaEventRecordExternal);
+}
+
+ProfMark::~ProfMark()
+{
+    if (!on) return;
+    cudaEventRecordWithFlags(c->ev[c->ev_used + 1], c->st, cudaEventRecordExternal);
+    c->ev_used += 2;
+}
+
+void one_step(qtb_ctx *c, int j)
+{
+    { ProfMark m(c, KC_INTEGRATE); launch_integrate(c->d, c->ml, j, c->st); }
+    { ProfMark m(c, KC_CELLS); launch_cells(c->d, c->ml, c->st); }
+    { ProfMark m(c, KC_FORCE); launch_force_kick(c->d, c->ml, c->tab, 1, c->st); }
+    { ProfMark m(c, KC_REDUCE); launch_reduce(c->d, c->ml, j, 1, c->st); }
+}
+
+int build_graph(qtb_ctx *c)
+{
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    cudaGraph_t g;
+    CUDA_TRY(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    c->ev_used = 0;
+    { ProfMark m(c, KC_WHITE); gen_white(c, LLONG_MIN); }  // block clock + Kb
+    { ProfMark m(c, KC_FILTER); filter_block(c); }
+    for (int j = 0; j < kBlockSteps; ++j) one_step(c, j);
+    launch_tick(c->d, c->st);
+    c->capturing = false;
+    c->ev_pairs = c->ev_used / 2;
+    cudaError_t e = cudaStreamEndCapture(c->st, &g);
+    if (e != cudaSuccess) return fail(QTB_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(QTB_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    c->graph_dirty = false;
+    return QTB_OK;
+}
+
+int ensure_kappa(qtb_ctx *c, int P)
+{
+    if (c->kappaF.count(P)) return QTB_OK;
+    const int n = 1024;
+    const double ymax = 1000.0, y0 = 1.0;
+    const int rows = 2 * n - 1;
+    double *F = (double *)c->alloc(sizeof(double) * n);
+    double *A = (double *)c->alloc(sizeof(double) * (size_t)rows * n);
+    double *b = (double *)c->alloc(sizeof(double) * rows);
+    double *M = (double *)c->alloc(sizeof(double) * (size_t)n * n);
+    if (!F || !A || !b || !M) return fail(QTB_ERR_OOM, "kappa_P solve: device allocation failed");
+    launch_kappa_solve(P, n, ymax, y0, A, b, M, F, c->d.err, c->st);
+    CUDA_TRY(cudaGetLastError());
+    int rc = check_err_word(c);
+    c->release(A);
+    c->release(b);
+    c->release(M);
+    if (rc) return rc;
+    c->kappaF[P] = F;
+    return QTB_OK;
+}
+
+// (re)build taps of every system from hs[].mode/n_taps/omega_max
+int rebuild_filters(qtb_ctx *c)
+{
+    const int ns = (int)c->hs.size();
+    int tot = 0, Kmax = 0;
+    std::vector<DSpec> spec(ns);
+    for (int s = 0; s < ns; ++s) {
+        const HSys &h = c->hs[s];
+        int K = (h.mode == QTB_NOISE_WHITE) ? 0 : (h.n_taps - 1) / 2;
+        c->ds[s].K = K;
+        c->ds[s].taps0 = tot;
+        tot += K + 1;
+        Kmax = std::max(Kmax, K);
+        DSpec &sp = spec[s];
+        sp.mode = h.mode;
+        sp.K = K;
+        sp.taps0 = c->ds[s].taps0;
+        sp.P = h.P;
+        sp.dt = c->p.dt;
+        sp.T = h.T;
+        sp.omega_max = h.omega_max;
+        sp.F = nullptr;
+        sp.n = 1024;
+        sp.ymax = 1000.0;
+        sp.y0 = 1.0;
+        if (h.mode == QTB_NOISE_QTB_PIMD) {
+            int rc = ensure_kappa(c, h.P);
+            if (rc) return rc;
+            sp.F = c->kappaF[h.P];
+        }
+    }
+    if (tot > c->taps_cap) {
+        c->release(c->d_taps64);
+        c->release(c->d_taps32);
+        c->release(c->dS);
+        c->d_taps64 = (double *)c->alloc(sizeof(double) * tot);
+        c->d_taps32 = (float *)c->alloc(sizeof(float) * tot);
+        c->dS = (double *)c->alloc(sizeof(double) * tot);
+        if (!c->d_taps64 || !c->d_taps32 || !c->dS) return fail(QTB_ERR_OOM, "taps allocation failed");
+        c->taps_cap = tot;
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->dspec, spec.data(), sizeof(DSpec) * ns, cudaMemcpyHostToDevice, c->st));
+    launch_spectrum_taps(c->dspec, ns, Kmax, c->dS, c->d_taps64, c->d_taps32, c->st);
+    CUDA_TRY(cudaGetLastError());
+    // ring geometry
+    const int Kb = (Kmax + kBlockSteps - 1) / kBlockSteps;
+    const int nslots = 2 * Kb + 1;
+    const size_t esz = (c->fk == FK_FP64) ? 8 : (c->fk == FK_FP32 ? 4 : 2);
+    const size_t need = esz * (size_t)nslots * (size_t)c->d.Dtot * kBlockSteps;
+    if (need > c->ring_bytes || nslots != c->d.nslots) {
+        if (need > c->ring_bytes) {
+            c->release(c->d.ring);
+            c->d.ring = c->alloc(need);
+            if (!c->d.ring) return fail(QTB_ERR_OOM, "noise ring allocation (%zu bytes) failed", need);
+            c->ring_bytes = need;
+        }
+        c->ring_hi = c->ring_lo = LLONG_MIN;
+    }
+    c->d.Kb = Kb;
+    c->d.nslots = nslots;
+    c->Kmax = Kmax;
+    CUDA_TRY(filter_simt_prepare(Kmax));
+    c->d.taps64 = c->d_taps64;
+    c->d.tapsR = (c->fk == FK_FP64) ? (const void *)c->d_taps64 : (const void *)c->d_taps32;
+    CUDA_TRY(cudaMemcpyAsync((void *)c->d.sys, c->ds.data(), sizeof(DSys) * ns, cudaMemcpyHostToDevice, c->st));
+    c->eta_blk = LLONG_MIN;
+    c->graph_dirty = true;
+    return QTB_OK;
+}
+
+int validate(const qtb_system *sys, int n_sys, const qtb_params *p)
+{
+    if (!sys || n_sys < 1 || !p) return fail(QTB_ERR_ARG, "qtb_init: need n_sys >= 1 systems and params");
+    if (p->n_types < 1 || p->n_types > kMaxTypes) return fail(QTB_ERR_ARG, "n_types must be 1..%d", kMaxTypes);
+    if (!p->mass) return fail(QTB_ERR_ARG, "mass table missing");
+    if (!(p->dt > 0)) return fail(QTB_ERR_ARG, "dt must be > 0");
+    if (p->potential < 0 || p->potential > 2) return fail(QTB_ERR_ARG, "unknown potential %d", p->potential);
+    if (p->precision != QTB_FP64 && p->precision != QTB_MIXED) return fail(QTB_ERR_ARG, "unknown precision");
+    if (p->filter_prec < 0 || p->filter_prec > 2) return fail(QTB_ERR_ARG, "unknown filter precision");
+    if (p->obs_stride < 1 || p->max_records < 1) return fail(QTB_ERR_ARG, "obs_stride and max_records must be >= 1");
+    if (p->potential == QTB_POT_PAIR) {
+        if (!p->charge || !p->buck_A || !p->buck_rho || !p->buck_C) return fail(QTB_ERR_ARG, "pair tables missing");
+        if (!(p->r_cut > 0)) return fail(QTB_ERR_ARG, "r_cut must be > 0");
+    }
+    for (int s = 0; s < n_sys; ++s) {
+        const qtb_system &q = sys[s];
+        if (q.n_atoms < 1 || q.n_beads < 1) return fail(QTB_ERR_ARG, "system %d: n_atoms, n_beads >= 1", s);
+        if (!md_supported_P(q.n_beads)) return fail(QTB_ERR_ARG, "system %d: n_beads %d not supported (1-6, 8, 16, 32)", s, q.n_beads);
+        if (!q.type || !q.pos) return fail(QTB_ERR_ARG, "system %d: type and pos required", s);
+        if (!(q.T > 0) || !(q.gamma >= 0)) return fail(QTB_ERR_ARG, "system %d: T > 0, gamma >= 0", s);
+        for (int i = 0; i < q.n_atoms; ++i)
+            if (q.type[i] < 0 || q.type[i] >= p->n_types) return fail(QTB_ERR_ARG, "system %d: bad type at %d", s, i);
+        if (p->potential == QTB_POT_PAIR)
+            for (int c = 0; c < 3; ++c)
+                if (!(q.box[c] >= p->r_cut)) return fail(QTB_ERR_ARG, "system %d: box edge %d must be >= r_cut", s, c);
+    }
+    return QTB_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+
+extern "C" {
+
+const char *qtb_last_error(void) { return g_err.c_str(); }
+
+int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *p, void *stream)
+{
+    if (!out) return fail(QTB_ERR_ARG, "qtb_init: out is NULL");
+    *out = nullptr;
+    int rc = validate(sys, n_sys, p);
+    if (rc) return rc;
+    qtb_ctx *c = new qtb_ctx();
+    c->st = (cudaStream_t)stream;
+    if (!c->st) {
+        // the legacy default stream cannot be captured into a graph: use our own
+        if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return fail(QTB_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        c->own_stream = true;
+    }
+    c->p = *p;
+    const int nt = p->n_types;
+    c->mass.assign(p->mass, p->mass + nt);
+    c->mixed = (p->precision == QTB_MIXED);
+    c->pair = (p->potential == QTB_POT_PAIR);
+    c->fk = c->mixed ? (p->filter_prec == QTB_FILTER_BF16 ? FK_BF16 : FK_FP32) : FK_FP64;
+    c->rsz = c->mixed ? 4 : 8;
+    auto bail = [&](int code) {
+        delete c;
+        return code;
+    };
+
+    // ---- pair table
+    PairTab &T = c->tab;
+    memset(&T, 0, sizeof T);
+    T.ntypes = nt;
+    T.potential = p->potential;
+    T.ext_omega = p->ext_omega;
+    T.ext_V0 = p->ext_V0;
+    T.ext_a = p->ext_a;
+    for (int a = 0; a < nt; ++a) T.mass[a] = p->mass[a];
+    if (c->pair) {
+        const double rc_ = p->r_cut, al = p->dsf_alpha;
+        T.rc = rc_;
+        T.alpha = al;
+        T.erfc_rc_over_rc = std::erfc(al * rc_) / rc_;
+        T.fshift = std::erfc(al * rc_) / (rc_ * rc_) + 2.0 * al / std::sqrt(kPi) * std::exp(-al * al * rc_ * rc_) / rc_;
+        for (int a = 0; a < nt; ++a)
+            for (int b = 0; b < nt; ++b) {
+                const int t = a * kMaxTypes + b, u = a * nt + b;
+                T.A[t] = p->buck_A[u];
+                T.inv_rho[t] = (p->buck_A[u] != 0.0) ? 1.0 / p->buck_rho[u] : 0.0;
+                T.C[t] = p->buck_C[u];
+                T.qq[t] = kCoulomb * p->charge[a] * p->charge[b];
+                double es = 0.0;
+                if (p->buck_A[u] != 0.0) es += p->buck_A[u] * std::exp(-rc_ / p->buck_rho[u]);
+                es -= p->buck_C[u] / std::pow(rc_, 6);
+                T.eshift[t] = es;
+            }
+    }
+
+    // ---- layout
+    long long G = 0, D = 0;
+    int icta = 0, nrep = 0, ncells = 0, maxN = 0, cap = 8;
+    int rot_tot = 0, nm_tot = 0;
+    std::map<int, int> nm_off;
+    std::vector<double> nmC_host;
+    c->hs.resize(n_sys);
+    c->ds.resize(n_sys);
+    for (int s = 0; s < n_sys; ++s) {
+        const qtb_system &q = sys[s];
+        HSys &h = c->hs[s];
+        h.N = q.n_atoms;
+        h.P = q.n_beads;
+        h.mode = QTB_NOISE_WHITE;
+        h.n_taps = 1;
+        h.omega_max = 0;
+        h.T = q.T;
+        h.gamma = q.gamma;
+        for (int k = 0; k < 3; ++k) h.box[k] = q.box[k];
+        DSys &S = c->ds[s];
+        memset(&S, 0, sizeof S);
+        S.N = h.N;
+        S.P = h.P;
+        S.g0 = (int)G;
+        S.dof0 = (int)D;
+        S.dofp = (int)roundup(3LL * h.N * h.P, kDofPad);
+        G += (long long)h.N * h.P;
+        D += S.dofp;
+        S.icta0 = icta;
+        icta += (int)((3LL * h.N + 127) / 128);
+        S.icta1 = icta;
+        for (int k = 0; k < 3; ++k) S.box[k] = q.box[k];
+        S.T = q.T;
+        S.gamma = q.gamma;
+        S.c1 = std::exp(-q.gamma * p->dt);
+        S.wP = std::sqrt((double)h.P) * kBoltz * q.T / kHbar;
+        S.rot0 = rot_tot;
+        rot_tot += h.P;
+        if (!nm_off.count(h.P)) {
+            std::vector<double> Cm;
+            nm_matrix(h.P, Cm);
+            nm_off[h.P] = nm_tot;
+            nm_tot += h.P * h.P;
+            nmC_host.insert(nmC_host.end(), Cm.begin(), Cm.end());
+        }
+        S.nm0 = nm_off[h.P];
+        S.rep0 = nrep;
+        maxN = std::max(maxN, h.N);
+        c->max_dofp = std::max(c->max_dofp, S.dofp);
+        if (c->pair) {
+            int nc[3];
+            for (int k = 0; k < 3; ++k) nc[k] = std::max(1, (int)std::floor(q.box[k] / p->r_cut));
+            const int cells = nc[0] * nc[1] * nc[2];
+            const double e = (double)h.N / cells;
+            int cp = (int)roundup((long long)std::ceil(1.25 * e + 4.0 * std::sqrt(e) + 8.0), 8);
+            cp = std::min(cp, (int)roundup(h.N, 8));
+            cap = std::max(cap, cp);
+            for (int b = 0; b < h.P; ++b) {
+                DRep R;
+                memset(&R, 0, sizeof R);
+                R.sys = s;
+                R.g0 = S.g0 + b * h.N;
+                R.N = h.N;
+                for (int k = 0; k < 3; ++k) {
+                    R.nc[k] = nc[k];
+                    R.box[k] = q.box[k];
+                }
+                R.cell0 = ncells;
+                ncells += cells;
+                c->dr.push_back(R);
+                for (int t = 0; t < cells; ++t) c->cell_rep.push_back(nrep);
+                ++nrep;
+            }
+        }
+    }
+    if (cap > 512) return bail(fail(QTB_ERR_ARG, "cell capacity %d > 512: box too dense for r_cut-sized cells", cap));
+    for (int s = 0; s < n_sys; ++s)
+        for (int t = c->ds[s].icta0; t < c->ds[s].icta1; ++t) c->icta_sys.push_back(s);
+    // force CTA ranges
+    const int cpc = cap / kWarpsPerForceCta;
+    int ext_gx = 0;
+    for (int s = 0; s < n_sys; ++s) ext_gx = std::max(ext_gx, (c->hs[s].N * c->hs[s].P + 127) / 128);
+    long long nforce = 0;
+    for (int s = 0; s < n_sys; ++s) {
+        DSys &S = c->ds[s];
+        if (c->pair) {
+            const DRep &R0 = c->dr[S.rep0];
+            const int cells = R0.nc[0] * R0.nc[1] * R0.nc[2];
+            S.fcta0 = R0.cell0 * cpc;
+            S.fcta1 = (R0.cell0 + cells * c->hs[s].P) * cpc;
+            nforce = S.fcta1;
+        } else {
+            S.fcta0 = s * ext_gx;
+            S.fcta1 = (s + 1) * ext_gx;
+            nforce = S.fcta1;
+        }
+    }
+
+    Dev &d = c->d;
+    d.nsys = n_sys;
+    d.nrep = nrep;
+    d.ncells = ncells;
+    d.cap = cap;
+    d.cpc = cpc;
+    d.G = G;
+    d.Dtot = D;
+    d.obs_stride = p->obs_stride;
+    d.max_records = p->max_records;
+    d.dt = p->dt;
+    d.seed = p->seed;
+    for (int a = 0; a < nt; ++a) d.mass_mvv[a] = p->mass[a] * kMvv2e;
+
+    MdLaunch &m = c->ml;
+    m.mixed = c->mixed;
+    m.pair = c->pair;
+    m.n_icta = icta;
+    m.n_bcta = (maxN + 255) / 256;
+    m.n_ecta = ext_gx;
+    m.nP = 0;
+    for (int s = 0; s < n_sys; ++s) {
+        bool seen = false;
+        for (int u = 0; u < m.nP; ++u) seen |= (m.Pvals[u] == c->hs[s].P);
+        if (!seen) {
+            if (m.nP == 8) return bail(fail(QTB_ERR_ARG, "at most 8 distinct bead counts per context"));
+            m.Pvals[m.nP++] = c->hs[s].P;
+        }
+    }
+
+    // tables
+    std::vector<double> rot;
+    for (int s = 0; s < n_sys; ++s) {
+        const DSys &S = c->ds[s];
+        for (int k = 0; k < S.P; ++k) {
+            const double w = 2.0 * S.wP * std::sin(kPi * k / S.P);
+            const double ph = 0.5 * p->dt * w;
+            if (w == 0.0) {
+                rot.push_back(1.0);
+                rot.push_back(0.5 * p->dt);
+                rot.push_back(0.0);
+            } else {
+                rot.push_back(std::cos(ph));
+                rot.push_back(std::sin(ph) / w);
+                rot.push_back(-w * std::sin(ph));
+            }
+        }
+    }
+    std::vector<double> hdt(nt), osig((size_t)n_sys * kMaxTypes, 0.0);
+    for (int a = 0; a < nt; ++a) hdt[a] = 0.5 * p->dt / (p->mass[a] * kMvv2e);
+    for (int s = 0; s < n_sys; ++s)
+        for (int a = 0; a < nt; ++a) {
+            const double c1 = c->ds[s].c1;
+            osig[(size_t)s * kMaxTypes + a] = std::sqrt((1.0 - c1 * c1) / (p->mass[a] * kMvv2e));
+        }
+    auto as_real = [&](const std::vector<double> &v) -> void * {
+        if (c->mixed) {
+            std::vector<float> f(v.begin(), v.end());
+            return upload(c, f);
+        }
+        return upload(c, v);
+    };
+    d.rot = as_real(rot);
+    d.nmC = as_real(nmC_host);
+    d.hdt_m = as_real(hdt);
+    d.osig = as_real(osig);
+    std::vector<int> typ((size_t)G);
+    for (int s = 0; s < n_sys; ++s)
+        for (int b = 0; b < c->hs[s].P; ++b)
+            for (int i = 0; i < c->hs[s].N; ++i) typ[(size_t)c->ds[s].g0 + (size_t)b * c->hs[s].N + i] = sys[s].type[i];
+    d.typ = upload(c, typ);
+    d.rep = upload(c, c->dr);
+    d.cell_rep = upload(c, c->cell_rep);
+    d.icta_sys = upload(c, c->icta_sys);
+    d.sys = upload(c, c->ds);
+    const size_t psz = c->pair && c->mixed ? 4 : c->rsz;
+    d.x = c->alloc(psz * 3 * (size_t)G);
+    d.v = c->alloc(c->rsz * 3 * (size_t)G);
+    d.f = c->alloc(c->rsz * 3 * (size_t)G);
+    d.cnt = (int *)c->alloc(sizeof(int) * std::max(ncells, 1));
+    d.ccount = (int *)c->alloc(sizeof(int) * std::max(ncells, 1));
+    d.cidx = (int *)c->alloc(sizeof(int) * (size_t)std::max(ncells, 1) * cap);
+    d.cpos = c->alloc((c->mixed ? 16 : 32) * (size_t)std::max(ncells, 1) * cap);
+    d.eta = c->alloc(c->rsz * (size_t)kBlockSteps * (size_t)D);
+    d.part = (double *)c->alloc(sizeof(double) * kNQ * (size_t)std::max(nforce, 1LL));
+    d.ipart = (double *)c->alloc(sizeof(double) * kNQ * (size_t)icta);
+    d.latest = (double *)c->alloc(sizeof(double) * QTB_NREC * n_sys);
+    d.series = (double *)c->alloc(sizeof(double) * QTB_NREC * (size_t)n_sys * p->max_records);
+    d.clock = (long long *)c->alloc(sizeof(long long));
+    d.err = (unsigned *)c->alloc(sizeof(unsigned));
+    c->dspec = (DSpec *)c->alloc(sizeof(DSpec) * n_sys);
+    if (!d.x || !d.v || !d.f || !d.cnt || !d.ccount || !d.cidx || !d.cpos || !d.eta || !d.part || !d.ipart ||
+        !d.latest || !d.series || !d.clock || !d.err || !d.typ || !d.sys || !c->dspec)
+        return bail(fail(QTB_ERR_OOM, "device allocation failed"));
+    cudaMemsetAsync(d.cnt, 0, sizeof(int) * std::max(ncells, 1), c->st);
+    cudaMemsetAsync(d.ccount, 0, sizeof(int) * std::max(ncells, 1), c->st);
+    cudaMemsetAsync(d.clock, 0, sizeof(long long), c->st);
+    cudaMemsetAsync(d.err, 0, sizeof(unsigned), c->st);
+    cudaMemsetAsync(d.series, 0, sizeof(double) * QTB_NREC * (size_t)n_sys * p->max_records, c->st);
+    cudaMemsetAsync(d.v, 0, c->rsz * 3 * (size_t)G, c->st);
+    cudaMemsetAsync(d.eta, 0, c->rsz * (size_t)kBlockSteps * (size_t)D, c->st);
+    c->dclock = 0;
+    for (int s = 0; s < n_sys; ++s) {
+        rc = upload_state(c, s, sys[s].pos, sys[s].vel);
+        if (rc) return bail(rc);
+    }
+    rc = rebuild_filters(c);
+    if (rc) return bail(rc);
+    rc = refresh_forces(c);
+    if (rc) return bail(rc);
+    rc = check_err_word(c);
+    if (rc) return bail(rc);
+    *out = c;
+    return QTB_OK;
+}
+
+void qtb_destroy(qtb_ctx *c) { delete c; }
+
+int qtb_set_filter(qtb_ctx *c, int sys, int mode, int n_taps, double omega_max)
+{
+    if (!c) return fail(QTB_ERR_ARG, "null context");
+    if (mode < 0 || mode > 3) return fail(QTB_ERR_ARG, "unknown noise mode %d", mode);
+    if (mode == QTB_NOISE_QTB_PIMD_MLP) return fail(QTB_ERR_STATE, "no learned kappa_P model is set");
+    if (mode != QTB_NOISE_WHITE && (n_taps < 1 || n_taps % 2 == 0))
+        return fail(QTB_ERR_ARG, "n_taps must be odd and >= 1");
+    const int ns = (int)c->hs.size();
+    if (sys < -1 || sys >= ns) return fail(QTB_ERR_ARG, "system %d out of range", sys);
+    for (int s = (sys < 0 ? 0 : sys); s < (sys < 0 ? ns : sys + 1); ++s) {
+        if (mode == QTB_NOISE_QTB && c->hs[s].P != 1)
+            return fail(QTB_ERR_ARG, "system %d: QTB needs n_beads = 1 (use QTB_PIMD)", s);
+    }
+    for (int s = (sys < 0 ? 0 : sys); s < (sys < 0 ? ns : sys + 1); ++s) {
+        c->hs[s].mode = mode;
+        c->hs[s].n_taps = (mode == QTB_NOISE_WHITE) ? 1 : n_taps;
+        c->hs[s].omega_max = omega_max;
+    }
+    return rebuild_filters(c);
+}
+
+int qtb_step_n(qtb_ctx *c, long long n)
+{
+    if (!c) return fail(QTB_ERR_ARG, "null context");
+    if (n < 0) return fail(QTB_ERR_ARG, "n_steps < 0");
+    while (n > 0) {
+        const long long b = floor_div(c->step, kBlockSteps);
+        const int j = (int)(c->step - b * kBlockSteps);
+        if (j == 0 && n >= kBlockSteps) {
+            // the graph generates white block b + Kb and filters block b
+            ensure_ring(c, b - c->d.Kb, b + c->d.Kb - 1);
+            set_clock(c, b);
+            if (c->graph_dirty || !c->gexec) {
+                int rc = build_graph(c);
+                if (rc) return rc;
+            }
+            CUDA_TRY(cudaGraphLaunch(c->gexec, c->st));
+            c->prof_launched = c->profiling;
+            c->ring_hi = b + c->d.Kb;
+            c->ring_lo = c->ring_hi - c->d.nslots + 1;
+            c->eta_blk = b;
+            c->dclock = b + 1;
+            c->step += kBlockSteps;
+            n -= kBlockSteps;
+            continue;
+        }
+        ensure_eta(c, b);
+        const long long mcount = std::min<long long>(n, kBlockSteps - j);
+        for (long long t = 0; t < mcount; ++t) one_step(c, j + (int)t);
+        c->step += mcount;
+        n -= mcount;
+        if (j + mcount == kBlockSteps) {
+            launch_tick(c->d, c->st);
+            c->dclock = b + 1;
+        }
+        CUDA_TRY(cudaGetLastError());
+    }
+    CUDA_TRY(cudaGetLastError());
+    return QTB_OK;
+}
+
+int qtb_sync(qtb_ctx *c)
+{
+    if (!c) return fail(QTB_ERR_ARG, "null context");
+    return check_err_word(c);
+}
+
+int qtb_observables(qtb_ctx *c, int sys, double *out)
+{
+    if (!c || !out) return fail(QTB_ERR_ARG, "null argument");
+    if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
+    int rc = check_err_word(c);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(out, c->d.latest + (size_t)sys * QTB_NREC, sizeof(double) * QTB_NREC,
+                             cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+    return QTB_OK;
+}
+
+int qtb_get_series(qtb_ctx *c, int sys, double *out, int max, int *n_out)
+{
+    if (!c || !out || !n_out) return fail(QTB_ERR_ARG, "null argument");
+    if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
+    int rc = check_err_word(c);
+    if (rc) return rc;
+    const long long total = c->step / c->p.obs_stride;
+    long long n = std::min<long long>(total, std::min(c->p.max_records, max));
+    const int ns = (int)c->hs.size();
+    std::vector<double> all((size_t)c->p.max_records * ns * QTB_NREC);
+    CUDA_TRY(cudaMemcpyAsync(all.data(), c->d.series, sizeof(double) * all.size(), cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+    for (long long i = 0; i < n; ++i) {
+        const long long r = total - n + i;
+        const int slot = (int)(r % c->p.max_records);
+        memcpy(out + i * QTB_NREC, all.data() + ((size_t)slot * ns + sys) * QTB_NREC, sizeof(double) * QTB_NREC);
+    }
+    *n_out = (int)n;
+    return QTB_OK;
+}
+
+int qtb_get_state(qtb_ctx *c, int sys, double *pos, double *vel)
+{
+    if (!c) return fail(QTB_ERR_ARG, "null context");
+    if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
+    int rc = check_err_word(c);
+    if (rc) return rc;
+    if (pos && (rc = download(c, sys, 0, pos))) return rc;
+    if (vel && (rc = download(c, sys, 1, vel))) return rc;
+    return QTB_OK;
+}
+
+int qtb_set_state(qtb_ctx *c, int sys, const double *pos, const double *vel)
+{
+    if (!c) return fail(QTB_ERR_ARG, "null context");
+    if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
+    int rc = upload_state(c, sys, pos, vel);
+    if (rc) return rc;
+    return refresh_forces(c);
+}
+
+int qtb_get_forces(qtb_ctx *c, int sys, double *f)
+{
+    if (!c || !f) return fail(QTB_ERR_ARG, "null argument");
+    if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
+    int rc = check_err_word(c);
+    if (rc) return rc;
+    return download(c, sys, 2, f);
+}
+
+int qtb_get_taps(qtb_ctx *c, int sys, double *h, int max, int *n_out)
+{
+    if (!c || !h || !n_out) return fail(QTB_ERR_ARG, "null argument");
+    if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
+    const DSys &S = c->ds[sys];
+    const int n = std::min(max, S.K + 1);
+    CUDA_TRY(cudaMemcpyAsync(h, c->d_taps64 + S.taps0, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+    *n_out = n;
+    return QTB_OK;
+}
+
+int qtb_get_noise(qtb_ctx *c, int sys, double *out, long long *block_out)
+{
+    if (!c || !out) return fail(QTB_ERR_ARG, "null argument");
+    if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
+    const long long b = floor_div(c->step, kBlockSteps);
+    ensure_eta(c, b);
+    CUDA_TRY(cudaGetLastError());
+    const DSys &S = c->ds[sys];
+    const int D = 3 * S.N * S.P;
+    if (c->mixed) {
+        std::vector<float> buf((size_t)kBlockSteps * D);
+        for (int j = 0; j < kBlockSteps; ++j)
+            CUDA_TRY(cudaMemcpyAsync(buf.data() + (size_t)j * D, (const float *)c->d.eta + (size_t)j * c->d.Dtot + S.dof0,
+                                     sizeof(float) * D, cudaMemcpyDeviceToHost, c->st));
+        CUDA_TRY(cudaStreamSynchronize(c->st));
+        for (size_t t = 0; t < buf.size(); ++t) out[t] = buf[t];
+    } else {
+        for (int j = 0; j < kBlockSteps; ++j)
+            CUDA_TRY(cudaMemcpyAsync(out + (size_t)j * D, (const double *)c->d.eta + (size_t)j * c->d.Dtot + S.dof0,
+                                     sizeof(double) * D, cudaMemcpyDeviceToHost, c->st));
+        CUDA_TRY(cudaStreamSynchronize(c->st));
+    }
+    if (block_out) *block_out = b;
+    return check_err_word(c);
+}
+
+int qtb_set_profiling(qtb_ctx *c, int enable)
+{
+    if (!c) return fail(QTB_ERR_ARG, "null context");
+    c->profiling = (enable != 0);
+    c->prof_launched = false;
+    c->graph_dirty = true;
+    return QTB_OK;
+}
+
+int qtb_kernel_times(qtb_ctx *c, double *mean_ms, int *counts, int n_classes)
+{
+    if (!c || !mean_ms || !counts || n_classes < 1) return fail(QTB_ERR_ARG, "null argument");
+    if (!c->prof_launched) return fail(QTB_ERR_STATE, "no profiled 256-step block has run");
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+    for (int k = 0; k < n_classes; ++k) {
+        mean_ms[k] = 0.0;
+        counts[k] = 0;
+    }
+    for (size_t pr = 0; pr < c->ev_pairs; ++pr) {
+        const int k = c->ev_cls[pr];
+        if (k >= n_classes) continue;
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[2 * pr], c->ev[2 * pr + 1]));
+        mean_ms[k] += ms;
+        counts[k] += 1;
+    }
+    for (int k = 0; k < n_classes; ++k)
+        if (counts[k]) mean_ms[k] /= counts[k];
+    return QTB_OK;
+}
+
+int qtb_get_step(qtb_ctx *c, long long *step)
+{
+    if (!c || !step) return fail(QTB_ERR_ARG, "null argument");
+    *step = c->step;
+    return QTB_OK;
+}
+
+int qtb_kappa_solve(int P, int n, double y_max, double y0, double *F)
+{
+    if (P < 1 || n < 8 || !(y_max > 0) || !(y0 > 0) || !F) return fail(QTB_ERR_ARG, "qtb_kappa_solve: bad arguments");
+    if (P == 1) {
+        const double dts = std::asinh(y_max / y0) / (n - 1);
+        for (int i = 0; i < n; ++i) {
+            const double x = y0 * std::sinh(i * dts);
+            F[i] = (x < 1e-6) ? 1.0 + x * x / 12.0 : x * (0.5 + 1.0 / std::expm1(x));
+        }
+        return QTB_OK;
+    }
+    const int rows = 2 * n - 1;
+    double *A = nullptr, *b = nullptr, *M = nullptr, *r = nullptr;
+    unsigned *err = nullptr;
+    size_t need = sizeof(double) * ((size_t)rows * n + rows + (size_t)n * n + n) + 16;
+    char *base = nullptr;
+    CUDA_TRY(cudaMalloc(&base, need));
+    A = (double *)base;
+    b = A + (size_t)rows * n;
+    M = b + rows;
+    r = M + (size_t)n * n;
+    err = (unsigned *)(r + n);
+    cudaMemset(err, 0, sizeof(unsigned));
+    launch_kappa_solve(P, n, y_max, y0, A, b, M, r, err, 0);
+    unsigned e = 0;
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaMemcpy(F, r, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess) ce = cudaMemcpy(&e, err, sizeof e, cudaMemcpyDeviceToHost);
+    cudaFree(base);
+    if (ce != cudaSuccess) return fail(QTB_ERR_CUDA, "qtb_kappa_solve: %s", cudaGetErrorString(ce));
+    if (e) return fail(QTB_ERR_SOLVE, "qtb_kappa_solve: non-positive pivot");
+    return QTB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,616 @@
+// md.cu -- cell lists, pair and external forces, the normal-mode BAOAB
+// integrator and the per-system reductions (sm_103a).
+//
+// Eq. 4: every bead feels -(1/P) grad V of its own replica plus the ring
+// springs; the springs are integrated exactly in normal-mode space (Sec. 2.3,
+// Eq. 11 with the physical force entering through the B kicks).  Eq. 8: the
+// Langevin O step carries the coloured random force.  Eq. 5: primitive energy
+// estimator, accumulated in FP64.
+#include <climits>
+#include <type_traits>
+
+#include "qtb_dev.cuh"
+#include "qtb_kernels.cuh"
+
+namespace qtb {
+
+struct alignas(32) D4 {  // packed FP64 position + type of one cell slot
+    double x, y, z, w;
+};
+
+// ---------------------------------------------------------------------------
+// position storage
+
+template <int PM, class R> struct PosT;
+
+template <class R> struct PosT<PM_BOX64, R> {  // FP64, wrapped into [0, L)
+    typedef double S;
+    __device__ static R rel(S a, S b, double L)
+    {
+        double d = a - b;
+        return (R)(d - L * rint(d / L));
+    }
+    __device__ static S add(S a, R delta, double L)
+    {
+        double x = a + (double)delta;
+        x -= L * floor(x / L);
+        return (x >= L || x < 0.0) ? 0.0 : x;
+    }
+};
+
+template <class R> struct PosT<PM_FIX, R> {  // 30-bit fixed point per box edge
+    typedef int S;
+    __device__ static R rel(S a, S b, double L)
+    {
+        return (R)fix_minimg(a - b) * (R)(L * (1.0 / (double)(1 << kFixBits)));
+    }
+    __device__ static S add(S a, R delta, double L)
+    {
+        int dq = __float2int_rn((float)(delta * (R)((double)(1 << kFixBits) / L)));
+        return (int)(((unsigned)a + (unsigned)dq) & ((1u << kFixBits) - 1u));
+    }
+};
+
+template <class R> struct PosT<PM_FREE, R> {  // unbounded (external potentials)
+    typedef R S;
+    __device__ static R rel(S a, S b, double) { return a - b; }
+    __device__ static S add(S a, R delta, double) { return a + delta; }
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// CTA-wide sum of kNQ doubles held by lane 0 of each warp into out[0..kNQ)
+__device__ void cta_store_partials(const double *acc, double (*red)[kNQ], double *out)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int q = 0; q < kNQ; ++q) red[warp][q] = acc[q];
+    __syncthreads();
+    if (threadIdx.x < kNQ) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Integrator: B(dt/2) in bead space, then A(dt/2) O A(dt/2) in normal-mode
+// space, one thread per (system, Cartesian component, atom).
+
+template <int P, int PM, class R>
+__global__ void __launch_bounds__(128) k_integrate(Dev d, int j)
+{
+    constexpr int UN = (P <= 8) ? P : 1;  // full unroll only for small rings
+    __shared__ R Cs[P * P];
+    __shared__ double red[4][kNQ];
+    const int cta = blockIdx.x;
+    const int s = d.icta_sys[cta];
+    const DSys S = d.sys[s];
+    if (S.P != P) return;  // another instantiation handles this system
+    for (int t = threadIdx.x; t < P * P; t += blockDim.x) Cs[t] = reinterpret_cast<const R *>(d.nmC)[S.nm0 + t];
+    __syncthreads();
+    const int N = S.N;
+    const int local = (cta - S.icta0) * blockDim.x + threadIdx.x;
+    double acc[kNQ];
+    for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+    double spring = 0.0;
+    if (local < 3 * N) {
+        typedef typename PosT<PM, R>::S PS;
+        PS *X = reinterpret_cast<PS *>(d.x);
+        R *V = reinterpret_cast<R *>(d.v);
+        const R *F = reinterpret_cast<const R *>(d.f);
+        const size_t G = (size_t)d.G;
+        const int c = local / N, i = local - c * N;
+        const int t = d.typ[S.g0 + i];
+        const R hdtm = reinterpret_cast<const R *>(d.hdt_m)[t];
+        const R sig = reinterpret_cast<const R *>(d.osig)[s * kMaxTypes + t];
+        const double L = S.box[c];
+        const size_t base = c * G + S.g0 + i;
+        const PS x0 = X[base];
+        R a[P], q[P];
+        // relative bead positions -> modes
+#pragma unroll(UN)
+        for (int b = 0; b < P; ++b) a[b] = (b == 0) ? R(0) : PosT<PM, R>::rel(X[base + (size_t)b * N], x0, L);
+#pragma unroll(UN)
+        for (int k = 0; k < P; ++k) {
+            R u = 0;
+#pragma unroll(UN)
+            for (int b = 0; b < P; ++b) u += Cs[b * P + k] * a[b];
+            q[k] = u;
+        }
+        // B: half kick with the current forces, bead velocities -> modes
+#pragma unroll(UN)
+        for (int b = 0; b < P; ++b) a[b] = V[base + (size_t)b * N] + hdtm * F[base + (size_t)b * N];
+        R p[P];
+#pragma unroll(UN)
+        for (int k = 0; k < P; ++k) {
+            R u = 0;
+#pragma unroll(UN)
+            for (int b = 0; b < P; ++b) u += Cs[b * P + k] * a[b];
+            p[k] = u;
+        }
+        const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
+        const R *eta = reinterpret_cast<const R *>(d.eta) + (size_t)j * d.Dtot + S.dof0;
+        const R c1 = (R)S.c1;
+#pragma unroll(UN)
+        for (int k = 0; k < P; ++k) {
+            const R cs = rot[3 * k], sw = rot[3 * k + 1], ws = rot[3 * k + 2];
+            R qk = q[k], pk = p[k];
+            R qn = qk * cs + pk * sw;        // A(dt/2): exact free ring-polymer rotation
+            R pn = qk * ws + pk * cs;
+            pn = c1 * pn + sig * eta[(size_t)(k * 3 + c) * N + i];  // O(dt)
+            q[k] = qn * cs + pn * sw;        // A(dt/2)
+            p[k] = qn * ws + pn * cs;
+        }
+        // modes -> beads
+#pragma unroll(UN)
+        for (int b = 0; b < P; ++b) {
+            R u = 0, w = 0;
+#pragma unroll(UN)
+            for (int k = 0; k < P; ++k) {
+                u += Cs[b * P + k] * q[k];
+                w += Cs[b * P + k] * p[k];
+            }
+            a[b] = u;
+            V[base + (size_t)b * N] = w;
+        }
+#pragma unroll(UN)
+        for (int b = 0; b < P; ++b) X[base + (size_t)b * N] = PosT<PM, R>::add(x0, a[b], L);
+        if (P > 1) {
+            R sp = 0;
+#pragma unroll(UN)
+            for (int b = 0; b < P; ++b) {
+                R dd = a[b] - a[(b + 1) % P];
+                sp += dd * dd;
+            }
+            spring = 0.5 * d.mass_mvv[t] * S.wP * S.wP * (double)sp;
+        }
+    }
+    spring = warp_sum(spring);
+    acc[Q_SPRING] = spring;
+    cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
+}
+
+// ---------------------------------------------------------------------------
+// Cell list: bin (atomic slots), then one warp per cell sorts its slots by
+// bead-atom index so that every later sum has a fixed order.
+
+template <int PM>
+__global__ void k_bin(Dev d)
+{
+    const DRep R = d.rep[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R.N) return;
+    const size_t G = (size_t)d.G;
+    const long long g = R.g0 + i;
+    int cc[3];
+    for (int c = 0; c < 3; ++c) {
+        int v;
+        if (PM == PM_FIX) {
+            unsigned xq = (unsigned)reinterpret_cast<const int *>(d.x)[c * G + g];
+            v = (int)(((unsigned long long)xq * (unsigned)R.nc[c]) >> kFixBits);
+        } else {
+            double x = reinterpret_cast<const double *>(d.x)[c * G + g];
+            v = (int)floor(x / R.box[c] * R.nc[c]);
+        }
+        cc[c] = min(max(v, 0), R.nc[c] - 1);
+    }
+    const int cell = R.cell0 + cc[0] + R.nc[0] * (cc[1] + R.nc[1] * cc[2]);
+    const int slot = atomicAdd(&d.cnt[cell], 1);
+    if (slot < d.cap)
+        d.cidx[(size_t)cell * d.cap + slot] = (int)g;
+    else
+        atomicOr(d.err, (unsigned)ERR_OVERFLOW);
+}
+
+template <int PM>
+__global__ void k_cellsort(Dev d)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cell = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (cell >= d.ncells) return;
+    constexpr int E = 16;  // cap <= 512
+    const int n = min(d.cnt[cell], d.cap);
+    int key[E], rank[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        int idx = lane + 32 * e;
+        key[e] = (idx < n) ? d.cidx[(size_t)cell * d.cap + idx] : INT_MAX;
+        rank[e] = 0;
+    }
+    const int ne = (n + 31) >> 5;
+    for (int e2 = 0; e2 < ne; ++e2)
+        for (int l = 0; l < 32; ++l) {
+            int other = __shfl_sync(0xffffffffu, key[e2], l);
+#pragma unroll
+            for (int e = 0; e < E; ++e) rank[e] += (other < key[e]) ? 1 : 0;
+        }
+    __syncwarp();
+    const size_t G = (size_t)d.G;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        int idx = lane + 32 * e;
+        if (idx < n) {
+            int g = key[e];
+            size_t o = (size_t)cell * d.cap + rank[e];
+            d.cidx[o] = g;
+            if (PM == PM_FIX) {
+                const int *X = reinterpret_cast<const int *>(d.x);
+                reinterpret_cast<int4 *>(d.cpos)[o] = make_int4(X[g], X[G + g], X[2 * G + g], d.typ[g]);
+            } else {
+                const double *X = reinterpret_cast<const double *>(d.x);
+                reinterpret_cast<D4 *>(d.cpos)[o] = D4{X[g], X[G + g], X[2 * G + g], (double)d.typ[g]};
+            }
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        d.ccount[cell] = n;
+        d.cnt[cell] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pair force: Buckingham (energy-shifted) + damped shifted force Coulomb.
+
+__device__ __forceinline__ float my_exp(float x) { return expf(x); }
+__device__ __forceinline__ double my_exp(double x) { return exp(x); }
+__device__ __forceinline__ float my_erfc(float x) { return erfcf(x); }
+__device__ __forceinline__ double my_erfc(double x) { return erfc(x); }
+__device__ __forceinline__ float my_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double my_rsqrt(double x) { return rsqrt(x); }
+
+template <class R>
+__device__ __forceinline__ void pair_eval(const PairTab &T, int tij, R r2, R &f_over_r, R &e)
+{
+    const R rinv = my_rsqrt(r2);
+    const R r = r2 * rinv;
+    R f = 0, en = 0;
+    const R A = (R)T.A[tij], Cc = (R)T.C[tij];
+    if (A != R(0)) {
+        const R ir = (R)T.inv_rho[tij];
+        const R ex = A * my_exp(-r * ir);
+        f += ex * ir;
+        en += ex;
+    }
+    if (Cc != R(0)) {
+        const R r2i = rinv * rinv;
+        const R r6i = r2i * r2i * r2i;
+        f -= R(6) * Cc * r6i * rinv;
+        en -= Cc * r6i;
+    }
+    en -= (R)T.eshift[tij];
+    const R qq = (R)T.qq[tij];
+    if (qq != R(0)) {
+        const R al = (R)T.alpha;
+        const R er = my_erfc(al * r);
+        const R gg = my_exp(-al * al * r2);
+        const R two_a_sqrtpi = (R)(2.0 * T.alpha / 1.7724538509055160273);
+        f += qq * (er * rinv * rinv + two_a_sqrtpi * gg * rinv - (R)T.fshift);
+        en += qq * (er * rinv - (R)T.erfc_rc_over_rc + (R)T.fshift * (r - (R)T.rc));
+    }
+    f_over_r = f * rinv;
+    e = en;
+}
+
+template <class R> struct Pack;
+template <> struct Pack<float> { typedef int4 T; };
+template <> struct Pack<double> { typedef D4 T; };
+
+template <int PM, class R>
+__global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_force_pair(Dev d, PairTab T, int kick)
+{
+    typedef typename std::conditional<sizeof(R) == 4, float4, D4>::type R4;
+    __shared__ R4 qbuf[kWarpsPerForceCta][64];
+    __shared__ double red[kWarpsPerForceCta][kNQ];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cell = blockIdx.x / d.cpc, chunk = blockIdx.x - cell * d.cpc;
+    const DRep RP = d.rep[d.cell_rep[cell]];
+    const DSys S = d.sys[RP.sys];
+    const int cnt = d.ccount[cell];
+    const int slot = chunk * kWarpsPerForceCta + warp;
+    double acc[kNQ];
+#pragma unroll
+    for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+    if (slot < cnt) {
+        const size_t hoff = (size_t)cell * d.cap + slot;
+        const int gi = d.cidx[hoff];
+        R hx, hy, hz;
+        int ti;
+        int ihx = 0, ihy = 0, ihz = 0;
+        if (PM == PM_FIX) {
+            int4 hp = reinterpret_cast<const int4 *>(d.cpos)[hoff];
+            ihx = hp.x; ihy = hp.y; ihz = hp.z; ti = hp.w;
+            hx = hy = hz = 0;
+        } else {
+            D4 hp = reinterpret_cast<const D4 *>(d.cpos)[hoff];
+            hx = (R)hp.x; hy = (R)hp.y; hz = (R)hp.z; ti = (int)hp.w;
+        }
+        const int lc = cell - RP.cell0;
+        const int cx = lc % RP.nc[0], cy = (lc / RP.nc[0]) % RP.nc[1], cz = lc / (RP.nc[0] * RP.nc[1]);
+        const R sx = (R)(RP.box[0] / (double)(1 << kFixBits)), sy = (R)(RP.box[1] / (double)(1 << kFixBits)),
+                sz = (R)(RP.box[2] / (double)(1 << kFixBits));
+        const R rc2 = (R)(T.rc * T.rc);
+        R fx = 0, fy = 0, fz = 0, en = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+        int qn = 0;
+        R4 *qb = qbuf[warp];
+        const unsigned lt = (1u << lane) - 1u;
+        auto consume = [&](int m) {
+            if (lane < m) {
+                R4 e4 = qb[lane];
+                int tj;
+                if (sizeof(R) == 4) tj = __float_as_int((float)e4.w); else tj = (int)e4.w;
+                R r2 = e4.x * e4.x + e4.y * e4.y + e4.z * e4.z;
+                R fo, ee;
+                pair_eval<R>(T, ti * kMaxTypes + tj, r2, fo, ee);
+                // d = r_i - r_j = -(stored displacement)
+                fx -= fo * e4.x; fy -= fo * e4.y; fz -= fo * e4.z;
+                en += ee;
+                w0 += fo * e4.x * e4.x; w1 += fo * e4.y * e4.y; w2 += fo * e4.z * e4.z;
+                w3 += fo * e4.x * e4.y; w4 += fo * e4.x * e4.z; w5 += fo * e4.y * e4.z;
+            }
+        };
+        for (int oz = -1; oz <= 1; ++oz)
+            for (int oy = -1; oy <= 1; ++oy)
+                for (int ox = -1; ox <= 1; ++ox) {
+                    int ux = cx + ox, uy = cy + oy, uz = cz + oz;
+                    int mx = (int)floor_div(ux, RP.nc[0]), my = (int)floor_div(uy, RP.nc[1]),
+                        mz = (int)floor_div(uz, RP.nc[2]);
+                    ux -= mx * RP.nc[0]; uy -= my * RP.nc[1]; uz -= mz * RP.nc[2];
+                    const int nc = RP.cell0 + ux + RP.nc[0] * (uy + RP.nc[1] * uz);
+                    const int ncnt = d.ccount[nc];
+                    const bool selfc = (ox == 0 && oy == 0 && oz == 0);
+                    const size_t nb = (size_t)nc * d.cap;
+                    for (int e0 = 0; e0 < ncnt; e0 += 32) {
+                        const int e = e0 + lane;
+                        R dx = 0, dy = 0, dz = 0;
+                        int tj = 0;
+                        bool take = false;
+                        if (e < ncnt && !(selfc && e == slot)) {
+                            if (PM == PM_FIX) {
+                                int4 pj = reinterpret_cast<const int4 *>(d.cpos)[nb + e];
+                                // displacement r_j + image - r_i, exact in int32
+                                int ix = (int)((unsigned)pj.x - (unsigned)ihx + (unsigned)mx * (1u << kFixBits));
+                                int iy = (int)((unsigned)pj.y - (unsigned)ihy + (unsigned)my * (1u << kFixBits));
+                                int iz = (int)((unsigned)pj.z - (unsigned)ihz + (unsigned)mz * (1u << kFixBits));
+                                dx = (R)ix * sx; dy = (R)iy * sy; dz = (R)iz * sz;
+                                tj = pj.w;
+                            } else {
+                                D4 pj = reinterpret_cast<const D4 *>(d.cpos)[nb + e];
+                                dx = (R)(pj.x + mx * RP.box[0]) - hx;
+                                dy = (R)(pj.y + my * RP.box[1]) - hy;
+                                dz = (R)(pj.z + mz * RP.box[2]) - hz;
+                                tj = (int)pj.w;
+                            }
+                            take = (dx * dx + dy * dy + dz * dz) < rc2;
+                        }
+                        const unsigned m = __ballot_sync(0xffffffffu, take);
+                        if (take) {
+                            R4 v;
+                            v.x = dx; v.y = dy; v.z = dz;
+                            if (sizeof(R) == 4) v.w = (R)__int_as_float(tj); else v.w = (R)tj;
+                            qb[qn + __popc(m & lt)] = v;
+                        }
+                        qn += __popc(m);
+                        __syncwarp();
+                        if (qn >= 32) {
+                            consume(32);
+                            __syncwarp();
+                            R4 carry;
+                            if (lane < qn - 32) carry = qb[32 + lane];
+                            __syncwarp();
+                            if (lane < qn - 32) qb[lane] = carry;
+                            qn -= 32;
+                            __syncwarp();
+                        }
+                    }
+                }
+        consume(qn);
+        fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz); en = warp_sum(en);
+        w0 = warp_sum(w0); w1 = warp_sum(w1); w2 = warp_sum(w2);
+        w3 = warp_sum(w3); w4 = warp_sum(w4); w5 = warp_sum(w5);
+        if (lane == 0) {
+            const size_t G = (size_t)d.G;
+            R *Fo = reinterpret_cast<R *>(d.f);
+            R *V = reinterpret_cast<R *>(d.v);
+            const R invP = (R)(1.0 / S.P);
+            const R f3[3] = {fx * invP, fy * invP, fz * invP};
+            const double m = T.mass[ti] * kMvv2e;
+            const R hdtm = (R)(0.5 * d.dt / m);
+            double ke = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                Fo[c * G + gi] = f3[c];
+                R v = V[c * G + gi];
+                if (kick) {
+                    v += hdtm * f3[c];
+                    V[c * G + gi] = v;
+                }
+                ke += 0.5 * m * (double)v * (double)v;
+                acc[Q_MOM + c] = T.mass[ti] * (double)v;
+            }
+            acc[Q_K] = ke;
+            acc[Q_V] = 0.5 * (double)en;
+            acc[Q_VIR + 0] = 0.5 * (double)w0; acc[Q_VIR + 1] = 0.5 * (double)w1; acc[Q_VIR + 2] = 0.5 * (double)w2;
+            acc[Q_VIR + 3] = 0.5 * (double)w3; acc[Q_VIR + 4] = 0.5 * (double)w4; acc[Q_VIR + 5] = 0.5 * (double)w5;
+        }
+    }
+    cta_store_partials(acc, red, d.part + (size_t)blockIdx.x * kNQ);
+}
+
+// External separable potentials, one thread per bead-atom.  grid = (gx, nsys)
+template <class R>
+__global__ void __launch_bounds__(128) k_force_ext(Dev d, PairTab T, int kick)
+{
+    __shared__ double red[4][kNQ];
+    const DSys S = d.sys[blockIdx.y];
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[kNQ];
+#pragma unroll
+    for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+    if (l < S.N * S.P) {
+        const size_t G = (size_t)d.G, g = S.g0 + l;
+        const int t = d.typ[g];
+        const double m = T.mass[t] * kMvv2e;
+        const R hdtm = (R)(0.5 * d.dt / m);
+        const R invP = (R)(1.0 / S.P);
+        const R *X = reinterpret_cast<const R *>(d.x);
+        R *Fo = reinterpret_cast<R *>(d.f);
+        R *V = reinterpret_cast<R *>(d.v);
+        double e = 0.0, ke = 0.0, x2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const R x = X[c * G + g];
+            R fx, ex;
+            if (T.potential == QTB_POT_HARMONIC) {
+                const R k = (R)(m * T.ext_omega * T.ext_omega);
+                fx = -k * x;
+                ex = R(0.5) * k * x * x;
+            } else {
+                const R ia2 = (R)(1.0 / (T.ext_a * T.ext_a)), V0 = (R)T.ext_V0;
+                const R u = x * x * ia2 - R(1);
+                fx = R(-4) * V0 * u * x * ia2;
+                ex = V0 * u * u;
+            }
+            const R fb = fx * invP;
+            Fo[c * G + g] = fb;
+            R v = V[c * G + g];
+            if (kick) {
+                v += hdtm * fb;
+                V[c * G + g] = v;
+            }
+            e += (double)ex;
+            ke += 0.5 * m * (double)v * (double)v;
+            x2 += (double)x * (double)x;
+            acc[Q_MOM + c] = T.mass[t] * (double)v;
+            acc[Q_VIR + c] = (double)x * (double)fx;
+        }
+        acc[Q_K] = ke;
+        acc[Q_V] = e;
+        acc[Q_X2] = x2;
+    }
+    for (int q = 0; q < kNQ; ++q) acc[q] = warp_sum(acc[q]);
+    cta_store_partials(acc, red, d.part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kNQ);
+}
+
+// ---------------------------------------------------------------------------
+// Per-system reduction into the observable record (fixed summation order).
+
+__global__ void k_reduce(Dev d, int j, int force_record)
+{
+    __shared__ double sh[128][kNQ + 1];
+    const int s = blockIdx.x;
+    const DSys S = d.sys[s];
+    double acc[kNQ + 1];
+    for (int q = 0; q <= kNQ; ++q) acc[q] = 0.0;
+    for (int c = S.fcta0 + threadIdx.x; c < S.fcta1; c += blockDim.x)
+        for (int q = 0; q < kNQ; ++q) acc[q] += d.part[(size_t)c * kNQ + q];
+    for (int c = S.icta0 + threadIdx.x; c < S.icta1; c += blockDim.x) acc[kNQ] += d.ipart[(size_t)c * kNQ + Q_SPRING];
+    for (int q = 0; q <= kNQ; ++q) sh[threadIdx.x][q] = acc[q];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q <= kNQ; ++q) sh[threadIdx.x][q] += sh[threadIdx.x + w][q];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const long long step = d.clock[0] * kBlockSteps + j + 1;  // steps completed
+        const double invP = 1.0 / S.P;
+        double rec[QTB_NREC];
+        for (int q = 0; q < QTB_NREC; ++q) rec[q] = 0.0;
+        const double K = sh[0][Q_K], V = sh[0][Q_V] * invP, sp = sh[0][kNQ];
+        rec[0] = (double)step;
+        rec[1] = K;
+        rec[2] = V;
+        rec[3] = sp;
+        rec[4] = K - sp + V;
+        const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};  // xx xy xz / yx yy yz / zx zy zz
+        for (int a = 0; a < 9; ++a) rec[5 + a] = sh[0][Q_VIR + map[a]] * invP;
+        for (int c = 0; c < 3; ++c) rec[14 + c] = sh[0][Q_MOM + c];
+        rec[17] = sh[0][Q_X2] * invP;
+        if (!isfinite(K) || !isfinite(V)) atomicOr(d.err, (unsigned)ERR_NONFINITE);
+        for (int q = 0; q < QTB_NREC; ++q) d.latest[(size_t)s * QTB_NREC + q] = rec[q];
+        if (force_record >= 0 && step % d.obs_stride == 0) {
+            long long r = step / d.obs_stride - 1;
+            int slot = (int)(r % d.max_records);
+            for (int q = 0; q < QTB_NREC; ++q) d.series[((size_t)slot * d.nsys + s) * QTB_NREC + q] = rec[q];
+        }
+    }
+}
+
+__global__ void k_tick(Dev d) { d.clock[0] += 1; }
+__global__ void k_setclock(Dev d, long long b) { d.clock[0] = b; }
+
+// ---------------------------------------------------------------------------
+// launchers
+
+bool md_supported_P(int P) { return (P >= 1 && P <= 6) || P == 8 || P == 16 || P == 32; }
+
+template <int PM, class R>
+static void integrate_all(const Dev &d, const MdLaunch &m, int j, cudaStream_t st)
+{
+    for (int u = 0; u < m.nP; ++u) {
+        switch (m.Pvals[u]) {
+#define QTB_P(PP) case PP: k_integrate<PP, PM, R><<<m.n_icta, 128, 0, st>>>(d, j); break;
+            QTB_P(1) QTB_P(2) QTB_P(3) QTB_P(4) QTB_P(5) QTB_P(6) QTB_P(8) QTB_P(16) QTB_P(32)
+#undef QTB_P
+            default: break;
+        }
+    }
+}
+
+void launch_integrate(const Dev &d, const MdLaunch &m, int j, cudaStream_t st)
+{
+    if (!m.pair) {
+        if (m.mixed) integrate_all<PM_FREE, float>(d, m, j, st);
+        else integrate_all<PM_FREE, double>(d, m, j, st);
+    } else {
+        if (m.mixed) integrate_all<PM_FIX, float>(d, m, j, st);
+        else integrate_all<PM_BOX64, double>(d, m, j, st);
+    }
+}
+
+void launch_cells(const Dev &d, const MdLaunch &m, cudaStream_t st)
+{
+    if (!m.pair) return;
+    dim3 g((unsigned)m.n_bcta, (unsigned)d.nrep);
+    if (m.mixed) {
+        k_bin<PM_FIX><<<g, 256, 0, st>>>(d);
+        k_cellsort<PM_FIX><<<(d.ncells + 7) / 8, 256, 0, st>>>(d);
+    } else {
+        k_bin<PM_BOX64><<<g, 256, 0, st>>>(d);
+        k_cellsort<PM_BOX64><<<(d.ncells + 7) / 8, 256, 0, st>>>(d);
+    }
+}
+
+void launch_force_kick(const Dev &d, const MdLaunch &m, const PairTab &T, int kick, cudaStream_t st)
+{
+    if (m.pair) {
+        const unsigned grid = (unsigned)(d.ncells * d.cpc);
+        if (m.mixed) k_force_pair<PM_FIX, float><<<grid, 32 * kWarpsPerForceCta, 0, st>>>(d, T, kick);
+        else k_force_pair<PM_BOX64, double><<<grid, 32 * kWarpsPerForceCta, 0, st>>>(d, T, kick);
+    } else {
+        dim3 g((unsigned)m.n_ecta, (unsigned)d.nsys);
+        if (m.mixed) k_force_ext<float><<<g, 128, 0, st>>>(d, T, kick);
+        else k_force_ext<double><<<g, 128, 0, st>>>(d, T, kick);
+    }
+}
+
+void launch_reduce(const Dev &d, const MdLaunch &m, int j, int record, cudaStream_t st)
+{
+    k_reduce<<<d.nsys, 128, 0, st>>>(d, j, record);
+}
+
+void launch_tick(const Dev &d, cudaStream_t st) { k_tick<<<1, 1, 0, st>>>(d); }
+void launch_setclock(const Dev &d, long long b, cudaStream_t st) { k_setclock<<<1, 1, 0, st>>>(d, b); }
+
+}  // namespace qtb

@@ -1,0 +1,377 @@
+// noise.cu -- white noise, SIMT noise filters, spectra, filter taps and the
+// FP64 kappa_P solve of the QTB / QTB-PIMD random force (sm_103a).
+//
+// Eqs. 6-7: the random force has spectral density 2 m gamma theta(w,T);
+// Eq. 12: QTB-PIMD uses kappa_P (Eq. 10) instead.  The force of the O step is
+// sqrt((1-c1^2)/m) eta_n, eta_n = sum_{k=-K..K} h_|k| xi_{n-k}: a zero-phase
+// time-domain filter of counter-based white noise xi whose response equals
+// sqrt(S(w_j)) on the grid w_j = 2 pi j/(L dt), S = theta W or kappa_P W.
+#include <cuda_bf16.h>
+
+#include "qtb_dev.cuh"
+#include "qtb_kernels.cuh"
+
+namespace qtb {
+
+// ---------------------------------------------------------------------------
+// White noise: one Philox call per (dof, 4 steps); Box-Muller pairs
+// (w0,w1) -> steps 4q, 4q+1 (cos, sin), (w2,w3) -> 4q+2, 4q+3.
+
+__device__ __forceinline__ void bm_pair(uint32_t a, uint32_t b, double &z0, double &z1)
+{
+    double u1 = ((double)a + 1.0) * 2.3283064365386963e-10;  // 2^-32, (0, 1]
+    double u2 = (double)b * 2.3283064365386963e-10;          // [0, 1)
+    double r = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+__device__ __forceinline__ void bm_pair(uint32_t a, uint32_t b, float &z0, float &z1)
+{
+    float u1 = ((float)a + 1.0f) * 2.3283064365386963e-10f;
+    float u2 = (float)b * 2.3283064365386963e-10f;
+    float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+template <class T> struct RingStore;
+template <> struct RingStore<double> {
+    __device__ static void put(double *p, double a, double b, double c, double d)
+    {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(a, b);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
+    }
+};
+template <> struct RingStore<float> {
+    __device__ static void put(float *p, float a, float b, float c, float d)
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+    }
+};
+template <> struct RingStore<__nv_bfloat16> {
+    __device__ static void put(__nv_bfloat16 *p, float a, float b, float c, float d)
+    {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t *>(&lo);
+        u.y = *reinterpret_cast<uint32_t *>(&hi);
+        *reinterpret_cast<uint2 *>(p) = u;
+    }
+};
+
+// Generate white block `blk` (blk_abs >= -2^40; blk_override == LLONG_MIN means
+// clock + Kb) into its ring slot.  grid = (ceil(max dofp * 64 / 256), nsys).
+template <class T, class C>
+__global__ void k_white(Dev d, long long blk_override)
+{
+    const DSys s = d.sys[blockIdx.y];
+    long long local = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int dofl = (int)(local >> 6), qi = (int)(local & 63);
+    if (dofl >= s.dofp) return;
+    long long blk = (blk_override == LLONG_MIN) ? d.clock[0] + d.Kb : blk_override;
+    int slot = (int)(blk - floor_div(blk, d.nslots) * d.nslots);
+    T *dst = reinterpret_cast<T *>(d.ring) + ((size_t)slot * d.Dtot + s.dof0 + dofl) * kBlockSteps + 4 * qi;
+    C z0 = 0, z1 = 0, z2 = 0, z3 = 0;
+    if (dofl < 3 * s.N * s.P) {
+        long long q = blk * (kBlockSteps / 4) + qi;
+        unsigned long long uq = (unsigned long long)q;
+        uint4 ctr = make_uint4((uint32_t)uq, (uint32_t)dofl, 0u, (uint32_t)(uq >> 32));
+        uint32_t sysid = (uint32_t)blockIdx.y;
+        uint4 w = philox4x32_10(ctr, (uint32_t)d.seed, (uint32_t)(d.seed >> 32) ^ sysid);
+        bm_pair(w.x, w.y, z0, z1);
+        bm_pair(w.z, w.w, z2, z3);
+    }
+    RingStore<T>::put(dst, z0, z1, z2, z3);
+}
+
+// ---------------------------------------------------------------------------
+// SIMT filter: one CTA (256 threads = 256 output steps) per dof.
+// grid = (max dofp, nsys); dynamic smem = (256 + 2 Kmax + Kmax + 1) * sizeof(T)
+template <class T>
+__global__ void k_filter_simt(Dev d)
+{
+    extern __shared__ unsigned char smraw[];
+    T *win = reinterpret_cast<T *>(smraw);
+    const DSys s = d.sys[blockIdx.y];
+    int dofl = blockIdx.x;
+    if (dofl >= s.dofp) return;
+    const int K = s.K, span = kBlockSteps + 2 * K;
+    T *h = win + span;
+    long long blk = d.clock[0];
+    T *eta = reinterpret_cast<T *>(d.eta);
+    const int j = threadIdx.x;
+    if (dofl >= 3 * s.N * s.P) {
+        eta[(size_t)j * d.Dtot + s.dof0 + dofl] = T(0);
+        return;
+    }
+    const T *ring = reinterpret_cast<const T *>(d.ring);
+    const T *taps = reinterpret_cast<const T *>(d.tapsR) + s.taps0;
+    for (int t = threadIdx.x; t < span; t += blockDim.x) {
+        long long n = blk * kBlockSteps - K + t;
+        long long rb = floor_div(n, kBlockSteps);
+        int slot = (int)(rb - floor_div(rb, d.nslots) * d.nslots);
+        win[t] = ring[((size_t)slot * d.Dtot + s.dof0 + dofl) * kBlockSteps + (int)(n - rb * kBlockSteps)];
+    }
+    for (int t = threadIdx.x; t <= K; t += blockDim.x) h[t] = taps[t];
+    __syncthreads();
+    // xi(n - k) with n = blk*256 + j sits at window index j + K - k
+    T acc = h[0] * win[j + K];
+    for (int k = 1; k <= K; ++k) acc += h[k] * (win[j + K - k] + win[j + K + k]);
+    eta[(size_t)j * d.Dtot + s.dof0 + dofl] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Spectra and taps (FP64).
+
+__device__ double theta_dev(double w, double T)
+{
+    w = fabs(w);
+    double kT = kBoltz * T;
+    double x = kHbar * w / kT;
+    if (x < 1e-6) return kT * (1.0 + x * x / 12.0);
+    return kHbar * w * (0.5 + 1.0 / expm1(x));
+}
+
+__device__ double fth_dev(double x)
+{
+    x = fabs(x);
+    if (x < 1e-6) return 1.0 + x * x / 12.0;
+    return x * (0.5 + 1.0 / expm1(x));
+}
+
+__device__ double kappa_tail_dev(int P, double y)
+{
+    if (P == 1) return fth_dev(y);
+    return fth_dev(sqrt((double)P) * y) / P + sqrt((double)P) / (2.0 * y);
+}
+
+// F_P at y from the collocation grid y_i = y0 sinh(i dts)
+__device__ double kappa_eval_dev(const DSpec &sp, double y)
+{
+    if (sp.P == 1) return fth_dev(y);
+    if (y > sp.ymax) return kappa_tail_dev(sp.P, y);
+    double dts = asinh(sp.ymax / sp.y0) / (sp.n - 1);
+    int i = (int)(asinh(y / sp.y0) / dts);
+    if (i > sp.n - 2) i = sp.n - 2;
+    double ya = sp.y0 * sinh(i * dts), yb = sp.y0 * sinh((i + 1) * dts);
+    double lam = (y - ya) / (yb - ya);
+    return sp.F[i] * (1.0 - lam) + sp.F[i + 1] * lam;
+}
+
+// S_j, j = 0..K, per system.  grid = (ceil((Kmax+1)/256), nsys)
+__global__ void k_spectrum(const DSpec *spec, double *S)
+{
+    const DSpec sp = spec[blockIdx.y];
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > sp.K) return;
+    int L = 2 * sp.K + 1;
+    double w = 2.0 * kPi * j / (L * sp.dt);
+    double base;
+    if (sp.mode == QTB_NOISE_WHITE) {
+        base = kBoltz * sp.T;
+    } else if (sp.mode == QTB_NOISE_QTB) {
+        base = theta_dev(w, sp.T);
+    } else {
+        double kT = kBoltz * sp.T;
+        base = kT * kappa_eval_dev(sp, kHbar * w / kT);
+    }
+    double W = 1.0;
+    if (sp.mode != QTB_NOISE_WHITE && sp.omega_max > 0.0)
+        W = 1.0 / (1.0 + exp((w - sp.omega_max) / (sp.omega_max / 50.0)));
+    S[sp.taps0 + j] = base * W;
+}
+
+// h_k = (1/L) [sqrt(S_0) + 2 sum_j sqrt(S_j) cos(2 pi j k / L)].  grid = (ceil((Kmax+1)/128), nsys)
+__global__ void k_taps(const DSpec *spec, const double *S, double *h64, float *h32)
+{
+    const DSpec sp = spec[blockIdx.y];
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > sp.K) return;
+    const int K = sp.K;
+    const long long L = 2 * K + 1;
+    const double *Sj = S + sp.taps0;
+    double acc = 0.0;
+    for (int j = 1; j <= K; ++j) {
+        long long m = ((long long)j * k) % L;
+        acc += sqrt(Sj[j]) * cospi(2.0 * (double)m / (double)L);
+    }
+    double h = (sqrt(Sj[0]) + 2.0 * acc) / (double)L;
+    h64[sp.taps0 + k] = h;
+    h32[sp.taps0 + k] = (float)h;
+}
+
+// ---------------------------------------------------------------------------
+// kappa_P solve (Eq. 10), FP64: dense collocation rows, normal equations,
+// Cholesky (one CTA), triangular solves (one CTA).
+
+// rows m < 2n-1; A is (2n-1) x n row-major, zeroed by the caller
+__global__ void k_kappa_rows(int P, int n, double ymax, double y0, double *A, double *b)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    int rows = 2 * n - 1;
+    if (m >= rows) return;
+    double dts = asinh(ymax / y0) / (n - 1);
+    double y = y0 * sinh(0.5 * m * dts);
+    double rhs = fth_dev(sqrt((double)P) * y);
+    double *Ar = A + (size_t)m * n;
+    for (int k = 0; k < P; ++k) {
+        double sk = sinpi((double)k / P);
+        double ck = 4.0 * P * sk * sk;
+        double yk = sqrt(y * y + ck);
+        double w = (k == 0) ? 1.0 : ((y * y + ck) > 0.0 ? y * y / (y * y + ck) : 0.0);
+        if (w == 0.0) continue;
+        if (yk <= ymax) {
+            int i = (int)(asinh(yk / y0) / dts);
+            if (i > n - 2) i = n - 2;
+            double ya = y0 * sinh(i * dts), yb = y0 * sinh((i + 1) * dts);
+            double lam = (yk - ya) / (yb - ya);
+            Ar[i] += w * (1.0 - lam);
+            Ar[i + 1] += w * lam;
+        } else {
+            rhs -= w * kappa_tail_dev(P, yk);
+        }
+    }
+    double sc = 1.0 / fth_dev(sqrt((double)P) * y);
+    for (int i = 0; i < n; ++i) Ar[i] *= sc;
+    b[m] = rhs * sc;
+}
+
+// M = A^T A (n x n), r = A^T b; 32x32 tiles, 256 threads (each 4 outputs)
+__global__ void k_kappa_normal(int rows, int n, const double *A, const double *b, double *M, double *r)
+{
+    __shared__ double ta[32][33], tb[32][33];
+    int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // ty in 0..7
+    double acc[4] = {0, 0, 0, 0};
+    for (int m0 = 0; m0 < rows; m0 += 32) {
+        for (int q = 0; q < 4; ++q) {
+            int mm = m0 + ty + 8 * q;
+            ta[ty + 8 * q][tx] = (mm < rows && i0 + tx < n) ? A[(size_t)mm * n + i0 + tx] : 0.0;
+            tb[ty + 8 * q][tx] = (mm < rows && j0 + tx < n) ? A[(size_t)mm * n + j0 + tx] : 0.0;
+        }
+        __syncthreads();
+        for (int mm = 0; mm < 32; ++mm)
+            for (int q = 0; q < 4; ++q) acc[q] += ta[mm][ty + 8 * q] * tb[mm][tx];
+        __syncthreads();
+    }
+    for (int q = 0; q < 4; ++q) {
+        int i = i0 + ty + 8 * q, j = j0 + tx;
+        if (i < n && j < n) M[(size_t)i * n + j] = acc[q];
+    }
+    if (blockIdx.x == 0) {
+        // r = A^T b for rows i0..i0+31
+        if (threadIdx.x < 32) {
+            int i = i0 + threadIdx.x;
+            if (i < n) {
+                double s = 0.0;
+                for (int mm = 0; mm < rows; ++mm) s += A[(size_t)mm * n + i] * b[mm];
+                r[i] = s;
+            }
+        }
+    }
+}
+
+// In-place Cholesky of the lower triangle of M (n x n); one CTA.
+__global__ void k_kappa_chol(int n, double *M, unsigned *err)
+{
+    __shared__ double dj;
+    for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) {
+            double v = M[(size_t)j * n + j];
+            if (!(v > 0.0)) { atomicOr(err, (unsigned)ERR_SOLVE); v = 1e-300; }
+            dj = sqrt(v);
+            M[(size_t)j * n + j] = dj;
+        }
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) M[(size_t)i * n + j] /= dj;
+        __syncthreads();
+        // trailing update of the lower triangle: rows i > j, columns j < k <= i
+        {
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+            for (int i = j + 1 + warp; i < n; i += nw) {
+                const double lij = M[(size_t)i * n + j];
+                for (int k = j + 1 + lane; k <= i; k += 32) M[(size_t)i * n + k] -= lij * M[(size_t)k * n + j];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Solve L L^T x = r in place (x overwrites r); one CTA.
+__global__ void k_kappa_trsv(int n, const double *M, double *r)
+{
+    __shared__ double xj;
+    for (int j = 0; j < n; ++j) {  // forward: L y = r
+        if (threadIdx.x == 0) { xj = r[j] / M[(size_t)j * n + j]; r[j] = xj; }
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) r[i] -= M[(size_t)i * n + j] * xj;
+        __syncthreads();
+    }
+    for (int j = n - 1; j >= 0; --j) {  // backward: L^T x = y
+        if (threadIdx.x == 0) { xj = r[j] / M[(size_t)j * n + j]; r[j] = xj; }
+        __syncthreads();
+        for (int i = threadIdx.x; i < j; i += blockDim.x) r[i] -= M[(size_t)j * n + i] * xj;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+void launch_white(const Dev &d, int filter_kind, int max_dofp, int nsys, long long blk, cudaStream_t st)
+{
+    dim3 grid((unsigned)(((long long)max_dofp * 64 + 255) / 256), (unsigned)nsys);
+    if (filter_kind == FK_FP64)
+        k_white<double, double><<<grid, 256, 0, st>>>(d, blk);
+    else if (filter_kind == FK_FP32)
+        k_white<float, float><<<grid, 256, 0, st>>>(d, blk);
+    else
+        k_white<__nv_bfloat16, float><<<grid, 256, 0, st>>>(d, blk);
+}
+
+void launch_filter_simt(const Dev &d, int filter_kind, int max_dofp, int nsys, int Kmax, cudaStream_t st)
+{
+    dim3 grid((unsigned)max_dofp, (unsigned)nsys);
+    if (filter_kind == FK_FP64) {
+        size_t sm = sizeof(double) * (kBlockSteps + 3 * Kmax + 1);
+        k_filter_simt<double><<<grid, kBlockSteps, sm, st>>>(d);
+    } else {
+        size_t sm = sizeof(float) * (kBlockSteps + 3 * Kmax + 1);
+        k_filter_simt<float><<<grid, kBlockSteps, sm, st>>>(d);
+    }
+}
+
+cudaError_t filter_simt_prepare(int Kmax)
+{
+    size_t sm = sizeof(double) * (kBlockSteps + 3 * Kmax + 1);
+    cudaError_t e = cudaFuncSetAttribute(k_filter_simt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_filter_simt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sm / 2 + 16));
+}
+
+void launch_spectrum_taps(const DSpec *spec, int nsys, int Kmax, double *S, double *h64, float *h32,
+                          cudaStream_t st)
+{
+    k_spectrum<<<dim3((Kmax + 1 + 255) / 256, nsys), 256, 0, st>>>(spec, S);
+    k_taps<<<dim3((Kmax + 1 + 127) / 128, nsys), 128, 0, st>>>(spec, S, h64, h32);
+}
+
+void launch_kappa_solve(int P, int n, double ymax, double y0, double *A, double *b, double *M, double *r,
+                        unsigned *err, cudaStream_t st)
+{
+    int rows = 2 * n - 1;
+    cudaMemsetAsync(A, 0, sizeof(double) * (size_t)rows * n, st);
+    k_kappa_rows<<<(rows + 127) / 128, 128, 0, st>>>(P, n, ymax, y0, A, b);
+    k_kappa_normal<<<dim3((n + 31) / 32, (n + 31) / 32), 256, 0, st>>>(rows, n, A, b, M, r);
+    k_kappa_chol<<<1, 1024, 0, st>>>(n, M, err);
+    k_kappa_trsv<<<1, 1024, 0, st>>>(n, M, r);
+}
+
+}  // namespace qtb

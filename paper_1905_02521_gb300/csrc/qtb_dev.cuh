@@ -1,0 +1,143 @@
+// qtb_dev.cuh -- device-side definitions shared by the CUDA translation units
+// of the QTB / QTB-PIMD hot path (sm_103a).
+//
+// Method: Dammak, Hayoun, Brieuc, Geneste, "Nuclear quantum effects in
+// molecular dynamics simulations" (Eqs. 1, 3-5, 6-8, 10-12).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qtb.h"
+
+namespace qtb {
+
+// Physical constants (CODATA 2018) and unit conversions: A, fs, eV, u, e, K.
+constexpr double kHbar = 0.6582119569;          // eV fs
+constexpr double kBoltz = 8.617333262e-5;       // eV / K
+constexpr double kMvv2e = 103.64269652680505;   // eV per u A^2 / fs^2
+constexpr double kCoulomb = 14.3996454784;      // e^2 / (4 pi eps0), eV A
+constexpr double kPi = 3.14159265358979323846;
+
+constexpr int kBlockSteps = 256;     // noise block length (steps)
+constexpr int kDofPad = 128;         // per-system dof padding (tensor-core M tile)
+constexpr int kNQ = 16;              // partial sums per CTA (see Q_* below)
+constexpr int kFixBits = 30;         // fixed-point positions: box edge = 2^30 units
+constexpr int kMaxTypes = 4;
+constexpr int kWarpsPerForceCta = 8;
+
+// partial-sum slots
+enum { Q_K = 0, Q_V = 1, Q_SPRING = 2, Q_VIR = 3 /* 6 slots: xx yy zz xy xz yz */, Q_MOM = 9 /* 3 */,
+       Q_X2 = 12 };
+
+// position storage modes
+enum { PM_BOX64 = 0, PM_FIX = 1, PM_FREE = 2 };
+
+// device error word bits
+enum { ERR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_SOLVE = 4 };
+
+struct DSys {
+    int N, P;          // atoms, beads
+    int g0;            // first bead-atom index (bead-major: g = g0 + b N + i)
+    int dof0;          // first noise dof (dof = dof0 + (k*3 + c) N + i)
+    int dofp;          // padded dof count of this system (multiple of kDofPad)
+    int K;             // filter half length (taps h_0..h_K)
+    int taps0;         // offset of h_0 in the taps arrays
+    int rep0;          // first replica (pair potential)
+    int icta0, icta1;  // integrator CTA range
+    int fcta0, fcta1;  // force CTA range
+    int rot0;          // offset of this system's mode rotation table
+    int nm0;           // offset of this system's normal-mode matrix
+    double box[3];
+    double T, gamma, c1, wP;
+};
+
+struct DRep {          // one replica (system, bead) of a pair-potential system
+    int sys, g0, N;
+    int nc[3];         // cells per edge
+    int cell0;         // first cell
+    int cta0;          // first binning CTA
+    double box[3];
+};
+
+struct PairTab {       // per type pair (a * kMaxTypes + b)
+    double A[kMaxTypes * kMaxTypes], inv_rho[kMaxTypes * kMaxTypes], C[kMaxTypes * kMaxTypes];
+    double qq[kMaxTypes * kMaxTypes];      // k_e q_a q_b
+    double eshift[kMaxTypes * kMaxTypes];  // Buckingham energy at r_cut
+    double alpha, rc, erfc_rc_over_rc, fshift;  // DSF constants
+    double mass[kMaxTypes];
+    double ext_omega, ext_V0, ext_a;
+    int ntypes, potential;
+};
+
+// Everything a kernel needs, passed by value.
+struct Dev {
+    // sizes
+    int nsys, nrep, ncells, cap, cpc;  // cpc = force CTAs per cell
+    long long G;                      // bead-atoms
+    long long Dtot;                   // padded dofs
+    int Kb, nslots;                   // noise ring: blocks of half-span, slots
+    int obs_stride, max_records;
+    double dt;
+    // tables
+    const DSys *sys;
+    const DRep *rep;
+    const int *cell_rep;  // [ncells]
+    const int *icta_sys;  // [integrator CTAs] system of each CTA
+    const int *ext_cta_sys;
+    // state
+    void *x;              // positions, SoA [3][G] (double, int32 or R by mode)
+    void *v;              // velocities [3][G] (R)
+    void *f;              // forces [3][G] (R), already multiplied by 1/P
+    const int *typ;       // [G] type of each bead-atom
+    // cells
+    int *cnt;             // [ncells] running counts (binning)
+    int *ccount;          // [ncells] counts after sorting
+    int *cidx;            // [ncells * cap] bead-atom index, sorted
+    void *cpos;           // [ncells * cap] packed positions (int4 or double4)
+    // noise
+    void *ring;           // [nslots][Dtot][256] white noise (double, float or bf16)
+    void *eta;            // [256][Dtot] coloured noise (R)
+    const double *taps64; // FP64 taps
+    const void *tapsR;    // taps in the filter type
+    // integrator tables
+    const void *rot;      // [sum P][3] (cos, sin/w, -w sin) per mode (R)
+    const void *nmC;      // normal-mode matrices (R)
+    const void *hdt_m;    // [ntypes] dt / (2 m mvv2e) (R)
+    const void *osig;     // [nsys * ntypes] sqrt((1 - c1^2)/(m mvv2e)) (R)
+    // reductions
+    double *part;         // [CTAs][kNQ]
+    double *ipart;        // [integrator CTAs][kNQ]
+    double *latest;       // [nsys][QTB_NREC]
+    double *series;       // [max_records][nsys][QTB_NREC]
+    long long *clock;     // [0] = current noise block
+    unsigned *err;        // error word
+    unsigned long long seed;
+    double mass_mvv[kMaxTypes];  // m * mvv2e per type (eV fs^2 / A^2)
+};
+
+// -------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11), written from its published
+// definition; counter = (lo32(q), dof, stream, hi32(q)), q = floor(n/4),
+// key = (lo32(seed), hi32(seed) ^ sys).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+__host__ __device__ inline long long floor_div(long long a, long long b)
+{
+    long long q = a / b;
+    return (q * b > a) ? q - 1 : q;
+}
+
+// sign-extend a 30-bit fixed-point difference (minimum image)
+__device__ __forceinline__ int fix_minimg(int d) { return (d << (32 - kFixBits)) >> (32 - kFixBits); }
+
+}  // namespace qtb

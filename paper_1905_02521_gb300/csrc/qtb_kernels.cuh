@@ -1,0 +1,51 @@
+// qtb_kernels.cuh -- launcher declarations shared by the host code and the
+// CUDA translation units.
+#pragma once
+#include "qtb_dev.cuh"
+
+namespace qtb {
+
+enum { FK_FP64 = 0, FK_FP32 = 1, FK_BF16 = 2 };  // filter / ring arithmetic
+
+// Spectrum parameters of one system (set_filter).
+struct DSpec {
+    int mode, K, taps0, P;
+    double dt, T, omega_max;
+    const double *F;  // kappa_P grid (device) for QTB-PIMD
+    int n;
+    double ymax, y0;
+};
+
+// noise.cu
+void launch_white(const Dev &d, int filter_kind, int max_dofp, int nsys, long long blk, cudaStream_t st);
+void launch_filter_simt(const Dev &d, int filter_kind, int max_dofp, int nsys, int Kmax, cudaStream_t st);
+cudaError_t filter_simt_prepare(int Kmax);
+void launch_spectrum_taps(const DSpec *spec, int nsys, int Kmax, double *S, double *h64, float *h32,
+                          cudaStream_t st);
+void launch_kappa_solve(int P, int n, double ymax, double y0, double *A, double *b, double *M, double *r,
+                        unsigned *err, cudaStream_t st);
+
+// md.cu
+struct MdLaunch {
+    int mixed;            // 0: FP64 form, 1: mixed form
+    int pair;             // pair potential (else external)
+    int n_icta;           // integrator CTAs
+    int n_bcta;           // binning CTAs
+    int n_ecta;           // external-force CTAs
+    int nP;               // number of distinct bead counts
+    int Pvals[8];         // distinct bead counts
+};
+void launch_integrate(const Dev &d, const MdLaunch &m, int j, cudaStream_t st);
+void launch_cells(const Dev &d, const MdLaunch &m, cudaStream_t st);
+void launch_force_kick(const Dev &d, const MdLaunch &m, const PairTab &T, int kick, cudaStream_t st);
+void launch_reduce(const Dev &d, const MdLaunch &m, int j, int record, cudaStream_t st);
+void launch_tick(const Dev &d, cudaStream_t st);
+void launch_setclock(const Dev &d, long long blk, cudaStream_t st);
+bool md_supported_P(int P);
+
+// filter_tc.cu
+cudaError_t filter_tc_prepare();
+void launch_filter_tc(const Dev &d, const void *tmapA, const void *tmapB, int n_mtiles, const int *mtile_sys,
+                      cudaStream_t st);
+
+}  // namespace qtb
