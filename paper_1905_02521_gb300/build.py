@@ -62,7 +62,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(o)
     objs = [o.split("\n")[0] for o in outs]
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"]
+    # the driver library is resolved at run time (dlopen), so the library also
+    # loads on machines without a GPU driver
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -4,6 +4,9 @@
 // padded to tensor-core tiles, cell lists per bead replica), the noise
 // pipeline (white blocks in a ring, coloured block per 256 steps) and the
 // CUDA graph that replays one 256-step block.
+#include <cuda.h>
+#include <dlfcn.h>
+
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -61,6 +64,7 @@ struct qtb_ctx {
     Dev d{};
     MdLaunch ml{};
     PairTab tab{};
+    PairTabT<float> tabf{};
     long long step = 0;
     long long dclock = 0;          // host mirror of the device clock
     long long ring_hi = LLONG_MIN; // highest white block in the ring
@@ -85,6 +89,12 @@ struct qtb_ctx {
     std::vector<int> ev_cls;            // class of each pair
     size_t ev_used = 0, ev_pairs = 0;
     bool prof_launched = false;
+    // tensor-core filter
+    alignas(64) CUtensorMap tmA, tmB;
+    void *d_Bt = nullptr;
+    size_t Bt_bytes = 0;
+    int *d_tiles = nullptr;
+    int n_tiles = 0;
 
     void *alloc(size_t bytes)
     {
@@ -157,6 +167,7 @@ int check_err_word(qtb_ctx *c)
     if (e & ERR_OVERFLOW) return fail(QTB_ERR_OVERFLOW, "a cell-list cell exceeded its capacity (%d)", c->d.cap);
     if (e & ERR_NONFINITE) return fail(QTB_ERR_NONFINITE, "non-finite energy: the integration blew up");
     if (e & ERR_SOLVE) return fail(QTB_ERR_SOLVE, "kappa_P solve: non-positive pivot");
+    if (e & ERR_TIMEOUT_TC) return fail(QTB_ERR_TIMEOUT, "tensor-core filter: a bounded barrier wait gave up");
     return QTB_OK;
 }
 
@@ -267,7 +278,7 @@ int refresh_forces(qtb_ctx *c)
 {
     set_clock(c, floor_div(c->step, kBlockSteps));
     launch_cells(c->d, c->ml, c->st);
-    launch_force_kick(c->d, c->ml, c->tab, 0, c->st);
+    launch_force_kick(c->d, c->ml, c->tabf, c->tab, 0, c->st);
     int j = (int)(c->step - c->dclock * kBlockSteps) - 1;
     launch_reduce(c->d, c->ml, j, -1, c->st);
     CUDA_TRY(cudaGetLastError());
@@ -281,9 +292,75 @@ void gen_white(qtb_ctx *c, long long blk)
 
 void filter_block(qtb_ctx *c)
 {
-    // the tensor-core form is added with its own translation unit; the SIMT
-    // forms filter in FP64 or FP32
-    launch_filter_simt(c->d, c->fk == FK_BF16 ? FK_FP32 : c->fk, c->max_dofp, c->d.nsys, c->Kmax, c->st);
+    if (c->fk == FK_BF16)
+        launch_filter_tc(c->d, &c->tmA, &c->tmB, c->n_tiles, c->d_tiles, c->st);
+    else
+        launch_filter_simt(c->d, c->fk, c->max_dofp, c->d.nsys, c->Kmax, c->st);
+}
+
+// cuTensorMapEncodeTiled from the driver library, resolved at run time so that
+// the shared library loads on machines without a driver.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *h = dlopen("libcuda.so.1", RTLD_NOW | RTLD_GLOBAL);
+        if (h) fn = (EncodeTiledFn)dlsym(h, "cuTensorMapEncodeTiled");
+    }
+    return fn;
+}
+
+// Tensor-core filter set-up: Toeplitz band (BF16) of every system's taps,
+// TMA descriptors of the white-noise ring (A) and of the band (B), tile table.
+int setup_tc(qtb_ctx *c)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(QTB_ERR_CUDA, "cuTensorMapEncodeTiled not available (libcuda.so.1)");
+    const int ns = (int)c->hs.size();
+    const int Ktot = kBlockSteps * c->d.nslots, Ke = kBlockSteps * c->d.Kb;
+    const size_t need = (size_t)ns * 256 * Ktot * 2;
+    if (need > c->Bt_bytes) {
+        c->release(c->d_Bt);
+        c->d_Bt = c->alloc(need);
+        if (!c->d_Bt) return fail(QTB_ERR_OOM, "Toeplitz band allocation failed");
+        c->Bt_bytes = need;
+    }
+    launch_build_toeplitz(c->d, c->d_Bt, Ktot, Ke, c->st);
+    CUDA_TRY(cudaGetLastError());
+    std::vector<int> tiles;
+    for (int s = 0; s < ns; ++s)
+        for (int m = 0; m < c->ds[s].dofp; m += 128) {
+            tiles.push_back(s);
+            tiles.push_back(m);
+        }
+    c->n_tiles = (int)tiles.size() / 2;
+    c->release(c->d_tiles);
+    c->d_tiles = upload(c, tiles);
+    if (!c->d_tiles) return fail(QTB_ERR_OOM, "tile table allocation failed");
+    {
+        const cuuint64_t dims[3] = {(cuuint64_t)kBlockSteps, (cuuint64_t)c->d.Dtot, (cuuint64_t)c->d.nslots};
+        const cuuint64_t strides[2] = {(cuuint64_t)kBlockSteps * 2, (cuuint64_t)c->d.Dtot * kBlockSteps * 2};
+        const cuuint32_t box[3] = {64, 128, 1}, es[3] = {1, 1, 1};
+        CUresult r = enc(&c->tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, c->d.ring, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(QTB_ERR_CUDA, "tensor map (noise ring) encode failed: %d", (int)r);
+    }
+    {
+        const cuuint64_t dims[3] = {(cuuint64_t)Ktot, 256, (cuuint64_t)ns};
+        const cuuint64_t strides[2] = {(cuuint64_t)Ktot * 2, (cuuint64_t)256 * Ktot * 2};
+        const cuuint32_t box[3] = {64, 256, 1}, es[3] = {1, 1, 1};
+        CUresult r = enc(&c->tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, c->d_Bt, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(QTB_ERR_CUDA, "tensor map (Toeplitz band) encode failed: %d", (int)r);
+    }
+    CUDA_TRY(filter_tc_prepare());
+    return QTB_OK;
 }
 
 // make the ring hold white blocks lo .. hi (hi - lo < nslots)
@@ -349,7 +426,7 @@ void one_step(qtb_ctx *c, int j)
 {
     { ProfMark m(c, KC_INTEGRATE); launch_integrate(c->d, c->ml, j, c->st); }
     { ProfMark m(c, KC_CELLS); launch_cells(c->d, c->ml, c->st); }
-    { ProfMark m(c, KC_FORCE); launch_force_kick(c->d, c->ml, c->tab, 1, c->st); }
+    { ProfMark m(c, KC_FORCE); launch_force_kick(c->d, c->ml, c->tabf, c->tab, 1, c->st); }
     { ProfMark m(c, KC_REDUCE); launch_reduce(c->d, c->ml, j, 1, c->st); }
 }
 
@@ -465,6 +542,10 @@ int rebuild_filters(qtb_ctx *c)
     c->d.taps64 = c->d_taps64;
     c->d.tapsR = (c->fk == FK_FP64) ? (const void *)c->d_taps64 : (const void *)c->d_taps32;
     CUDA_TRY(cudaMemcpyAsync((void *)c->d.sys, c->ds.data(), sizeof(DSys) * ns, cudaMemcpyHostToDevice, c->st));
+    if (c->fk == FK_BF16) {
+        int rc = setup_tc(c);
+        if (rc) return rc;
+    }
     c->eta_blk = LLONG_MIN;
     c->graph_dirty = true;
     return QTB_OK;
@@ -535,19 +616,26 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         return code;
     };
 
-    // ---- pair table
+    // ---- pair table (FP64 master, FP32 copy for the mixed kernels)
     PairTab &T = c->tab;
     memset(&T, 0, sizeof T);
     T.ntypes = nt;
     T.potential = p->potential;
-    T.ext_omega = p->ext_omega;
     T.ext_V0 = p->ext_V0;
-    T.ext_a = p->ext_a;
-    for (int a = 0; a < nt; ++a) T.mass[a] = p->mass[a];
+    T.ext_ia2 = 1.0 / (p->ext_a * p->ext_a);
+    for (int a = 0; a < nt; ++a) {
+        T.mass[a] = p->mass[a];
+        T.mass_mvv[a] = p->mass[a] * kMvv2e;
+        T.hdt_m[a] = 0.5 * p->dt / (p->mass[a] * kMvv2e);
+        T.ext_k[a] = p->mass[a] * kMvv2e * p->ext_omega * p->ext_omega;
+    }
     if (c->pair) {
         const double rc_ = p->r_cut, al = p->dsf_alpha;
         T.rc = rc_;
+        T.rc2 = rc_ * rc_;
         T.alpha = al;
+        T.alpha2 = al * al;
+        T.two_a_sqrtpi = 2.0 * al / std::sqrt(kPi);
         T.erfc_rc_over_rc = std::erfc(al * rc_) / rc_;
         T.fshift = std::erfc(al * rc_) / (rc_ * rc_) + 2.0 * al / std::sqrt(kPi) * std::exp(-al * al * rc_ * rc_) / rc_;
         for (int a = 0; a < nt; ++a)
@@ -555,13 +643,32 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
                 const int t = a * kMaxTypes + b, u = a * nt + b;
                 T.A[t] = p->buck_A[u];
                 T.inv_rho[t] = (p->buck_A[u] != 0.0) ? 1.0 / p->buck_rho[u] : 0.0;
+                T.A_over_rho[t] = p->buck_A[u] * T.inv_rho[t];
                 T.C[t] = p->buck_C[u];
+                T.C6[t] = 6.0 * p->buck_C[u];
                 T.qq[t] = kCoulomb * p->charge[a] * p->charge[b];
                 double es = 0.0;
                 if (p->buck_A[u] != 0.0) es += p->buck_A[u] * std::exp(-rc_ / p->buck_rho[u]);
                 es -= p->buck_C[u] / std::pow(rc_, 6);
                 T.eshift[t] = es;
             }
+    }
+    {
+        PairTabT<float> &F = c->tabf;
+        memset(&F, 0, sizeof F);
+        const int NT = kMaxTypes * kMaxTypes;
+        for (int t = 0; t < NT; ++t) {
+            F.A[t] = (float)T.A[t]; F.inv_rho[t] = (float)T.inv_rho[t]; F.A_over_rho[t] = (float)T.A_over_rho[t];
+            F.C[t] = (float)T.C[t]; F.C6[t] = (float)T.C6[t]; F.qq[t] = (float)T.qq[t]; F.eshift[t] = (float)T.eshift[t];
+        }
+        F.alpha = (float)T.alpha; F.alpha2 = (float)T.alpha2; F.two_a_sqrtpi = (float)T.two_a_sqrtpi;
+        F.rc = (float)T.rc; F.rc2 = (float)T.rc2; F.erfc_rc_over_rc = (float)T.erfc_rc_over_rc; F.fshift = (float)T.fshift;
+        for (int a = 0; a < kMaxTypes; ++a) {
+            F.hdt_m[a] = (float)T.hdt_m[a]; F.ext_k[a] = (float)T.ext_k[a];
+            F.mass[a] = T.mass[a]; F.mass_mvv[a] = T.mass_mvv[a];
+        }
+        F.ext_V0 = (float)T.ext_V0; F.ext_ia2 = (float)T.ext_ia2;
+        F.ntypes = T.ntypes; F.potential = T.potential;
     }
 
     // ---- layout
@@ -600,6 +707,13 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         S.gamma = q.gamma;
         S.c1 = std::exp(-q.gamma * p->dt);
         S.wP = std::sqrt((double)h.P) * kBoltz * q.T / kHbar;
+        S.invP = 1.0 / h.P;
+        S.invP_f = (float)S.invP;
+        S.c1_f = (float)S.c1;
+        for (int k = 0; k < 3; ++k) {
+            S.fix_scale[k] = (float)(q.box[k] / (double)(1 << kFixBits));
+            S.fix_inv[k] = (q.box[k] > 0) ? (float)((double)(1 << kFixBits) / q.box[k]) : 0.f;
+        }
         S.rot0 = rot_tot;
         rot_tot += h.P;
         if (!nm_off.count(h.P)) {
@@ -630,6 +744,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
                 for (int k = 0; k < 3; ++k) {
                     R.nc[k] = nc[k];
                     R.box[k] = q.box[k];
+                    R.fix_scale[k] = S.fix_scale[k];
                 }
                 R.cell0 = ncells;
                 ncells += cells;

@@ -6,6 +6,11 @@
 // Eq. 11 with the physical force entering through the B kicks).  Eq. 8: the
 // Langevin O step carries the coloured random force.  Eq. 5: primitive energy
 // estimator, accumulated in FP64.
+//
+// Mixed form: positions in 30-bit fixed point per box edge (exact integer
+// displacements, periodic wrap by masking), FP32 arithmetic, per-atom forces
+// summed in float-float (error-free TwoSum per lane and across the warp), so
+// that the only FP32 errors left are those of the individual pair terms.
 #include <climits>
 #include <type_traits>
 
@@ -25,12 +30,12 @@ template <int PM, class R> struct PosT;
 
 template <class R> struct PosT<PM_BOX64, R> {  // FP64, wrapped into [0, L)
     typedef double S;
-    __device__ static R rel(S a, S b, double L)
+    __device__ static R rel(S a, S b, double L, float, float)
     {
         double d = a - b;
         return (R)(d - L * rint(d / L));
     }
-    __device__ static S add(S a, R delta, double L)
+    __device__ static S add(S a, R delta, double L, float, float)
     {
         double x = a + (double)delta;
         x -= L * floor(x / L);
@@ -40,21 +45,18 @@ template <class R> struct PosT<PM_BOX64, R> {  // FP64, wrapped into [0, L)
 
 template <class R> struct PosT<PM_FIX, R> {  // 30-bit fixed point per box edge
     typedef int S;
-    __device__ static R rel(S a, S b, double L)
+    __device__ static R rel(S a, S b, double, float scale, float) { return (R)fix_minimg(a - b) * (R)scale; }
+    __device__ static S add(S a, R delta, double, float, float inv)
     {
-        return (R)fix_minimg(a - b) * (R)(L * (1.0 / (double)(1 << kFixBits)));
-    }
-    __device__ static S add(S a, R delta, double L)
-    {
-        int dq = __float2int_rn((float)(delta * (R)((double)(1 << kFixBits) / L)));
+        const int dq = __float2int_rn((float)delta * inv);
         return (int)(((unsigned)a + (unsigned)dq) & ((1u << kFixBits) - 1u));
     }
 };
 
 template <class R> struct PosT<PM_FREE, R> {  // unbounded (external potentials)
     typedef R S;
-    __device__ static R rel(S a, S b, double) { return a - b; }
-    __device__ static S add(S a, R delta, double) { return a + delta; }
+    __device__ static R rel(S a, S b, double, float, float) { return a - b; }
+    __device__ static S add(S a, R delta, double, float, float) { return a + delta; }
 };
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -69,6 +71,46 @@ __device__ __forceinline__ float warp_sum(float v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+
+// error-free sum: s + e = a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// float-float accumulator
+struct FF {
+    float hi, lo;
+    __device__ void add(float x)
+    {
+        float s, e;
+        two_sum(hi, x, s, e);
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ void warp_reduce()
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+            float s, e;
+            two_sum(hi, oh, s, e);
+            hi = s;
+            lo = __fadd_rn(__fadd_rn(lo, ol), e);
+        }
+    }
+    __device__ float value() const { return __fadd_rn(hi, lo); }
+};
+
+// plain accumulator with the same interface (FP64 form)
+struct DD {
+    double hi;
+    __device__ void add(double x) { hi += x; }
+    __device__ void warp_reduce() { hi = warp_sum(hi); }
+    __device__ double value() const { return hi; }
+};
 
 // CTA-wide sum of kNQ doubles held by lane 0 of each warp into out[0..kNQ)
 __device__ void cta_store_partials(const double *acc, double (*red)[kNQ], double *out)
@@ -116,12 +158,14 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j)
         const R hdtm = reinterpret_cast<const R *>(d.hdt_m)[t];
         const R sig = reinterpret_cast<const R *>(d.osig)[s * kMaxTypes + t];
         const double L = S.box[c];
+        const float fsc = S.fix_scale[c], finv = S.fix_inv[c];
         const size_t base = c * G + S.g0 + i;
         const PS x0 = X[base];
         R a[P], q[P];
         // relative bead positions -> modes
 #pragma unroll(UN)
-        for (int b = 0; b < P; ++b) a[b] = (b == 0) ? R(0) : PosT<PM, R>::rel(X[base + (size_t)b * N], x0, L);
+        for (int b = 0; b < P; ++b)
+            a[b] = (b == 0) ? R(0) : PosT<PM, R>::rel(X[base + (size_t)b * N], x0, L, fsc, finv);
 #pragma unroll(UN)
         for (int k = 0; k < P; ++k) {
             R u = 0;
@@ -142,7 +186,7 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j)
         }
         const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
         const R *eta = reinterpret_cast<const R *>(d.eta) + (size_t)j * d.Dtot + S.dof0;
-        const R c1 = (R)S.c1;
+        const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
 #pragma unroll(UN)
         for (int k = 0; k < P; ++k) {
             const R cs = rot[3 * k], sw = rot[3 * k + 1], ws = rot[3 * k + 2];
@@ -166,7 +210,7 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j)
             V[base + (size_t)b * N] = w;
         }
 #pragma unroll(UN)
-        for (int b = 0; b < P; ++b) X[base + (size_t)b * N] = PosT<PM, R>::add(x0, a[b], L);
+        for (int b = 0; b < P; ++b) X[base + (size_t)b * N] = PosT<PM, R>::add(x0, a[b], L, fsc, finv);
         if (P > 1) {
             R sp = 0;
 #pragma unroll(UN)
@@ -222,6 +266,7 @@ __global__ void k_cellsort(Dev d)
     if (cell >= d.ncells) return;
     constexpr int E = 16;  // cap <= 512
     const int n = min(d.cnt[cell], d.cap);
+    const int ne = (n + 31) >> 5;
     int key[E], rank[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -229,13 +274,18 @@ __global__ void k_cellsort(Dev d)
         key[e] = (idx < n) ? d.cidx[(size_t)cell * d.cap + idx] : INT_MAX;
         rank[e] = 0;
     }
-    const int ne = (n + 31) >> 5;
-    for (int e2 = 0; e2 < ne; ++e2)
-        for (int l = 0; l < 32; ++l) {
-            int other = __shfl_sync(0xffffffffu, key[e2], l);
+    for (int e2 = 0; e2 < ne; ++e2) {
+        int kv = 0;
 #pragma unroll
-            for (int e = 0; e < E; ++e) rank[e] += (other < key[e]) ? 1 : 0;
+        for (int e = 0; e < E; ++e)
+            if (e == e2) kv = key[e];
+        for (int l = 0; l < 32; ++l) {
+            const int other = __shfl_sync(0xffffffffu, kv, l);
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (e < ne) rank[e] += (other < key[e]) ? 1 : 0;
         }
+    }
     __syncwarp();
     const size_t G = (size_t)d.G;
 #pragma unroll
@@ -268,56 +318,50 @@ __device__ __forceinline__ float my_exp(float x) { return expf(x); }
 __device__ __forceinline__ double my_exp(double x) { return exp(x); }
 __device__ __forceinline__ float my_erfc(float x) { return erfcf(x); }
 __device__ __forceinline__ double my_erfc(double x) { return erfc(x); }
-__device__ __forceinline__ float my_rsqrt(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double my_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float my_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double my_sqrt(double x) { return sqrt(x); }
 
+// -dV/dr / r and V of one pair at squared distance r2 < rc^2
 template <class R>
-__device__ __forceinline__ void pair_eval(const PairTab &T, int tij, R r2, R &f_over_r, R &e)
+__device__ __forceinline__ void pair_eval(const PairTabT<R> &T, int tij, R r2, R &f_over_r, R &e)
 {
-    const R rinv = my_rsqrt(r2);
-    const R r = r2 * rinv;
+    const R r = my_sqrt(r2);
+    const R rinv = R(1) / r;
     R f = 0, en = 0;
-    const R A = (R)T.A[tij], Cc = (R)T.C[tij];
+    const R A = T.A[tij], Cc = T.C[tij];
     if (A != R(0)) {
-        const R ir = (R)T.inv_rho[tij];
-        const R ex = A * my_exp(-r * ir);
-        f += ex * ir;
-        en += ex;
+        const R ex = my_exp(-r * T.inv_rho[tij]);
+        f += T.A_over_rho[tij] * ex;
+        en += A * ex;
     }
     if (Cc != R(0)) {
         const R r2i = rinv * rinv;
         const R r6i = r2i * r2i * r2i;
-        f -= R(6) * Cc * r6i * rinv;
+        f -= T.C6[tij] * r6i * rinv;
         en -= Cc * r6i;
     }
-    en -= (R)T.eshift[tij];
-    const R qq = (R)T.qq[tij];
+    en -= T.eshift[tij];
+    const R qq = T.qq[tij];
     if (qq != R(0)) {
-        const R al = (R)T.alpha;
-        const R er = my_erfc(al * r);
-        const R gg = my_exp(-al * al * r2);
-        const R two_a_sqrtpi = (R)(2.0 * T.alpha / 1.7724538509055160273);
-        f += qq * (er * rinv * rinv + two_a_sqrtpi * gg * rinv - (R)T.fshift);
-        en += qq * (er * rinv - (R)T.erfc_rc_over_rc + (R)T.fshift * (r - (R)T.rc));
+        const R er = my_erfc(T.alpha * r);
+        const R gg = my_exp(-T.alpha2 * r2);
+        f += qq * (er * rinv * rinv + T.two_a_sqrtpi * gg * rinv - T.fshift);
+        en += qq * (er * rinv - T.erfc_rc_over_rc + T.fshift * (r - T.rc));
     }
     f_over_r = f * rinv;
     e = en;
 }
 
-template <class R> struct Pack;
-template <> struct Pack<float> { typedef int4 T; };
-template <> struct Pack<double> { typedef D4 T; };
-
 template <int PM, class R>
-__global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_force_pair(Dev d, PairTab T, int kick)
+__global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_force_pair(Dev d, PairTabT<R> T, int kick)
 {
     typedef typename std::conditional<sizeof(R) == 4, float4, D4>::type R4;
+    typedef typename std::conditional<sizeof(R) == 4, FF, DD>::type ACC;
     __shared__ R4 qbuf[kWarpsPerForceCta][64];
     __shared__ double red[kWarpsPerForceCta][kNQ];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cell = blockIdx.x / d.cpc, chunk = blockIdx.x - cell * d.cpc;
     const DRep RP = d.rep[d.cell_rep[cell]];
-    const DSys S = d.sys[RP.sys];
     const int cnt = d.ccount[cell];
     const int slot = chunk * kWarpsPerForceCta + warp;
     double acc[kNQ];
@@ -326,23 +370,22 @@ __global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_force_pair(Dev d, Pa
     if (slot < cnt) {
         const size_t hoff = (size_t)cell * d.cap + slot;
         const int gi = d.cidx[hoff];
-        R hx, hy, hz;
+        R hx = 0, hy = 0, hz = 0;
         int ti;
         int ihx = 0, ihy = 0, ihz = 0;
         if (PM == PM_FIX) {
             int4 hp = reinterpret_cast<const int4 *>(d.cpos)[hoff];
             ihx = hp.x; ihy = hp.y; ihz = hp.z; ti = hp.w;
-            hx = hy = hz = 0;
         } else {
             D4 hp = reinterpret_cast<const D4 *>(d.cpos)[hoff];
             hx = (R)hp.x; hy = (R)hp.y; hz = (R)hp.z; ti = (int)hp.w;
         }
         const int lc = cell - RP.cell0;
         const int cx = lc % RP.nc[0], cy = (lc / RP.nc[0]) % RP.nc[1], cz = lc / (RP.nc[0] * RP.nc[1]);
-        const R sx = (R)(RP.box[0] / (double)(1 << kFixBits)), sy = (R)(RP.box[1] / (double)(1 << kFixBits)),
-                sz = (R)(RP.box[2] / (double)(1 << kFixBits));
-        const R rc2 = (R)(T.rc * T.rc);
-        R fx = 0, fy = 0, fz = 0, en = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+        const R sx = (R)RP.fix_scale[0], sy = (R)RP.fix_scale[1], sz = (R)RP.fix_scale[2];
+        const R rc2 = T.rc2;
+        ACC fx{}, fy{}, fz{};
+        R en = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
         int qn = 0;
         R4 *qb = qbuf[warp];
         const unsigned lt = (1u << lane) - 1u;
@@ -354,8 +397,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_force_pair(Dev d, Pa
                 R r2 = e4.x * e4.x + e4.y * e4.y + e4.z * e4.z;
                 R fo, ee;
                 pair_eval<R>(T, ti * kMaxTypes + tj, r2, fo, ee);
-                // d = r_i - r_j = -(stored displacement)
-                fx -= fo * e4.x; fy -= fo * e4.y; fz -= fo * e4.z;
+                // stored displacement is r_j - r_i: the force on i is -fo (r_j - r_i)
+                fx.add(-fo * e4.x); fy.add(-fo * e4.y); fz.add(-fo * e4.z);
                 en += ee;
                 w0 += fo * e4.x * e4.x; w1 += fo * e4.y * e4.y; w2 += fo * e4.z * e4.z;
                 w3 += fo * e4.x * e4.y; w4 += fo * e4.x * e4.z; w5 += fo * e4.y * e4.z;
@@ -365,8 +408,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_force_pair(Dev d, Pa
             for (int oy = -1; oy <= 1; ++oy)
                 for (int ox = -1; ox <= 1; ++ox) {
                     int ux = cx + ox, uy = cy + oy, uz = cz + oz;
-                    int mx = (int)floor_div(ux, RP.nc[0]), my = (int)floor_div(uy, RP.nc[1]),
-                        mz = (int)floor_div(uz, RP.nc[2]);
+                    const int mx = (int)floor_div(ux, RP.nc[0]), my = (int)floor_div(uy, RP.nc[1]),
+                              mz = (int)floor_div(uz, RP.nc[2]);
                     ux -= mx * RP.nc[0]; uy -= my * RP.nc[1]; uz -= mz * RP.nc[2];
                     const int nc = RP.cell0 + ux + RP.nc[0] * (uy + RP.nc[1] * uz);
                     const int ncnt = d.ccount[nc];
@@ -381,9 +424,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_force_pair(Dev d, Pa
                             if (PM == PM_FIX) {
                                 int4 pj = reinterpret_cast<const int4 *>(d.cpos)[nb + e];
                                 // displacement r_j + image - r_i, exact in int32
-                                int ix = (int)((unsigned)pj.x - (unsigned)ihx + (unsigned)mx * (1u << kFixBits));
-                                int iy = (int)((unsigned)pj.y - (unsigned)ihy + (unsigned)my * (1u << kFixBits));
-                                int iz = (int)((unsigned)pj.z - (unsigned)ihz + (unsigned)mz * (1u << kFixBits));
+                                const int ix = (int)((unsigned)pj.x - (unsigned)ihx + (unsigned)mx * (1u << kFixBits));
+                                const int iy = (int)((unsigned)pj.y - (unsigned)ihy + (unsigned)my * (1u << kFixBits));
+                                const int iz = (int)((unsigned)pj.z - (unsigned)ihz + (unsigned)mz * (1u << kFixBits));
                                 dx = (R)ix * sx; dy = (R)iy * sy; dz = (R)iz * sz;
                                 tj = pj.w;
                             } else {
@@ -417,17 +460,18 @@ __global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_force_pair(Dev d, Pa
                     }
                 }
         consume(qn);
-        fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz); en = warp_sum(en);
+        fx.warp_reduce(); fy.warp_reduce(); fz.warp_reduce();
+        en = warp_sum(en);
         w0 = warp_sum(w0); w1 = warp_sum(w1); w2 = warp_sum(w2);
         w3 = warp_sum(w3); w4 = warp_sum(w4); w5 = warp_sum(w5);
         if (lane == 0) {
+            const DSys &S = d.sys[RP.sys];
             const size_t G = (size_t)d.G;
             R *Fo = reinterpret_cast<R *>(d.f);
             R *V = reinterpret_cast<R *>(d.v);
-            const R invP = (R)(1.0 / S.P);
-            const R f3[3] = {fx * invP, fy * invP, fz * invP};
-            const double m = T.mass[ti] * kMvv2e;
-            const R hdtm = (R)(0.5 * d.dt / m);
+            const R invP = sizeof(R) == 4 ? (R)S.invP_f : (R)S.invP;
+            const R f3[3] = {(R)fx.value() * invP, (R)fy.value() * invP, (R)fz.value() * invP};
+            const R hdtm = T.hdt_m[ti];
             double ke = 0.0;
             for (int c = 0; c < 3; ++c) {
                 Fo[c * G + gi] = f3[c];
@@ -436,7 +480,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_force_pair(Dev d, Pa
                     v += hdtm * f3[c];
                     V[c * G + gi] = v;
                 }
-                ke += 0.5 * m * (double)v * (double)v;
+                ke += 0.5 * T.mass_mvv[ti] * (double)v * (double)v;
                 acc[Q_MOM + c] = T.mass[ti] * (double)v;
             }
             acc[Q_K] = ke;
@@ -450,7 +494,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_force_pair(Dev d, Pa
 
 // External separable potentials, one thread per bead-atom.  grid = (gx, nsys)
 template <class R>
-__global__ void __launch_bounds__(128) k_force_ext(Dev d, PairTab T, int kick)
+__global__ void __launch_bounds__(128) k_force_ext(Dev d, PairTabT<R> T, int kick)
 {
     __shared__ double red[4][kNQ];
     const DSys S = d.sys[blockIdx.y];
@@ -461,9 +505,8 @@ __global__ void __launch_bounds__(128) k_force_ext(Dev d, PairTab T, int kick)
     if (l < S.N * S.P) {
         const size_t G = (size_t)d.G, g = S.g0 + l;
         const int t = d.typ[g];
-        const double m = T.mass[t] * kMvv2e;
-        const R hdtm = (R)(0.5 * d.dt / m);
-        const R invP = (R)(1.0 / S.P);
+        const R hdtm = T.hdt_m[t];
+        const R invP = sizeof(R) == 4 ? (R)S.invP_f : (R)S.invP;
         const R *X = reinterpret_cast<const R *>(d.x);
         R *Fo = reinterpret_cast<R *>(d.f);
         R *V = reinterpret_cast<R *>(d.v);
@@ -472,14 +515,13 @@ __global__ void __launch_bounds__(128) k_force_ext(Dev d, PairTab T, int kick)
             const R x = X[c * G + g];
             R fx, ex;
             if (T.potential == QTB_POT_HARMONIC) {
-                const R k = (R)(m * T.ext_omega * T.ext_omega);
+                const R k = T.ext_k[t];
                 fx = -k * x;
                 ex = R(0.5) * k * x * x;
             } else {
-                const R ia2 = (R)(1.0 / (T.ext_a * T.ext_a)), V0 = (R)T.ext_V0;
-                const R u = x * x * ia2 - R(1);
-                fx = R(-4) * V0 * u * x * ia2;
-                ex = V0 * u * u;
+                const R u = x * x * T.ext_ia2 - R(1);
+                fx = R(-4) * T.ext_V0 * u * x * T.ext_ia2;
+                ex = T.ext_V0 * u * u;
             }
             const R fb = fx * invP;
             Fo[c * G + g] = fb;
@@ -489,7 +531,7 @@ __global__ void __launch_bounds__(128) k_force_ext(Dev d, PairTab T, int kick)
                 V[c * G + g] = v;
             }
             e += (double)ex;
-            ke += 0.5 * m * (double)v * (double)v;
+            ke += 0.5 * T.mass_mvv[t] * (double)v * (double)v;
             x2 += (double)x * (double)x;
             acc[Q_MOM + c] = T.mass[t] * (double)v;
             acc[Q_VIR + c] = (double)x * (double)fx;
@@ -505,7 +547,7 @@ __global__ void __launch_bounds__(128) k_force_ext(Dev d, PairTab T, int kick)
 // ---------------------------------------------------------------------------
 // Per-system reduction into the observable record (fixed summation order).
 
-__global__ void k_reduce(Dev d, int j, int force_record)
+__global__ void k_reduce(Dev d, int j, int record)
 {
     __shared__ double sh[128][kNQ + 1];
     const int s = blockIdx.x;
@@ -524,7 +566,7 @@ __global__ void k_reduce(Dev d, int j, int force_record)
     }
     if (threadIdx.x == 0) {
         const long long step = d.clock[0] * kBlockSteps + j + 1;  // steps completed
-        const double invP = 1.0 / S.P;
+        const double invP = S.invP;
         double rec[QTB_NREC];
         for (int q = 0; q < QTB_NREC; ++q) rec[q] = 0.0;
         const double K = sh[0][Q_K], V = sh[0][Q_V] * invP, sp = sh[0][kNQ];
@@ -539,7 +581,7 @@ __global__ void k_reduce(Dev d, int j, int force_record)
         rec[17] = sh[0][Q_X2] * invP;
         if (!isfinite(K) || !isfinite(V)) atomicOr(d.err, (unsigned)ERR_NONFINITE);
         for (int q = 0; q < QTB_NREC; ++q) d.latest[(size_t)s * QTB_NREC + q] = rec[q];
-        if (force_record >= 0 && step % d.obs_stride == 0) {
+        if (record >= 0 && step % d.obs_stride == 0) {
             long long r = step / d.obs_stride - 1;
             int slot = (int)(r % d.max_records);
             for (int q = 0; q < QTB_NREC; ++q) d.series[((size_t)slot * d.nsys + s) * QTB_NREC + q] = rec[q];
@@ -592,16 +634,17 @@ void launch_cells(const Dev &d, const MdLaunch &m, cudaStream_t st)
     }
 }
 
-void launch_force_kick(const Dev &d, const MdLaunch &m, const PairTab &T, int kick, cudaStream_t st)
+void launch_force_kick(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,
+                       int kick, cudaStream_t st)
 {
     if (m.pair) {
         const unsigned grid = (unsigned)(d.ncells * d.cpc);
-        if (m.mixed) k_force_pair<PM_FIX, float><<<grid, 32 * kWarpsPerForceCta, 0, st>>>(d, T, kick);
-        else k_force_pair<PM_BOX64, double><<<grid, 32 * kWarpsPerForceCta, 0, st>>>(d, T, kick);
+        if (m.mixed) k_force_pair<PM_FIX, float><<<grid, 32 * kWarpsPerForceCta, 0, st>>>(d, Tf, kick);
+        else k_force_pair<PM_BOX64, double><<<grid, 32 * kWarpsPerForceCta, 0, st>>>(d, Td, kick);
     } else {
         dim3 g((unsigned)m.n_ecta, (unsigned)d.nsys);
-        if (m.mixed) k_force_ext<float><<<g, 128, 0, st>>>(d, T, kick);
-        else k_force_ext<double><<<g, 128, 0, st>>>(d, T, kick);
+        if (m.mixed) k_force_ext<float><<<g, 128, 0, st>>>(d, Tf, kick);
+        else k_force_ext<double><<<g, 128, 0, st>>>(d, Td, kick);
     }
 }
 

@@ -33,7 +33,7 @@ enum { Q_K = 0, Q_V = 1, Q_SPRING = 2, Q_VIR = 3 /* 6 slots: xx yy zz xy xz yz *
 enum { PM_BOX64 = 0, PM_FIX = 1, PM_FREE = 2 };
 
 // device error word bits
-enum { ERR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_SOLVE = 4 };
+enum { ERR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_SOLVE = 4, ERR_TIMEOUT_TC = 8 };
 
 struct DSys {
     int N, P;          // atoms, beads
@@ -49,6 +49,10 @@ struct DSys {
     int nm0;           // offset of this system's normal-mode matrix
     double box[3];
     double T, gamma, c1, wP;
+    float fix_scale[3];      // box / 2^30 (A per fixed-point unit)
+    float fix_inv[3];        // 2^30 / box
+    float invP_f, c1_f;      // 1/P, c1 in FP32
+    double invP;
 };
 
 struct DRep {          // one replica (system, bead) of a pair-potential system
@@ -57,17 +61,25 @@ struct DRep {          // one replica (system, bead) of a pair-potential system
     int cell0;         // first cell
     int cta0;          // first binning CTA
     double box[3];
+    float fix_scale[3];  // box / 2^30
 };
 
-struct PairTab {       // per type pair (a * kMaxTypes + b)
-    double A[kMaxTypes * kMaxTypes], inv_rho[kMaxTypes * kMaxTypes], C[kMaxTypes * kMaxTypes];
-    double qq[kMaxTypes * kMaxTypes];      // k_e q_a q_b
-    double eshift[kMaxTypes * kMaxTypes];  // Buckingham energy at r_cut
-    double alpha, rc, erfc_rc_over_rc, fshift;  // DSF constants
-    double mass[kMaxTypes];
-    double ext_omega, ext_V0, ext_a;
+// Interaction table in the arithmetic type R of the force kernel (no FP64
+// arithmetic leaks into the FP32 kernels).  Index of a type pair: a * kMaxTypes + b.
+template <class R> struct PairTabT {
+    R A[kMaxTypes * kMaxTypes], inv_rho[kMaxTypes * kMaxTypes], A_over_rho[kMaxTypes * kMaxTypes];
+    R C[kMaxTypes * kMaxTypes], C6[kMaxTypes * kMaxTypes];
+    R qq[kMaxTypes * kMaxTypes];      // k_e q_a q_b
+    R eshift[kMaxTypes * kMaxTypes];  // Buckingham energy at r_cut
+    R alpha, alpha2, two_a_sqrtpi, rc, rc2, erfc_rc_over_rc, fshift;  // DSF constants
+    R hdt_m[kMaxTypes];               // dt / (2 m mvv2e)
+    R ext_k[kMaxTypes];               // HARMONIC: m mvv2e w0^2
+    R ext_V0, ext_ia2;                // DOUBLEWELL: V0, 1/a^2
+    double mass[kMaxTypes];           // u (momentum)
+    double mass_mvv[kMaxTypes];       // m mvv2e (kinetic energy, FP64 accumulation)
     int ntypes, potential;
 };
+typedef PairTabT<double> PairTab;
 
 // Everything a kernel needs, passed by value.
 struct Dev {

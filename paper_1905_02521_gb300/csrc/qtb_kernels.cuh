@@ -37,7 +37,8 @@ struct MdLaunch {
 };
 void launch_integrate(const Dev &d, const MdLaunch &m, int j, cudaStream_t st);
 void launch_cells(const Dev &d, const MdLaunch &m, cudaStream_t st);
-void launch_force_kick(const Dev &d, const MdLaunch &m, const PairTab &T, int kick, cudaStream_t st);
+void launch_force_kick(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,
+                       int kick, cudaStream_t st);
 void launch_reduce(const Dev &d, const MdLaunch &m, int j, int record, cudaStream_t st);
 void launch_tick(const Dev &d, cudaStream_t st);
 void launch_setclock(const Dev &d, long long blk, cudaStream_t st);
@@ -45,6 +46,7 @@ bool md_supported_P(int P);
 
 // filter_tc.cu
 cudaError_t filter_tc_prepare();
+void launch_build_toeplitz(const Dev &d, void *Bt, int Ktot, int Ke, cudaStream_t st);
 void launch_filter_tc(const Dev &d, const void *tmapA, const void *tmapB, int n_mtiles, const int *mtile_sys,
                       cudaStream_t st);
 

@@ -29,6 +29,13 @@ def minimg(d, box):
     return d - box * np.round(d / box)
 
 
+def rel_l2(a, b):
+    """||a - b||_2 / ||b||_2  (relative error of a vector)."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum())
+
+
 def rel_inf(a, b):
     """max |a - b| / RMS(b)  (norm-wise relative error)."""
     a = np.asarray(a, np.float64)
