@@ -50,6 +50,12 @@ struct HSys {
 
 }  // namespace
 
+int qtb::set_last_error(int code, const char *msg)
+{
+    g_err = msg;
+    return code;
+}
+
 struct qtb_ctx {
     cudaStream_t st = nullptr;
     qtb_params p{};
@@ -422,12 +428,17 @@ ProfMark::~ProfMark()
     c->ev_used += 2;
 }
 
+// Per-step kernels.  Profiling samples every 16th step of a captured block
+// (event nodes cost about a microsecond each, so they are not put on every launch).
 void one_step(qtb_ctx *c, int j)
 {
+    const bool keep = c->capturing;
+    if (j % 16 != 0) c->capturing = false;
     { ProfMark m(c, KC_INTEGRATE); launch_integrate(c->d, c->ml, j, c->st); }
     { ProfMark m(c, KC_CELLS); launch_cells(c->d, c->ml, c->st); }
     { ProfMark m(c, KC_FORCE); launch_force_kick(c->d, c->ml, c->tabf, c->tab, 1, c->st); }
     { ProfMark m(c, KC_REDUCE); launch_reduce(c->d, c->ml, j, 1, c->st); }
+    c->capturing = keep;
 }
 
 int build_graph(qtb_ctx *c)
@@ -758,7 +769,12 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     for (int s = 0; s < n_sys; ++s)
         for (int t = c->ds[s].icta0; t < c->ds[s].icta1; ++t) c->icta_sys.push_back(s);
     // force CTA ranges
-    const int cpc = cap / kWarpsPerForceCta;
+    // staged force kernel when the 27-cell neighbourhood fits in shared memory
+    const bool staged = c->pair && force_staged_smem(cap, c->mixed ? 1 : 0) <= 190 * 1024;
+    const int cpc = staged ? (cap + kForceChunkHost - 1) / kForceChunkHost : cap / kWarpsPerForceCta;
+    c->ml.staged = staged ? 1 : 0;
+    if (staged && force_staged_prepare(cap, c->mixed ? 1 : 0) != cudaSuccess)
+        return bail(fail(QTB_ERR_CUDA, "cannot reserve shared memory for the force kernel"));
     int ext_gx = 0;
     for (int s = 0; s < n_sys; ++s) ext_gx = std::max(ext_gx, (c->hs[s].N * c->hs[s].P + 127) / 128);
     long long nforce = 0;

@@ -492,6 +492,187 @@ __global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_force_pair(Dev d, Pa
     cta_store_partials(acc, red, d.part + (size_t)blockIdx.x * kNQ);
 }
 
+// Pair force with the 27-cell neighbourhood staged in shared memory.
+// One CTA = (home cell, chunk of kForceChunk home slots); its 8 warps take the
+// chunk's home atoms in turn.  Staging copies every stencil cell (sorted slots)
+// once, with its periodic image shift already added (fixed point: + m 2^30,
+// which stays inside int32 because positions are < 2^30), so the candidate scan
+// is one flat loop over shared memory.  Dynamic shared memory: 27 cap entries.
+constexpr int kForceChunk = 32;
+
+template <int PM, class R>
+__global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_force_cells(Dev d, PairTabT<R> T, int kick)
+{
+    typedef typename std::conditional<sizeof(R) == 4, float4, D4>::type R4;
+    typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
+    typedef typename std::conditional<sizeof(R) == 4, FF, DD>::type ACC;
+    extern __shared__ __align__(32) unsigned char fsm[];
+    __shared__ R4 qbuf[kWarpsPerForceCta][64];
+    __shared__ double red[kWarpsPerForceCta][kNQ];
+    __shared__ int soff[28], scell[27], simg[27][3];
+    E4 *stage = reinterpret_cast<E4 *>(fsm);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cpc = d.cpc;
+    const int cell = blockIdx.x / cpc, chunk = blockIdx.x - cell * cpc;
+    const int cnt = d.ccount[cell];
+    const int first = chunk * kForceChunk;
+    double acc[kNQ];
+#pragma unroll
+    for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+    if (first >= cnt) {  // empty chunk: write zero partials
+        if (threadIdx.x < kNQ) d.part[(size_t)blockIdx.x * kNQ + threadIdx.x] = 0.0;
+        return;
+    }
+    const DRep RP = d.rep[d.cell_rep[cell]];
+    const int lc = cell - RP.cell0;
+    const int cx = lc % RP.nc[0], cy = (lc / RP.nc[0]) % RP.nc[1], cz = lc / (RP.nc[0] * RP.nc[1]);
+    if (threadIdx.x < 27) {
+        const int t = threadIdx.x;
+        const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = t / 9 - 1;
+        int ux = cx + ox, uy = cy + oy, uz = cz + oz;
+        const int mx = (int)floor_div(ux, RP.nc[0]), my = (int)floor_div(uy, RP.nc[1]), mz = (int)floor_div(uz, RP.nc[2]);
+        ux -= mx * RP.nc[0]; uy -= my * RP.nc[1]; uz -= mz * RP.nc[2];
+        scell[t] = RP.cell0 + ux + RP.nc[0] * (uy + RP.nc[1] * uz);
+        simg[t][0] = mx; simg[t][1] = my; simg[t][2] = mz;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int o = 0;
+        for (int t = 0; t < 27; ++t) {
+            soff[t] = o;
+            o += d.ccount[scell[t]];
+        }
+        soff[27] = o;
+    }
+    __syncthreads();
+    const int total = soff[27];
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        int t = 0;
+        while (soff[t + 1] <= e) ++t;
+        const size_t src = (size_t)scell[t] * d.cap + (e - soff[t]);
+        if (PM == PM_FIX) {
+            int4 p = reinterpret_cast<const int4 *>(d.cpos)[src];
+            p.x = (int)((unsigned)p.x + (unsigned)simg[t][0] * (1u << kFixBits));
+            p.y = (int)((unsigned)p.y + (unsigned)simg[t][1] * (1u << kFixBits));
+            p.z = (int)((unsigned)p.z + (unsigned)simg[t][2] * (1u << kFixBits));
+            reinterpret_cast<int4 *>(stage)[e] = p;
+        } else {
+            D4 p = reinterpret_cast<const D4 *>(d.cpos)[src];
+            p.x += simg[t][0] * RP.box[0];
+            p.y += simg[t][1] * RP.box[1];
+            p.z += simg[t][2] * RP.box[2];
+            reinterpret_cast<D4 *>(stage)[e] = p;
+        }
+    }
+    __syncthreads();
+    const int self0 = soff[13];  // stencil (0,0,0) is entry 13
+    const R sx = (R)RP.fix_scale[0], sy = (R)RP.fix_scale[1], sz = (R)RP.fix_scale[2];
+    const R rc2 = T.rc2;
+    const DSys &S = d.sys[RP.sys];
+    const R invP = sizeof(R) == 4 ? (R)S.invP_f : (R)S.invP;
+    const unsigned lt = (1u << lane) - 1u;
+    R4 *qb = qbuf[warp];
+    const int last = min(cnt, first + kForceChunk);
+    for (int slot = first + warp; slot < last; slot += kWarpsPerForceCta) {
+        const E4 hp = stage[self0 + slot];
+        int ti;
+        if (PM == PM_FIX) ti = hp.w; else ti = (int)hp.w;
+        ACC fx{}, fy{}, fz{};
+        R en = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+        int qn = 0;
+        auto consume = [&](int m) {
+            if (lane < m) {
+                R4 e4 = qb[lane];
+                int tj;
+                if (sizeof(R) == 4) tj = __float_as_int((float)e4.w); else tj = (int)e4.w;
+                R r2 = e4.x * e4.x + e4.y * e4.y + e4.z * e4.z;
+                R fo, ee;
+                pair_eval<R>(T, ti * kMaxTypes + tj, r2, fo, ee);
+                fx.add(-fo * e4.x); fy.add(-fo * e4.y); fz.add(-fo * e4.z);
+                en += ee;
+                w0 += fo * e4.x * e4.x; w1 += fo * e4.y * e4.y; w2 += fo * e4.z * e4.z;
+                w3 += fo * e4.x * e4.y; w4 += fo * e4.x * e4.z; w5 += fo * e4.y * e4.z;
+            }
+        };
+        for (int e0 = 0; e0 < total; e0 += 32) {
+            const int e = e0 + lane;
+            R dx = 0, dy = 0, dz = 0;
+            int tj = 0;
+            bool take = false;
+            if (e < total && e != self0 + slot) {
+                const E4 pj = stage[e];
+                if (PM == PM_FIX) {
+                    dx = (R)(int)((unsigned)pj.x - (unsigned)hp.x) * sx;
+                    dy = (R)(int)((unsigned)pj.y - (unsigned)hp.y) * sy;
+                    dz = (R)(int)((unsigned)pj.z - (unsigned)hp.z) * sz;
+                    tj = pj.w;
+                } else {
+                    dx = (R)(pj.x - hp.x);
+                    dy = (R)(pj.y - hp.y);
+                    dz = (R)(pj.z - hp.z);
+                    tj = (int)pj.w;
+                }
+                take = (dx * dx + dy * dy + dz * dz) < rc2;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, take);
+            if (take) {
+                R4 v;
+                v.x = dx; v.y = dy; v.z = dz;
+                if (sizeof(R) == 4) v.w = (R)__int_as_float(tj); else v.w = (R)tj;
+                qb[qn + __popc(m & lt)] = v;
+            }
+            qn += __popc(m);
+            __syncwarp();
+            if (qn >= 32) {
+                consume(32);
+                __syncwarp();
+                R4 carry;
+                if (lane < qn - 32) carry = qb[32 + lane];
+                __syncwarp();
+                if (lane < qn - 32) qb[lane] = carry;
+                qn -= 32;
+                __syncwarp();
+            }
+        }
+        consume(qn);
+        __syncwarp();
+        fx.warp_reduce(); fy.warp_reduce(); fz.warp_reduce();
+        en = warp_sum(en);
+        w0 = warp_sum(w0); w1 = warp_sum(w1); w2 = warp_sum(w2);
+        w3 = warp_sum(w3); w4 = warp_sum(w4); w5 = warp_sum(w5);
+        if (lane == 0) {
+            const int gi = d.cidx[(size_t)cell * d.cap + slot];
+            const size_t G = (size_t)d.G;
+            R *Fo = reinterpret_cast<R *>(d.f);
+            R *V = reinterpret_cast<R *>(d.v);
+            const R f3[3] = {(R)fx.value() * invP, (R)fy.value() * invP, (R)fz.value() * invP};
+            const R hdtm = T.hdt_m[ti];
+            double ke = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                Fo[c * G + gi] = f3[c];
+                R v = V[c * G + gi];
+                if (kick) {
+                    v += hdtm * f3[c];
+                    V[c * G + gi] = v;
+                }
+                ke += 0.5 * T.mass_mvv[ti] * (double)v * (double)v;
+                acc[Q_MOM + c] += T.mass[ti] * (double)v;
+            }
+            acc[Q_K] += ke;
+            acc[Q_V] += 0.5 * (double)en;
+            acc[Q_VIR + 0] += 0.5 * (double)w0; acc[Q_VIR + 1] += 0.5 * (double)w1; acc[Q_VIR + 2] += 0.5 * (double)w2;
+            acc[Q_VIR + 3] += 0.5 * (double)w3; acc[Q_VIR + 4] += 0.5 * (double)w4; acc[Q_VIR + 5] += 0.5 * (double)w5;
+        }
+    }
+    cta_store_partials(acc, red, d.part + (size_t)blockIdx.x * kNQ);
+}
+
+template <int PM, class R> size_t force_cells_smem(int cap)
+{
+    typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
+    return (size_t)27 * cap * sizeof(E4);
+}
+
 // External separable potentials, one thread per bead-atom.  grid = (gx, nsys)
 template <class R>
 __global__ void __launch_bounds__(128) k_force_ext(Dev d, PairTabT<R> T, int kick)
@@ -550,6 +731,9 @@ __global__ void __launch_bounds__(128) k_force_ext(Dev d, PairTabT<R> T, int kic
 __global__ void k_reduce(Dev d, int j, int record)
 {
     __shared__ double sh[128][kNQ + 1];
+    const long long step = d.clock[0] * kBlockSteps + j + 1;  // steps completed
+    // during stepping only the recorded steps are reduced (record < 0: always)
+    if (record >= 0 && step % d.obs_stride != 0) return;
     const int s = blockIdx.x;
     const DSys S = d.sys[s];
     double acc[kNQ + 1];
@@ -565,7 +749,6 @@ __global__ void k_reduce(Dev d, int j, int record)
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const long long step = d.clock[0] * kBlockSteps + j + 1;  // steps completed
         const double invP = S.invP;
         double rec[QTB_NREC];
         for (int q = 0; q < QTB_NREC; ++q) rec[q] = 0.0;
@@ -634,10 +817,27 @@ void launch_cells(const Dev &d, const MdLaunch &m, cudaStream_t st)
     }
 }
 
+size_t force_staged_smem(int cap, int mixed)
+{
+    return mixed ? force_cells_smem<PM_FIX, float>(cap) : force_cells_smem<PM_BOX64, double>(cap);
+}
+
+cudaError_t force_staged_prepare(int cap, int mixed)
+{
+    const int sm = (int)force_staged_smem(cap, mixed);
+    if (mixed) return cudaFuncSetAttribute(k_force_cells<PM_FIX, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return cudaFuncSetAttribute(k_force_cells<PM_BOX64, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
 void launch_force_kick(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,
                        int kick, cudaStream_t st)
 {
-    if (m.pair) {
+    if (m.pair && m.staged) {
+        const unsigned grid = (unsigned)(d.ncells * d.cpc);
+        const size_t sm = force_staged_smem(d.cap, m.mixed);
+        if (m.mixed) k_force_cells<PM_FIX, float><<<grid, 32 * kWarpsPerForceCta, sm, st>>>(d, Tf, kick);
+        else k_force_cells<PM_BOX64, double><<<grid, 32 * kWarpsPerForceCta, sm, st>>>(d, Td, kick);
+    } else if (m.pair) {
         const unsigned grid = (unsigned)(d.ncells * d.cpc);
         if (m.mixed) k_force_pair<PM_FIX, float><<<grid, 32 * kWarpsPerForceCta, 0, st>>>(d, Tf, kick);
         else k_force_pair<PM_BOX64, double><<<grid, 32 * kWarpsPerForceCta, 0, st>>>(d, Td, kick);

@@ -16,6 +16,9 @@ struct DSpec {
     double ymax, y0;
 };
 
+// capi.cu: record the message returned by qtb_last_error(); returns code
+int set_last_error(int code, const char *msg);
+
 // noise.cu
 void launch_white(const Dev &d, int filter_kind, int max_dofp, int nsys, long long blk, cudaStream_t st);
 void launch_filter_simt(const Dev &d, int filter_kind, int max_dofp, int nsys, int Kmax, cudaStream_t st);
@@ -34,7 +37,11 @@ struct MdLaunch {
     int n_ecta;           // external-force CTAs
     int nP;               // number of distinct bead counts
     int Pvals[8];         // distinct bead counts
+    int staged;           // pair force with the neighbourhood staged in shared memory
 };
+size_t force_staged_smem(int cap, int mixed);
+cudaError_t force_staged_prepare(int cap, int mixed);
+constexpr int kForceChunkHost = 32;  // home slots per CTA of the staged force kernel
 void launch_integrate(const Dev &d, const MdLaunch &m, int j, cudaStream_t st);
 void launch_cells(const Dev &d, const MdLaunch &m, cudaStream_t st);
 void launch_force_kick(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,

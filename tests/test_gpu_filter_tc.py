@@ -78,7 +78,10 @@ def test_tc_filter_white_limit_and_batched_systems(qtb, oracle):
         eta_b, _ = qtb.qtb_get_noise(ctx, 1, 192)
         kT = 8.617333262e-5 * 200.0
         xi = oracle.white_block(77, 0, 192, 0, 256).T
-        assert np.abs(eta_a - bf16(np.sqrt(kT)) * bf16(xi)).max() < 1e-5
+        # FP32 and FP64 Box-Muller may round to neighbouring BF16 values: one BF16 ulp
+        ref_a = bf16(np.sqrt(kT)) * bf16(xi)
+        assert np.all(np.abs(eta_a - ref_a) <= 2.0 ** -7 * np.abs(ref_a) + 1e-7)
+        assert np.sqrt(((eta_a - ref_a) ** 2).mean()) < 1e-3 * np.sqrt((ref_a ** 2).mean())
         h = S.taps(1025, 1.0, 600.0, 0.3)
         ref = oracle.colored_block(77, 1, 192, 0, 256, h).T
         rms = np.sqrt((ref ** 2).mean())
