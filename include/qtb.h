@@ -189,6 +189,25 @@ int qtb_get_step(qtb_ctx *c, long long *step);
  * y_max.  F: [n] host output. */
 int qtb_kappa_solve(int P, int n, double y_max, double y0, double *F);
 
+/* Same solve as qtb_kappa_solve for callers that cannot allocate device
+ * memory (no counterpart in the paper; an interface convenience).  Callers in
+ * a stream-capture region, processes whose device memory is all reserved by
+ * another allocator, or latency-critical loops cannot call cudaMalloc; this
+ * entry point allocates nothing: its scratch is a static __device__ array of
+ * 6.3 MB in the library, present on every device that loads the library until
+ * the process exits.
+ *   n        collocation nodes, 8 <= n <= 512 (QTB_ERR_ARG beyond: the scratch
+ *            is sized for 512)
+ *   F_dev    [n] DEVICE output buffer owned by the caller (F_P at the nodes)
+ *   stream   cudaStream_t to run on (NULL = legacy default stream); the call
+ *            synchronises it before returning.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one array and it keeps the last
+ * call's contents (the solver clears what must start at zero): calls that
+ * overlap on the GPU, from different streams or threads, race. */
+int qtb_kappa_solve_noalloc(int P, int n, double y_max, double y0, double *F_dev, void *stream);
+
 void qtb_destroy(qtb_ctx *c);
 
 /* Message of the last failed call in this thread (never NULL). */

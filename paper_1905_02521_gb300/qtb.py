@@ -83,6 +83,7 @@ def lib():
             "qtb_set_profiling": ([vp, i], i),
             "qtb_kernel_times": ([vp, vp, vp, i], i),
             "qtb_kappa_solve": ([i, i, d, d, vp], i),
+            "qtb_kappa_solve_noalloc": ([i, i, d, d, vp, vp], i),
             "qtb_destroy": ([vp], None),
             "qtb_last_error": ([], C.c_char_p),
         }
@@ -269,6 +270,11 @@ def qtb_kappa_solve(P, n=1024, y_max=1000.0, y0=1.0):
     F = np.zeros(n)
     _check(lib().qtb_kappa_solve(P, n, y_max, y0, F.ctypes.data))
     return F
+
+
+def qtb_kappa_solve_noalloc(P, n, y_max, y0, F_dev_ptr, stream=None):
+    """F_dev_ptr: device address of a caller-owned [n] float64 buffer."""
+    _check(lib().qtb_kappa_solve_noalloc(P, n, y_max, y0, F_dev_ptr, stream))
 
 
 def qtb_destroy(ctx):
