@@ -165,6 +165,37 @@ void nm_matrix(int P, std::vector<double> &C)
         }
 }
 
+// exp(x^2) erfc(x) on 0 <= x <= xmax as a degree-11 polynomial in
+// u = 2 x / xmax - 1: Chebyshev interpolation at the 12 Chebyshev nodes
+// (near-minimax, relative error ~4e-9), converted to monomial coefficients.
+void fit_erfcx(double xmax, double c[12])
+{
+    const int n = 12;
+    for (int k = 0; k < n; ++k) c[k] = 0.0;
+    if (!(xmax > 0.0)) {
+        c[0] = 1.0;
+        return;
+    }
+    double a[12];
+    for (int k = 0; k < n; ++k) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const double th = kPi * (i + 0.5) / n;
+            const double x = (std::cos(th) + 1.0) * 0.5 * xmax;
+            s += std::exp(x * x) * std::erfc(x) * std::cos(k * th);
+        }
+        a[k] = 2.0 * s / n;
+    }
+    a[0] *= 0.5;
+    double Tm[12][12] = {{0}};  // monomial coefficients of the Chebyshev polynomials
+    Tm[0][0] = 1.0;
+    Tm[1][1] = 1.0;
+    for (int k = 2; k < n; ++k)
+        for (int j = 0; j < n; ++j) Tm[k][j] = (j > 0 ? 2.0 * Tm[k - 1][j - 1] : 0.0) - Tm[k - 2][j];
+    for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j) c[j] += a[k] * Tm[k][j];
+}
+
 int check_err_word(qtb_ctx *c)
 {
     unsigned e = 0;
@@ -283,10 +314,10 @@ void set_clock(qtb_ctx *c, long long b)
 int refresh_forces(qtb_ctx *c)
 {
     set_clock(c, floor_div(c->step, kBlockSteps));
+    const int j = (int)(c->step - c->dclock * kBlockSteps) - 1;
     launch_cells(c->d, c->ml, c->st);
-    launch_force_kick(c->d, c->ml, c->tabf, c->tab, 0, c->st);
-    int j = (int)(c->step - c->dclock * kBlockSteps) - 1;
-    launch_reduce(c->d, c->ml, j, -1, c->st);
+    launch_force_kick(c->d, c->ml, c->tabf, c->tab, 0, j, c->st);
+    if (!c->ml.staged) launch_reduce(c->d, c->ml, j, -1, c->st);  // the staged force kernel reduces itself
     CUDA_TRY(cudaGetLastError());
     return QTB_OK;
 }
@@ -436,8 +467,11 @@ void one_step(qtb_ctx *c, int j)
     if (j % 16 != 0) c->capturing = false;
     { ProfMark m(c, KC_INTEGRATE); launch_integrate(c->d, c->ml, j, c->st); }
     { ProfMark m(c, KC_CELLS); launch_cells(c->d, c->ml, c->st); }
-    { ProfMark m(c, KC_FORCE); launch_force_kick(c->d, c->ml, c->tabf, c->tab, 1, c->st); }
-    { ProfMark m(c, KC_REDUCE); launch_reduce(c->d, c->ml, j, 1, c->st); }
+    { ProfMark m(c, KC_FORCE); launch_force_kick(c->d, c->ml, c->tabf, c->tab, 1, j, c->st); }
+    if (!c->ml.staged) {
+        ProfMark m(c, KC_REDUCE);
+        launch_reduce(c->d, c->ml, j, 1, c->st);
+    }
     c->capturing = keep;
 }
 
@@ -680,6 +714,14 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         }
         F.ext_V0 = (float)T.ext_V0; F.ext_ia2 = (float)T.ext_ia2;
         F.ntypes = T.ntypes; F.potential = T.potential;
+        const double log2e = 1.4426950408889634;
+        for (int t = 0; t < NT; ++t) F.inv_rho_l2e[t] = (float)(T.inv_rho[t] * log2e);
+        F.alpha2_l2e = (float)(T.alpha2 * log2e);
+        const double xmax = T.alpha * T.rc;
+        F.erfc_us = (xmax > 0.0) ? (float)(2.0 / xmax) : 0.0f;
+        double cfit[12];
+        fit_erfcx(xmax, cfit);
+        for (int k = 0; k < 12; ++k) F.erfc_c[k] = (float)cfit[k];
     }
 
     // ---- layout
@@ -690,6 +732,36 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     std::vector<double> nmC_host;
     c->hs.resize(n_sys);
     c->ds.resize(n_sys);
+    // Cell geometry: cells >= r_cut/2 with a 5^3 stencil for the staged force
+    // kernel; cells >= r_cut (27 stencil) for the unstaged kernel when a staged
+    // neighbourhood would not fit in shared memory.
+    auto cell_cap = [&](const qtb_system &q, double edge) {
+        int nc[3];
+        for (int k = 0; k < 3; ++k) nc[k] = std::max(1, (int)std::floor(q.box[k] / edge));
+        const double e = (double)q.n_atoms / (nc[0] * nc[1] * nc[2]);
+        int cp = (int)roundup((long long)std::ceil(1.25 * e + 4.0 * std::sqrt(e) + 8.0), 8);
+        return std::min(cp, (int)roundup(q.n_atoms, 8));
+    };
+    double cell_edge = p->r_cut;
+    bool staged = false;
+    int stage_cap = 0;
+    if (c->pair) {
+        // staged entries per CTA: twice the expected neighbourhood population plus a
+        // margin, never more than 125 full cells (a larger population is reported
+        // as QTB_ERR_OVERFLOW)
+        int cap2 = 8;
+        double ecell = 0.0;
+        for (int s = 0; s < n_sys; ++s) {
+            cap2 = std::max(cap2, cell_cap(sys[s], 0.5 * p->r_cut));
+            int nc[3];
+            for (int k = 0; k < 3; ++k) nc[k] = std::max(1, (int)std::floor(sys[s].box[k] / (0.5 * p->r_cut)));
+            ecell = std::max(ecell, (double)sys[s].n_atoms / (nc[0] * nc[1] * nc[2]));
+        }
+        stage_cap = (int)std::min(roundup((long long)kStencilCells * cap2, 64),
+                                  roundup((long long)std::ceil(2.0 * kStencilCells * ecell) + 256, 64));
+        staged = force_staged_smem(stage_cap, c->mixed ? 1 : 0) <= 190 * 1024;
+        if (staged) cell_edge = 0.5 * p->r_cut;
+    }
     for (int s = 0; s < n_sys; ++s) {
         const qtb_system &q = sys[s];
         HSys &h = c->hs[s];
@@ -740,12 +812,9 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         c->max_dofp = std::max(c->max_dofp, S.dofp);
         if (c->pair) {
             int nc[3];
-            for (int k = 0; k < 3; ++k) nc[k] = std::max(1, (int)std::floor(q.box[k] / p->r_cut));
+            for (int k = 0; k < 3; ++k) nc[k] = std::max(1, (int)std::floor(q.box[k] / cell_edge));
             const int cells = nc[0] * nc[1] * nc[2];
-            const double e = (double)h.N / cells;
-            int cp = (int)roundup((long long)std::ceil(1.25 * e + 4.0 * std::sqrt(e) + 8.0), 8);
-            cp = std::min(cp, (int)roundup(h.N, 8));
-            cap = std::max(cap, cp);
+            cap = std::max(cap, cell_cap(q, cell_edge));
             for (int b = 0; b < h.P; ++b) {
                 DRep R;
                 memset(&R, 0, sizeof R);
@@ -768,12 +837,10 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     if (cap > 512) return bail(fail(QTB_ERR_ARG, "cell capacity %d > 512: box too dense for r_cut-sized cells", cap));
     for (int s = 0; s < n_sys; ++s)
         for (int t = c->ds[s].icta0; t < c->ds[s].icta1; ++t) c->icta_sys.push_back(s);
-    // force CTA ranges
-    // staged force kernel when the 27-cell neighbourhood fits in shared memory
-    const bool staged = c->pair && force_staged_smem(cap, c->mixed ? 1 : 0) <= 190 * 1024;
-    const int cpc = staged ? (cap + kForceChunkHost - 1) / kForceChunkHost : cap / kWarpsPerForceCta;
+    // force CTA ranges: one CTA per cell (staged) or cap/8 CTAs per cell
+    const int cpc = staged ? 1 : cap / kWarpsPerForceCta;
     c->ml.staged = staged ? 1 : 0;
-    if (staged && force_staged_prepare(cap, c->mixed ? 1 : 0) != cudaSuccess)
+    if (staged && force_staged_prepare(stage_cap, c->mixed ? 1 : 0) != cudaSuccess)
         return bail(fail(QTB_ERR_CUDA, "cannot reserve shared memory for the force kernel"));
     int ext_gx = 0;
     for (int s = 0; s < n_sys; ++s) ext_gx = std::max(ext_gx, (c->hs[s].N * c->hs[s].P + 127) / 128);
@@ -798,6 +865,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     d.nrep = nrep;
     d.ncells = ncells;
     d.cap = cap;
+    d.stage_cap = stage_cap;
     d.cpc = cpc;
     d.G = G;
     d.Dtot = D;
@@ -883,6 +951,9 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     d.series = (double *)c->alloc(sizeof(double) * QTB_NREC * (size_t)n_sys * p->max_records);
     d.clock = (long long *)c->alloc(sizeof(long long));
     d.err = (unsigned *)c->alloc(sizeof(unsigned));
+    d.done = (unsigned *)c->alloc(sizeof(unsigned) * n_sys);
+    if (!d.done) return bail(fail(QTB_ERR_OOM, "device allocation failed"));
+    cudaMemsetAsync(d.done, 0, sizeof(unsigned) * n_sys, c->st);
     c->dspec = (DSpec *)c->alloc(sizeof(DSpec) * n_sys);
     if (!d.x || !d.v || !d.f || !d.cnt || !d.ccount || !d.cidx || !d.cpos || !d.eta || !d.part || !d.ipart ||
         !d.latest || !d.series || !d.clock || !d.err || !d.typ || !d.sys || !c->dspec)

@@ -321,9 +321,38 @@ __device__ __forceinline__ double my_erfc(double x) { return erfc(x); }
 __device__ __forceinline__ float my_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double my_sqrt(double x) { return sqrt(x); }
 
-// -dV/dr / r and V of one pair at squared distance r2 < rc^2
+// -dV/dr / r and V of one pair at squared distance r2 < rc^2, FP32 form:
+// branch-free, 1/r from rsqrt + one Newton step, exponentials through exp2,
+// erfc(x) = exp(-x^2) P(u) with the fitted polynomial of the table.
+__device__ __forceinline__ void pair_eval(const PairTabT<float> &T, int tij, float r2, float &f_over_r, float &e,
+                                          bool energy = true)
+{
+    float rinv = rsqrtf(r2);
+    rinv = rinv * fmaf(-0.5f * r2, rinv * rinv, 1.5f);
+    const float r = r2 * rinv;
+    const float r2i = rinv * rinv;
+    const float r6i = r2i * r2i * r2i;
+    const float ex = exp2f(-r * T.inv_rho_l2e[tij]);        // exp(-r/rho); A = 0 rows give 0 below
+    float f = T.A_over_rho[tij] * ex - T.C6[tij] * r6i * rinv;
+    const float gg = exp2f(-T.alpha2_l2e * r2);              // exp(-alpha^2 r^2)
+    const float u = fmaf(T.alpha * r, T.erfc_us, -1.0f);
+    float P = T.erfc_c[11];
+#pragma unroll
+    for (int k = 10; k >= 0; --k) P = fmaf(P, u, T.erfc_c[k]);
+    const float er = gg * P;                                  // erfc(alpha r)
+    const float qq = T.qq[tij];
+    f += qq * (er * r2i + T.two_a_sqrtpi * gg * rinv - T.fshift);
+    f_over_r = f * rinv;
+    if (energy)
+        e = T.A[tij] * ex - T.C[tij] * r6i - T.eshift[tij] +
+            qq * (er * rinv - T.erfc_rc_over_rc + T.fshift * (r - T.rc));
+    else
+        e = 0.0f;
+}
+
+// FP64 form: library exp / erfc / sqrt (the reference-accuracy path)
 template <class R>
-__device__ __forceinline__ void pair_eval(const PairTabT<R> &T, int tij, R r2, R &f_over_r, R &e)
+__device__ __forceinline__ void pair_eval(const PairTabT<R> &T, int tij, R r2, R &f_over_r, R &e, bool energy = true)
 {
     const R r = my_sqrt(r2);
     const R rinv = R(1) / r;
@@ -492,185 +521,314 @@ __global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_force_pair(Dev d, Pa
     cta_store_partials(acc, red, d.part + (size_t)blockIdx.x * kNQ);
 }
 
-// Pair force with the 27-cell neighbourhood staged in shared memory.
-// One CTA = (home cell, chunk of kForceChunk home slots); its 8 warps take the
-// chunk's home atoms in turn.  Staging copies every stencil cell (sorted slots)
-// once, with its periodic image shift already added (fixed point: + m 2^30,
-// which stays inside int32 because positions are < 2^30), so the candidate scan
-// is one flat loop over shared memory.  Dynamic shared memory: 27 cap entries.
-constexpr int kForceChunk = 32;
+// Per-system reduction of the CTA partials into the observable record
+// (fixed summation order, FP64).  Executed by one CTA.
+__device__ void reduce_system(const Dev &d, int s, long long step, int record, double (*sh)[kNQ + 1])
+{
+    const DSys S = d.sys[s];
+    const int nt = min((int)blockDim.x, 128);  // threads taking part (a power of two)
+    if ((int)threadIdx.x < nt) {
+        double acc[kNQ + 1];
+        for (int q = 0; q <= kNQ; ++q) acc[q] = 0.0;
+        for (int c = S.fcta0 + (int)threadIdx.x; c < S.fcta1; c += nt)
+            for (int q = 0; q < kNQ; ++q) acc[q] += d.part[(size_t)c * kNQ + q];
+        for (int c = S.icta0 + (int)threadIdx.x; c < S.icta1; c += nt) acc[kNQ] += d.ipart[(size_t)c * kNQ + Q_SPRING];
+        for (int q = 0; q <= kNQ; ++q) sh[threadIdx.x][q] = acc[q];
+    }
+    __syncthreads();
+    for (int w = nt / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int q = 0; q <= kNQ; ++q) sh[threadIdx.x][q] += sh[threadIdx.x + w][q];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double invP = S.invP;
+        double rec[QTB_NREC];
+        for (int q = 0; q < QTB_NREC; ++q) rec[q] = 0.0;
+        const double K = sh[0][Q_K], V = sh[0][Q_V] * invP, sp = sh[0][kNQ];
+        rec[0] = (double)step;
+        rec[1] = K;
+        rec[2] = V;
+        rec[3] = sp;
+        rec[4] = K - sp + V;
+        const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};  // xx xy xz / yx yy yz / zx zy zz
+        for (int a = 0; a < 9; ++a) rec[5 + a] = sh[0][Q_VIR + map[a]] * invP;
+        for (int c = 0; c < 3; ++c) rec[14 + c] = sh[0][Q_MOM + c];
+        rec[17] = sh[0][Q_X2] * invP;
+        if (!isfinite(K) || !isfinite(V)) atomicOr(d.err, (unsigned)ERR_NONFINITE);
+        for (int q = 0; q < QTB_NREC; ++q) d.latest[(size_t)s * QTB_NREC + q] = rec[q];
+        if (record >= 0 && step % d.obs_stride == 0) {
+            long long r = step / d.obs_stride - 1;
+            int slot = (int)(r % d.max_records);
+            for (int q = 0; q < QTB_NREC; ++q) d.series[((size_t)slot * d.nsys + s) * QTB_NREC + q] = rec[q];
+        }
+    }
+}
+
+// Pair force with the neighbourhood staged in shared memory.
+// Cells are >= r_c / 2, the stencil is the 5^3 surrounding cells (with
+// explicit periodic images).  One CTA per home cell: its warps stage every
+// stencil cell (sorted slots, image shift already added: fixed point + m 2^30
+// stays inside int32 because positions are < 2^30), then each warp takes one
+// home atom at a time and scans the flat staged array, compacting the pairs
+// within r_c into a shared-memory queue that all 32 lanes evaluate together.
+// Energies, virials and kinetic energies are formed only on recorded steps;
+// the last CTA of a system to finish then reduces the system's partials.
+constexpr int kStencilHalf = 2;
+constexpr int kStencil = (2 * kStencilHalf + 1) * (2 * kStencilHalf + 1) * (2 * kStencilHalf + 1);
 
 template <int PM, class R>
-__global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_force_cells(Dev d, PairTabT<R> T, int kick)
+__global__ void __launch_bounds__(32 * kWarpsPerForceCta, sizeof(R) == 4 ? 3 : 1)
+    k_force_cells(Dev d, PairTabT<R> T, int kick, int j)
 {
     typedef typename std::conditional<sizeof(R) == 4, float4, D4>::type R4;
     typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
     typedef typename std::conditional<sizeof(R) == 4, FF, DD>::type ACC;
+    constexpr int SH = kStencilHalf, SW = 2 * kStencilHalf + 1;
     extern __shared__ __align__(32) unsigned char fsm[];
-    __shared__ R4 qbuf[kWarpsPerForceCta][64];
+    __shared__ R4 qbuf[kWarpsPerForceCta][128];
     __shared__ double red[kWarpsPerForceCta][kNQ];
-    __shared__ int soff[28], scell[27], simg[27][3];
+    __shared__ int soff[kStencil + 1], scell[kStencil], simg[kStencil][3];
+    __shared__ int s_last;
     E4 *stage = reinterpret_cast<E4 *>(fsm);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cpc = d.cpc;
-    const int cell = blockIdx.x / cpc, chunk = blockIdx.x - cell * cpc;
+    const int cell = blockIdx.x;
     const int cnt = d.ccount[cell];
-    const int first = chunk * kForceChunk;
+    const long long step = d.clock[0] * kBlockSteps + j + 1;
+    const bool rec = (kick == 0) || (step % d.obs_stride == 0);
+    const DRep RP = d.rep[d.cell_rep[cell]];
     double acc[kNQ];
 #pragma unroll
     for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
-    if (first >= cnt) {  // empty chunk: write zero partials
-        if (threadIdx.x < kNQ) d.part[(size_t)blockIdx.x * kNQ + threadIdx.x] = 0.0;
-        return;
-    }
-    const DRep RP = d.rep[d.cell_rep[cell]];
-    const int lc = cell - RP.cell0;
-    const int cx = lc % RP.nc[0], cy = (lc / RP.nc[0]) % RP.nc[1], cz = lc / (RP.nc[0] * RP.nc[1]);
-    if (threadIdx.x < 27) {
-        const int t = threadIdx.x;
-        const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = t / 9 - 1;
-        int ux = cx + ox, uy = cy + oy, uz = cz + oz;
-        const int mx = (int)floor_div(ux, RP.nc[0]), my = (int)floor_div(uy, RP.nc[1]), mz = (int)floor_div(uz, RP.nc[2]);
-        ux -= mx * RP.nc[0]; uy -= my * RP.nc[1]; uz -= mz * RP.nc[2];
-        scell[t] = RP.cell0 + ux + RP.nc[0] * (uy + RP.nc[1] * uz);
-        simg[t][0] = mx; simg[t][1] = my; simg[t][2] = mz;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int o = 0;
-        for (int t = 0; t < 27; ++t) {
-            soff[t] = o;
-            o += d.ccount[scell[t]];
+    if (cnt > 0) {
+        const int lc = cell - RP.cell0;
+        const int cx = lc % RP.nc[0], cy = (lc / RP.nc[0]) % RP.nc[1], cz = lc / (RP.nc[0] * RP.nc[1]);
+        for (int t = threadIdx.x; t < kStencil; t += blockDim.x) {
+            const int ox = t % SW - SH, oy = (t / SW) % SW - SH, oz = t / (SW * SW) - SH;
+            int ux = cx + ox, uy = cy + oy, uz = cz + oz;
+            const int mx = (int)floor_div(ux, RP.nc[0]), my = (int)floor_div(uy, RP.nc[1]), mz = (int)floor_div(uz, RP.nc[2]);
+            ux -= mx * RP.nc[0]; uy -= my * RP.nc[1]; uz -= mz * RP.nc[2];
+            const int nc = RP.cell0 + ux + RP.nc[0] * (uy + RP.nc[1] * uz);
+            scell[t] = nc;
+            simg[t][0] = mx; simg[t][1] = my; simg[t][2] = mz;
+            soff[t + 1] = d.ccount[nc];
         }
-        soff[27] = o;
-    }
-    __syncthreads();
-    const int total = soff[27];
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        int t = 0;
-        while (soff[t + 1] <= e) ++t;
-        const size_t src = (size_t)scell[t] * d.cap + (e - soff[t]);
-        if (PM == PM_FIX) {
-            int4 p = reinterpret_cast<const int4 *>(d.cpos)[src];
-            p.x = (int)((unsigned)p.x + (unsigned)simg[t][0] * (1u << kFixBits));
-            p.y = (int)((unsigned)p.y + (unsigned)simg[t][1] * (1u << kFixBits));
-            p.z = (int)((unsigned)p.z + (unsigned)simg[t][2] * (1u << kFixBits));
-            reinterpret_cast<int4 *>(stage)[e] = p;
-        } else {
-            D4 p = reinterpret_cast<const D4 *>(d.cpos)[src];
-            p.x += simg[t][0] * RP.box[0];
-            p.y += simg[t][1] * RP.box[1];
-            p.z += simg[t][2] * RP.box[2];
-            reinterpret_cast<D4 *>(stage)[e] = p;
-        }
-    }
-    __syncthreads();
-    const int self0 = soff[13];  // stencil (0,0,0) is entry 13
-    const R sx = (R)RP.fix_scale[0], sy = (R)RP.fix_scale[1], sz = (R)RP.fix_scale[2];
-    const R rc2 = T.rc2;
-    const DSys &S = d.sys[RP.sys];
-    const R invP = sizeof(R) == 4 ? (R)S.invP_f : (R)S.invP;
-    const unsigned lt = (1u << lane) - 1u;
-    R4 *qb = qbuf[warp];
-    const int last = min(cnt, first + kForceChunk);
-    for (int slot = first + warp; slot < last; slot += kWarpsPerForceCta) {
-        const E4 hp = stage[self0 + slot];
-        int ti;
-        if (PM == PM_FIX) ti = hp.w; else ti = (int)hp.w;
-        ACC fx{}, fy{}, fz{};
-        R en = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
-        int qn = 0;
-        auto consume = [&](int m) {
-            if (lane < m) {
-                R4 e4 = qb[lane];
-                int tj;
-                if (sizeof(R) == 4) tj = __float_as_int((float)e4.w); else tj = (int)e4.w;
-                R r2 = e4.x * e4.x + e4.y * e4.y + e4.z * e4.z;
-                R fo, ee;
-                pair_eval<R>(T, ti * kMaxTypes + tj, r2, fo, ee);
-                fx.add(-fo * e4.x); fy.add(-fo * e4.y); fz.add(-fo * e4.z);
-                en += ee;
-                w0 += fo * e4.x * e4.x; w1 += fo * e4.y * e4.y; w2 += fo * e4.z * e4.z;
-                w3 += fo * e4.x * e4.y; w4 += fo * e4.x * e4.z; w5 += fo * e4.y * e4.z;
+        __syncthreads();
+        if (warp == 0) {  // exclusive scan of the stencil counts (<= 128 entries)
+            int v[4], run = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int t = lane * 4 + k;
+                v[k] = (t < kStencil) ? soff[t + 1] : 0;
+                run += v[k];
             }
-        };
-        for (int e0 = 0; e0 < total; e0 += 32) {
-            const int e = e0 + lane;
-            R dx = 0, dy = 0, dz = 0;
-            int tj = 0;
-            bool take = false;
-            if (e < total && e != self0 + slot) {
-                const E4 pj = stage[e];
+            int incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            int base = incl - run;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int t = lane * 4 + k;
+                if (t < kStencil) soff[t] = base;
+                base += v[k];
+                if (t == kStencil - 1) soff[kStencil] = base;
+            }
+        }
+        __syncthreads();
+        // capacity of the staging buffer (sentinel padding to a multiple of 64 included)
+        int total = soff[kStencil];
+        if (((total + 63) & ~63) > d.stage_cap) {
+            if (threadIdx.x == 0) atomicOr(d.err, (unsigned)ERR_OVERFLOW);
+            total = (d.stage_cap & ~63);
+        }
+        const int padded = (total + 63) & ~63;
+        // flat staging: every thread first issues all of its (independent) loads,
+        // then shifts by the image and stores, so the CTA pays one memory latency
+        {
+            constexpr int U = 8;  // entries per thread per round (2048 per round for 256 threads)
+            for (int base = 0; base < total; base += U * (int)blockDim.x) {
+                E4 buf[U];
+                int tcell[U], dst[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = base + u * (int)blockDim.x + (int)threadIdx.x;
+                    dst[u] = -1;
+                    tcell[u] = 0;
+                    if (e < total) {
+                        int lo = 0, hi = kStencil - 1;  // stencil cell t with soff[t] <= e < soff[t+1]
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (soff[mid] <= e) lo = mid; else hi = mid - 1;
+                        }
+                        tcell[u] = lo;
+                        dst[u] = e;
+                        buf[u] = reinterpret_cast<const E4 *>(d.cpos)[(size_t)scell[lo] * d.cap + (e - soff[lo])];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (dst[u] < 0) continue;
+                    E4 p = buf[u];
+                    const int t = tcell[u];
+                    if (PM == PM_FIX) {
+                        p.x = (int)((unsigned)p.x + (unsigned)simg[t][0] * (1u << kFixBits));
+                        p.y = (int)((unsigned)p.y + (unsigned)simg[t][1] * (1u << kFixBits));
+                        p.z = (int)((unsigned)p.z + (unsigned)simg[t][2] * (1u << kFixBits));
+                    } else {
+                        p.x += simg[t][0] * RP.box[0];
+                        p.y += simg[t][1] * RP.box[1];
+                        p.z += simg[t][2] * RP.box[2];
+                    }
+                    stage[dst[u]] = p;
+                }
+            }
+        }
+        // sentinel entries far outside r_cut pad the scan to a multiple of 64
+        for (int e = total + threadIdx.x; e < padded; e += blockDim.x) {
+            if (PM == PM_FIX) reinterpret_cast<int4 *>(stage)[e] = make_int4(-(1 << kFixBits), -(1 << kFixBits), -(1 << kFixBits), 0);
+            else reinterpret_cast<D4 *>(stage)[e] = D4{-1e30, -1e30, -1e30, 0.0};
+        }
+        __syncthreads();
+        const int self0 = soff[kStencil / 2];  // stencil offset (0,0,0)
+        const R sx = (R)RP.fix_scale[0], sy = (R)RP.fix_scale[1], sz = (R)RP.fix_scale[2];
+        const R rc2 = T.rc2;
+        const DSys &S = d.sys[RP.sys];
+        const R invP = sizeof(R) == 4 ? (R)S.invP_f : (R)S.invP;
+        const unsigned lt = (1u << lane) - 1u;
+        R4 *qb = qbuf[warp];  // ring of 128 queued pairs
+        for (int slot = warp; slot < cnt; slot += kWarpsPerForceCta) {
+            const E4 hp = stage[self0 + slot];
+            int ti;
+            if (PM == PM_FIX) ti = hp.w; else ti = (int)hp.w;
+            ACC fx{}, fy{}, fz{};
+            R en = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+            int qh = 0, qn = 0;  // ring head, queued count
+            auto consume = [&](int m) {
+                if (lane < m) {
+                    R4 e4 = qb[(qh + lane) & 127];
+                    int tj;
+                    if (sizeof(R) == 4) tj = __float_as_int((float)e4.w); else tj = (int)e4.w;
+                    R r2 = e4.x * e4.x + e4.y * e4.y + e4.z * e4.z;
+                    R fo, ee;
+                    pair_eval<R>(T, ti * kMaxTypes + tj, r2, fo, ee, rec);
+                    // stored displacement is r_j - r_i: the force on i is -fo (r_j - r_i)
+                    fx.add(-fo * e4.x); fy.add(-fo * e4.y); fz.add(-fo * e4.z);
+                    if (rec) {
+                        en += ee;
+                        w0 += fo * e4.x * e4.x; w1 += fo * e4.y * e4.y; w2 += fo * e4.z * e4.z;
+                        w3 += fo * e4.x * e4.y; w4 += fo * e4.x * e4.z; w5 += fo * e4.y * e4.z;
+                    }
+                }
+            };
+            auto disp = [&](const E4 &pj, R &dx, R &dy, R &dz) {
                 if (PM == PM_FIX) {
                     dx = (R)(int)((unsigned)pj.x - (unsigned)hp.x) * sx;
                     dy = (R)(int)((unsigned)pj.y - (unsigned)hp.y) * sy;
                     dz = (R)(int)((unsigned)pj.z - (unsigned)hp.z) * sz;
-                    tj = pj.w;
                 } else {
                     dx = (R)(pj.x - hp.x);
                     dy = (R)(pj.y - hp.y);
                     dz = (R)(pj.z - hp.z);
-                    tj = (int)pj.w;
                 }
-                take = (dx * dx + dy * dy + dz * dz) < rc2;
+            };
+            auto push = [&](bool take, R dx, R dy, R dz, int tj) {
+                const unsigned m = __ballot_sync(0xffffffffu, take);
+                if (take) {
+                    R4 v;
+                    v.x = dx; v.y = dy; v.z = dz;
+                    if (sizeof(R) == 4) v.w = (R)__int_as_float(tj); else v.w = (R)tj;
+                    qb[(qh + qn + __popc(m & lt)) & 127] = v;
+                }
+                qn += __popc(m);
+            };
+            // two independent candidates per lane per iteration; the home atom
+            // itself (r2 == 0) and the sentinels (r2 >= rc2) fail the test
+            for (int e0 = 0; e0 < padded; e0 += 64) {
+                const E4 pa = stage[e0 + lane], pb = stage[e0 + 32 + lane];
+                R ax, ay, az, bx, by, bz;
+                disp(pa, ax, ay, az);
+                disp(pb, bx, by, bz);
+                const R ra = ax * ax + ay * ay + az * az, rb = bx * bx + by * by + bz * bz;
+                int ta, tb;
+                if (PM == PM_FIX) { ta = pa.w; tb = pb.w; } else { ta = (int)pa.w; tb = (int)pb.w; }
+                push(ra < rc2 && ra > R(0), ax, ay, az, ta);
+                push(rb < rc2 && rb > R(0), bx, by, bz, tb);
+                __syncwarp();
+                while (qn >= 32) {
+                    consume(32);
+                    qh = (qh + 32) & 127;
+                    qn -= 32;
+                }
+                __syncwarp();
             }
-            const unsigned m = __ballot_sync(0xffffffffu, take);
-            if (take) {
-                R4 v;
-                v.x = dx; v.y = dy; v.z = dz;
-                if (sizeof(R) == 4) v.w = (R)__int_as_float(tj); else v.w = (R)tj;
-                qb[qn + __popc(m & lt)] = v;
-            }
-            qn += __popc(m);
+            consume(qn);
             __syncwarp();
-            if (qn >= 32) {
-                consume(32);
-                __syncwarp();
-                R4 carry;
-                if (lane < qn - 32) carry = qb[32 + lane];
-                __syncwarp();
-                if (lane < qn - 32) qb[lane] = carry;
-                qn -= 32;
-                __syncwarp();
+            fx.warp_reduce(); fy.warp_reduce(); fz.warp_reduce();
+            if (rec) {
+                en = warp_sum(en);
+                w0 = warp_sum(w0); w1 = warp_sum(w1); w2 = warp_sum(w2);
+                w3 = warp_sum(w3); w4 = warp_sum(w4); w5 = warp_sum(w5);
             }
-        }
-        consume(qn);
-        __syncwarp();
-        fx.warp_reduce(); fy.warp_reduce(); fz.warp_reduce();
-        en = warp_sum(en);
-        w0 = warp_sum(w0); w1 = warp_sum(w1); w2 = warp_sum(w2);
-        w3 = warp_sum(w3); w4 = warp_sum(w4); w5 = warp_sum(w5);
-        if (lane == 0) {
-            const int gi = d.cidx[(size_t)cell * d.cap + slot];
-            const size_t G = (size_t)d.G;
-            R *Fo = reinterpret_cast<R *>(d.f);
-            R *V = reinterpret_cast<R *>(d.v);
-            const R f3[3] = {(R)fx.value() * invP, (R)fy.value() * invP, (R)fz.value() * invP};
-            const R hdtm = T.hdt_m[ti];
-            double ke = 0.0;
-            for (int c = 0; c < 3; ++c) {
-                Fo[c * G + gi] = f3[c];
-                R v = V[c * G + gi];
-                if (kick) {
-                    v += hdtm * f3[c];
-                    V[c * G + gi] = v;
+            if (lane == 0) {
+                const int gi = d.cidx[(size_t)cell * d.cap + slot];
+                const size_t G = (size_t)d.G;
+                R *Fo = reinterpret_cast<R *>(d.f);
+                R *V = reinterpret_cast<R *>(d.v);
+                const R f3[3] = {(R)fx.value() * invP, (R)fy.value() * invP, (R)fz.value() * invP};
+                const R hdtm = T.hdt_m[ti];
+                R v3[3];
+                for (int c = 0; c < 3; ++c) {
+                    Fo[c * G + gi] = f3[c];
+                    R v = V[c * G + gi];
+                    if (kick) {
+                        v += hdtm * f3[c];
+                        V[c * G + gi] = v;
+                    }
+                    v3[c] = v;
                 }
-                ke += 0.5 * T.mass_mvv[ti] * (double)v * (double)v;
-                acc[Q_MOM + c] += T.mass[ti] * (double)v;
+                if (rec) {
+                    double ke = 0.0;
+                    for (int c = 0; c < 3; ++c) {
+                        ke += 0.5 * T.mass_mvv[ti] * (double)v3[c] * (double)v3[c];
+                        acc[Q_MOM + c] += T.mass[ti] * (double)v3[c];
+                    }
+                    acc[Q_K] += ke;
+                    acc[Q_V] += 0.5 * (double)en;
+                    acc[Q_VIR + 0] += 0.5 * (double)w0; acc[Q_VIR + 1] += 0.5 * (double)w1;
+                    acc[Q_VIR + 2] += 0.5 * (double)w2; acc[Q_VIR + 3] += 0.5 * (double)w3;
+                    acc[Q_VIR + 4] += 0.5 * (double)w4; acc[Q_VIR + 5] += 0.5 * (double)w5;
+                }
             }
-            acc[Q_K] += ke;
-            acc[Q_V] += 0.5 * (double)en;
-            acc[Q_VIR + 0] += 0.5 * (double)w0; acc[Q_VIR + 1] += 0.5 * (double)w1; acc[Q_VIR + 2] += 0.5 * (double)w2;
-            acc[Q_VIR + 3] += 0.5 * (double)w3; acc[Q_VIR + 4] += 0.5 * (double)w4; acc[Q_VIR + 5] += 0.5 * (double)w5;
         }
     }
+    if (!rec) return;
     cta_store_partials(acc, red, d.part + (size_t)blockIdx.x * kNQ);
+    // last CTA of this system reduces (partials made visible first)
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const DSys &S = d.sys[RP.sys];
+        const unsigned prev = atomicAdd(&d.done[RP.sys], 1u);
+        s_last = (prev == (unsigned)(S.fcta1 - S.fcta0 - 1)) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        // the staging buffer is free now: reuse it for the reduction
+        reduce_system(d, RP.sys, step, kick ? 1 : -1, reinterpret_cast<double (*)[kNQ + 1]>(fsm));
+        if (threadIdx.x == 0) d.done[RP.sys] = 0u;
+    }
 }
 
-template <int PM, class R> size_t force_cells_smem(int cap)
+template <int PM, class R> size_t force_cells_smem(int entries)
 {
     typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
-    return (size_t)27 * cap * sizeof(E4);
+    const size_t stage = (size_t)entries * sizeof(E4);
+    const size_t redn = (size_t)128 * (kNQ + 1) * sizeof(double);
+    return stage > redn ? stage : redn;
 }
 
 // External separable potentials, one thread per bead-atom.  grid = (gx, nsys)
@@ -734,42 +892,7 @@ __global__ void k_reduce(Dev d, int j, int record)
     const long long step = d.clock[0] * kBlockSteps + j + 1;  // steps completed
     // during stepping only the recorded steps are reduced (record < 0: always)
     if (record >= 0 && step % d.obs_stride != 0) return;
-    const int s = blockIdx.x;
-    const DSys S = d.sys[s];
-    double acc[kNQ + 1];
-    for (int q = 0; q <= kNQ; ++q) acc[q] = 0.0;
-    for (int c = S.fcta0 + threadIdx.x; c < S.fcta1; c += blockDim.x)
-        for (int q = 0; q < kNQ; ++q) acc[q] += d.part[(size_t)c * kNQ + q];
-    for (int c = S.icta0 + threadIdx.x; c < S.icta1; c += blockDim.x) acc[kNQ] += d.ipart[(size_t)c * kNQ + Q_SPRING];
-    for (int q = 0; q <= kNQ; ++q) sh[threadIdx.x][q] = acc[q];
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-            for (int q = 0; q <= kNQ; ++q) sh[threadIdx.x][q] += sh[threadIdx.x + w][q];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double invP = S.invP;
-        double rec[QTB_NREC];
-        for (int q = 0; q < QTB_NREC; ++q) rec[q] = 0.0;
-        const double K = sh[0][Q_K], V = sh[0][Q_V] * invP, sp = sh[0][kNQ];
-        rec[0] = (double)step;
-        rec[1] = K;
-        rec[2] = V;
-        rec[3] = sp;
-        rec[4] = K - sp + V;
-        const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};  // xx xy xz / yx yy yz / zx zy zz
-        for (int a = 0; a < 9; ++a) rec[5 + a] = sh[0][Q_VIR + map[a]] * invP;
-        for (int c = 0; c < 3; ++c) rec[14 + c] = sh[0][Q_MOM + c];
-        rec[17] = sh[0][Q_X2] * invP;
-        if (!isfinite(K) || !isfinite(V)) atomicOr(d.err, (unsigned)ERR_NONFINITE);
-        for (int q = 0; q < QTB_NREC; ++q) d.latest[(size_t)s * QTB_NREC + q] = rec[q];
-        if (record >= 0 && step % d.obs_stride == 0) {
-            long long r = step / d.obs_stride - 1;
-            int slot = (int)(r % d.max_records);
-            for (int q = 0; q < QTB_NREC; ++q) d.series[((size_t)slot * d.nsys + s) * QTB_NREC + q] = rec[q];
-        }
-    }
+    reduce_system(d, blockIdx.x, step, record, sh);
 }
 
 __global__ void k_tick(Dev d) { d.clock[0] += 1; }
@@ -830,13 +953,13 @@ cudaError_t force_staged_prepare(int cap, int mixed)
 }
 
 void launch_force_kick(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,
-                       int kick, cudaStream_t st)
+                       int kick, int j, cudaStream_t st)
 {
     if (m.pair && m.staged) {
-        const unsigned grid = (unsigned)(d.ncells * d.cpc);
-        const size_t sm = force_staged_smem(d.cap, m.mixed);
-        if (m.mixed) k_force_cells<PM_FIX, float><<<grid, 32 * kWarpsPerForceCta, sm, st>>>(d, Tf, kick);
-        else k_force_cells<PM_BOX64, double><<<grid, 32 * kWarpsPerForceCta, sm, st>>>(d, Td, kick);
+        const unsigned grid = (unsigned)d.ncells;
+        const size_t sm = force_staged_smem(d.stage_cap, m.mixed);
+        if (m.mixed) k_force_cells<PM_FIX, float><<<grid, 32 * kWarpsPerForceCta, sm, st>>>(d, Tf, kick, j);
+        else k_force_cells<PM_BOX64, double><<<grid, 32 * kWarpsPerForceCta, sm, st>>>(d, Td, kick, j);
     } else if (m.pair) {
         const unsigned grid = (unsigned)(d.ncells * d.cpc);
         if (m.mixed) k_force_pair<PM_FIX, float><<<grid, 32 * kWarpsPerForceCta, 0, st>>>(d, Tf, kick);

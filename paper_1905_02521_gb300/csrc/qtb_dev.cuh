@@ -72,6 +72,12 @@ template <class R> struct PairTabT {
     R qq[kMaxTypes * kMaxTypes];      // k_e q_a q_b
     R eshift[kMaxTypes * kMaxTypes];  // Buckingham energy at r_cut
     R alpha, alpha2, two_a_sqrtpi, rc, rc2, erfc_rc_over_rc, fshift;  // DSF constants
+    // FP32 form only: exp(-r/rho) = 2^(-r inv_rho log2 e); erfc(x) = exp(-x^2) P(u),
+    // u = x us - 1 in [-1, 1] on 0 <= x <= alpha r_cut, P a degree-11 least-squares
+    // fit of exp(x^2) erfc(x) made at context creation (relative error ~2e-7)
+    R inv_rho_l2e[kMaxTypes * kMaxTypes];
+    R alpha2_l2e, erfc_us;
+    R erfc_c[12];
     R hdt_m[kMaxTypes];               // dt / (2 m mvv2e)
     R ext_k[kMaxTypes];               // HARMONIC: m mvv2e w0^2
     R ext_V0, ext_ia2;                // DOUBLEWELL: V0, 1/a^2
@@ -123,6 +129,8 @@ struct Dev {
     double *series;       // [max_records][nsys][QTB_NREC]
     long long *clock;     // [0] = current noise block
     unsigned *err;        // error word
+    unsigned *done;       // [nsys] CTAs finished (last-CTA reduction), reset by the last one
+    int stage_cap;        // staged neighbourhood entries per CTA of the staged force kernel
     unsigned long long seed;
     double mass_mvv[kMaxTypes];  // m * mvv2e per type (eV fs^2 / A^2)
 };

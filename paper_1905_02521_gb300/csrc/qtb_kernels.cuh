@@ -39,13 +39,16 @@ struct MdLaunch {
     int Pvals[8];         // distinct bead counts
     int staged;           // pair force with the neighbourhood staged in shared memory
 };
-size_t force_staged_smem(int cap, int mixed);
-cudaError_t force_staged_prepare(int cap, int mixed);
+// dynamic shared memory of the staged force kernel for `entries` staged neighbours
+size_t force_staged_smem(int entries, int mixed);
+cudaError_t force_staged_prepare(int entries, int mixed);
+constexpr int kStencilCells = 125;  // 5^3 stencil of r_cut/2 cells
 constexpr int kForceChunkHost = 32;  // home slots per CTA of the staged force kernel
 void launch_integrate(const Dev &d, const MdLaunch &m, int j, cudaStream_t st);
 void launch_cells(const Dev &d, const MdLaunch &m, cudaStream_t st);
+// staged pair force (m.staged): also reduces the observables of recorded steps
 void launch_force_kick(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,
-                       int kick, cudaStream_t st);
+                       int kick, int j, cudaStream_t st);
 void launch_reduce(const Dev &d, const MdLaunch &m, int j, int record, cudaStream_t st);
 void launch_tick(const Dev &d, cudaStream_t st);
 void launch_setclock(const Dev &d, long long blk, cudaStream_t st);
