@@ -57,6 +57,27 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seed(base, rank):
+    """Every rank simulates an independent replica (weak scaling, no exchange)."""
+    return base + rank
+
+
+def max_over_ranks(t_ms, device="cpu"):
+    """Slowest rank's time (the job's time); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(t_ms)
+    t = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_units_per_rank, steps, world_size, t_ms):
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return world_size * n_units_per_rank * steps / (t_ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
 
@@ -145,7 +166,7 @@ def run_ours(args):
     if filt == "auto":
         filt = "bf16" if _tc_filter_available() else "fp32"
     s, pot, params = workload(args.ncell, args.precision, filt)
-    params["seed"] = 12345 + rank        # independent replica per rank (weak scaling)
+    params["seed"] = replica_seed(12345, rank)
     N = len(s["types"])
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -180,13 +201,8 @@ def run_ours(args):
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
-    t_ms = float(np.sum(step_ms))
-    if ws > 1:
-        t = torch.tensor([t_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
-    total_units = ws * N * BLOCK * args.steps
-    value = total_units / (t_ms / 1e3)
+    t_ms = max_over_ranks(float(np.sum(step_ms)), device="cuda")
+    value = job_throughput(N * BLOCK, args.steps, ws, t_ms)
     obs = qtb.qtb_observables(ctx, 0)
 
     # roofline of the dominant kernel (pair force): algorithmic flops / mean launch time
@@ -219,8 +235,9 @@ def run_ours(args):
                    "n_ions": N, "n_beads": 1, "md_steps_per_bench_step": BLOCK, "precision": args.precision,
                    "filter": filt, "parallelism": f"replicas x{ws}",
                    "l2": "256 MB buffer written between timed steps (flush)"},
-        "roofline": {"bound": "alu", "kernel": "k_force_pair", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+        "roofline": {"bound": "alu", "kernel": "k_force_cells", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": measured_traffic("k_force_cells"),
+                     "peak_source": "152 SM x 128 FP32 lanes x 2 flop x sm_max_mhz of MEASURED_PEAKS.json",
                      "flops_per_launch": PAIR_FLOPS * pairs, "pairs_per_launch": pairs, "mean_launch_ms": force_ms},
         "kernel_ms_per_bench_step": step_breakdown,
         "clocks": clocks,
@@ -237,6 +254,21 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu capture, or None when the
+    kernel's source has changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != rec["source_sha1"]:
+                return None
+        return rec["dram_bytes_per_launch"]
+    except Exception:
+        return None
 
 
 def alu_peak_tflops():
