@@ -189,6 +189,54 @@ int qtb_get_step(qtb_ctx *c, long long *step);
  * y_max.  F: [n] host output. */
 int qtb_kappa_solve(int P, int n, double y_max, double y0, double *F);
 
+/* ---- Learned kappa_P (stand-in for the solve of Eq. 10) -------------------
+ * A 2-64-64-1 SiLU network maps (y = beta hbar w, P) to kappa_P/theta; inputs
+ * x1 = asinh(y)/asinh(1000), x2 = (ln P - ln 2)/(ln 32 - ln 2).  It is trained on
+ * the GPU (FP32 forward/backward/Adam kernels) on F_P produced by
+ * qtb_kappa_solve, and the solver judges it: for each trained P the maximum
+ * deviation of kappa_P/theta from the solver on held-out frequencies is kept,
+ * and QTB_NOISE_QTB_PIMD_MLP uses the model only for P whose deviation is
+ * within the tolerance given at training (otherwise the solver: fallback).
+ * Parameters: 4417 floats, W1[64][2], b1[64], W2[64][64], b2[64], W3[64], b3.
+ * The model owns its device memory (cudaMalloc); calls run on the legacy
+ * default stream and synchronise. */
+typedef struct qtb_kappa_model qtb_kappa_model;
+
+/* New model with seeded uniform (He) initial weights. */
+int qtb_kappa_model_create(qtb_kappa_model **out, unsigned long long seed);
+
+/* Train on P_list (each in 2..32): n_per_P samples per P with y uniform in
+ * asinh(y) on [0, asinh(1000)]; `iters` full-batch Adam steps (learning rate
+ * 3e-3 decaying exponentially to 1e-5), replayed as CUDA graphs of 50 steps; tol: largest
+ * accepted deviation of kappa_P/theta (e.g. 2e-3). */
+int qtb_kappa_model_train(qtb_kappa_model *m, const int *P_list, int nP, int n_per_P, int iters, double tol);
+
+/* Mean squared error loss and its gradient (4417 floats) for n samples with
+ * features x[n][2] and targets t[n] (host arrays), with the current weights;
+ * no update. */
+int qtb_kappa_model_grad(qtb_kappa_model *m, const float *x, const float *t, int n, float *grad, float *loss);
+
+/* Model ratio kappa_P/theta at n values of y (host arrays). */
+int qtb_kappa_model_eval(qtb_kappa_model *m, int P, const double *y, int n, double *ratio);
+
+/* Weights (4417 floats, host). */
+int qtb_kappa_model_get_weights(qtb_kappa_model *m, float *w, int n);
+int qtb_kappa_model_set_weights(qtb_kappa_model *m, const float *w, int n);
+
+/* Solver-judged deviation per trained P (up to max entries), training time (ms)
+ * and final loss. */
+int qtb_kappa_model_info(qtb_kappa_model *m, int *P_out, double *err_out, int max, int *n_out, double *train_ms,
+                         double *final_loss);
+
+void qtb_kappa_model_destroy(qtb_kappa_model *m);
+
+/* Use `model` (borrowed; it must outlive its use) for QTB_NOISE_QTB_PIMD_MLP. */
+int qtb_set_kappa_model(qtb_ctx *c, const qtb_kappa_model *model);
+
+/* Source of system sys's spectrum after qtb_set_filter: 0 theta (QTB) or
+ * k_B T (white), 1 the kappa_P solver, 2 the learned model. */
+int qtb_filter_source(qtb_ctx *c, int sys, int *source);
+
 /* Same solve as qtb_kappa_solve for callers that cannot allocate device
  * memory (no counterpart in the paper; an interface convenience).  Callers in
  * a stream-capture region, processes whose device memory is all reserved by

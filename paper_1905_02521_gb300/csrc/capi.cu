@@ -101,6 +101,9 @@ struct qtb_ctx {
     size_t Bt_bytes = 0;
     int *d_tiles = nullptr;
     int n_tiles = 0;
+    // learned kappa_P model (borrowed) and the source of each system's spectrum
+    const qtb_kappa_model *kmodel = nullptr;
+    std::vector<int> ksrc;  // 0: theta or white, 1: kappa_P solver, 2: learned model
 
     void *alloc(size_t bytes)
     {
@@ -547,7 +550,17 @@ int rebuild_filters(qtb_ctx *c)
         sp.n = 1024;
         sp.ymax = 1000.0;
         sp.y0 = 1.0;
-        if (h.mode == QTB_NOISE_QTB_PIMD) {
+        c->ksrc[s] = (h.mode == QTB_NOISE_QTB_PIMD) ? 1 : 0;
+        if (h.mode == QTB_NOISE_QTB_PIMD_MLP) {
+            // the learned model where the solver judged it within tolerance, else the solver
+            if (h.P >= 2 && kappa_model_accepts(c->kmodel, h.P)) {
+                c->ksrc[s] = 2;
+            } else {
+                sp.mode = QTB_NOISE_QTB_PIMD;
+                c->ksrc[s] = 1;
+            }
+        }
+        if (sp.mode == QTB_NOISE_QTB_PIMD) {
             int rc = ensure_kappa(c, h.P);
             if (rc) return rc;
             sp.F = c->kappaF[h.P];
@@ -564,7 +577,7 @@ int rebuild_filters(qtb_ctx *c)
         c->taps_cap = tot;
     }
     CUDA_TRY(cudaMemcpyAsync(c->dspec, spec.data(), sizeof(DSpec) * ns, cudaMemcpyHostToDevice, c->st));
-    launch_spectrum_taps(c->dspec, ns, Kmax, c->dS, c->d_taps64, c->d_taps32, c->st);
+    launch_spectrum_taps(c->dspec, ns, Kmax, c->dS, c->d_taps64, c->d_taps32, kappa_model_weights(c->kmodel), c->st);
     CUDA_TRY(cudaGetLastError());
     // ring geometry
     const int Kb = (Kmax + kBlockSteps - 1) / kBlockSteps;
@@ -731,6 +744,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     std::map<int, int> nm_off;
     std::vector<double> nmC_host;
     c->hs.resize(n_sys);
+    c->ksrc.assign(n_sys, 0);
     c->ds.resize(n_sys);
     // Cell geometry: cells >= r_cut/2 with a 5^3 stencil for the staged force
     // kernel; cells >= r_cut (27 stencil) for the unstaged kernel when a staged
@@ -986,7 +1000,7 @@ int qtb_set_filter(qtb_ctx *c, int sys, int mode, int n_taps, double omega_max)
 {
     if (!c) return fail(QTB_ERR_ARG, "null context");
     if (mode < 0 || mode > 3) return fail(QTB_ERR_ARG, "unknown noise mode %d", mode);
-    if (mode == QTB_NOISE_QTB_PIMD_MLP) return fail(QTB_ERR_STATE, "no learned kappa_P model is set");
+    if (mode == QTB_NOISE_QTB_PIMD_MLP && !c->kmodel) return fail(QTB_ERR_STATE, "no learned kappa_P model is set");
     if (mode != QTB_NOISE_WHITE && (n_taps < 1 || n_taps % 2 == 0))
         return fail(QTB_ERR_ARG, "n_taps must be odd and >= 1");
     const int ns = (int)c->hs.size();
@@ -1177,6 +1191,21 @@ int qtb_kernel_times(qtb_ctx *c, double *mean_ms, int *counts, int n_classes)
     }
     for (int k = 0; k < n_classes; ++k)
         if (counts[k]) mean_ms[k] /= counts[k];
+    return QTB_OK;
+}
+
+int qtb_set_kappa_model(qtb_ctx *c, const qtb_kappa_model *model)
+{
+    if (!c) return fail(QTB_ERR_ARG, "null context");
+    c->kmodel = model;
+    return QTB_OK;
+}
+
+int qtb_filter_source(qtb_ctx *c, int sys, int *source)
+{
+    if (!c || !source) return fail(QTB_ERR_ARG, "null argument");
+    if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
+    *source = c->ksrc[sys];
     return QTB_OK;
 }
 

@@ -172,7 +172,9 @@ __global__ void k_spectrum(const DSpec *spec, double *S)
     int L = 2 * sp.K + 1;
     double w = 2.0 * kPi * j / (L * sp.dt);
     double base;
-    if (sp.mode == QTB_NOISE_WHITE) {
+    if (sp.mode == QTB_NOISE_QTB_PIMD_MLP) {
+        return;  // filled by the learned model's spectrum kernel (mlp.cu)
+    } else if (sp.mode == QTB_NOISE_WHITE) {
         base = kBoltz * sp.T;
     } else if (sp.mode == QTB_NOISE_QTB) {
         base = theta_dev(w, sp.T);
@@ -357,9 +359,10 @@ cudaError_t filter_simt_prepare(int Kmax)
 }
 
 void launch_spectrum_taps(const DSpec *spec, int nsys, int Kmax, double *S, double *h64, float *h32,
-                          cudaStream_t st)
+                          const float *mlp_w, cudaStream_t st)
 {
     k_spectrum<<<dim3((Kmax + 1 + 255) / 256, nsys), 256, 0, st>>>(spec, S);
+    if (mlp_w) launch_spectrum_mlp(spec, nsys, Kmax, S, mlp_w, st);
     k_taps<<<dim3((Kmax + 1 + 127) / 128, nsys), 128, 0, st>>>(spec, S, h64, h32);
 }
 

@@ -19,12 +19,19 @@ struct DSpec {
 // capi.cu: record the message returned by qtb_last_error(); returns code
 int set_last_error(int code, const char *msg);
 
+// mlp.cu: learned kappa_P model (device weights, solver-judged acceptance per P)
+const float *kappa_model_weights(const qtb_kappa_model *M);
+bool kappa_model_accepts(const qtb_kappa_model *M, int P);
+
 // noise.cu
 void launch_white(const Dev &d, int filter_kind, int max_dofp, int nsys, long long blk, cudaStream_t st);
 void launch_filter_simt(const Dev &d, int filter_kind, int max_dofp, int nsys, int Kmax, cudaStream_t st);
 cudaError_t filter_simt_prepare(int Kmax);
 void launch_spectrum_taps(const DSpec *spec, int nsys, int Kmax, double *S, double *h64, float *h32,
-                          cudaStream_t st);
+                          const float *mlp_w, cudaStream_t st);
+
+// mlp.cu: spectrum S_j = kT f(y_j) ratio_model(y_j, P) W(w_j) for systems in the learned mode
+void launch_spectrum_mlp(const DSpec *spec, int nsys, int Kmax, double *S, const float *w, cudaStream_t st);
 void launch_kappa_solve(int P, int n, double ymax, double y0, double *A, double *b, double *M, double *r,
                         unsigned *err, cudaStream_t st);
 

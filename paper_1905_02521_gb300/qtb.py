@@ -85,6 +85,16 @@ def lib():
             "qtb_kernel_times": ([vp, vp, vp, i], i),
             "qtb_kappa_solve": ([i, i, d, d, vp], i),
             "qtb_kappa_solve_noalloc": ([i, i, d, d, vp, vp], i),
+            "qtb_kappa_model_create": ([C.POINTER(vp), C.c_ulonglong], i),
+            "qtb_kappa_model_train": ([vp, vp, i, i, i, d], i),
+            "qtb_kappa_model_grad": ([vp, vp, vp, i, vp, vp], i),
+            "qtb_kappa_model_eval": ([vp, i, vp, i, vp], i),
+            "qtb_kappa_model_get_weights": ([vp, vp, i], i),
+            "qtb_kappa_model_set_weights": ([vp, vp, i], i),
+            "qtb_kappa_model_info": ([vp, vp, vp, i, C.POINTER(i), C.POINTER(d), C.POINTER(d)], i),
+            "qtb_kappa_model_destroy": ([vp], None),
+            "qtb_set_kappa_model": ([vp, vp], i),
+            "qtb_filter_source": ([vp, i, C.POINTER(i)], i),
             "qtb_destroy": ([vp], None),
             "qtb_last_error": ([], C.c_char_p),
         }
@@ -276,6 +286,72 @@ def qtb_kappa_solve(P, n=1024, y_max=1000.0, y0=1.0):
 def qtb_kappa_solve_noalloc(P, n, y_max, y0, F_dev_ptr, stream=None):
     """F_dev_ptr: device address of a caller-owned [n] float64 buffer."""
     _check(lib().qtb_kappa_solve_noalloc(P, n, y_max, y0, F_dev_ptr, stream))
+
+
+NPARAM = 4417
+
+
+def qtb_kappa_model_create(seed=1):
+    h = C.c_void_p()
+    _check(lib().qtb_kappa_model_create(C.byref(h), int(seed)))
+    return h.value
+
+
+def qtb_kappa_model_train(model, P_list, n_per_P=3200, iters=4000, tol=2e-3):
+    P = np.ascontiguousarray(P_list, np.int32)
+    _check(lib().qtb_kappa_model_train(model, P.ctypes.data, len(P), n_per_P, iters, tol))
+
+
+def qtb_kappa_model_grad(model, x, t):
+    x = np.ascontiguousarray(x, np.float32)
+    t = np.ascontiguousarray(t, np.float32)
+    g = np.zeros(NPARAM, np.float32)
+    loss = np.zeros(1, np.float32)
+    _check(lib().qtb_kappa_model_grad(model, x.ctypes.data, t.ctypes.data, len(t), g.ctypes.data, loss.ctypes.data))
+    return float(loss[0]), g
+
+
+def qtb_kappa_model_eval(model, P, y):
+    y = np.ascontiguousarray(y, np.float64)
+    r = np.zeros_like(y)
+    _check(lib().qtb_kappa_model_eval(model, int(P), y.ctypes.data, len(y), r.ctypes.data))
+    return r
+
+
+def qtb_kappa_model_get_weights(model):
+    w = np.zeros(NPARAM, np.float32)
+    _check(lib().qtb_kappa_model_get_weights(model, w.ctypes.data, NPARAM))
+    return w
+
+
+def qtb_kappa_model_set_weights(model, w):
+    w = np.ascontiguousarray(w, np.float32)
+    _check(lib().qtb_kappa_model_set_weights(model, w.ctypes.data, len(w)))
+
+
+def qtb_kappa_model_info(model, max_p=64):
+    P = np.zeros(max_p, np.int32)
+    e = np.zeros(max_p)
+    n = C.c_int(0)
+    ms, loss = C.c_double(0), C.c_double(0)
+    _check(lib().qtb_kappa_model_info(model, P.ctypes.data, e.ctypes.data, max_p, C.byref(n), C.byref(ms),
+                                      C.byref(loss)))
+    return {"P": P[:n.value].tolist(), "err": e[:n.value].tolist(), "train_ms": ms.value, "loss": loss.value}
+
+
+def qtb_kappa_model_destroy(model):
+    if model:
+        lib().qtb_kappa_model_destroy(model)
+
+
+def qtb_set_kappa_model(ctx, model):
+    _check(lib().qtb_set_kappa_model(ctx, model))
+
+
+def qtb_filter_source(ctx, sys):
+    s = C.c_int(0)
+    _check(lib().qtb_filter_source(ctx, sys, C.byref(s)))
+    return s.value
 
 
 def qtb_destroy(ctx):
