@@ -43,7 +43,7 @@ typedef enum {
     QTB_ERR_TIMEOUT = -4,   /* reserved: a bounded device wait gave up          */
     QTB_ERR_NONFINITE = -5, /* a force or velocity became NaN/Inf               */
     QTB_ERR_SOLVE = -6,     /* kappa_P solve failed (non-positive pivot or PSD) */
-    QTB_ERR_OVERFLOW = -7,  /* a cell of the cell list overflowed its capacity  */
+    QTB_ERR_OVERFLOW = -7,  /* a cell or a neighbour list overflowed its capacity */
     QTB_ERR_STATE = -8      /* call not valid in the current state              */
 } qtb_status;
 
@@ -108,6 +108,11 @@ typedef struct {
     qtb_alloc_fn dev_alloc;  /* optional device allocator                          */
     qtb_free_fn dev_free;    /* its matching free                                  */
     void *alloc_user;        /* passed to both                                     */
+    double skin;           /* PAIR: Verlet-list skin, A, < r_cut/2.  Lists hold every
+                              pair within r_cut + skin and are rebuilt (on the device)
+                              once some bead-atom has moved skin/2 since the last
+                              rebuild.  0 selects min(0.8, r_cut/4); < 0: no skin.
+                              Forces do not depend on it (up to summation order). */
 } qtb_params;
 
 /* Observable record (FP64), one per recorded step and system:
@@ -170,14 +175,20 @@ int qtb_get_taps(qtb_ctx *c, int sys, double *h, int max, int *n_out);
 int qtb_get_noise(qtb_ctx *c, int sys, double *out, long long *block_out);
 
 /* Profiling of whole 256-step blocks: when enabled, the captured block records
- * a CUDA event pair around every kernel launch (classes: 0 white noise,
- * 1 filter, 2 integrator, 3 cell list, 4 force, 5 reduction).  Takes effect at
- * the next block. */
+ * a CUDA event pair around the launches of every 16th step and around the
+ * per-block noise launches (classes: 0 white noise, 1 filter, 2 integrator,
+ * 3 neighbour-list rebuild branch, 4 force (for one-bead systems with the
+ * first half of the next step fused in), 5 reduction).  Takes effect at the
+ * next block. */
 int qtb_set_profiling(qtb_ctx *c, int enable);
 
 /* Mean device time (ms) and launch count per kernel class over the last
  * profiled block (synchronises).  mean_ms, counts: [n_classes]. */
 int qtb_kernel_times(qtb_ctx *c, double *mean_ms, int *counts, int n_classes);
+
+/* Number of neighbour-list rebuilds carried out so far (PAIR; 0 otherwise),
+ * the one made by qtb_init / qtb_set_state included.  Synchronises. */
+int qtb_list_rebuilds(qtb_ctx *c, long long *count);
 
 /* Current step index (number of steps taken). */
 int qtb_get_step(qtb_ctx *c, long long *step);

@@ -19,6 +19,9 @@ OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libqtb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# md.cu writes every fused multiply-add out explicitly (the integrator and the
+# fused force epilogue must round alike): no automatic contraction there
+EXTRA = {"md.cu": ["--fmad=false"]}
 
 
 def nvcc() -> str:
@@ -39,7 +42,7 @@ def _headers():
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-           "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
+           "-I", os.path.join(ROOT, "include"), *EXTRA.get(os.path.basename(src), []), "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

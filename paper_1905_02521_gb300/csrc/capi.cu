@@ -1,9 +1,10 @@
 // capi.cu -- host side of the C ABI declared in include/qtb.h.
 //
 // Owns the device layout of every system (bead-major SoA state, noise dofs
-// padded to tensor-core tiles, cell lists per bead replica), the noise
-// pipeline (white blocks in a ring, coloured block per 256 steps) and the
-// CUDA graph that replays one 256-step block.
+// padded to tensor-core tiles, cell and neighbour lists per bead replica), the
+// noise pipeline (white blocks in a ring, coloured block per 256 steps) and the
+// CUDA graph that replays one 256-step block, with the neighbour-list rebuild
+// of each step as a conditional node decided on the device.
 #include <cuda.h>
 #include <dlfcn.h>
 
@@ -58,6 +59,9 @@ int qtb::set_last_error(int code, const char *msg)
 
 struct qtb_ctx {
     cudaStream_t st = nullptr;
+    cudaStream_t st2 = nullptr;  // captures the bodies of the conditional rebuild nodes
+    bool cond_ok = true;         // conditional graph nodes usable (else flag-tested launches)
+    double skin = 0.0;           // neighbour-list skin, A
     qtb_params p{};
     std::vector<double> mass, charge, bA, brho, bC;
     bool mixed = false, pair = true;
@@ -66,7 +70,7 @@ struct qtb_ctx {
     std::vector<HSys> hs;
     std::vector<DSys> ds;
     std::vector<DRep> dr;
-    std::vector<int> cell_rep, icta_sys;
+    std::vector<int> cell_rep, icta_sys, lcta_rep;
     Dev d{};
     MdLaunch ml{};
     PairTab tab{};
@@ -138,6 +142,7 @@ struct qtb_ctx {
             else cudaFree(ptr);
         }
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (st2) cudaStreamDestroy(st2);
         if (own_stream) cudaStreamDestroy(st);
     }
 };
@@ -205,6 +210,8 @@ int check_err_word(qtb_ctx *c)
     CUDA_TRY(cudaMemcpyAsync(&e, c->d.err, sizeof e, cudaMemcpyDeviceToHost, c->st));
     CUDA_TRY(cudaStreamSynchronize(c->st));
     if (e & ERR_OVERFLOW) return fail(QTB_ERR_OVERFLOW, "a cell-list cell exceeded its capacity (%d)", c->d.cap);
+    if (e & ERR_NBR_OVERFLOW)
+        return fail(QTB_ERR_OVERFLOW, "a neighbour list exceeded its capacity (%d entries)", c->d.maxnb);
     if (e & ERR_NONFINITE) return fail(QTB_ERR_NONFINITE, "non-finite energy: the integration blew up");
     if (e & ERR_SOLVE) return fail(QTB_ERR_SOLVE, "kappa_P solve: non-positive pivot");
     if (e & ERR_TIMEOUT_TC) return fail(QTB_ERR_TIMEOUT, "tensor-core filter: a bounded barrier wait gave up");
@@ -282,8 +289,9 @@ int download(qtb_ctx *c, int s, int which, double *out)
             std::vector<int> buf(NP);
             CUDA_TRY(cudaMemcpyAsync(buf.data(), (int *)c->d.x + comp * G + S.g0, NP * 4, cudaMemcpyDeviceToHost, c->st));
             CUDA_TRY(cudaStreamSynchronize(c->st));
+            // positions move unwrapped between list rebuilds: report them in [0, L)
             const double sc = h.box[comp] / (double)(1 << kFixBits);
-            for (size_t t = 0; t < NP; ++t) out[t * 3 + comp] = (double)buf[t] * sc;
+            for (size_t t = 0; t < NP; ++t) out[t * 3 + comp] = (double)(buf[t] & ((1 << kFixBits) - 1)) * sc;
         } else {
             const void *src = (which == 0) ? c->d.x : (which == 1) ? c->d.v : c->d.f;
             const bool f32 = c->mixed;  // positions of PAIR+MIXED handled above
@@ -296,7 +304,16 @@ int download(qtb_ctx *c, int s, int which, double *out)
                 std::vector<double> buf(NP);
                 CUDA_TRY(cudaMemcpyAsync(buf.data(), (const double *)src + comp * G + S.g0, NP * 8, cudaMemcpyDeviceToHost, c->st));
                 CUDA_TRY(cudaStreamSynchronize(c->st));
-                for (size_t t = 0; t < NP; ++t) out[t * 3 + comp] = buf[t];
+                const double L = h.box[comp];
+                const bool wrap = (which == 0 && c->pair);
+                for (size_t t = 0; t < NP; ++t) {
+                    double x = buf[t];
+                    if (wrap) {
+                        x -= L * std::floor(x / L);
+                        if (x >= L || x < 0) x = 0;
+                    }
+                    out[t * 3 + comp] = x;
+                }
             }
         }
     }
@@ -313,14 +330,19 @@ void set_clock(qtb_ctx *c, long long b)
     }
 }
 
-// forces (and energies) at the current positions; no velocity kick
+// forces (and energies) at the current positions, lists rebuilt; no velocity kick
 int refresh_forces(qtb_ctx *c)
 {
     set_clock(c, floor_div(c->step, kBlockSteps));
     const int j = (int)(c->step - c->dclock * kBlockSteps) - 1;
-    launch_cells(c->d, c->ml, c->st);
-    launch_force_kick(c->d, c->ml, c->tabf, c->tab, 0, j, c->st);
-    if (!c->ml.staged) launch_reduce(c->d, c->ml, j, -1, c->st);  // the staged force kernel reduces itself
+    const int cur = (int)(c->step & 1);  // positions of step s live in pos[s & 1]
+    if (c->pair) {
+        CUDA_TRY(cudaMemsetAsync(c->d.flag, 0, 2 * sizeof(unsigned), c->st));
+        CUDA_TRY(cudaMemsetAsync(c->d.flag + cur, 1, 1, c->st));
+        launch_rebuild(c->d, c->ml, c->tabf, c->tab, cur, c->st);
+    }
+    launch_force(c->d, c->ml, c->tabf, c->tab, 0, j, cur, 0, 1, 0, c->st);
+    if (!c->pair) launch_reduce(c->d, c->ml, j, -1, c->st);  // the list force kernel reduces itself
     CUDA_TRY(cudaGetLastError());
     return QTB_OK;
 }
@@ -462,20 +484,114 @@ ProfMark::~ProfMark()
     c->ev_used += 2;
 }
 
-// Per-step kernels.  Profiling samples every 16th step of a captured block
-// (event nodes cost about a microsecond each, so they are not put on every launch).
-void one_step(qtb_ctx *c, int j)
+// A conditional handle of the graph being captured on c->st (0 when
+// conditional nodes are not in use).
+cudaError_t new_cond(qtb_ctx *c, cudaGraphConditionalHandle *h)
 {
-    const bool keep = c->capturing;
-    if (j % 16 != 0) c->capturing = false;
-    { ProfMark m(c, KC_INTEGRATE); launch_integrate(c->d, c->ml, j, c->st); }
-    { ProfMark m(c, KC_CELLS); launch_cells(c->d, c->ml, c->st); }
-    { ProfMark m(c, KC_FORCE); launch_force_kick(c->d, c->ml, c->tabf, c->tab, 1, j, c->st); }
-    if (!c->ml.staged) {
-        ProfMark m(c, KC_REDUCE);
-        launch_reduce(c->d, c->ml, j, 1, c->st);
+    *h = 0;
+    if (!c->cond_ok) return cudaSuccess;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(c->st, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    return cudaGraphConditionalHandleCreate(h, g, 0, 0);
+}
+
+// The rebuild of the step whose positions are in pos[cur]: inside a capture an
+// IF node on the handle the producing kernel sets (body: bin, sort, build,
+// captured on c->st2); otherwise the three launches, which test the request.
+cudaError_t rebuild_step(qtb_ctx *c, int cur, cudaGraphConditionalHandle h)
+{
+    if (!h) {
+        launch_rebuild(c->d, c->ml, c->tabf, c->tab, cur, c->st);
+        return cudaGetLastError();
     }
-    c->capturing = keep;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(c->st, &cs, nullptr, &g, &deps, &ed, &nd);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, deps, ed, nd, &np);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamUpdateCaptureDependencies(c->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCaptureToGraph(c->st2, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    launch_rebuild(c->d, c->ml, c->tabf, c->tab, cur, c->st2);
+    cudaGraph_t body = nullptr;
+    return cudaStreamEndCapture(c->st2, &body);
+}
+
+// Steps j0 .. j0+count-1 of the current block, captured (graph) or launched.
+// Positions of step s are in pos[s & 1].  Unfused: integrate, rebuild, force.
+// Fused (one-bead systems): integrate once, then rebuild + force per step, each
+// force launch but the last also doing the first half of the next step.
+// Profiling samples every 16th step of a captured block (event nodes cost
+// about a microsecond each, so they are not put on every launch).
+int run_steps(qtb_ctx *c, int j0, int count, bool graph)
+{
+    const MdLaunch &m = c->ml;
+    const int obs = c->p.obs_stride;
+    cudaGraphConditionalHandle h = 0;
+    for (int t = 0; t < count; ++t) {
+        const int j = j0 + t, cur = j & 1;
+        const bool keep = c->capturing;
+        if (j % 16 != 0) c->capturing = false;
+        if (!m.fused || t == 0) {
+            if (graph && m.pair) CUDA_TRY(new_cond(c, &h));
+            ProfMark pm(c, KC_INTEGRATE);
+            launch_integrate(c->d, m, j, cur, h, c->st);
+        }
+        if (m.pair) {
+            ProfMark pm(c, KC_CELLS);
+            CUDA_TRY(rebuild_step(c, cur, h));
+        }
+        const int adv = (m.fused && t < count - 1) ? 1 : 0;
+        cudaGraphConditionalHandle hn = 0;
+        if (adv && graph) CUDA_TRY(new_cond(c, &hn));
+        // may this step be recorded? (inside the graph the block index is only known on the device)
+        int rec;
+        if (graph) rec = (kBlockSteps % obs == 0) ? ((j + 1) % obs == 0) : 1;
+        else rec = ((c->step + t + 1) % obs == 0) ? 1 : 0;
+        {
+            ProfMark pm(c, KC_FORCE);
+            launch_force(c->d, m, c->tabf, c->tab, 1, j, cur, adv, rec, hn, c->st);
+        }
+        if (!m.pair) {
+            ProfMark pm(c, KC_REDUCE);
+            launch_reduce(c->d, m, j, 1, c->st);
+        }
+        h = hn;
+        c->capturing = keep;
+    }
+    return QTB_OK;
+}
+
+int capture_block(qtb_ctx *c, cudaGraph_t *g)
+{
+    CUDA_TRY(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    c->ev_used = 0;
+    int rc;
+    { ProfMark m(c, KC_WHITE); gen_white(c, LLONG_MIN); }  // block clock + Kb
+    { ProfMark m(c, KC_FILTER); filter_block(c); }
+    rc = run_steps(c, 0, kBlockSteps, true);
+    launch_tick(c->d, c->st);
+    c->capturing = false;
+    c->ev_pairs = c->ev_used / 2;
+    cudaError_t e = cudaStreamEndCapture(c->st, g);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(QTB_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    return QTB_OK;
 }
 
 int build_graph(qtb_ctx *c)
@@ -484,20 +600,21 @@ int build_graph(qtb_ctx *c)
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
     }
-    cudaGraph_t g;
-    CUDA_TRY(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
-    c->capturing = true;
-    c->ev_used = 0;
-    { ProfMark m(c, KC_WHITE); gen_white(c, LLONG_MIN); }  // block clock + Kb
-    { ProfMark m(c, KC_FILTER); filter_block(c); }
-    for (int j = 0; j < kBlockSteps; ++j) one_step(c, j);
-    launch_tick(c->d, c->st);
-    c->capturing = false;
-    c->ev_pairs = c->ev_used / 2;
-    cudaError_t e = cudaStreamEndCapture(c->st, &g);
-    if (e != cudaSuccess) return fail(QTB_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&c->gexec, g, 0);
-    cudaGraphDestroy(g);
+    cudaGraph_t g = nullptr;
+    int rc = capture_block(c, &g);
+    cudaError_t e = cudaSuccess;
+    if (rc == QTB_OK) {
+        e = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+    }
+    if ((rc != QTB_OK || e != cudaSuccess) && c->cond_ok) {
+        // conditional nodes refused: capture again with flag-tested rebuild launches
+        cudaGetLastError();
+        c->gexec = nullptr;
+        c->cond_ok = false;
+        return build_graph(c);
+    }
+    if (rc) return rc;
     if (e != cudaSuccess) return fail(QTB_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
     c->graph_dirty = false;
     return QTB_OK;
@@ -609,6 +726,13 @@ int rebuild_filters(qtb_ctx *c)
     return QTB_OK;
 }
 
+// skin of the neighbour lists: 0 selects min(0.8 A, r_cut/4), < 0 means none
+double effective_skin(const qtb_params *p)
+{
+    if (p->skin == 0.0) return std::min(0.8, 0.25 * p->r_cut);
+    return p->skin < 0.0 ? 0.0 : p->skin;
+}
+
 int validate(const qtb_system *sys, int n_sys, const qtb_params *p)
 {
     if (!sys || n_sys < 1 || !p) return fail(QTB_ERR_ARG, "qtb_init: need n_sys >= 1 systems and params");
@@ -622,10 +746,12 @@ int validate(const qtb_system *sys, int n_sys, const qtb_params *p)
     if (p->potential == QTB_POT_PAIR) {
         if (!p->charge || !p->buck_A || !p->buck_rho || !p->buck_C) return fail(QTB_ERR_ARG, "pair tables missing");
         if (!(p->r_cut > 0)) return fail(QTB_ERR_ARG, "r_cut must be > 0");
+        if (!(effective_skin(p) < 0.5 * p->r_cut)) return fail(QTB_ERR_ARG, "skin must be < r_cut/2");
     }
     for (int s = 0; s < n_sys; ++s) {
         const qtb_system &q = sys[s];
         if (q.n_atoms < 1 || q.n_beads < 1) return fail(QTB_ERR_ARG, "system %d: n_atoms, n_beads >= 1", s);
+        if (q.n_atoms > (int)kNbIdx) return fail(QTB_ERR_ARG, "system %d: more than 2^26 - 1 atoms", s);
         if (!md_supported_P(q.n_beads)) return fail(QTB_ERR_ARG, "system %d: n_beads %d not supported (1-6, 8, 16, 32)", s, q.n_beads);
         if (!q.type || !q.pos) return fail(QTB_ERR_ARG, "system %d: type and pos required", s);
         if (!(q.T > 0) || !(q.gamma >= 0)) return fail(QTB_ERR_ARG, "system %d: T > 0, gamma >= 0", s);
@@ -662,7 +788,12 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         }
         c->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return fail(QTB_ERR_CUDA, "cudaStreamCreate failed");
+    }
     c->p = *p;
+    c->skin = effective_skin(p);
     const int nt = p->n_types;
     c->mass.assign(p->mass, p->mass + nt);
     c->mixed = (p->precision == QTB_MIXED);
@@ -695,6 +826,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         T.alpha2 = al * al;
         T.two_a_sqrtpi = 2.0 * al / std::sqrt(kPi);
         T.erfc_rc_over_rc = std::erfc(al * rc_) / rc_;
+        T.rl2 = (rc_ + c->skin) * (rc_ + c->skin);
         T.fshift = std::erfc(al * rc_) / (rc_ * rc_) + 2.0 * al / std::sqrt(kPi) * std::exp(-al * al * rc_ * rc_) / rc_;
         for (int a = 0; a < nt; ++a)
             for (int b = 0; b < nt; ++b) {
@@ -728,8 +860,8 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         F.ext_V0 = (float)T.ext_V0; F.ext_ia2 = (float)T.ext_ia2;
         F.ntypes = T.ntypes; F.potential = T.potential;
         const double log2e = 1.4426950408889634;
-        for (int t = 0; t < NT; ++t) F.inv_rho_l2e[t] = (float)(T.inv_rho[t] * log2e);
         F.alpha2_l2e = (float)(T.alpha2 * log2e);
+        F.rl2 = (float)T.rl2;
         const double xmax = T.alpha * T.rc;
         F.erfc_us = (xmax > 0.0) ? (float)(2.0 / xmax) : 0.0f;
         double cfit[12];
@@ -746,9 +878,10 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     c->hs.resize(n_sys);
     c->ksrc.assign(n_sys, 0);
     c->ds.resize(n_sys);
-    // Cell geometry: cells >= r_cut/2 with a 5^3 stencil for the staged force
-    // kernel; cells >= r_cut (27 stencil) for the unstaged kernel when a staged
-    // neighbourhood would not fit in shared memory.
+    // Neighbour lists within r_list = r_cut + skin, built from cells >=
+    // r_list/2 with a 5^3 stencil whose neighbourhood streams through shared
+    // memory in chunks.
+    const double r_list = p->r_cut + c->skin;
     auto cell_cap = [&](const qtb_system &q, double edge) {
         int nc[3];
         for (int k = 0; k < 3; ++k) nc[k] = std::max(1, (int)std::floor(q.box[k] / edge));
@@ -756,26 +889,24 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         int cp = (int)roundup((long long)std::ceil(1.25 * e + 4.0 * std::sqrt(e) + 8.0), 8);
         return std::min(cp, (int)roundup(q.n_atoms, 8));
     };
-    double cell_edge = p->r_cut;
-    bool staged = false;
-    int stage_cap = 0;
+    const double cell_edge = 0.5 * r_list;
+    int stage_cap = 0, maxnb = 32;
     if (c->pair) {
-        // staged entries per CTA: twice the expected neighbourhood population plus a
-        // margin, never more than 125 full cells (a larger population is reported
-        // as QTB_ERR_OVERFLOW)
-        int cap2 = 8;
         double ecell = 0.0;
+        const double vlist = 4.0 / 3.0 * kPi * r_list * r_list * r_list;
         for (int s = 0; s < n_sys; ++s) {
-            cap2 = std::max(cap2, cell_cap(sys[s], 0.5 * p->r_cut));
             int nc[3];
-            for (int k = 0; k < 3; ++k) nc[k] = std::max(1, (int)std::floor(sys[s].box[k] / (0.5 * p->r_cut)));
+            for (int k = 0; k < 3; ++k) nc[k] = std::max(1, (int)std::floor(sys[s].box[k] / cell_edge));
             ecell = std::max(ecell, (double)sys[s].n_atoms / (nc[0] * nc[1] * nc[2]));
+            // list capacity: 1.5 x the mean population of the list sphere plus a margin
+            const double rho = sys[s].n_atoms / (sys[s].box[0] * sys[s].box[1] * sys[s].box[2]);
+            maxnb = std::max(maxnb, (int)roundup((long long)std::ceil(1.5 * rho * vlist + 64.0), 32));
         }
-        stage_cap = (int)std::min(roundup((long long)kStencilCells * cap2, 64),
-                                  roundup((long long)std::ceil(2.0 * kStencilCells * ecell) + 256, 64));
-        staged = force_staged_smem(stage_cap, c->mixed ? 1 : 0) <= 190 * 1024;
-        if (staged) cell_edge = 0.5 * p->r_cut;
+        // staging chunk: 1.5 x the mean stencil population plus a margin, at
+        // most 4096 entries (larger neighbourhoods take several chunks)
+        stage_cap = (int)std::min(roundup((long long)std::ceil(1.5 * kStencilCells * ecell) + 128, 64), 4096LL);
     }
+    int nlcta = 0;
     for (int s = 0; s < n_sys; ++s) {
         const qtb_system &q = sys[s];
         HSys &h = c->hs[s];
@@ -797,7 +928,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         G += (long long)h.N * h.P;
         D += S.dofp;
         S.icta0 = icta;
-        icta += (int)((3LL * h.N + 127) / 128);
+        icta += (h.N + kIntAtomsPerCta - 1) / kIntAtomsPerCta;
         S.icta1 = icta;
         for (int k = 0; k < 3; ++k) S.box[k] = q.box[k];
         S.T = q.T;
@@ -807,6 +938,8 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         S.invP = 1.0 / h.P;
         S.invP_f = (float)S.invP;
         S.c1_f = (float)S.c1;
+        S.skin2 = 0.25 * c->skin * c->skin;
+        S.skin2_f = (float)S.skin2;
         for (int k = 0; k < 3; ++k) {
             S.fix_scale[k] = (float)(q.box[k] / (double)(1 << kFixBits));
             S.fix_inv[k] = (q.box[k] > 0) ? (float)((double)(1 << kFixBits) / q.box[k]) : 0.f;
@@ -842,30 +975,31 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
                 }
                 R.cell0 = ncells;
                 ncells += cells;
+                R.fcta0 = nlcta;
+                const int nl = (h.N + kListWarps - 1) / kListWarps;
+                nlcta += nl;
                 c->dr.push_back(R);
                 for (int t = 0; t < cells; ++t) c->cell_rep.push_back(nrep);
+                for (int t = 0; t < nl; ++t) c->lcta_rep.push_back(nrep);
                 ++nrep;
             }
         }
     }
-    if (cap > 512) return bail(fail(QTB_ERR_ARG, "cell capacity %d > 512: box too dense for r_cut-sized cells", cap));
+    if (cap > kMaxCellCap)
+        return bail(fail(QTB_ERR_ARG, "cell capacity %d > %d: box too dense for (r_cut + skin)/2 cells", cap, kMaxCellCap));
     for (int s = 0; s < n_sys; ++s)
         for (int t = c->ds[s].icta0; t < c->ds[s].icta1; ++t) c->icta_sys.push_back(s);
-    // force CTA ranges: one CTA per cell (staged) or cap/8 CTAs per cell
-    const int cpc = staged ? 1 : cap / kWarpsPerForceCta;
-    c->ml.staged = staged ? 1 : 0;
-    if (staged && force_staged_prepare(stage_cap, c->mixed ? 1 : 0) != cudaSuccess)
-        return bail(fail(QTB_ERR_CUDA, "cannot reserve shared memory for the force kernel"));
+    if (c->pair && list_build_prepare(stage_cap, c->mixed ? 1 : 0) != cudaSuccess)
+        return bail(fail(QTB_ERR_CUDA, "cannot reserve shared memory for the list build kernel"));
     int ext_gx = 0;
     for (int s = 0; s < n_sys; ++s) ext_gx = std::max(ext_gx, (c->hs[s].N * c->hs[s].P + 127) / 128);
     long long nforce = 0;
     for (int s = 0; s < n_sys; ++s) {
         DSys &S = c->ds[s];
         if (c->pair) {
-            const DRep &R0 = c->dr[S.rep0];
-            const int cells = R0.nc[0] * R0.nc[1] * R0.nc[2];
-            S.fcta0 = R0.cell0 * cpc;
-            S.fcta1 = (R0.cell0 + cells * c->hs[s].P) * cpc;
+            // the system's replicas are consecutive, and so are their list force CTAs
+            S.fcta0 = c->dr[S.rep0].fcta0;
+            S.fcta1 = c->dr[S.rep0 + c->hs[s].P - 1].fcta0 + (c->hs[s].N + kListWarps - 1) / kListWarps;
             nforce = S.fcta1;
         } else {
             S.fcta0 = s * ext_gx;
@@ -880,7 +1014,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     d.ncells = ncells;
     d.cap = cap;
     d.stage_cap = stage_cap;
-    d.cpc = cpc;
+    d.maxnb = maxnb;
     d.G = G;
     d.Dtot = D;
     d.obs_stride = p->obs_stride;
@@ -895,6 +1029,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     m.n_icta = icta;
     m.n_bcta = (maxN + 255) / 256;
     m.n_ecta = ext_gx;
+    m.n_lcta = nlcta;
     m.nP = 0;
     for (int s = 0; s < n_sys; ++s) {
         bool seen = false;
@@ -904,6 +1039,9 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
             m.Pvals[m.nP++] = c->hs[s].P;
         }
     }
+    m.fused = c->pair ? 1 : 0;
+    for (int s = 0; s < n_sys; ++s)
+        if (c->hs[s].P != 1) m.fused = 0;
 
     // tables
     std::vector<double> rot;
@@ -948,6 +1086,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     d.typ = upload(c, typ);
     d.rep = upload(c, c->dr);
     d.cell_rep = upload(c, c->cell_rep);
+    d.lcta_rep = upload(c, c->lcta_rep);
     d.icta_sys = upload(c, c->icta_sys);
     d.sys = upload(c, c->ds);
     const size_t psz = c->pair && c->mixed ? 4 : c->rsz;
@@ -958,6 +1097,35 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     d.ccount = (int *)c->alloc(sizeof(int) * std::max(ncells, 1));
     d.cidx = (int *)c->alloc(sizeof(int) * (size_t)std::max(ncells, 1) * cap);
     d.cpos = c->alloc((c->mixed ? 16 : 32) * (size_t)std::max(ncells, 1) * cap);
+    if (c->pair) {
+        for (int k = 0; k < 2; ++k) d.pos[k] = c->alloc((c->mixed ? 16 : 32) * (size_t)G);
+        d.xref = c->alloc(psz * 3 * (size_t)G);
+        d.nbr = (unsigned *)c->alloc(sizeof(unsigned) * (size_t)G * maxnb);
+        d.nnb = (int *)c->alloc(sizeof(int) * (size_t)G);
+        if (!d.pos[0] || !d.pos[1] || !d.xref || !d.nbr || !d.nnb)
+            return bail(fail(QTB_ERR_OOM, "neighbour-list allocation failed"));
+        // the type word of both packed position buffers (positions follow)
+        for (int k = 0; k < 2; ++k) {
+            if (c->mixed) {
+                std::vector<int4> pk((size_t)G);
+                for (size_t g = 0; g < (size_t)G; ++g) pk[g] = make_int4(0, 0, 0, typ[g]);
+                cudaMemcpyAsync(d.pos[k], pk.data(), sizeof(int4) * G, cudaMemcpyHostToDevice, c->st);
+            } else {
+                std::vector<double> pk(4 * (size_t)G, 0.0);
+                for (size_t g = 0; g < (size_t)G; ++g) pk[4 * g + 3] = (double)typ[g];
+                cudaMemcpyAsync(d.pos[k], pk.data(), sizeof(double) * 4 * G, cudaMemcpyHostToDevice, c->st);
+            }
+            if (cudaStreamSynchronize(c->st) != cudaSuccess) return bail(fail(QTB_ERR_CUDA, "upload failed"));
+        }
+        cudaMemsetAsync(d.nnb, 0, sizeof(int) * (size_t)G, c->st);
+    }
+    d.flag = (unsigned *)c->alloc(2 * sizeof(unsigned));
+    d.gdone = (unsigned *)c->alloc(sizeof(unsigned));
+    d.nrebuild = (unsigned long long *)c->alloc(sizeof(unsigned long long));
+    if (!d.flag || !d.gdone || !d.nrebuild) return bail(fail(QTB_ERR_OOM, "device allocation failed"));
+    cudaMemsetAsync(d.nrebuild, 0, sizeof(unsigned long long), c->st);
+    cudaMemsetAsync(d.flag, 0, 2 * sizeof(unsigned), c->st);
+    cudaMemsetAsync(d.gdone, 0, sizeof(unsigned), c->st);
     d.eta = c->alloc(c->rsz * (size_t)kBlockSteps * (size_t)D);
     d.part = (double *)c->alloc(sizeof(double) * kNQ * (size_t)std::max(nforce, 1LL));
     d.ipart = (double *)c->alloc(sizeof(double) * kNQ * (size_t)icta);
@@ -1044,7 +1212,8 @@ int qtb_step_n(qtb_ctx *c, long long n)
         }
         ensure_eta(c, b);
         const long long mcount = std::min<long long>(n, kBlockSteps - j);
-        for (long long t = 0; t < mcount; ++t) one_step(c, j + (int)t);
+        int rc = run_steps(c, j, (int)mcount, false);
+        if (rc) return rc;
         c->step += mcount;
         n -= mcount;
         if (j + mcount == kBlockSteps) {
@@ -1206,6 +1375,18 @@ int qtb_filter_source(qtb_ctx *c, int sys, int *source)
     if (!c || !source) return fail(QTB_ERR_ARG, "null argument");
     if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
     *source = c->ksrc[sys];
+    return QTB_OK;
+}
+
+int qtb_list_rebuilds(qtb_ctx *c, long long *count)
+{
+    if (!c || !count) return fail(QTB_ERR_ARG, "null argument");
+    unsigned long long n = 0;
+    if (c->pair) {
+        CUDA_TRY(cudaMemcpyAsync(&n, c->d.nrebuild, sizeof n, cudaMemcpyDeviceToHost, c->st));
+        CUDA_TRY(cudaStreamSynchronize(c->st));
+    }
+    *count = (long long)n;
     return QTB_OK;
 }
 

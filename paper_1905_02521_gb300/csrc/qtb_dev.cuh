@@ -23,7 +23,7 @@ constexpr int kDofPad = 128;         // per-system dof padding (tensor-core M ti
 constexpr int kNQ = 16;              // partial sums per CTA (see Q_* below)
 constexpr int kFixBits = 30;         // fixed-point positions: box edge = 2^30 units
 constexpr int kMaxTypes = 4;
-constexpr int kWarpsPerForceCta = 8;
+constexpr int kWarpsPerForceCta = 8;  // warps of the list build kernel
 
 // partial-sum slots
 enum { Q_K = 0, Q_V = 1, Q_SPRING = 2, Q_VIR = 3 /* 6 slots: xx yy zz xy xz yz */, Q_MOM = 9 /* 3 */,
@@ -33,7 +33,15 @@ enum { Q_K = 0, Q_V = 1, Q_SPRING = 2, Q_VIR = 3 /* 6 slots: xx yy zz xy xz yz *
 enum { PM_BOX64 = 0, PM_FIX = 1, PM_FREE = 2 };
 
 // device error word bits
-enum { ERR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_SOLVE = 4, ERR_TIMEOUT_TC = 8 };
+enum { ERR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_SOLVE = 4, ERR_TIMEOUT_TC = 8, ERR_NBR_OVERFLOW = 16 };
+
+// Neighbour-list entry (32 bits): replica-local index j in bits 0..25, the
+// periodic image m of the entry (per component m mod 4, two bits each: x at
+// bit 26, y at 28, z at 30).  With 30-bit fixed point the image shift is
+// (m mod 4) * 2^30, exact in wrapping 32-bit arithmetic.
+constexpr unsigned kNbIdx = (1u << 26) - 1u;
+constexpr int kMaxCellCap = 512;        // slots per cell of the cell list
+constexpr int kListWarps = 4;        // home bead-atoms (one warp each) per CTA of the list force kernel
 
 struct DSys {
     int N, P;          // atoms, beads
@@ -53,6 +61,10 @@ struct DSys {
     float fix_inv[3];        // 2^30 / box
     float invP_f, c1_f;      // 1/P, c1 in FP32
     double invP;
+    // neighbour-list validity: a bead-atom may move (skin/2) since the last
+    // rebuild; squared, in A^2
+    double skin2;
+    float skin2_f;
 };
 
 struct DRep {          // one replica (system, bead) of a pair-potential system
@@ -60,6 +72,7 @@ struct DRep {          // one replica (system, bead) of a pair-potential system
     int nc[3];         // cells per edge
     int cell0;         // first cell
     int cta0;          // first binning CTA
+    int fcta0;         // first CTA of the list force kernel (kListWarps bead-atoms each)
     double box[3];
     float fix_scale[3];  // box / 2^30
 };
@@ -72,11 +85,12 @@ template <class R> struct PairTabT {
     R qq[kMaxTypes * kMaxTypes];      // k_e q_a q_b
     R eshift[kMaxTypes * kMaxTypes];  // Buckingham energy at r_cut
     R alpha, alpha2, two_a_sqrtpi, rc, rc2, erfc_rc_over_rc, fshift;  // DSF constants
-    // FP32 form only: exp(-r/rho) = 2^(-r inv_rho log2 e); erfc(x) = exp(-x^2) P(u),
-    // u = x us - 1 in [-1, 1] on 0 <= x <= alpha r_cut, P a degree-11 least-squares
-    // fit of exp(x^2) erfc(x) made at context creation (relative error ~2e-7)
-    R inv_rho_l2e[kMaxTypes * kMaxTypes];
+    // FP32 form only: exp(-alpha^2 r^2) = 2^(-r^2 alpha^2 log2 e); erfc(x) =
+    // exp(-x^2) P(u), u = x us - 1 in [-1, 1] on 0 <= x <= alpha r_cut, P a
+    // degree-11 Chebyshev interpolant of exp(x^2) erfc(x) made at context
+    // creation (relative error ~2e-7 in FP32)
     R alpha2_l2e, erfc_us;
+    R rl2;                            // (r_cut + skin)^2: neighbour-list radius
     R erfc_c[12];
     R hdt_m[kMaxTypes];               // dt / (2 m mvv2e)
     R ext_k[kMaxTypes];               // HARMONIC: m mvv2e w0^2
@@ -90,7 +104,7 @@ typedef PairTabT<double> PairTab;
 // Everything a kernel needs, passed by value.
 struct Dev {
     // sizes
-    int nsys, nrep, ncells, cap, cpc;  // cpc = force CTAs per cell
+    int nsys, nrep, ncells, cap;
     long long G;                      // bead-atoms
     long long Dtot;                   // padded dofs
     int Kb, nslots;                   // noise ring: blocks of half-span, slots
@@ -100,6 +114,7 @@ struct Dev {
     const DSys *sys;
     const DRep *rep;
     const int *cell_rep;  // [ncells]
+    const int *lcta_rep;  // [list force CTAs] replica of each CTA
     const int *icta_sys;  // [integrator CTAs] system of each CTA
     const int *ext_cta_sys;
     // state
@@ -111,7 +126,16 @@ struct Dev {
     int *cnt;             // [ncells] running counts (binning)
     int *ccount;          // [ncells] counts after sorting
     int *cidx;            // [ncells * cap] bead-atom index, sorted
-    void *cpos;           // [ncells * cap] packed positions (int4 or double4)
+    void *cpos;           // [ncells * cap] packed {x, y, z, replica-local index} (int4 or 4 doubles)
+    // neighbour lists (pair potential)
+    void *pos[2];         // [G] packed {x, y, z, type} (int4 or 4 doubles); step s reads pos[s & 1]
+    void *xref;           // [3][G] positions at the last rebuild (type of x)
+    unsigned *nbr;        // [G][maxnb] list entries (see kNbIdx)
+    int *nnb;             // [G] entries per bead-atom
+    int maxnb;
+    unsigned *flag;       // [2] rebuild requests; flag[s & 1] is set by whoever produces the positions of step s
+    unsigned *gdone;      // CTAs finished (grid-wide last-CTA decisions), reset by the last one
+    unsigned long long *nrebuild;  // list rebuilds carried out
     // noise
     void *ring;           // [nslots][Dtot][256] white noise (double, float or bf16)
     void *eta;            // [256][Dtot] coloured noise (R)
@@ -130,7 +154,7 @@ struct Dev {
     long long *clock;     // [0] = current noise block
     unsigned *err;        // error word
     unsigned *done;       // [nsys] CTAs finished (last-CTA reduction), reset by the last one
-    int stage_cap;        // staged neighbourhood entries per CTA of the staged force kernel
+    int stage_cap;        // staged neighbourhood entries per CTA of the list build kernel
     unsigned long long seed;
     double mass_mvv[kMaxTypes];  // m * mvv2e per type (eV fs^2 / A^2)
 };

@@ -40,22 +40,31 @@ struct MdLaunch {
     int mixed;            // 0: FP64 form, 1: mixed form
     int pair;             // pair potential (else external)
     int n_icta;           // integrator CTAs
-    int n_bcta;           // binning CTAs
-    int n_ecta;           // external-force CTAs
+    int n_bcta;           // binning CTAs per replica
+    int n_ecta;           // external-force CTAs per system
+    int n_lcta;           // list force CTAs (kListWarps bead-atoms each)
     int nP;               // number of distinct bead counts
     int Pvals[8];         // distinct bead counts
-    int staged;           // pair force with the neighbourhood staged in shared memory
+    int fused;            // all systems one-bead with a pair potential: the force kernel
+                          // carries out the first half of the next step
 };
-// dynamic shared memory of the staged force kernel for `entries` staged neighbours
-size_t force_staged_smem(int entries, int mixed);
-cudaError_t force_staged_prepare(int entries, int mixed);
-constexpr int kStencilCells = 125;  // 5^3 stencil of r_cut/2 cells
-constexpr int kForceChunkHost = 32;  // home slots per CTA of the staged force kernel
-void launch_integrate(const Dev &d, const MdLaunch &m, int j, cudaStream_t st);
-void launch_cells(const Dev &d, const MdLaunch &m, cudaStream_t st);
-// staged pair force (m.staged): also reduces the observables of recorded steps
-void launch_force_kick(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,
-                       int kick, int j, cudaStream_t st);
+constexpr int kIntAtomsPerWarp = 10;                   // integrator: lanes 3a + c, a < 10
+constexpr int kIntAtomsPerCta = 4 * kIntAtomsPerWarp;  // 128 threads
+constexpr int kStencilCells = 125;                     // 5^3 stencil of (r_cut + skin)/2 cells
+// dynamic shared memory of the list build kernel for `entries` staged neighbours
+size_t list_build_smem(int entries, int mixed);
+cudaError_t list_build_prepare(int entries, int mixed);
+// positions of step s: the integrator writes pos[cur], cur = s & 1, and with a
+// conditional handle decides the graph's rebuild branch
+void launch_integrate(const Dev &d, const MdLaunch &m, int j, int cur, cudaGraphConditionalHandle h, cudaStream_t st);
+// bin, sort, build lists; each launch returns at once unless flag[cur] is set
+void launch_rebuild(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td, int cur,
+                    cudaStream_t st);
+// pair force from the lists (kick: closing B step; adv: also the first half of
+// step j + 1, positions to pos[cur ^ 1], rebuild decision through h; rec: the
+// step may be recorded, then the kernel also reduces the observables)
+void launch_force(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td, int kick,
+                  int j, int cur, int adv, int rec, cudaGraphConditionalHandle h, cudaStream_t st);
 void launch_reduce(const Dev &d, const MdLaunch &m, int j, int record, cudaStream_t st);
 void launch_tick(const Dev &d, cudaStream_t st);
 void launch_setclock(const Dev &d, long long blk, cudaStream_t st);

@@ -49,7 +49,7 @@ class qtb_params(C.Structure):
                 ("ext_V0", C.c_double), ("ext_a", C.c_double), ("dt", C.c_double), ("precision", C.c_int),
                 ("filter_prec", C.c_int), ("seed", C.c_ulonglong), ("obs_stride", C.c_int),
                 ("max_records", C.c_int), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
-                ("alloc_user", C.c_void_p)]
+                ("alloc_user", C.c_void_p), ("skin", C.c_double)]
 
 
 _lib = None
@@ -81,6 +81,7 @@ def lib():
             "qtb_get_taps": ([vp, i, vp, i, C.POINTER(i)], i),
             "qtb_get_noise": ([vp, i, vp, C.POINTER(ll)], i),
             "qtb_get_step": ([vp, C.POINTER(ll)], i),
+            "qtb_list_rebuilds": ([vp, C.POINTER(ll)], i),
             "qtb_set_profiling": ([vp, i], i),
             "qtb_kernel_times": ([vp, vp, vp, i], i),
             "qtb_kappa_solve": ([i, i, d, d, vp], i),
@@ -188,6 +189,7 @@ def qtb_init(systems, params, stream=None):
     p.seed = int(params.get("seed", 12345))
     p.obs_stride = int(params.get("obs_stride", 1))
     p.max_records = int(params.get("max_records", 4096))
+    p.skin = float(params.get("skin", 0.0))
     if params.get("torch_alloc", True):
         a, f = _torch_allocator()
         p.dev_alloc, p.dev_free = a, f
@@ -256,13 +258,19 @@ def qtb_get_noise(ctx, sys, ndof):
     return out, b.value
 
 
+def qtb_list_rebuilds(ctx):
+    n = C.c_longlong()
+    _check(lib().qtb_list_rebuilds(ctx, C.byref(n)))
+    return int(n.value)
+
+
 def qtb_get_step(ctx):
     s = C.c_longlong(0)
     _check(lib().qtb_get_step(ctx, C.byref(s)))
     return s.value
 
 
-KERNEL_CLASSES = ("white", "filter", "integrate", "cells", "force", "reduce")
+KERNEL_CLASSES = ("white", "filter", "integrate", "rebuild", "force", "reduce")
 
 
 def qtb_set_profiling(ctx, enable=True):

@@ -1,0 +1,88 @@
+"""Verlet neighbour lists on the GPU.
+
+* rebuilds decided and carried out on the device (conditional graph node
+  inside the captured block, flag-tested launches outside it) keep the forces
+  equal to the oracle's brute force on the GPU's own configuration, in small
+  boxes (several periodic images per pair) and larger ones, FP64 and mixed;
+* the skin changes nothing but the summation order (FP64 trajectories with
+  and without a skin agree to rounding);
+* a cold crystal with the default skin rebuilds (almost) never.
+Bit-identical fused (graph) and unfused (single-step) stepping is checked by
+test_gpu_parity.py::test_stepping_is_deterministic_and_split_invariant.
+"""
+import numpy as np
+import pytest
+
+from helpers import gpu_ctx, minimg, rel_inf, rel_l2
+from paper_1905_02521_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+from tolerances import F32_INF, F32_L2  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def qtb():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1905_02521_gb300 import build
+    build.build()
+    from paper_1905_02521_gb300 import qtb as q
+    return q
+
+
+@pytest.mark.parametrize("ncell", [2, 5])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rebuilds_keep_forces_exact(qtb, oracle, ncell, precision):
+    # hot crystal (2000 K, white Langevin) with a small skin: ions cross skin/2
+    # every few tens of steps; 300 direct steps, one captured block, 50 direct
+    s, pot = W.mgo_system(ncell, 2000.0, sigma=0.05, seed=7)
+    N = len(s["types"])
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=precision, seed=3, skin=0.3)
+    try:
+        r0 = qtb.qtb_list_rebuilds(ctx)
+        assert r0 == 1
+        for n in (300, 256, 50):
+            qtb.qtb_step_n(ctx, n)
+            x, _ = qtb.qtb_get_state(ctx, 0, 1, N)
+            f = qtb.qtb_get_forces(ctx, 0, 1, N)[0]
+            fo, eo, _ = oracle.pair_forces(x[0], s["types"], s["box"], pot)
+            if precision == 0:
+                assert rel_inf(f, fo) < 1e-12
+            else:
+                assert rel_l2(f, fo) < F32_L2 and rel_inf(f, fo) < F32_INF, (rel_l2(f, fo), rel_inf(f, fo))
+        nreb = qtb.qtb_list_rebuilds(ctx) - r0
+        print("ncell %d precision %d: %d rebuilds in 606 steps" % (ncell, precision, nreb))
+        assert nreb >= 5
+    finally:
+        qtb.qtb_destroy(ctx)
+
+
+def test_skin_only_changes_summation_order(qtb):
+    s, pot = W.mgo_system(3, 300.0, seed=11)
+    N = len(s["types"])
+    out = []
+    for skin in (-1.0, 0.8):      # no skin (rebuild whenever anything moved) / default
+        ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=0, seed=21, skin=skin)
+        try:
+            qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB, 513, 0.3)
+            qtb.qtb_step_n(ctx, 512 + 40)
+            out.append((qtb.qtb_get_state(ctx, 0, 1, N), qtb.qtb_list_rebuilds(ctx)))
+        finally:
+            qtb.qtb_destroy(ctx)
+    (x0, v0), n0 = out[0]
+    (x1, v1), n1 = out[1]
+    assert n0 == 553 and n1 < n0
+    assert np.abs(minimg(x1 - x0, s["box"])).max() < 1e-9
+    assert rel_inf(v1, v0) < 1e-9
+
+
+def test_cold_crystal_rarely_rebuilds(qtb):
+    s, pot = W.mgo_system(4, 100.0)
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=1, filter_prec=1, seed=2)
+    try:
+        qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB, 1025, 0.3)
+        qtb.qtb_step_n(ctx, 1024)
+        assert qtb.qtb_list_rebuilds(ctx) <= 3
+    finally:
+        qtb.qtb_destroy(ctx)

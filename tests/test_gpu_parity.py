@@ -13,10 +13,7 @@ import pytest
 
 from helpers import gpu_ctx, minimg, oracle_sim, rel_inf, rel_l2
 
-# FP32 force criterion: relative L2 error <= 1e-5; the max-norm error relative
-# to the RMS force is bounded at 2e-5 (single FP32 pair terms of ~10 eV/A
-# cancel to net forces of ~0.5 eV/A in the crystal).
-F32_L2, F32_INF = 1e-5, 2e-5
+from tolerances import F32_INF, F32_L2  # FP32 criterion and its max-norm guard (see tolerances.py)
 
 
 def assert_force_parity(f, fo, tol):
