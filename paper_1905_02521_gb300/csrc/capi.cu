@@ -976,7 +976,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
                 R.cell0 = ncells;
                 ncells += cells;
                 R.fcta0 = nlcta;
-                const int nl = (h.N + kListWarps - 1) / kListWarps;
+                const int nl = (h.N + kListAtoms - 1) / kListAtoms;
                 nlcta += nl;
                 c->dr.push_back(R);
                 for (int t = 0; t < cells; ++t) c->cell_rep.push_back(nrep);
@@ -999,7 +999,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         if (c->pair) {
             // the system's replicas are consecutive, and so are their list force CTAs
             S.fcta0 = c->dr[S.rep0].fcta0;
-            S.fcta1 = c->dr[S.rep0 + c->hs[s].P - 1].fcta0 + (c->hs[s].N + kListWarps - 1) / kListWarps;
+            S.fcta1 = c->dr[S.rep0 + c->hs[s].P - 1].fcta0 + (c->hs[s].N + kListAtoms - 1) / kListAtoms;
             nforce = S.fcta1;
         } else {
             S.fcta0 = s * ext_gx;

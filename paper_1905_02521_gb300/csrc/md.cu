@@ -116,6 +116,18 @@ struct FF {
             lo = __fadd_rn(__fadd_rn(lo, ol), e);
         }
     }
+    // sum over aligned groups of W lanes (W a power of two <= 32)
+    template <int W> __device__ void group_reduce()
+    {
+#pragma unroll
+        for (int o = W / 2; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+            float s, e;
+            two_sum(hi, oh, s, e);
+            hi = s;
+            lo = __fadd_rn(__fadd_rn(lo, ol), e);
+        }
+    }
     __device__ float value() const { return __fadd_rn(hi, lo); }
 };
 
@@ -124,8 +136,20 @@ struct DD {
     double hi;
     __device__ void add(double x) { hi += x; }
     __device__ void warp_reduce() { hi = warp_sum(hi); }
+    template <int W> __device__ void group_reduce()
+    {
+#pragma unroll
+        for (int o = W / 2; o > 0; o >>= 1) hi += __shfl_xor_sync(0xffffffffu, hi, o);
+    }
     __device__ double value() const { return hi; }
 };
+
+template <int W, class T> __device__ __forceinline__ T group_sum(T v)
+{
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // CTA-wide sum of kNQ doubles held by lane 0 of each warp into out[0..kNQ)
 __device__ void cta_store_partials(const double *acc, double (*red)[kNQ], double *out)
@@ -700,15 +724,16 @@ __device__ void reduce_system(const Dev &d, int s, long long step, int record, d
 }
 
 // ---------------------------------------------------------------------------
-// Pair force from the neighbour lists: one warp per home bead-atom, the lanes
-// stride through its list (two independent entries per lane per iteration),
-// every entry is evaluated and masked by r < r_cut (no divergent branch).
-// Epilogue on lanes 0..2 (one Cartesian component each): force (times 1/P,
-// Eq. 4), the closing B(dt/2) kick, the observables of recorded steps and,
-// with ADV (one-bead systems), the first half of the next step: B(dt/2),
-// A(dt/2) O(dt) A(dt/2) with the next step's coloured noise, written to x and
-// pos[cur ^ 1], and the rebuild test for the next step.  Recorded steps: the
-// last CTA of a system reduces its partials.
+// Pair force from the neighbour lists: kListLanes lanes per home bead-atom
+// (two bead-atoms per warp), each lane strides through the list with two
+// independent entries per iteration and the next iteration's entries already
+// requested; every entry is evaluated and masked by r < r_cut (no divergent
+// branch).  Epilogue on the first three lanes of a group (one Cartesian
+// component each): force (times 1/P, Eq. 4), the closing B(dt/2) kick, the
+// observables of recorded steps and, with ADV (one-bead systems), the first
+// half of the next step: B(dt/2), A(dt/2) O(dt) A(dt/2) with the next step's
+// coloured noise, written to x and pos[cur ^ 1], and the rebuild test for the
+// next step.  Recorded steps: the last CTA of a system reduces its partials.
 
 template <int PM, class R, int ADV, int REC>
 __global__ void __launch_bounds__(32 * kListWarps) k_force_list(Dev d, PairTabT<R> T, int kick, int j, int cur,
@@ -717,130 +742,141 @@ __global__ void __launch_bounds__(32 * kListWarps) k_force_list(Dev d, PairTabT<
     typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
     typedef typename std::conditional<sizeof(R) == 4, FF, DD>::type ACC;
     typedef typename PosT<PM, R>::S PS;
+    constexpr int LPA = kListLanes, APW = 32 / kListLanes;
     __shared__ double red[kListWarps][kNQ];
     __shared__ double rsh[kListWarps][kNQ + 1];
     __shared__ int s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = lane & (LPA - 1), grp = lane / LPA;
     const DRep RP = d.rep[d.lcta_rep[blockIdx.x]];
-    const int i = (blockIdx.x - RP.fcta0) * kListWarps + warp;
+    const int i = (blockIdx.x - RP.fcta0) * kListAtoms + warp * APW + grp;
+    const bool act = i < RP.N;
     const long long step = d.clock[0] * kBlockSteps + j + 1;
     const bool rec = REC && ((kick == 0) || (step % d.obs_stride == 0));
     if (blockIdx.x == 0 && threadIdx.x == 0) d.flag[cur] = 0u;  // this step's rebuild request is consumed
     const DSys &S = d.sys[RP.sys];
+    const size_t G = (size_t)d.G;
+    const long long gi = RP.g0 + (act ? i : 0);
+    const E4 *Pc = reinterpret_cast<const E4 *>(d.pos[cur]);
+    const E4 *Pr = Pc + RP.g0;
+    const E4 hp = Pc[gi];
+    int ti;
+    if (PM == PM_FIX) ti = hp.w; else ti = (int)hp.w;
+    const int n = act ? min(d.nnb[gi], d.maxnb) : 0;
+    const unsigned *row = d.nbr + (size_t)gi * d.maxnb;
+    const R sx = (R)RP.fix_scale[0], sy = (R)RP.fix_scale[1], sz = (R)RP.fix_scale[2];
+    const R rc2 = T.rc2;
+    ACC fx{}, fy{}, fz{};
+    R en = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+    auto pair = [&](unsigned e, bool valid) {
+        const E4 pj = Pr[e & kNbIdx];
+        R dx, dy, dz;
+        int tj;
+        if (PM == PM_FIX) {
+            // r_j + image - r_i, exact in wrapping 32-bit arithmetic
+            dx = (R)(int)((unsigned)pj.x + ((e << 4) & 0xC0000000u) - (unsigned)hp.x) * sx;
+            dy = (R)(int)((unsigned)pj.y + ((e << 2) & 0xC0000000u) - (unsigned)hp.y) * sy;
+            dz = (R)(int)((unsigned)pj.z + (e & 0xC0000000u) - (unsigned)hp.z) * sz;
+            tj = pj.w;
+        } else {
+            // image from m mod 4: code 2 is +2 or -2, told apart by the sign of
+            // the raw difference (the box exceeds r_cut/2 + skin)
+            const double pd[3] = {(double)pj.x - (double)hp.x, (double)pj.y - (double)hp.y, (double)pj.z - (double)hp.z};
+            R dv[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int code = (int)((e >> (26 + 2 * c)) & 3u);
+                const int m = (code == 3) ? -1 : (code == 2) ? (pd[c] > 0.0 ? -2 : 2) : code;
+                dv[c] = (R)(pd[c] + m * RP.box[c]);
+            }
+            dx = dv[0]; dy = dv[1]; dz = dv[2];
+            tj = (int)pj.w;
+        }
+        const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        R fo, ee;
+        pair_eval(T, ti * kMaxTypes + tj, r2, fo, ee, REC && rec);
+        const bool in = valid && (r2 < rc2);
+        fo = in ? fo : R(0);
+        // stored displacement is r_j - r_i: the force on i is -fo (r_j - r_i)
+        fx.add(-fo * dx); fy.add(-fo * dy); fz.add(-fo * dz);
+        if (REC && rec) {
+            en += in ? ee : R(0);
+            w0 = fma(fo * dx, dx, w0); w1 = fma(fo * dy, dy, w1); w2 = fma(fo * dz, dz, w2);
+            w3 = fma(fo * dx, dy, w3); w4 = fma(fo * dx, dz, w4); w5 = fma(fo * dy, dz, w5);
+        }
+    };
+    {
+        // entries k and k + LPA of this lane; the next pair is requested before
+        // the current one is evaluated (invalid slots repeat a valid entry, masked)
+        int k = sub;
+        unsigned ea = (k < n) ? row[k] : 0u, eb = (k + LPA < n) ? row[k + LPA] : ea;
+        for (; k < n; k += 2 * LPA) {
+            const int kn = k + 2 * LPA;
+            const unsigned na = (kn < n) ? row[kn] : ea, nb = (kn + LPA < n) ? row[kn + LPA] : ea;
+            pair(ea, true);
+            pair(eb, k + LPA < n);
+            ea = na;
+            eb = nb;
+        }
+    }
+    fx.template group_reduce<LPA>(); fy.template group_reduce<LPA>(); fz.template group_reduce<LPA>();
     double acc[kNQ];
 #pragma unroll
     for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
-    if (i < RP.N) {
-        const size_t G = (size_t)d.G;
-        const long long gi = RP.g0 + i;
-        const E4 *Pc = reinterpret_cast<const E4 *>(d.pos[cur]);
-        const E4 *Pr = Pc + RP.g0;
-        const E4 hp = Pc[gi];
-        int ti;
-        if (PM == PM_FIX) ti = hp.w; else ti = (int)hp.w;
-        const int n = min(d.nnb[gi], d.maxnb);
-        const unsigned *row = d.nbr + (size_t)gi * d.maxnb;
-        const R sx = (R)RP.fix_scale[0], sy = (R)RP.fix_scale[1], sz = (R)RP.fix_scale[2];
-        const R rc2 = T.rc2;
-        ACC fx{}, fy{}, fz{};
-        R en = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
-        auto pair = [&](unsigned e, bool valid) {
-            const E4 pj = Pr[e & kNbIdx];
-            R dx, dy, dz;
-            int tj;
-            if (PM == PM_FIX) {
-                // r_j + image - r_i, exact in wrapping 32-bit arithmetic
-                dx = (R)(int)((unsigned)pj.x + ((e << 4) & 0xC0000000u) - (unsigned)hp.x) * sx;
-                dy = (R)(int)((unsigned)pj.y + ((e << 2) & 0xC0000000u) - (unsigned)hp.y) * sy;
-                dz = (R)(int)((unsigned)pj.z + (e & 0xC0000000u) - (unsigned)hp.z) * sz;
-                tj = pj.w;
-            } else {
-                // image from m mod 4: code 2 is +2 or -2, told apart by the sign of
-                // the raw difference (the box exceeds r_cut/2 + skin)
-                const double pd[3] = {(double)pj.x - (double)hp.x, (double)pj.y - (double)hp.y, (double)pj.z - (double)hp.z};
-                R dv[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const int code = (int)((e >> (26 + 2 * c)) & 3u);
-                    const int m = (code == 3) ? -1 : (code == 2) ? (pd[c] > 0.0 ? -2 : 2) : code;
-                    dv[c] = (R)(pd[c] + m * RP.box[c]);
-                }
-                dx = dv[0]; dy = dv[1]; dz = dv[2];
-                tj = (int)pj.w;
-            }
-            const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-            R fo, ee;
-            pair_eval(T, ti * kMaxTypes + tj, r2, fo, ee, REC && rec);
-            const bool in = valid && (r2 < rc2);
-            fo = in ? fo : R(0);
-            // stored displacement is r_j - r_i: the force on i is -fo (r_j - r_i)
-            fx.add(-fo * dx); fy.add(-fo * dy); fz.add(-fo * dz);
-            if (REC && rec) {
-                en += in ? ee : R(0);
-                w0 = fma(fo * dx, dx, w0); w1 = fma(fo * dy, dy, w1); w2 = fma(fo * dz, dz, w2);
-                w3 = fma(fo * dx, dy, w3); w4 = fma(fo * dx, dz, w4); w5 = fma(fo * dy, dz, w5);
-            }
-        };
-        for (int k = lane; k < n; k += 64) {
-            const bool hb = (k + 32) < n;
-            const unsigned ea = row[k];
-            const unsigned eb = hb ? row[k + 32] : ea;
-            pair(ea, true);
-            pair(eb, hb);
+    if (REC && rec) {
+        en = group_sum<LPA>(en);
+        w0 = group_sum<LPA>(w0); w1 = group_sum<LPA>(w1); w2 = group_sum<LPA>(w2);
+        w3 = group_sum<LPA>(w3); w4 = group_sum<LPA>(w4); w5 = group_sum<LPA>(w5);
+        if (act && sub == 0) {
+            acc[Q_V] = 0.5 * (double)en;
+            acc[Q_VIR + 0] = 0.5 * (double)w0; acc[Q_VIR + 1] = 0.5 * (double)w1;
+            acc[Q_VIR + 2] = 0.5 * (double)w2; acc[Q_VIR + 3] = 0.5 * (double)w3;
+            acc[Q_VIR + 4] = 0.5 * (double)w4; acc[Q_VIR + 5] = 0.5 * (double)w5;
         }
-        fx.warp_reduce(); fy.warp_reduce(); fz.warp_reduce();
+    }
+    R dd = 0;  // squared displacement component since the last rebuild (ADV)
+    if (act && sub < 3) {
+        const int c = sub;
+        const R invP = sizeof(R) == 4 ? (R)S.invP_f : (R)S.invP;
+        const R fc = (R)(c == 0 ? fx.value() : c == 1 ? fy.value() : fz.value()) * invP;
+        R *Fo = reinterpret_cast<R *>(d.f);
+        R *V = reinterpret_cast<R *>(d.v);
+        const size_t o = (size_t)c * G + gi;
+        Fo[o] = fc;
+        const R hdtm = T.hdt_m[ti];
+        R v = V[o];
+        if (kick) v = fma(hdtm, fc, v);
         if (REC && rec) {
-            en = warp_sum(en);
-            w0 = warp_sum(w0); w1 = warp_sum(w1); w2 = warp_sum(w2);
-            w3 = warp_sum(w3); w4 = warp_sum(w4); w5 = warp_sum(w5);
-            if (lane == 0) {
-                acc[Q_V] = 0.5 * (double)en;
-                acc[Q_VIR + 0] = 0.5 * (double)w0; acc[Q_VIR + 1] = 0.5 * (double)w1;
-                acc[Q_VIR + 2] = 0.5 * (double)w2; acc[Q_VIR + 3] = 0.5 * (double)w3;
-                acc[Q_VIR + 4] = 0.5 * (double)w4; acc[Q_VIR + 5] = 0.5 * (double)w5;
-            }
+            acc[Q_K] += 0.5 * T.mass_mvv[ti] * (double)v * (double)v;
+            acc[Q_MOM + c] += T.mass[ti] * (double)v;
         }
-        bool moved = false;
-        if (lane < 3) {
-            const int c = lane;
-            const R invP = sizeof(R) == 4 ? (R)S.invP_f : (R)S.invP;
-            const R fc = (R)(c == 0 ? fx.value() : c == 1 ? fy.value() : fz.value()) * invP;
-            R *Fo = reinterpret_cast<R *>(d.f);
-            R *V = reinterpret_cast<R *>(d.v);
-            const size_t o = (size_t)c * G + gi;
-            Fo[o] = fc;
-            const R hdtm = T.hdt_m[ti];
-            R v = V[o];
-            if (kick) v = fma(hdtm, fc, v);
-            if (REC && rec) {
-                acc[Q_K] += 0.5 * T.mass_mvv[ti] * (double)v * (double)v;
-                acc[Q_MOM + c] += T.mass[ti] * (double)v;
-            }
-            if (ADV) {
-                // next step, one bead (the mode is the bead): B(dt/2), A(dt/2) O(dt) A(dt/2)
-                const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
-                const R cs = rot[0], sw = rot[1], ws = rot[2];
-                const R sig = reinterpret_cast<const R *>(d.osig)[RP.sys * kMaxTypes + ti];
-                const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
-                const R eta = reinterpret_cast<const R *>(d.eta)[(size_t)(j + 1) * d.Dtot + S.dof0 + (size_t)c * S.N + i];
-                R pk = fma(hdtm, fc, v);
-                R qq = 0;
-                mode_aoa(qq, pk, cs, sw, ws, c1, sig * eta);
-                v = pk;
-                PS *X = reinterpret_cast<PS *>(d.x);
-                const float fsc = S.fix_scale[c];
-                const PS xn = PosT<PM, R>::add(X[o], qq, S.box[c], fsc, S.fix_inv[c]);
-                X[o] = xn;
-                reinterpret_cast<PS *>(d.pos[cur ^ 1])[4 * (size_t)gi + c] = xn;
-                const R dc = PosT<PM, R>::diff(xn, reinterpret_cast<const PS *>(d.xref)[o], fsc);
-                const R dd = dc * dc;
-                const R tot = __shfl_sync(0x7u, dd, 0) + __shfl_sync(0x7u, dd, 1) + __shfl_sync(0x7u, dd, 2);
-                const R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
-                moved = (c == 0) && tot > lim;
-            }
-            if (kick || ADV) V[o] = v;
+        if (ADV) {
+            // next step, one bead (the mode is the bead): B(dt/2), A(dt/2) O(dt) A(dt/2)
+            const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
+            const R cs = rot[0], sw = rot[1], ws = rot[2];
+            const R sig = reinterpret_cast<const R *>(d.osig)[RP.sys * kMaxTypes + ti];
+            const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
+            const R eta = reinterpret_cast<const R *>(d.eta)[(size_t)(j + 1) * d.Dtot + S.dof0 + (size_t)c * S.N + i];
+            R pk = fma(hdtm, fc, v);
+            R qq = 0;
+            mode_aoa(qq, pk, cs, sw, ws, c1, sig * eta);
+            v = pk;
+            PS *X = reinterpret_cast<PS *>(d.x);
+            const float fsc = S.fix_scale[c];
+            const PS xn = PosT<PM, R>::add(X[o], qq, S.box[c], fsc, S.fix_inv[c]);
+            X[o] = xn;
+            reinterpret_cast<PS *>(d.pos[cur ^ 1])[4 * (size_t)gi + c] = xn;
+            const R dc = PosT<PM, R>::diff(xn, reinterpret_cast<const PS *>(d.xref)[o], fsc);
+            dd = dc * dc;
         }
-        if (ADV && moved) atomicOr(&d.flag[cur ^ 1], 1u);
+        if (kick || ADV) V[o] = v;
+    }
+    if (ADV) {
+        const int b0 = grp * LPA;
+        const R tot = __shfl_sync(0xffffffffu, dd, b0) + __shfl_sync(0xffffffffu, dd, b0 + 1) +
+                      __shfl_sync(0xffffffffu, dd, b0 + 2);
+        const R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
+        if (__any_sync(0xffffffffu, act && sub == 0 && tot > lim) && lane == 0) atomicOr(&d.flag[cur ^ 1], 1u);
     }
     if (REC && rec) {
 #pragma unroll

@@ -41,7 +41,9 @@ enum { ERR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_SOLVE = 4, ERR_TIMEOUT_TC = 8, E
 // (m mod 4) * 2^30, exact in wrapping 32-bit arithmetic.
 constexpr unsigned kNbIdx = (1u << 26) - 1u;
 constexpr int kMaxCellCap = 512;        // slots per cell of the cell list
-constexpr int kListWarps = 4;        // home bead-atoms (one warp each) per CTA of the list force kernel
+constexpr int kListWarps = 4;        // warps per CTA of the list force kernel
+constexpr int kListLanes = 16;       // lanes per home bead-atom
+constexpr int kListAtoms = kListWarps * 32 / kListLanes;  // home bead-atoms per CTA
 
 struct DSys {
     int N, P;          // atoms, beads
@@ -72,7 +74,7 @@ struct DRep {          // one replica (system, bead) of a pair-potential system
     int nc[3];         // cells per edge
     int cell0;         // first cell
     int cta0;          // first binning CTA
-    int fcta0;         // first CTA of the list force kernel (kListWarps bead-atoms each)
+    int fcta0;         // first CTA of the list force kernel (kListAtoms bead-atoms each)
     double box[3];
     float fix_scale[3];  // box / 2^30
 };

@@ -42,7 +42,7 @@ struct MdLaunch {
     int n_icta;           // integrator CTAs
     int n_bcta;           // binning CTAs per replica
     int n_ecta;           // external-force CTAs per system
-    int n_lcta;           // list force CTAs (kListWarps bead-atoms each)
+    int n_lcta;           // list force CTAs (kListAtoms bead-atoms each)
     int nP;               // number of distinct bead counts
     int Pvals[8];         // distinct bead counts
     int fused;            // all systems one-bead with a pair potential: the force kernel
