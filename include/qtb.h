@@ -177,9 +177,10 @@ int qtb_get_noise(qtb_ctx *c, int sys, double *out, long long *block_out);
 /* Profiling of whole 256-step blocks: when enabled, the captured block records
  * a CUDA event pair around the launches of every 16th step and around the
  * per-block noise launches (classes: 0 white noise, 1 filter, 2 integrator,
- * 3 neighbour-list rebuild branch, 4 force (for one-bead systems with the
- * first half of the next step fused in), 5 reduction).  Takes effect at the
- * next block. */
+ * 3 unused (list rebuilds run inside the force launch), 4 force (pair
+ * potential: the step kernel, with a list rebuild when one is due and, for
+ * one-bead systems, the first half of the next step), 5 reduction).  Takes
+ * effect at the next block. */
 int qtb_set_profiling(qtb_ctx *c, int enable);
 
 /* Mean device time (ms) and launch count per kernel class over the last

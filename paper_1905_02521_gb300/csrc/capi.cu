@@ -59,8 +59,6 @@ int qtb::set_last_error(int code, const char *msg)
 
 struct qtb_ctx {
     cudaStream_t st = nullptr;
-    cudaStream_t st2 = nullptr;  // captures the bodies of the conditional rebuild nodes
-    bool cond_ok = true;         // conditional graph nodes usable (else flag-tested launches)
     double skin = 0.0;           // neighbour-list skin, A
     qtb_params p{};
     std::vector<double> mass, charge, bA, brho, bC;
@@ -142,7 +140,6 @@ struct qtb_ctx {
             else cudaFree(ptr);
         }
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
-        if (st2) cudaStreamDestroy(st2);
         if (own_stream) cudaStreamDestroy(st);
     }
 };
@@ -215,6 +212,7 @@ int check_err_word(qtb_ctx *c)
     if (e & ERR_NONFINITE) return fail(QTB_ERR_NONFINITE, "non-finite energy: the integration blew up");
     if (e & ERR_SOLVE) return fail(QTB_ERR_SOLVE, "kappa_P solve: non-positive pivot");
     if (e & ERR_TIMEOUT_TC) return fail(QTB_ERR_TIMEOUT, "tensor-core filter: a bounded barrier wait gave up");
+    if (e & ERR_TIMEOUT_BAR) return fail(QTB_ERR_TIMEOUT, "step kernel: a bounded grid-barrier wait gave up");
     return QTB_OK;
 }
 
@@ -339,9 +337,8 @@ int refresh_forces(qtb_ctx *c)
     if (c->pair) {
         CUDA_TRY(cudaMemsetAsync(c->d.flag, 0, 2 * sizeof(unsigned), c->st));
         CUDA_TRY(cudaMemsetAsync(c->d.flag + cur, 1, 1, c->st));
-        launch_rebuild(c->d, c->ml, c->tabf, c->tab, cur, c->st);
     }
-    launch_force(c->d, c->ml, c->tabf, c->tab, 0, j, cur, 0, 1, 0, c->st);
+    CUDA_TRY(launch_force(c->d, c->ml, c->tabf, c->tab, 0, j, cur, 0, 1, c->st));
     if (!c->pair) launch_reduce(c->d, c->ml, j, -1, c->st);  // the list force kernel reduces itself
     CUDA_TRY(cudaGetLastError());
     return QTB_OK;
@@ -484,93 +481,38 @@ ProfMark::~ProfMark()
     c->ev_used += 2;
 }
 
-// A conditional handle of the graph being captured on c->st (0 when
-// conditional nodes are not in use).
-cudaError_t new_cond(qtb_ctx *c, cudaGraphConditionalHandle *h)
-{
-    *h = 0;
-    if (!c->cond_ok) return cudaSuccess;
-    cudaStreamCaptureStatus cs;
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamGetCaptureInfo(c->st, &cs, nullptr, &g, nullptr, nullptr, nullptr);
-    if (e != cudaSuccess) return e;
-    return cudaGraphConditionalHandleCreate(h, g, 0, 0);
-}
-
-// The rebuild of the step whose positions are in pos[cur]: inside a capture an
-// IF node on the handle the producing kernel sets (body: bin, sort, build,
-// captured on c->st2); otherwise the three launches, which test the request.
-cudaError_t rebuild_step(qtb_ctx *c, int cur, cudaGraphConditionalHandle h)
-{
-    if (!h) {
-        launch_rebuild(c->d, c->ml, c->tabf, c->tab, cur, c->st);
-        return cudaGetLastError();
-    }
-    cudaStreamCaptureStatus cs;
-    cudaGraph_t g = nullptr;
-    const cudaGraphNode_t *deps = nullptr;
-    const cudaGraphEdgeData *ed = nullptr;
-    size_t nd = 0;
-    cudaError_t e = cudaStreamGetCaptureInfo(c->st, &cs, nullptr, &g, &deps, &ed, &nd);
-    if (e != cudaSuccess) return e;
-    cudaGraphNodeParams np = {};
-    np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = h;
-    np.conditional.type = cudaGraphCondTypeIf;
-    np.conditional.size = 1;
-    cudaGraphNode_t node;
-    e = cudaGraphAddNode(&node, g, deps, ed, nd, &np);
-    if (e != cudaSuccess) return e;
-    e = cudaStreamUpdateCaptureDependencies(c->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
-    if (e != cudaSuccess) return e;
-    e = cudaStreamBeginCaptureToGraph(c->st2, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                      cudaStreamCaptureModeRelaxed);
-    if (e != cudaSuccess) return e;
-    launch_rebuild(c->d, c->ml, c->tabf, c->tab, cur, c->st2);
-    cudaGraph_t body = nullptr;
-    return cudaStreamEndCapture(c->st2, &body);
-}
-
 // Steps j0 .. j0+count-1 of the current block, captured (graph) or launched.
-// Positions of step s are in pos[s & 1].  Unfused: integrate, rebuild, force.
-// Fused (one-bead systems): integrate once, then rebuild + force per step, each
-// force launch but the last also doing the first half of the next step.
-// Profiling samples every 16th step of a captured block (event nodes cost
-// about a microsecond each, so they are not put on every launch).
+// Positions of step s are in pos[s & 1].  Unfused: integrate, force.  Fused
+// (one-bead systems): integrate once, then one force launch per step, each but
+// the last also doing the first half of the next step.  A list rebuild, when
+// requested, runs inside the force launch.  Profiling samples every 16th step
+// of a captured block (event nodes cost about a microsecond each, so they are
+// not put on every launch).
 int run_steps(qtb_ctx *c, int j0, int count, bool graph)
 {
     const MdLaunch &m = c->ml;
     const int obs = c->p.obs_stride;
-    cudaGraphConditionalHandle h = 0;
     for (int t = 0; t < count; ++t) {
         const int j = j0 + t, cur = j & 1;
         const bool keep = c->capturing;
         if (j % 16 != 0) c->capturing = false;
         if (!m.fused || t == 0) {
-            if (graph && m.pair) CUDA_TRY(new_cond(c, &h));
             ProfMark pm(c, KC_INTEGRATE);
-            launch_integrate(c->d, m, j, cur, h, c->st);
-        }
-        if (m.pair) {
-            ProfMark pm(c, KC_CELLS);
-            CUDA_TRY(rebuild_step(c, cur, h));
+            launch_integrate(c->d, m, j, cur, c->st);
         }
         const int adv = (m.fused && t < count - 1) ? 1 : 0;
-        cudaGraphConditionalHandle hn = 0;
-        if (adv && graph) CUDA_TRY(new_cond(c, &hn));
         // may this step be recorded? (inside the graph the block index is only known on the device)
         int rec;
         if (graph) rec = (kBlockSteps % obs == 0) ? ((j + 1) % obs == 0) : 1;
         else rec = ((c->step + t + 1) % obs == 0) ? 1 : 0;
         {
             ProfMark pm(c, KC_FORCE);
-            launch_force(c->d, m, c->tabf, c->tab, 1, j, cur, adv, rec, hn, c->st);
+            CUDA_TRY(launch_force(c->d, m, c->tabf, c->tab, 1, j, cur, adv, rec, c->st));
         }
         if (!m.pair) {
             ProfMark pm(c, KC_REDUCE);
             launch_reduce(c->d, m, j, 1, c->st);
         }
-        h = hn;
         c->capturing = keep;
     }
     return QTB_OK;
@@ -606,13 +548,6 @@ int build_graph(qtb_ctx *c)
     if (rc == QTB_OK) {
         e = cudaGraphInstantiate(&c->gexec, g, 0);
         cudaGraphDestroy(g);
-    }
-    if ((rc != QTB_OK || e != cudaSuccess) && c->cond_ok) {
-        // conditional nodes refused: capture again with flag-tested rebuild launches
-        cudaGetLastError();
-        c->gexec = nullptr;
-        c->cond_ok = false;
-        return build_graph(c);
     }
     if (rc) return rc;
     if (e != cudaSuccess) return fail(QTB_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
@@ -788,10 +723,6 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         }
         c->own_stream = true;
     }
-    if (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess) {
-        delete c;
-        return fail(QTB_ERR_CUDA, "cudaStreamCreate failed");
-    }
     c->p = *p;
     c->skin = effective_skin(p);
     const int nt = p->n_types;
@@ -871,7 +802,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
 
     // ---- layout
     long long G = 0, D = 0;
-    int icta = 0, nrep = 0, ncells = 0, maxN = 0, cap = 8;
+    int icta = 0, nrep = 0, ncells = 0, cap = 8;
     int rot_tot = 0, nm_tot = 0;
     std::map<int, int> nm_off;
     std::vector<double> nmC_host;
@@ -902,9 +833,11 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
             const double rho = sys[s].n_atoms / (sys[s].box[0] * sys[s].box[1] * sys[s].box[2]);
             maxnb = std::max(maxnb, (int)roundup((long long)std::ceil(1.5 * rho * vlist + 64.0), 32));
         }
-        // staging chunk: 1.5 x the mean stencil population plus a margin, at
-        // most 4096 entries (larger neighbourhoods take several chunks)
-        stage_cap = (int)std::min(roundup((long long)std::ceil(1.5 * kStencilCells * ecell) + 128, 64), 4096LL);
+        // staging chunk of the list build: 1.5 x the mean stencil population plus a
+        // margin, between 512 entries (the sort keys share the buffer) and 1024
+        // (the buffer is allocated for every CTA of the step kernel, a larger
+        // neighbourhood takes several chunks)
+        stage_cap = (int)std::max(512LL, std::min(roundup((long long)std::ceil(1.5 * kStencilCells * ecell) + 128, 64), 1024LL));
     }
     int nlcta = 0;
     for (int s = 0; s < n_sys; ++s) {
@@ -955,7 +888,6 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         }
         S.nm0 = nm_off[h.P];
         S.rep0 = nrep;
-        maxN = std::max(maxN, h.N);
         c->max_dofp = std::max(c->max_dofp, S.dofp);
         if (c->pair) {
             int nc[3];
@@ -989,8 +921,9 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         return bail(fail(QTB_ERR_ARG, "cell capacity %d > %d: box too dense for (r_cut + skin)/2 cells", cap, kMaxCellCap));
     for (int s = 0; s < n_sys; ++s)
         for (int t = c->ds[s].icta0; t < c->ds[s].icta1; ++t) c->icta_sys.push_back(s);
-    if (c->pair && list_build_prepare(stage_cap, c->mixed ? 1 : 0) != cudaSuccess)
-        return bail(fail(QTB_ERR_CUDA, "cannot reserve shared memory for the list build kernel"));
+    c->ml.mixed = c->mixed;
+    if (c->pair && step_prepare(c->ml, stage_cap) != cudaSuccess)
+        return bail(fail(QTB_ERR_CUDA, "cannot prepare the cooperative step kernel (shared memory, occupancy)"));
     int ext_gx = 0;
     for (int s = 0; s < n_sys; ++s) ext_gx = std::max(ext_gx, (c->hs[s].N * c->hs[s].P + 127) / 128);
     long long nforce = 0;
@@ -1014,6 +947,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     d.ncells = ncells;
     d.cap = cap;
     d.stage_cap = stage_cap;
+    d.nunits = nlcta;
     d.maxnb = maxnb;
     d.G = G;
     d.Dtot = D;
@@ -1027,9 +961,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     m.mixed = c->mixed;
     m.pair = c->pair;
     m.n_icta = icta;
-    m.n_bcta = (maxN + 255) / 256;
     m.n_ecta = ext_gx;
-    m.n_lcta = nlcta;
     m.nP = 0;
     for (int s = 0; s < n_sys; ++s) {
         bool seen = false;
@@ -1120,12 +1052,12 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         cudaMemsetAsync(d.nnb, 0, sizeof(int) * (size_t)G, c->st);
     }
     d.flag = (unsigned *)c->alloc(2 * sizeof(unsigned));
-    d.gdone = (unsigned *)c->alloc(sizeof(unsigned));
+    d.gbar = (unsigned *)c->alloc(2 * sizeof(unsigned));
     d.nrebuild = (unsigned long long *)c->alloc(sizeof(unsigned long long));
-    if (!d.flag || !d.gdone || !d.nrebuild) return bail(fail(QTB_ERR_OOM, "device allocation failed"));
+    if (!d.flag || !d.gbar || !d.nrebuild) return bail(fail(QTB_ERR_OOM, "device allocation failed"));
     cudaMemsetAsync(d.nrebuild, 0, sizeof(unsigned long long), c->st);
     cudaMemsetAsync(d.flag, 0, 2 * sizeof(unsigned), c->st);
-    cudaMemsetAsync(d.gdone, 0, sizeof(unsigned), c->st);
+    cudaMemsetAsync(d.gbar, 0, 2 * sizeof(unsigned), c->st);
     d.eta = c->alloc(c->rsz * (size_t)kBlockSteps * (size_t)D);
     d.part = (double *)c->alloc(sizeof(double) * kNQ * (size_t)std::max(nforce, 1LL));
     d.ipart = (double *)c->alloc(sizeof(double) * kNQ * (size_t)icta);

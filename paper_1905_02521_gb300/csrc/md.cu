@@ -19,6 +19,7 @@
 // skin/2 since the last one: then no pair outside a list can have come within
 // r_cut.  For one-bead systems the force kernel also carries out the first
 // half of the next step (B, A, O, A), so that a step is one launch.
+#include <algorithm>
 #include <climits>
 #include <type_traits>
 
@@ -165,25 +166,36 @@ __device__ void cta_store_partials(const double *acc, double (*red)[kNQ], double
     }
 }
 
-// Grid-wide decision once every CTA of the launch has passed this point: the
-// last CTA to arrive reads the rebuild request flag[par] and sets the graph's
-// conditional (the rebuild branch before the next force evaluation).  Called
-// by all threads of every CTA; h == 0 (direct launches) does nothing.
-__device__ __forceinline__ void grid_set_rebuild(const Dev &d, int par, cudaGraphConditionalHandle h)
+// Grid-wide barrier of a cooperative launch (all CTAs co-resident): arrival
+// counter bar[0] and generation bar[1].  The wait is bounded: after about a
+// second it records ERR_TIMEOUT_BAR and lets the CTA go on (the results of
+// that launch are then void, the host reports QTB_ERR_TIMEOUT).  Called by
+// all threads of every CTA.
+__device__ void grid_barrier(const Dev &d)
 {
-    if (!h) return;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned total = gridDim.x * gridDim.y;
-        const unsigned prev = atomicAdd(d.gdone, 1u);
-        if (prev == total - 1u) {
+        volatile unsigned *gen = d.gbar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(d.gbar, 1u);
+        if (arrived == gridDim.x * gridDim.y - 1u) {
+            d.gbar[0] = 0u;
             __threadfence();
-            const unsigned f = *(volatile const unsigned *)&d.flag[par];
-            cudaGraphSetConditional(h, f ? 1u : 0u);
-            *d.gdone = 0u;
+            atomicAdd(d.gbar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g0) {
+                if (++spins > (1LL << 25)) {
+                    atomicOr(d.err, (unsigned)ERR_TIMEOUT_BAR);
+                    break;
+                }
+                __nanosleep(32);
+            }
         }
+        __threadfence();
     }
+    __syncthreads();
 }
 
 // One normal mode: A(dt/2) (exact free ring-polymer rotation, (cos, sin/w,
@@ -212,7 +224,7 @@ __device__ __forceinline__ void mode_aoa(R &q, R &p, R cs, R sw, R ws, R c1, R n
 // bead-atom has moved more than skin/2 since the last one.
 
 template <int P, int PM, class R>
-__global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur, cudaGraphConditionalHandle hcond)
+__global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
 {
     constexpr int UN = (P <= 8) ? P : 1;  // full unroll only for small rings
     typedef typename PosT<PM, R>::S PS;
@@ -327,92 +339,80 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur, cudaGr
     spring = warp_sum(spring);
     acc[Q_SPRING] = spring;
     if (mine) cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
-    grid_set_rebuild(d, cur, hcond);
 }
 
 // ---------------------------------------------------------------------------
-// List rebuild, three launches that do nothing unless flag[cur] is set:
-// k_bin wraps the positions into the box (x, its packed copy pos[cur] and the
-// reference xref) and bins them into cells >= (r_cut + skin)/2 with atomic
-// slots; k_cellsort puts each cell's slots in bead-atom order (so that every
-// list, and every later sum, has a fixed order); k_build_list scans the 5^3
-// stencil of each cell.
+// List rebuild: three phases of the cooperative step kernel, separated by grid
+// barriers, run only when flag[cur] is set.  bin_phase wraps the positions
+// into the box (x, its packed copy pos[cur] and the reference xref) and bins
+// them into cells >= (r_cut + skin)/2 with atomic slots; sort_phase puts each
+// cell's slots in bead-atom order (so that every list, and every later sum,
+// has a fixed order); build_cell scans the 5^3 stencil of one cell.
 
-template <int PM>
-__global__ void k_bin(Dev d, int cur)
+__device__ __forceinline__ int rep_of(const Dev &d, long long g)  // replica holding bead-atom g
 {
-    if (d.flag[cur] == 0u) return;
-    typedef typename PosT<PM, double>::S PS;
-    typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
-    const DRep R = d.rep[blockIdx.y];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= R.N) return;
-    const size_t G = (size_t)d.G;
-    const long long g = R.g0 + i;
-    PS *X = reinterpret_cast<PS *>(d.x);
-    PS *XR = reinterpret_cast<PS *>(d.xref);
-    PS w[3];
-    int cc[3];
-    for (int c = 0; c < 3; ++c) {
-        const PS xw = PosT<PM, double>::wrap(X[c * G + g], R.box[c]);
-        X[c * G + g] = xw;
-        XR[c * G + g] = xw;
-        w[c] = xw;
-        int v;
-        if (PM == PM_FIX) v = (int)(((unsigned long long)(unsigned)xw * (unsigned)R.nc[c]) >> kFixBits);
-        else v = (int)floor((double)xw / R.box[c] * R.nc[c]);
-        cc[c] = min(max(v, 0), R.nc[c] - 1);
+    int lo = 0, hi = d.nrep - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d.rep[mid].g0 <= g) lo = mid; else hi = mid - 1;
     }
-    E4 p;
-    p.x = w[0]; p.y = w[1]; p.z = w[2];
-    if (PM == PM_FIX) p.w = d.typ[g]; else p.w = (double)d.typ[g];
-    reinterpret_cast<E4 *>(d.pos[cur])[g] = p;
-    const int cell = R.cell0 + cc[0] + R.nc[0] * (cc[1] + R.nc[1] * cc[2]);
-    const int slot = atomicAdd(&d.cnt[cell], 1);
-    if (slot < d.cap)
-        d.cidx[(size_t)cell * d.cap + slot] = (int)g;
-    else
-        atomicOr(d.err, (unsigned)ERR_OVERFLOW);
+    return lo;
 }
 
 template <int PM>
-__global__ void k_cellsort(Dev d, int cur)
+__device__ void bin_phase(const Dev &d, int cur)
 {
-    if (d.flag[cur] == 0u) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cell = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (cell >= d.ncells) return;
-    constexpr int E = kMaxCellCap / 32;
-    const int n = min(d.cnt[cell], d.cap);
-    const int ne = (n + 31) >> 5;
-    int key[E], rank[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        int idx = lane + 32 * e;
-        key[e] = (idx < n) ? d.cidx[(size_t)cell * d.cap + idx] : INT_MAX;
-        rank[e] = 0;
-    }
-    for (int e2 = 0; e2 < ne; ++e2) {
-        int kv = 0;
-#pragma unroll
-        for (int e = 0; e < E; ++e)
-            if (e == e2) kv = key[e];
-        for (int l = 0; l < 32; ++l) {
-            const int other = __shfl_sync(0xffffffffu, kv, l);
-#pragma unroll
-            for (int e = 0; e < E; ++e)
-                if (e < ne) rank[e] += (other < key[e]) ? 1 : 0;
-        }
-    }
-    __syncwarp();
+    typedef typename PosT<PM, double>::S PS;
+    typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
     const size_t G = (size_t)d.G;
-    const int g0 = d.rep[d.cell_rep[cell]].g0;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        int idx = lane + 32 * e;
-        if (idx < n) {
-            int g = key[e];
-            size_t o = (size_t)cell * d.cap + rank[e];
+    PS *X = reinterpret_cast<PS *>(d.x);
+    PS *XR = reinterpret_cast<PS *>(d.xref);
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += (long long)gridDim.x * blockDim.x) {
+        const DRep &R = d.rep[rep_of(d, g)];
+        PS w[3];
+        int cc[3];
+        for (int c = 0; c < 3; ++c) {
+            const double L = R.box[c];
+            const int ncc = R.nc[c];
+            const PS xw = PosT<PM, double>::wrap(X[c * G + g], L);
+            X[c * G + g] = xw;
+            XR[c * G + g] = xw;
+            w[c] = xw;
+            int v;
+            if (PM == PM_FIX) v = (int)(((unsigned long long)(unsigned)xw * (unsigned)ncc) >> kFixBits);
+            else v = (int)floor((double)xw / L * ncc);
+            cc[c] = min(max(v, 0), ncc - 1);
+        }
+        E4 p;
+        p.x = w[0]; p.y = w[1]; p.z = w[2];
+        if (PM == PM_FIX) p.w = d.typ[g]; else p.w = (double)d.typ[g];
+        reinterpret_cast<E4 *>(d.pos[cur])[g] = p;
+        const int cell = R.cell0 + cc[0] + R.nc[0] * (cc[1] + R.nc[1] * cc[2]);
+        const int slot = atomicAdd(&d.cnt[cell], 1);
+        if (slot < d.cap)
+            d.cidx[(size_t)cell * d.cap + slot] = (int)g;
+        else
+            atomicOr(d.err, (unsigned)ERR_OVERFLOW);
+    }
+}
+
+// one warp per cell; keys: kMaxCellCap ints of shared memory per warp
+template <int PM>
+__device__ void sort_phase(const Dev &d, int *keys)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    int *kw = keys + warp * kMaxCellCap;
+    const size_t G = (size_t)d.G;
+    for (int cell = blockIdx.x * nw + warp; cell < d.ncells; cell += gridDim.x * nw) {
+        const int n = min(d.cnt[cell], d.cap);
+        for (int e = lane; e < n; e += 32) kw[e] = d.cidx[(size_t)cell * d.cap + e];
+        __syncwarp();
+        const int g0 = d.rep[d.cell_rep[cell]].g0;
+        for (int e = lane; e < n; e += 32) {
+            const int g = kw[e];
+            int rank = 0;
+            for (int t = 0; t < n; ++t) rank += (kw[t] < g) ? 1 : 0;
+            const size_t o = (size_t)cell * d.cap + rank;
             d.cidx[o] = g;
             if (PM == PM_FIX) {
                 const int *X = reinterpret_cast<const int *>(d.x);
@@ -422,11 +422,11 @@ __global__ void k_cellsort(Dev d, int cur)
                 reinterpret_cast<D4 *>(d.cpos)[o] = D4{X[g], X[G + g], X[2 * G + g], (double)(g - g0)};
             }
         }
-    }
-    __syncwarp();
-    if (lane == 0) {
-        d.ccount[cell] = n;
-        d.cnt[cell] = 0;
+        __syncwarp();
+        if (lane == 0) {
+            d.ccount[cell] = n;
+            d.cnt[cell] = 0;
+        }
     }
 }
 
@@ -439,19 +439,22 @@ __global__ void k_cellsort(Dev d, int cur)
 constexpr int kStencilHalf = 2;
 constexpr int kStencil = (2 * kStencilHalf + 1) * (2 * kStencilHalf + 1) * (2 * kStencilHalf + 1);
 
+// shared memory of build_cell (besides the staging chunk)
+struct BuildSmem {
+    int soff[kStencil + 1], scell[kStencil], simg[kStencil][3];
+    int scount[kMaxCellCap];
+};
+
 template <int PM, class R>
-__global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_build_list(Dev d, R rl2, int cur)
+__device__ void build_cell(const Dev &d, R rl2, int cell, void *stage_mem, BuildSmem &B)
 {
-    if (d.flag[cur] == 0u) return;
     typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
     constexpr int SH = kStencilHalf, SW = 2 * kStencilHalf + 1;
-    extern __shared__ __align__(32) unsigned char fsm[];
-    __shared__ int soff[kStencil + 1], scell[kStencil], simg[kStencil][3];
-    __shared__ int scount[kMaxCellCap];
-    E4 *stage = reinterpret_cast<E4 *>(fsm);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cell = blockIdx.x;
-    if (cell == 0 && threadIdx.x == 0) atomicAdd(d.nrebuild, 1ull);
+    int *soff = B.soff, *scell = B.scell, *scount = B.scount;
+    int (*simg)[3] = B.simg;
+    E4 *stage = reinterpret_cast<E4 *>(stage_mem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    __syncthreads();  // the previous cell of this CTA is done with the shared memory
     const int cnt = d.ccount[cell];
     if (cnt == 0) return;  // uniform over the CTA
     const DRep RP = d.rep[d.cell_rep[cell]];
@@ -506,7 +509,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_build_list(Dev d, R 
         __syncthreads();  // the previous chunk is scanned
         // flat staging: every thread first issues all of its (independent) loads,
         // then shifts by the image and stores
-        constexpr int U = 8;
+        constexpr int U = 4;
         for (int base = 0; base < cn; base += U * (int)blockDim.x) {
             E4 buf[U];
             int tcell[U], dst[U];
@@ -554,7 +557,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_build_list(Dev d, R 
             else reinterpret_cast<D4 *>(stage)[e] = D4{-1e30, -1e30, -1e30, 0.0};
         }
         __syncthreads();
-        for (int slot = warp; slot < cnt; slot += kWarpsPerForceCta) {
+        for (int slot = warp; slot < cnt; slot += nwarp) {
             // the home bead-atom: its own cell, image 0
             const E4 hp = reinterpret_cast<const E4 *>(d.cpos)[(size_t)cell * d.cap + slot];
             const int gi = d.cidx[(size_t)cell * d.cap + slot];
@@ -597,11 +600,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerForceCta) k_build_list(Dev d, R 
     }
 }
 
-template <int PM> size_t build_list_smem(int entries)
-{
-    typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
-    return (size_t)entries * sizeof(E4);
-}
 
 // ---------------------------------------------------------------------------
 // Pair force: Buckingham (energy-shifted) + damped shifted force Coulomb.
@@ -736,24 +734,20 @@ __device__ void reduce_system(const Dev &d, int s, long long step, int record, d
 // next step.  Recorded steps: the last CTA of a system reduces its partials.
 
 template <int PM, class R, int ADV, int REC>
-__global__ void __launch_bounds__(32 * kListWarps) k_force_list(Dev d, PairTabT<R> T, int kick, int j, int cur,
-                                                             cudaGraphConditionalHandle hnext)
+__device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, int kick, int j, int cur, int u,
+                                           double (*red)[kNQ], double (*rsh)[kNQ + 1], int &s_last)
 {
     typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
     typedef typename std::conditional<sizeof(R) == 4, FF, DD>::type ACC;
     typedef typename PosT<PM, R>::S PS;
     constexpr int LPA = kListLanes, APW = 32 / kListLanes;
-    __shared__ double red[kListWarps][kNQ];
-    __shared__ double rsh[kListWarps][kNQ + 1];
-    __shared__ int s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sub = lane & (LPA - 1), grp = lane / LPA;
-    const DRep RP = d.rep[d.lcta_rep[blockIdx.x]];
-    const int i = (blockIdx.x - RP.fcta0) * kListAtoms + warp * APW + grp;
+    const DRep RP = d.rep[d.lcta_rep[u]];
+    const int i = (u - RP.fcta0) * kListAtoms + warp * APW + grp;
     const bool act = i < RP.N;
     const long long step = d.clock[0] * kBlockSteps + j + 1;
     const bool rec = REC && ((kick == 0) || (step % d.obs_stride == 0));
-    if (blockIdx.x == 0 && threadIdx.x == 0) d.flag[cur] = 0u;  // this step's rebuild request is consumed
     const DSys &S = d.sys[RP.sys];
     const size_t G = (size_t)d.G;
     const long long gi = RP.g0 + (act ? i : 0);
@@ -881,8 +875,8 @@ __global__ void __launch_bounds__(32 * kListWarps) k_force_list(Dev d, PairTabT<
     if (REC && rec) {
 #pragma unroll
         for (int q = 0; q < kNQ; ++q) acc[q] = warp_sum(acc[q]);
-        cta_store_partials(acc, red, d.part + (size_t)blockIdx.x * kNQ);
-        // last CTA of this system reduces (partials made visible first)
+        cta_store_partials(acc, red, d.part + (size_t)u * kNQ);
+        // the CTA with the system's last unit reduces (partials made visible first)
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -896,7 +890,37 @@ __global__ void __launch_bounds__(32 * kListWarps) k_force_list(Dev d, PairTabT<
             if (threadIdx.x == 0) d.done[RP.sys] = 0u;
         }
     }
-    if (ADV) grid_set_rebuild(d, cur ^ 1, hnext);
+}
+
+// One step of the pair-potential systems, a cooperative launch whose CTAs
+// (at most one wave) loop over the force units (kListAtoms bead-atoms each).
+// When the producer of this step's positions requested a rebuild (flag[cur]),
+// the grid first bins, sorts and builds the lists, phases separated by grid
+// barriers.  Dynamic shared memory: the staging chunk of the list build
+// (stage_cap entries; also the sort keys).
+template <int PM, class R, int ADV, int REC>
+__global__ void __launch_bounds__(32 * kListWarps, sizeof(R) == 4 ? 10 : 4) k_step(Dev d, PairTabT<R> T, int kick, int j, int cur)
+{
+    extern __shared__ __align__(32) unsigned char fsm[];
+    __shared__ BuildSmem B;
+    __shared__ double red[kListWarps][kNQ];
+    __shared__ double rsh[kListWarps][kNQ + 1];
+    __shared__ int s_last;
+    // read by every thread before the flag can be cleared (after the first barrier)
+    const bool rebuild = *(volatile const unsigned *)&d.flag[cur] != 0u;
+    if (rebuild) {
+        bin_phase<PM>(d, cur);
+        grid_barrier(d);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            d.flag[cur] = 0u;  // this step's rebuild request is consumed
+            atomicAdd(d.nrebuild, 1ull);
+        }
+        sort_phase<PM>(d, reinterpret_cast<int *>(fsm));
+        grid_barrier(d);
+        for (int cell = blockIdx.x; cell < d.ncells; cell += gridDim.x) build_cell<PM, R>(d, T.rl2, cell, fsm, B);
+        grid_barrier(d);
+    }
+    for (int u = blockIdx.x; u < d.nunits; u += gridDim.x) force_unit<PM, R, ADV, REC>(d, T, kick, j, cur, u, red, rsh, s_last);
 }
 
 // External separable potentials, one thread per bead-atom.  grid = (gx, nsys)
@@ -971,14 +995,11 @@ __global__ void k_setclock(Dev d, long long b) { d.clock[0] = b; }
 bool md_supported_P(int P) { return (P >= 1 && P <= 6) || P == 8 || P == 16 || P == 32; }
 
 template <int PM, class R>
-static void integrate_all(const Dev &d, const MdLaunch &m, int j, int cur, cudaGraphConditionalHandle h,
-                          cudaStream_t st)
+static void integrate_all(const Dev &d, const MdLaunch &m, int j, int cur, cudaStream_t st)
 {
     for (int u = 0; u < m.nP; ++u) {
-        // only the last launch of the step decides the rebuild branch
-        const cudaGraphConditionalHandle hu = (u == m.nP - 1) ? h : 0;
         switch (m.Pvals[u]) {
-#define QTB_P(PP) case PP: k_integrate<PP, PM, R><<<m.n_icta, 128, 0, st>>>(d, j, cur, hu); break;
+#define QTB_P(PP) case PP: k_integrate<PP, PM, R><<<m.n_icta, 128, 0, st>>>(d, j, cur); break;
             QTB_P(1) QTB_P(2) QTB_P(3) QTB_P(4) QTB_P(5) QTB_P(6) QTB_P(8) QTB_P(16) QTB_P(32)
 #undef QTB_P
             default: break;
@@ -986,69 +1007,90 @@ static void integrate_all(const Dev &d, const MdLaunch &m, int j, int cur, cudaG
     }
 }
 
-void launch_integrate(const Dev &d, const MdLaunch &m, int j, int cur, cudaGraphConditionalHandle h, cudaStream_t st)
+void launch_integrate(const Dev &d, const MdLaunch &m, int j, int cur, cudaStream_t st)
 {
     if (!m.pair) {
-        if (m.mixed) integrate_all<PM_FREE, float>(d, m, j, cur, 0, st);
-        else integrate_all<PM_FREE, double>(d, m, j, cur, 0, st);
+        if (m.mixed) integrate_all<PM_FREE, float>(d, m, j, cur, st);
+        else integrate_all<PM_FREE, double>(d, m, j, cur, st);
     } else {
-        if (m.mixed) integrate_all<PM_FIX, float>(d, m, j, cur, h, st);
-        else integrate_all<PM_BOX64, double>(d, m, j, cur, h, st);
+        if (m.mixed) integrate_all<PM_FIX, float>(d, m, j, cur, st);
+        else integrate_all<PM_BOX64, double>(d, m, j, cur, st);
     }
 }
 
-size_t list_build_smem(int entries, int mixed)
+template <int PM, class R, int ADV, int REC>
+static cudaError_t step_prepare_one(size_t smem, int nsm, int &grid)
 {
-    return mixed ? build_list_smem<PM_FIX>(entries) : build_list_smem<PM_BOX64>(entries);
+    cudaError_t e = cudaFuncSetAttribute(k_step<PM, R, ADV, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<PM, R, ADV, REC>, 32 * kListWarps, smem);
+    grid = per_sm * nsm;
+    return e;
 }
 
-cudaError_t list_build_prepare(int entries, int mixed)
+cudaError_t step_prepare(MdLaunch &m, int stage_entries)
 {
-    const int sm = (int)list_build_smem(entries, mixed);
-    if (mixed) return cudaFuncSetAttribute(k_build_list<PM_FIX, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    return cudaFuncSetAttribute(k_build_list<PM_BOX64, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-}
-
-void launch_rebuild(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td, int cur,
-                    cudaStream_t st)
-{
-    if (!m.pair) return;
-    dim3 g((unsigned)m.n_bcta, (unsigned)d.nrep);
-    const size_t sm = list_build_smem(d.stage_cap, m.mixed);
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    m.step_smem = (size_t)stage_entries * (m.mixed ? sizeof(int4) : sizeof(D4));
     if (m.mixed) {
-        k_bin<PM_FIX><<<g, 256, 0, st>>>(d, cur);
-        k_cellsort<PM_FIX><<<(d.ncells + 7) / 8, 256, 0, st>>>(d, cur);
-        k_build_list<PM_FIX, float><<<d.ncells, 32 * kWarpsPerForceCta, sm, st>>>(d, Tf.rl2, cur);
+        if ((e = step_prepare_one<PM_FIX, float, 0, 0>(m.step_smem, nsm, m.step_grid[0])) != cudaSuccess) return e;
+        if ((e = step_prepare_one<PM_FIX, float, 0, 1>(m.step_smem, nsm, m.step_grid[1])) != cudaSuccess) return e;
+        if ((e = step_prepare_one<PM_FIX, float, 1, 0>(m.step_smem, nsm, m.step_grid[2])) != cudaSuccess) return e;
+        e = step_prepare_one<PM_FIX, float, 1, 1>(m.step_smem, nsm, m.step_grid[3]);
     } else {
-        k_bin<PM_BOX64><<<g, 256, 0, st>>>(d, cur);
-        k_cellsort<PM_BOX64><<<(d.ncells + 7) / 8, 256, 0, st>>>(d, cur);
-        k_build_list<PM_BOX64, double><<<d.ncells, 32 * kWarpsPerForceCta, sm, st>>>(d, Td.rl2, cur);
+        if ((e = step_prepare_one<PM_BOX64, double, 0, 0>(m.step_smem, nsm, m.step_grid[0])) != cudaSuccess) return e;
+        if ((e = step_prepare_one<PM_BOX64, double, 0, 1>(m.step_smem, nsm, m.step_grid[1])) != cudaSuccess) return e;
+        if ((e = step_prepare_one<PM_BOX64, double, 1, 0>(m.step_smem, nsm, m.step_grid[2])) != cudaSuccess) return e;
+        e = step_prepare_one<PM_BOX64, double, 1, 1>(m.step_smem, nsm, m.step_grid[3]);
     }
+    return e;
+}
+
+// cooperative launch: all CTAs resident at once (the grid barriers need it)
+template <int PM, class R, int ADV, int REC>
+static cudaError_t step_launch(const Dev &d, const MdLaunch &m, const PairTabT<R> &T, int kick, int j, int cur,
+                               cudaStream_t st)
+{
+    const int grid = std::min(d.nunits, m.step_grid[ADV * 2 + REC]);
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(32 * kListWarps);
+    cfg.dynamicSmemBytes = m.step_smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_step<PM, R, ADV, REC>, d, T, kick, j, cur);
 }
 
 template <int PM, class R>
-static void force_list(const Dev &d, const MdLaunch &m, const PairTabT<R> &T, int kick, int j, int cur, int adv,
-                       int rec, cudaGraphConditionalHandle h, cudaStream_t st)
+static cudaError_t step_any(const Dev &d, const MdLaunch &m, const PairTabT<R> &T, int kick, int j, int cur, int adv,
+                            int rec, cudaStream_t st)
 {
-    const unsigned grid = (unsigned)m.n_lcta;
-    const int blk = 32 * kListWarps;
-    if (adv && rec) k_force_list<PM, R, 1, 1><<<grid, blk, 0, st>>>(d, T, kick, j, cur, h);
-    else if (adv) k_force_list<PM, R, 1, 0><<<grid, blk, 0, st>>>(d, T, kick, j, cur, h);
-    else if (rec) k_force_list<PM, R, 0, 1><<<grid, blk, 0, st>>>(d, T, kick, j, cur, 0);
-    else k_force_list<PM, R, 0, 0><<<grid, blk, 0, st>>>(d, T, kick, j, cur, 0);
+    if (adv && rec) return step_launch<PM, R, 1, 1>(d, m, T, kick, j, cur, st);
+    if (adv) return step_launch<PM, R, 1, 0>(d, m, T, kick, j, cur, st);
+    if (rec) return step_launch<PM, R, 0, 1>(d, m, T, kick, j, cur, st);
+    return step_launch<PM, R, 0, 0>(d, m, T, kick, j, cur, st);
 }
 
-void launch_force(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td, int kick,
-                  int j, int cur, int adv, int rec, cudaGraphConditionalHandle h, cudaStream_t st)
+cudaError_t launch_force(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,
+                         int kick, int j, int cur, int adv, int rec, cudaStream_t st)
 {
     if (m.pair) {
-        if (m.mixed) force_list<PM_FIX, float>(d, m, Tf, kick, j, cur, adv, rec, h, st);
-        else force_list<PM_BOX64, double>(d, m, Td, kick, j, cur, adv, rec, h, st);
-    } else {
-        dim3 g((unsigned)m.n_ecta, (unsigned)d.nsys);
-        if (m.mixed) k_force_ext<float><<<g, 128, 0, st>>>(d, Tf, kick);
-        else k_force_ext<double><<<g, 128, 0, st>>>(d, Td, kick);
+        if (m.mixed) return step_any<PM_FIX, float>(d, m, Tf, kick, j, cur, adv, rec, st);
+        return step_any<PM_BOX64, double>(d, m, Td, kick, j, cur, adv, rec, st);
     }
+    dim3 g((unsigned)m.n_ecta, (unsigned)d.nsys);
+    if (m.mixed) k_force_ext<float><<<g, 128, 0, st>>>(d, Tf, kick);
+    else k_force_ext<double><<<g, 128, 0, st>>>(d, Td, kick);
+    return cudaGetLastError();
 }
 
 void launch_reduce(const Dev &d, const MdLaunch &m, int j, int record, cudaStream_t st)

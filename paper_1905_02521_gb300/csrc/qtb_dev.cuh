@@ -33,7 +33,7 @@ enum { Q_K = 0, Q_V = 1, Q_SPRING = 2, Q_VIR = 3 /* 6 slots: xx yy zz xy xz yz *
 enum { PM_BOX64 = 0, PM_FIX = 1, PM_FREE = 2 };
 
 // device error word bits
-enum { ERR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_SOLVE = 4, ERR_TIMEOUT_TC = 8, ERR_NBR_OVERFLOW = 16 };
+enum { ERR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_SOLVE = 4, ERR_TIMEOUT_TC = 8, ERR_NBR_OVERFLOW = 16, ERR_TIMEOUT_BAR = 32 };
 
 // Neighbour-list entry (32 bits): replica-local index j in bits 0..25, the
 // periodic image m of the entry (per component m mod 4, two bits each: x at
@@ -116,7 +116,8 @@ struct Dev {
     const DSys *sys;
     const DRep *rep;
     const int *cell_rep;  // [ncells]
-    const int *lcta_rep;  // [list force CTAs] replica of each CTA
+    const int *lcta_rep;  // [nunits] replica of each force unit (kListAtoms bead-atoms)
+    int nunits;           // force units
     const int *icta_sys;  // [integrator CTAs] system of each CTA
     const int *ext_cta_sys;
     // state
@@ -136,7 +137,7 @@ struct Dev {
     int *nnb;             // [G] entries per bead-atom
     int maxnb;
     unsigned *flag;       // [2] rebuild requests; flag[s & 1] is set by whoever produces the positions of step s
-    unsigned *gdone;      // CTAs finished (grid-wide last-CTA decisions), reset by the last one
+    unsigned *gbar;       // [2] grid barrier of the cooperative step kernel: arrivals, generation
     unsigned long long *nrebuild;  // list rebuilds carried out
     // noise
     void *ring;           // [nslots][Dtot][256] white noise (double, float or bf16)

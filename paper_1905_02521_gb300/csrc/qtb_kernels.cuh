@@ -40,31 +40,28 @@ struct MdLaunch {
     int mixed;            // 0: FP64 form, 1: mixed form
     int pair;             // pair potential (else external)
     int n_icta;           // integrator CTAs
-    int n_bcta;           // binning CTAs per replica
     int n_ecta;           // external-force CTAs per system
-    int n_lcta;           // list force CTAs (kListAtoms bead-atoms each)
     int nP;               // number of distinct bead counts
     int Pvals[8];         // distinct bead counts
-    int fused;            // all systems one-bead with a pair potential: the force kernel
+    int fused;            // all systems one-bead with a pair potential: the step kernel
                           // carries out the first half of the next step
+    int step_grid[4];     // resident CTAs of the step kernel, by (adv, rec)
+    size_t step_smem;     // its dynamic shared memory (list build staging chunk)
 };
 constexpr int kIntAtomsPerWarp = 10;                   // integrator: lanes 3a + c, a < 10
 constexpr int kIntAtomsPerCta = 4 * kIntAtomsPerWarp;  // 128 threads
 constexpr int kStencilCells = 125;                     // 5^3 stencil of (r_cut + skin)/2 cells
-// dynamic shared memory of the list build kernel for `entries` staged neighbours
-size_t list_build_smem(int entries, int mixed);
-cudaError_t list_build_prepare(int entries, int mixed);
-// positions of step s: the integrator writes pos[cur], cur = s & 1, and with a
-// conditional handle decides the graph's rebuild branch
-void launch_integrate(const Dev &d, const MdLaunch &m, int j, int cur, cudaGraphConditionalHandle h, cudaStream_t st);
-// bin, sort, build lists; each launch returns at once unless flag[cur] is set
-void launch_rebuild(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td, int cur,
-                    cudaStream_t st);
-// pair force from the lists (kick: closing B step; adv: also the first half of
-// step j + 1, positions to pos[cur ^ 1], rebuild decision through h; rec: the
-// step may be recorded, then the kernel also reduces the observables)
-void launch_force(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td, int kick,
-                  int j, int cur, int adv, int rec, cudaGraphConditionalHandle h, cudaStream_t st);
+// attributes and resident grid sizes of the cooperative step kernel
+cudaError_t step_prepare(MdLaunch &m, int stage_entries);
+// positions of step s: the integrator writes pos[cur], cur = s & 1, and
+// requests a list rebuild in flag[cur] when some bead-atom moved skin/2
+void launch_integrate(const Dev &d, const MdLaunch &m, int j, int cur, cudaStream_t st);
+// one step's force (pair potential: the cooperative step kernel, which first
+// rebuilds the lists when flag[cur] is set).  kick: closing B step; adv: also
+// the first half of step j + 1, positions to pos[cur ^ 1]; rec: the step may
+// be recorded, then the kernel also reduces the observables
+cudaError_t launch_force(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,
+                         int kick, int j, int cur, int adv, int rec, cudaStream_t st);
 void launch_reduce(const Dev &d, const MdLaunch &m, int j, int record, cudaStream_t st);
 void launch_tick(const Dev &d, cudaStream_t st);
 void launch_setclock(const Dev &d, long long blk, cudaStream_t st);
