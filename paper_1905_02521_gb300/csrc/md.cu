@@ -611,36 +611,49 @@ __device__ __forceinline__ double my_erfc(double x) { return erfc(x); }
 __device__ __forceinline__ float my_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double my_sqrt(double x) { return sqrt(x); }
 
+// Coefficients of one type pair, staged in shared memory by the step kernel
+// (the pair type varies across the lanes of a warp).
+template <class R> struct alignas(8 * sizeof(R)) PairRow {
+    R inv_rho, A_over_rho, C6, qq, A, C, eshift, pad;
+};
+
+template <class R> __device__ __forceinline__ PairRow<R> pair_row(const PairTabT<R> &T, int t)
+{
+    PairRow<R> p;
+    p.inv_rho = T.inv_rho[t]; p.A_over_rho = T.A_over_rho[t]; p.C6 = T.C6[t]; p.qq = T.qq[t];
+    p.A = T.A[t]; p.C = T.C[t]; p.eshift = T.eshift[t]; p.pad = R(0);
+    return p;
+}
+
 // -dV/dr / r and V of one pair at squared distance r2 < rc^2, FP32 form:
 // branch-free, 1/r from rsqrt + one Newton step, the steep Buckingham
 // exponential by expf (its argument reaches ~50), exp(-alpha^2 r^2) (argument
 // < 3) through exp2, erfc(x) = exp(-x^2) P(u) with the fitted polynomial of the
-// table.  This
-// file is compiled without automatic multiply-add contraction: every fused
-// multiply-add is written out, so that all kernels round alike.
-__device__ __forceinline__ void pair_eval(const PairTabT<float> &T, int tij, float r2, float &f_over_r, float &e,
-                                          bool energy = true)
+// table.  This file is compiled without automatic multiply-add contraction:
+// every fused multiply-add is written out, so that all kernels round alike.
+__device__ __forceinline__ void pair_eval(const PairTabT<float> &T, const PairRow<float> &P2, float r2, float &f_over_r,
+                                          float &e, bool energy = true)
 {
     float rinv = rsqrtf(r2);
     rinv = rinv * fmaf(-0.5f * r2, rinv * rinv, 1.5f);
     const float r = r2 * rinv;
     const float r2i = rinv * rinv;
     const float r6i = r2i * r2i * r2i;
-    const float ex = expf(-r * T.inv_rho[tij]);              // exp(-r/rho); A = 0 rows give 0 below
+    const float ex = expf(-r * P2.inv_rho);                  // exp(-r/rho); A = 0 rows give 0 below
     const float gg = exp2f(-T.alpha2_l2e * r2);              // exp(-alpha^2 r^2)
     const float u = fmaf(T.alpha * r, T.erfc_us, -1.0f);
     float P = T.erfc_c[11];
 #pragma unroll
     for (int k = 10; k >= 0; --k) P = fmaf(P, u, T.erfc_c[k]);
     const float er = gg * P;                                  // erfc(alpha r)
-    const float qq = T.qq[tij];
+    const float qq = P2.qq;
     // A/rho e^{-r/rho} - 6C/r^7 + qq (erfc/r^2 + 2a/sqrt(pi) e^{-a^2 r^2}/r - fshift), times 1/r
-    const float fb = fmaf(T.A_over_rho[tij], ex, -(T.C6[tij] * r6i * rinv));
+    const float fb = fmaf(P2.A_over_rho, ex, -(P2.C6 * r6i * rinv));
     const float fc = fmaf(er, r2i, fmaf(T.two_a_sqrtpi * gg, rinv, -T.fshift));
     f_over_r = fmaf(qq, fc, fb) * rinv;
     if (energy) {
         const float ec = fmaf(er, rinv, fmaf(T.fshift, r - T.rc, -T.erfc_rc_over_rc));
-        e = fmaf(qq, ec, fmaf(T.A[tij], ex, fmaf(-T.C[tij], r6i, -T.eshift[tij])));
+        e = fmaf(qq, ec, fmaf(P2.A, ex, fmaf(-P2.C, r6i, -P2.eshift)));
     } else {
         e = 0.0f;
     }
@@ -648,25 +661,26 @@ __device__ __forceinline__ void pair_eval(const PairTabT<float> &T, int tij, flo
 
 // FP64 form: library exp / erfc / sqrt (the reference-accuracy path)
 template <class R>
-__device__ __forceinline__ void pair_eval(const PairTabT<R> &T, int tij, R r2, R &f_over_r, R &e, bool energy = true)
+__device__ __forceinline__ void pair_eval(const PairTabT<R> &T, const PairRow<R> &P2, R r2, R &f_over_r, R &e,
+                                          bool energy = true)
 {
     const R r = my_sqrt(r2);
     const R rinv = R(1) / r;
     R f = 0, en = 0;
-    const R A = T.A[tij], Cc = T.C[tij];
+    const R A = P2.A, Cc = P2.C;
     if (A != R(0)) {
-        const R ex = my_exp(-r * T.inv_rho[tij]);
-        f = T.A_over_rho[tij] * ex;
+        const R ex = my_exp(-r * P2.inv_rho);
+        f = P2.A_over_rho * ex;
         en = A * ex;
     }
     if (Cc != R(0)) {
         const R r2i = rinv * rinv;
         const R r6i = r2i * r2i * r2i;
-        f = fma(-T.C6[tij] * r6i, rinv, f);
+        f = fma(-P2.C6 * r6i, rinv, f);
         en = fma(-Cc, r6i, en);
     }
-    en -= T.eshift[tij];
-    const R qq = T.qq[tij];
+    en -= P2.eshift;
+    const R qq = P2.qq;
     if (qq != R(0)) {
         const R er = my_erfc(T.alpha * r);
         const R gg = my_exp(-T.alpha2 * r2);
@@ -734,8 +748,9 @@ __device__ void reduce_system(const Dev &d, int s, long long step, int record, d
 // next step.  Recorded steps: the last CTA of a system reduces its partials.
 
 template <int PM, class R, int ADV, int REC>
-__device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, int kick, int j, int cur, int u,
-                                           double (*red)[kNQ], double (*rsh)[kNQ + 1], int &s_last)
+__device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, const PairRow<R> *ptab, int kick,
+                                           int j, int cur, int u, double (*red)[kNQ], double (*rsh)[kNQ + 1],
+                                           int &s_last)
 {
     typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
     typedef typename std::conditional<sizeof(R) == 4, FF, DD>::type ACC;
@@ -788,7 +803,7 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, i
         }
         const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         R fo, ee;
-        pair_eval(T, ti * kMaxTypes + tj, r2, fo, ee, REC && rec);
+        pair_eval(T, ptab[ti * kMaxTypes + tj], r2, fo, ee, REC && rec);
         const bool in = valid && (r2 < rc2);
         fo = in ? fo : R(0);
         // stored displacement is r_j - r_i: the force on i is -fo (r_j - r_i)
@@ -800,17 +815,22 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, i
         }
     };
     {
-        // entries k and k + LPA of this lane; the next pair is requested before
-        // the current one is evaluated (invalid slots repeat a valid entry, masked)
+        // entries k + q LPA (q < NE) of this lane; the next NE are requested before
+        // the current ones are evaluated (slots past the end read entry 0, masked)
+        constexpr int NE = 4;
         int k = sub;
-        unsigned ea = (k < n) ? row[k] : 0u, eb = (k + LPA < n) ? row[k + LPA] : ea;
-        for (; k < n; k += 2 * LPA) {
-            const int kn = k + 2 * LPA;
-            const unsigned na = (kn < n) ? row[kn] : ea, nb = (kn + LPA < n) ? row[kn + LPA] : ea;
-            pair(ea, true);
-            pair(eb, k + LPA < n);
-            ea = na;
-            eb = nb;
+        unsigned e[NE];
+#pragma unroll
+        for (int q = 0; q < NE; ++q) e[q] = (k + q * LPA < n) ? row[k + q * LPA] : 0u;
+        for (; k < n; k += NE * LPA) {
+            const int kn = k + NE * LPA;
+            unsigned e2[NE];
+#pragma unroll
+            for (int q = 0; q < NE; ++q) e2[q] = (kn + q * LPA < n) ? row[kn + q * LPA] : 0u;
+#pragma unroll
+            for (int q = 0; q < NE; ++q) pair(e[q], k + q * LPA < n);
+#pragma unroll
+            for (int q = 0; q < NE; ++q) e[q] = e2[q];
         }
     }
     fx.template group_reduce<LPA>(); fy.template group_reduce<LPA>(); fz.template group_reduce<LPA>();
@@ -899,10 +919,13 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, i
 // barriers.  Dynamic shared memory: the staging chunk of the list build
 // (stage_cap entries; also the sort keys).
 template <int PM, class R, int ADV, int REC>
-__global__ void __launch_bounds__(32 * kListWarps, sizeof(R) == 4 ? 10 : 4) k_step(Dev d, PairTabT<R> T, int kick, int j, int cur)
+__global__ void __launch_bounds__(32 * kListWarps, sizeof(R) == 4 ? 8 : 4) k_step(Dev d, PairTabT<R> T, int kick, int j, int cur)
 {
     extern __shared__ __align__(32) unsigned char fsm[];
     __shared__ BuildSmem B;
+    __shared__ PairRow<R> ptab[kMaxTypes * kMaxTypes];
+    if (threadIdx.x < kMaxTypes * kMaxTypes) ptab[threadIdx.x] = pair_row(T, threadIdx.x);
+    __syncthreads();
     __shared__ double red[kListWarps][kNQ];
     __shared__ double rsh[kListWarps][kNQ + 1];
     __shared__ int s_last;
@@ -920,7 +943,8 @@ __global__ void __launch_bounds__(32 * kListWarps, sizeof(R) == 4 ? 10 : 4) k_st
         for (int cell = blockIdx.x; cell < d.ncells; cell += gridDim.x) build_cell<PM, R>(d, T.rl2, cell, fsm, B);
         grid_barrier(d);
     }
-    for (int u = blockIdx.x; u < d.nunits; u += gridDim.x) force_unit<PM, R, ADV, REC>(d, T, kick, j, cur, u, red, rsh, s_last);
+    for (int u = blockIdx.x; u < d.nunits; u += gridDim.x)
+        force_unit<PM, R, ADV, REC>(d, T, ptab, kick, j, cur, u, red, rsh, s_last);
 }
 
 // External separable potentials, one thread per bead-atom.  grid = (gx, nsys)
