@@ -446,7 +446,7 @@ struct BuildSmem {
 };
 
 template <int PM, class R>
-__device__ void build_cell(const Dev &d, R rl2, int cell, void *stage_mem, BuildSmem &B)
+__device__ void build_cell(const Dev &d, R rc2, R rl2, int cell, void *stage_mem, BuildSmem &B)
 {
     typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
     constexpr int SH = kStencilHalf, SW = 2 * kStencilHalf + 1;
@@ -503,6 +503,9 @@ __device__ void build_cell(const Dev &d, R rl2, int cell, void *stage_mem, Build
     const R sx = (R)RP.fix_scale[0], sy = (R)RP.fix_scale[1], sz = (R)RP.fix_scale[2];
     const unsigned lt = (1u << lane) - 1u;
     const int maxnb = d.maxnb;
+    // pass 0 lists the entries within r_cut, pass 1 those of the skin shell, so
+    // that the shell entries close every list (the force loop can skip them)
+    for (int pass = 0; pass < 2; ++pass)
     for (int c0 = 0; c0 < total; c0 += CH) {
         const int cn = min(CH, total - c0);
         const int padded = (cn + 63) & ~63;
@@ -576,7 +579,7 @@ __device__ void build_cell(const Dev &d, R rl2, int cell, void *stage_mem, Build
                 }
                 const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
                 // the home bead-atom itself (r2 == 0) and the sentinels fail
-                const bool take = r2 < rl2 && r2 > R(0);
+                const bool take = pass == 0 ? (r2 < rc2 && r2 > R(0)) : (r2 >= rc2 && r2 < rl2);
                 const unsigned m = __ballot_sync(0xffffffffu, take);
                 if (take) {
                     const int k = n + __popc(m & lt);
@@ -777,16 +780,20 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
     const R rc2 = T.rc2;
     ACC fx{}, fy{}, fz{};
     R en = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
-    auto pair = [&](unsigned e, bool valid) {
-        const E4 pj = Pr[e & kNbIdx];
-        R dx, dy, dz;
+    struct Geo {
+        R dx, dy, dz, r2;
         int tj;
+    };
+    // r_j + image - r_i of one list entry
+    auto geo = [&](unsigned e) {
+        const E4 pj = Pr[e & kNbIdx];
+        Geo g;
         if (PM == PM_FIX) {
-            // r_j + image - r_i, exact in wrapping 32-bit arithmetic
-            dx = (R)(int)((unsigned)pj.x + ((e << 4) & 0xC0000000u) - (unsigned)hp.x) * sx;
-            dy = (R)(int)((unsigned)pj.y + ((e << 2) & 0xC0000000u) - (unsigned)hp.y) * sy;
-            dz = (R)(int)((unsigned)pj.z + (e & 0xC0000000u) - (unsigned)hp.z) * sz;
-            tj = pj.w;
+            // exact in wrapping 32-bit arithmetic
+            g.dx = (R)(int)((unsigned)pj.x + ((e << 4) & 0xC0000000u) - (unsigned)hp.x) * sx;
+            g.dy = (R)(int)((unsigned)pj.y + ((e << 2) & 0xC0000000u) - (unsigned)hp.y) * sy;
+            g.dz = (R)(int)((unsigned)pj.z + (e & 0xC0000000u) - (unsigned)hp.z) * sz;
+            g.tj = pj.w;
         } else {
             // image from m mod 4: code 2 is +2 or -2, told apart by the sign of
             // the raw difference (the box exceeds r_cut/2 + skin)
@@ -798,37 +805,56 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
                 const int m = (code == 3) ? -1 : (code == 2) ? (pd[c] > 0.0 ? -2 : 2) : code;
                 dv[c] = (R)(pd[c] + m * RP.box[c]);
             }
-            dx = dv[0]; dy = dv[1]; dz = dv[2];
-            tj = (int)pj.w;
+            g.dx = dv[0]; g.dy = dv[1]; g.dz = dv[2];
+            g.tj = (int)pj.w;
         }
-        const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        g.r2 = fma(g.dx, g.dx, fma(g.dy, g.dy, g.dz * g.dz));
+        return g;
+    };
+    // force (and on recorded steps energy and virial) of one entry, masked by `in`
+    auto force = [&](const Geo &g, bool in) {
         R fo, ee;
-        pair_eval(T, ptab[ti * kMaxTypes + tj], r2, fo, ee, REC && rec);
-        const bool in = valid && (r2 < rc2);
+        pair_eval(T, ptab[ti * kMaxTypes + g.tj], g.r2, fo, ee, REC && rec);
         fo = in ? fo : R(0);
         // stored displacement is r_j - r_i: the force on i is -fo (r_j - r_i)
-        fx.add(-fo * dx); fy.add(-fo * dy); fz.add(-fo * dz);
+        fx.add(-fo * g.dx); fy.add(-fo * g.dy); fz.add(-fo * g.dz);
         if (REC && rec) {
             en += in ? ee : R(0);
-            w0 = fma(fo * dx, dx, w0); w1 = fma(fo * dy, dy, w1); w2 = fma(fo * dz, dz, w2);
-            w3 = fma(fo * dx, dy, w3); w4 = fma(fo * dx, dz, w4); w5 = fma(fo * dy, dz, w5);
+            w0 = fma(fo * g.dx, g.dx, w0); w1 = fma(fo * g.dy, g.dy, w1); w2 = fma(fo * g.dz, g.dz, w2);
+            w3 = fma(fo * g.dx, g.dy, w3); w4 = fma(fo * g.dx, g.dz, w4); w5 = fma(fo * g.dy, g.dz, w5);
         }
     };
     {
         // entries k + q LPA (q < NE) of this lane; the next NE are requested before
-        // the current ones are evaluated (slots past the end read entry 0, masked)
+        // the current ones are evaluated (slots past the end read entry 0, masked).
+        // The lists end with the skin-shell entries: a round in which no lane of
+        // the warp has an entry within r_cut skips the pair terms (they would add
+        // exact zeros).  The trip count is the warp's longest list, so the vote
+        // is uniform.
         constexpr int NE = 4;
-        int k = sub;
+        int nmax = n;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
         unsigned e[NE];
 #pragma unroll
-        for (int q = 0; q < NE; ++q) e[q] = (k + q * LPA < n) ? row[k + q * LPA] : 0u;
-        for (; k < n; k += NE * LPA) {
-            const int kn = k + NE * LPA;
+        for (int q = 0; q < NE; ++q) e[q] = (sub + q * LPA < n) ? row[sub + q * LPA] : 0u;
+        for (int k0 = 0; k0 < nmax; k0 += NE * LPA) {
+            const int k = k0 + sub, kn = k + NE * LPA;
             unsigned e2[NE];
 #pragma unroll
             for (int q = 0; q < NE; ++q) e2[q] = (kn + q * LPA < n) ? row[kn + q * LPA] : 0u;
+            Geo g[NE];
+            bool in[NE], any = false;
 #pragma unroll
-            for (int q = 0; q < NE; ++q) pair(e[q], k + q * LPA < n);
+            for (int q = 0; q < NE; ++q) {
+                g[q] = geo(e[q]);
+                in[q] = (k + q * LPA < n) && (g[q].r2 < rc2);
+                any |= in[q];
+            }
+            if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+                for (int q = 0; q < NE; ++q) force(g[q], in[q]);
+            }
 #pragma unroll
             for (int q = 0; q < NE; ++q) e[q] = e2[q];
         }
@@ -940,7 +966,7 @@ __global__ void __launch_bounds__(32 * kListWarps, sizeof(R) == 4 ? 8 : 4) k_ste
         }
         sort_phase<PM>(d, reinterpret_cast<int *>(fsm));
         grid_barrier(d);
-        for (int cell = blockIdx.x; cell < d.ncells; cell += gridDim.x) build_cell<PM, R>(d, T.rl2, cell, fsm, B);
+        for (int cell = blockIdx.x; cell < d.ncells; cell += gridDim.x) build_cell<PM, R>(d, T.rc2, T.rl2, cell, fsm, B);
         grid_barrier(d);
     }
     for (int u = blockIdx.x; u < d.nunits; u += gridDim.x)
