@@ -31,7 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "atom*bead-steps/s on 1 GB300 (QTB-MD, mixed precision)"
+METRIC = "atom*bead-steps/s on 1 GB300 (QTB / QTB-PIMD step, mixed precision)"
 UNIT = "atom*bead-steps/s"
 BLOCK = 256
 
@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ncell", type=int, default=10)
+    ap.add_argument("--workload", default="mgo8000", choices=WORKLOADS)
+    ap.add_argument("--ncell", type=int, default=10, help="cells per side of the mgo8000 workload")
     ap.add_argument("--filter", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -127,32 +128,67 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def workload(ncell, precision, filt):
+WORKLOADS = ("mgo8000", "lih_qtbpimd_p8", "lih_pimd_p32", "sweep64")
+
+
+def workload(name, ncell, precision, filt):
+    """Systems, potential, context parameters, filter set-up and a description.
+
+    mgo8000: MgO 10^3 cells (8000 ions), QTB-MD 100 K, dt 1 fs, 2049 taps, w_max 0.3 rad/fs.
+    lih_qtbpimd_p8: LiH 6^3 cells (1728 ions), QTB-PIMD P = 8 (kappa_P from the solver), 50 K,
+        dt 0.25 fs, 2049 taps, w_max 0.6 rad/fs.
+    lih_pimd_p32: the same crystal, standard PIMD P = 32 with a white Langevin bath.
+    sweep64: 64 MgO systems of 3..8 cells per side (216-4096 ions) at T_i = 10 150^(i/63) K,
+        QTB-MD, one context (batched), dt 1 fs, 2049 taps, w_max 0.3 rad/fs.
+    """
     from paper_1905_02521_gb300 import qtb, workloads as W
-    s, pot = W.mgo_system(ncell, 100.0, gamma=1e-3)
     prec = qtb.MIXED if precision == "mixed" else qtb.FP64
     fp = qtb.FILTER_BF16 if filt == "bf16" else qtb.FILTER_FP32
+    dt, setup = 1.0, None
+    if name == "mgo8000":
+        s, pot = W.mgo_system(ncell, 100.0, gamma=1e-3)
+        systems = [s]
+        setup = (qtb.NOISE_QTB, 2049, 0.3)
+        desc = (f"MgO rock salt {ncell}x{ncell}x{ncell} cells ({len(s['types'])} ions), QTB-MD 100 K, dt 1 fs, "
+                f"2049-tap {filt} noise filter, 256-step blocks")
+    elif name in ("lih_qtbpimd_p8", "lih_pimd_p32"):
+        P = 8 if name == "lih_qtbpimd_p8" else 32
+        s, pot = W.lih_system(6, 50.0, gamma=1e-3, n_beads=P)
+        systems = [s]
+        dt = 0.25
+        if P == 8:
+            setup = (qtb.NOISE_QTB_PIMD, 2049, 0.6)
+            desc = f"LiH rock salt 6x6x6 cells (1728 ions) x 8 beads, QTB-PIMD (kappa_P solver) 50 K, dt 0.25 fs, 2049-tap {filt} filter"
+        else:
+            desc = "LiH rock salt 6x6x6 cells (1728 ions) x 32 beads, PIMD with white Langevin bath 50 K, dt 0.25 fs"
+    elif name == "sweep64":
+        systems, pot = W.sweep_systems(64, gamma=1e-3)
+        setup = (qtb.NOISE_QTB, 2049, 0.3)
+        desc = (f"batched heat-capacity sweep: 64 MgO systems of 3..8 cells per side "
+                f"({sum(len(x['types']) for x in systems)} ions), T = 10-1500 K (log grid), QTB-MD, dt 1 fs, "
+                f"2049-tap {filt} filter, one context")
+    else:
+        raise ValueError(name)
     params = {k: pot[k] for k in ("mass", "charge", "buck_A", "buck_rho", "buck_C")}
-    params.update(dsf_alpha=pot["dsf_alpha"], r_cut=pot["r_cut"], dt=1.0, precision=prec, filter_prec=fp,
+    params.update(dsf_alpha=pot["dsf_alpha"], r_cut=pot["r_cut"], dt=dt, precision=prec, filter_prec=fp,
                   seed=12345, obs_stride=BLOCK, max_records=64)
-    return s, pot, params
+    return systems, pot, params, setup, desc
 
 
 def count_pairs(pos, box, rc):
-    """In-range ordered pairs (all images) of one configuration (host, numpy)."""
-    pos = np.asarray(pos)
+    """In-range ordered pairs (all periodic images) of one configuration (host, k-d tree)."""
+    from scipy.spatial import cKDTree
+    box = np.asarray(box, np.float64)
+    pos = np.mod(np.asarray(pos, np.float64), box)
     n = len(pos)
-    tot = 0
-    nmax = [int(np.ceil(rc / b)) for b in box]
-    shifts = np.array([[i, j, k] for i in range(-nmax[0], nmax[0] + 1) for j in range(-nmax[1], nmax[1] + 1)
-                       for k in range(-nmax[2], nmax[2] + 1)], np.float64) * box
-    for a in range(0, n, 256):
-        d = pos[a:a + 256, None, :] - pos[None, :, :]
-        d -= box * np.round(d / box)
-        for sh in shifts:
-            r2 = ((d + sh) ** 2).sum(-1)
-            tot += int(((r2 < rc * rc) & (r2 > 1e-12)).sum())
-    return tot
+    if box.min() >= 2.0 * rc:
+        tree = cKDTree(pos, boxsize=box)
+    else:
+        nmax = [int(np.ceil(rc / b)) for b in box]
+        shifts = np.array([[i, j, k] for i in range(-nmax[0], nmax[0] + 1) for j in range(-nmax[1], nmax[1] + 1)
+                           for k in range(-nmax[2], nmax[2] + 1)], np.float64) * box
+        tree = cKDTree((pos[None, :, :] + shifts[:, None, :]).reshape(-1, 3))
+    return int(tree.query_ball_point(pos, rc, return_length=True).sum()) - n
 
 
 def l2_flush_buffer(torch):
@@ -171,13 +207,15 @@ def run_ours(args):
     filt = args.filter
     if filt == "auto":
         filt = "bf16" if _tc_filter_available() else "fp32"
-    s, pot, params = workload(args.ncell, args.precision, filt)
+    systems, pot, params, setup, desc = workload(args.workload, args.ncell, args.precision, filt)
     params["seed"] = replica_seed(12345, rank)
-    N = len(s["types"])
+    sizes = [(len(x["types"]), int(x["pos"].shape[0])) for x in systems]   # (N, P)
+    units = sum(n * p for n, p in sizes)                                    # atom*bead per MD step
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        ctx = qtb.qtb_init([s], params, stream=stream.cuda_stream)
-    qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB, 2049, 0.3)
+        ctx = qtb.qtb_init(systems, params, stream=stream.cuda_stream)
+    if setup is not None:
+        qtb.qtb_set_filter(ctx, -1, *setup)
     qtb.qtb_set_profiling(ctx, not args.direct)
     flush = l2_flush_buffer(torch)
 
@@ -219,58 +257,64 @@ def run_ours(args):
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
     t_ms = max_over_ranks(float(np.sum(step_ms)), device="cuda")
-    value = job_throughput(N * BLOCK, args.steps, ws, t_ms)
+    value = job_throughput(units * BLOCK, args.steps, ws, t_ms)
     obs = qtb.qtb_observables(ctx, 0)
     rebuilds = (qtb.qtb_list_rebuilds(ctx) - rebuilds0) / args.steps
 
     # roofline of the dominant kernel (pair force): algorithmic flops / mean launch time
-    x, _ = qtb.qtb_get_state(ctx, 0, 1, N)
-    pairs = count_pairs(x[0], s["box"], pot["r_cut"])
+    pairs = 0
+    states = []
+    for k, (n, p) in enumerate(sizes):
+        x, v = qtb.qtb_get_state(ctx, k, p, n)
+        states.append((x, v))
+        pairs += sum(count_pairs(x[b], systems[k]["box"], pot["r_cut"]) for b in range(p))
     force_ms = kernel_ms["force"] / max(kernel_n["force"], 1)
     achieved = PAIR_FLOPS * pairs / (force_ms * 1e-3) / 1e12 if force_ms > 0 else None
     peak = alu_peak_tflops()
     step_breakdown = {k: round(kernel_ms[k] / max(args.steps, 1), 4) for k in kernel_ms}
 
     # end to end through the C ABI with host buffers: H2D state, 256 steps, D2H observables
-    pos_h, vel_h = qtb.qtb_get_state(ctx, 0, 1, N)
     e2e_ms = []
     for i in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        qtb.qtb_set_state(ctx, 0, pos_h, vel_h)
+        for k, (x, v) in enumerate(states):
+            qtb.qtb_set_state(ctx, k, x, v)
         qtb.qtb_step_n(ctx, BLOCK)
-        rec = qtb.qtb_observables(ctx, 0)
+        for k in range(len(systems)):
+            qtb.qtb_observables(ctx, k)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_value = ws * N * BLOCK * args.steps / (np.sum(e2e_ms) / 1e3)
+    e2e_value = ws * units * BLOCK * args.steps / (np.sum(e2e_ms) / 1e3)
+    integ = 1 if all(p == 1 for _, p in sizes) else BLOCK * len({p for _, p in sizes})
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+fixed30+f64acc" if args.precision == "mixed" else "f64",
-        "data": "synthetic: seeded rock-salt MgO, sigma 0.02 A, Maxwell-Boltzmann velocities",
-        "config": {"workload": f"MgO rock salt {args.ncell}x{args.ncell}x{args.ncell} cells ({N} ions), QTB-MD 100 K, "
-                               f"dt 1 fs, 2049-tap {filt} noise filter, 256-step blocks",
-                   "n_ions": N, "n_beads": 1, "md_steps_per_bench_step": BLOCK, "precision": args.precision,
-                   "filter": filt, "parallelism": f"replicas x{ws}",
+        "data": "synthetic: seeded rock-salt crystals, sigma 0.02 A, Maxwell-Boltzmann velocities",
+        "config": {"workload": desc, "name": args.workload, "systems": len(systems),
+                   "atom_beads_per_md_step": units, "md_steps_per_bench_step": BLOCK, "precision": args.precision,
+                   "filter": filt if setup is not None else "none (white noise)", "parallelism": f"replicas x{ws}",
                    "launch": "direct (2 x 128-step calls per block)" if args.direct else "CUDA graph per 256-step block",
                    "l2": "256 MB buffer written between timed steps (flush)"},
-        "roofline": {"bound": "alu", "kernel": "k_force_list", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if achieved else None, "traffic": measured_traffic("k_force_list"),
+        "roofline": {"bound": "alu", "kernel": "k_step", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if achieved else None, "traffic": measured_traffic("k_step", args.workload),
                      "peak_source": "152 SM x 128 FP32 lanes x 2 flop x sm_max_mhz of MEASURED_PEAKS.json",
                      "flops_per_launch": PAIR_FLOPS * pairs, "pairs_per_launch": pairs, "mean_launch_ms": force_ms},
         "kernel_ms_per_bench_step": step_breakdown,
         "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * N * 3 * 8),
-                "d2h_bytes_per_step": int(qtb.NREC * 8)},
-        # per block: white, filter, one integrator launch, 256 step launches (a list
-        # rebuild runs inside the step launch that needs it), the block clock
-        "gpu_launches": 2 + 1 + BLOCK + 1,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * units * 3 * 8),
+                "d2h_bytes_per_step": int(len(systems) * qtb.NREC * 8)},
+        # per block: white, filter, the integrator (once for one-bead systems, else every
+        # step per distinct bead count), 256 step launches (a list rebuild runs inside the
+        # step launch that needs it), the block clock
+        "gpu_launches": 2 + integ + BLOCK + 1,
         "list_rebuilds_per_bench_step": rebuilds,
         "wall_s": wall,
         "observables": {"K_eV": float(obs[1]), "V_eV": float(obs[2]), "step": int(obs[0])},
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sample_atoms=64)
+        line["cpu_baseline"] = cpu_baseline(args.workload, sample_atoms=64)
     qtb.qtb_destroy(ctx)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -278,13 +322,14 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
-def measured_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu capture, or None when the
-    kernel's source has changed since the counters were taken."""
+def measured_traffic(kernel, workload_name):
+    """DRAM bytes per launch from the committed ncu capture of this kernel on
+    this workload, or None when there is none or the kernel's source has
+    changed since the counters were taken."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            rec = json.load(f)[kernel]
+            rec = json.load(f)[f"{kernel}/{workload_name}"]
         with open(os.path.join(ROOT, rec["source"]), "rb") as f:
             if hashlib.sha1(f.read()).hexdigest() != rec["source_sha1"]:
                 return None
@@ -312,57 +357,64 @@ def _tc_filter_available():
         return False
 
 
-def cpu_baseline(sample_atoms=64, steps=1):
-    """The FP64 oracle on a bounded sample of the workload: forces on
-    `sample_atoms` ions of the 8000-ion crystal (brute force over all ions and
-    images) plus the coloured noise of their 3 dofs, per MD step."""
+def oracle_sample(name, ncell, n_sample):
+    """A bounded sample of one MD step of the workload for the FP64 oracle:
+    forces on `n_sample` bead-atoms of bead 0 of the first system (brute force
+    over all ions and images) and the random force of their 3 dofs (2049-tap
+    direct convolution; white noise for standard PIMD).  Returns a callable
+    one(n) for step n and the number of bead-atoms it covers."""
     import oracle
     from oracle import spectra as S
-    from paper_1905_02521_gb300 import workloads as W
-    s, pot = W.mgo_system(10, 100.0)
-    h = S.taps(2049, 1.0, 100.0, 0.3)
-    sel = np.arange(0, len(s["types"]), len(s["types"]) // sample_atoms)[:sample_atoms]
+    systems, pot, params, setup, desc = workload(name, ncell, "fp64", "fp32")
+    s = systems[-1] if name == "sweep64" else systems[0]
+    T, dt = s["T"], params["dt"]
+    if setup is None:
+        h = np.array([np.sqrt(8.617333262e-5 * T)])
+    else:
+        mode, L, wmax = setup
+        P = int(s["pos"].shape[0]) if mode == 2 else 1
+        h = S.taps(L, dt, T, wmax, P=P, sol=S.kappa_solve(P) if P > 1 else None)
+    n = len(s["types"])
+    sel = np.arange(0, n, max(1, n // n_sample))[:n_sample]
     oracle.build()
-    t0 = time.perf_counter()
-    for n in range(steps):
+
+    def one(step):
         oracle.pair_forces(s["pos"][0], s["types"], s["box"], pot, sel=sel)
-        oracle.colored_block(12345, 0, 3 * sample_atoms, n, 1, h)
+        oracle.colored_block(12345, 0, 3 * len(sel), step, 1, h)
+
+    return one, len(sel), n
+
+
+def cpu_baseline(name, sample_atoms=64, steps=1):
+    """The FP64 oracle timed on a bounded sample of the workload (see oracle_sample)."""
+    one, k, n = oracle_sample(name, 10, sample_atoms)
+    t0 = time.perf_counter()
+    for st in range(steps):
+        one(st)
     dt = time.perf_counter() - t0
-    return {"value": sample_atoms * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sample_atoms} of 8000 ions x {steps} step(s): brute-force periodic forces + "
-                      f"2049-tap direct noise convolution, single thread, {dt:.1f} s"}
+    return {"value": k * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{k} of {n} bead-atoms x {steps} step(s): brute-force periodic forces + "
+                      f"random force of their dofs, single thread, {dt:.1f} s"}
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    import oracle
-    from oracle import spectra as S
-    from paper_1905_02521_gb300 import workloads as W
-    oracle.build()
-    s, pot = W.mgo_system(args.ncell, 100.0)
-    h = S.taps(2049, 1.0, 100.0, 0.3)
-    n_sample = 32
-    sel = np.arange(0, len(s["types"]), max(1, len(s["types"]) // n_sample))[:n_sample]
-
-    def one(n):
-        oracle.pair_forces(s["pos"][0], s["types"], s["box"], pot, sel=sel)
-        oracle.colored_block(12345, 0, 3 * len(sel), n, 1, h)
-
+    one, k, n = oracle_sample(args.workload, args.ncell, 32)
     for i in range(args.warmup):
         one(i)
     t0 = time.perf_counter()
     for i in range(args.steps):
         one(args.warmup + i)
     dt = time.perf_counter() - t0
-    value = len(sel) * args.steps / dt
+    value = k * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"MgO rock salt {args.ncell}^3 cells, QTB-MD, 2049-tap filter (oracle sample)"},
+            "config": {"workload": f"{args.workload}: FP64 oracle on {k} of {n} bead-atoms per step", "name": args.workload},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{len(sel)} ions per step: forces + noise of the FP64 oracle"},
+                             "sample": f"{k} bead-atoms per step: forces + random force of the FP64 oracle"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
