@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mgo8000", choices=WORKLOADS)
     ap.add_argument("--ncell", type=int, default=10, help="cells per side of the mgo8000 workload")
+    ap.add_argument("--skin", type=float, default=0.0, help="neighbour-list skin, A (0: library default)")
     ap.add_argument("--filter", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -209,6 +210,7 @@ def run_ours(args):
         filt = "bf16" if _tc_filter_available() else "fp32"
     systems, pot, params, setup, desc = workload(args.workload, args.ncell, args.precision, filt)
     params["seed"] = replica_seed(12345, rank)
+    params["skin"] = args.skin
     sizes = [(len(x["types"]), int(x["pos"].shape[0])) for x in systems]   # (N, P)
     units = sum(n * p for n, p in sizes)                                    # atom*bead per MD step
     stream = torch.cuda.Stream()
@@ -295,6 +297,7 @@ def run_ours(args):
         "config": {"workload": desc, "name": args.workload, "systems": len(systems),
                    "atom_beads_per_md_step": units, "md_steps_per_bench_step": BLOCK, "precision": args.precision,
                    "filter": filt if setup is not None else "none (white noise)", "parallelism": f"replicas x{ws}",
+                   "skin_A": args.skin if args.skin else "default",
                    "launch": "direct (2 x 128-step calls per block)" if args.direct else "CUDA graph per 256-step block",
                    "l2": "256 MB buffer written between timed steps (flush)"},
         "roofline": {"bound": "alu", "kernel": "k_step", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
     const size_t base = act ? (size_t)c * G + S.g0 + i : 0;
     const float fsc = S.fix_scale[c], finv = S.fix_inv[c];
     PS x0{};
-    R a[P];
+    R a[P], a0[P];  // bead positions relative to bead 0: new, old
     if (act) {
         R *V = reinterpret_cast<R *>(d.v);
         const R *F = reinterpret_cast<const R *>(d.f);
@@ -262,8 +262,10 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
         R q[P];
         // relative bead positions -> modes
 #pragma unroll(UN)
-        for (int b = 0; b < P; ++b)
+        for (int b = 0; b < P; ++b) {
             a[b] = (b == 0) ? R(0) : PosT<PM, R>::rel(X[base + (size_t)b * N], x0, L, fsc, finv);
+            a0[b] = a[b];
+        }
 #pragma unroll(UN)
         for (int k = 0; k < P; ++k) {
             R u = 0;
@@ -310,8 +312,11 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
             spring = 0.5 * d.mass_mvv[t] * S.wP * S.wP * (double)sp;
         }
     }
-    // new bead positions; with a pair potential also the packed copy and the
-    // displacement test (the three components meet through shuffles)
+    // new bead positions: each bead moves by the change of its position relative
+    // to bead 0, so that it stays in its own periodic image (after a list rebuild
+    // the beads of an atom on the box boundary may be wrapped into different
+    // images); with a pair potential also the packed copy and the displacement
+    // test (the three components meet through shuffles)
     bool moved = false;
     const int l0 = 3 * aw;
 #pragma unroll(UN)
@@ -319,7 +324,7 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
         R dd = 0;
         if (act) {
             const size_t o = base + (size_t)b * N;
-            const PS xn = PosT<PM, R>::add(x0, a[b], S.box[c], fsc, finv);
+            const PS xn = PosT<PM, R>::add(X[o], a[b] - a0[b], S.box[c], fsc, finv);
             X[o] = xn;
             if (PM != PM_FREE) {
                 const size_t g = S.g0 + (size_t)b * N + i;

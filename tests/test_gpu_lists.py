@@ -86,3 +86,26 @@ def test_cold_crystal_rarely_rebuilds(qtb):
         assert qtb.qtb_list_rebuilds(ctx) <= 3
     finally:
         qtb.qtb_destroy(ctx)
+
+
+def test_pimd_beads_keep_their_images(qtb, oracle):
+    # Mg ions sit on the box boundary: after a rebuild the beads of one ion can
+    # be wrapped into different periodic images; the integrator must move each
+    # bead within its own image (else every later step sees a box-length jump
+    # and rebuilds).  Per-bead forces stay exact (1/P of the replica's forces).
+    P = 4
+    s, pot = W.mgo_system(3, 300.0, n_beads=P, seed=5)
+    N = len(s["types"])
+    ctx = gpu_ctx(qtb, [s], pot, 0.5, precision=0, seed=9, skin=0.4)
+    try:
+        qtb.qtb_step_n(ctx, 600)
+        nreb = qtb.qtb_list_rebuilds(ctx)
+        x, _ = qtb.qtb_get_state(ctx, 0, P, N)
+        f = qtb.qtb_get_forces(ctx, 0, P, N)
+        for b in range(P):
+            fo, _, _ = oracle.pair_forces(x[b], s["types"], s["box"], pot)
+            assert rel_inf(f[b], fo / P) < 1e-12
+    finally:
+        qtb.qtb_destroy(ctx)
+    print("P = 4 MgO, skin 0.4: %d list rebuilds in 600 steps" % nreb)
+    assert 2 <= nreb < 150
