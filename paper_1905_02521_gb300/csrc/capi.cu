@@ -861,7 +861,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         G += (long long)h.N * h.P;
         D += S.dofp;
         S.icta0 = icta;
-        icta += (h.N + kIntAtomsPerCta - 1) / kIntAtomsPerCta;
+        icta += (h.N + integrate_atoms_per_cta(h.P) - 1) / integrate_atoms_per_cta(h.P);
         S.icta1 = icta;
         for (int k = 0; k < 3; ++k) S.box[k] = q.box[k];
         S.T = q.T;

@@ -346,6 +346,167 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
     if (mine) cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
 }
 
+// Ring-polymer integrator for P >= 2 with the normal-mode transforms in shared
+// memory.  A CTA takes A = nm_values(P) / (3 P) atoms of one system, i.e. 3 A
+// columns (component c, atom a; col = c A + a) of P beads.  Phase 1 (thread per
+// (bead b, column)): relative bead positions and half-kicked bead velocities
+// (B, dt/2) into shared memory.  Phase 2 (thread per (mode k, column)): the
+// forward transforms, A(dt/2) O(dt) A(dt/2) of mode k.  Phase 3 (thread per
+// (bead, column), the mapping of phase 1): back to beads, each bead moved
+// within its own periodic image, spring energy, displacement test of each
+// bead-atom against skin/2.
+// values per CTA and threads: small rings take fewer atoms per CTA (more CTAs)
+__host__ __device__ constexpr int nm_values(int P) { return P >= 16 ? 768 : 192; }
+__host__ __device__ constexpr int nm_threads(int P) { return P >= 16 ? 128 : 64; }
+
+template <int P, int PM, class R>
+__global__ void __launch_bounds__(nm_threads(P)) k_integrate_nm(Dev d, int j, int cur)
+{
+    typedef typename PosT<PM, R>::S PS;
+    constexpr int kNmThreads = nm_threads(P), kNmPer = nm_values(P) / nm_threads(P);
+    constexpr int A = nm_values(P) / (3 * P);
+    constexpr int COLS = 3 * A, NV = COLS * P;
+    __shared__ R Cs[P * P];
+    __shared__ R xs[NV], ps[NV];  // [b or k][col]
+    __shared__ R dd[NV];          // squared displacement component per (b, col)
+    __shared__ double red[kNmThreads / 32][kNQ];
+    const int cta = blockIdx.x;
+    const int s = d.icta_sys[cta];
+    const DSys S = d.sys[s];
+    const bool mine = (S.P == P);  // another instantiation handles the other systems
+    if (!mine) return;             // uniform over the CTA; no grid-wide step in this kernel
+    for (int t = threadIdx.x; t < P * P; t += blockDim.x) Cs[t] = reinterpret_cast<const R *>(d.nmC)[S.nm0 + t];
+    const int N = S.N;
+    const int i0 = (cta - S.icta0) * A;
+    const size_t G = (size_t)d.G;
+    PS *X = reinterpret_cast<PS *>(d.x);
+    R *V = reinterpret_cast<R *>(d.v);
+    const R *F = reinterpret_cast<const R *>(d.f);
+    const R *hdt = reinterpret_cast<const R *>(d.hdt_m);
+    // phase 1: relative positions and B(dt/2) velocities, bead space
+    R xrel[kNmPer];
+    PS xold[kNmPer];
+#pragma unroll
+    for (int u = 0; u < kNmPer; ++u) {
+        const int idx = threadIdx.x + u * kNmThreads;
+        xrel[u] = 0;
+        if (idx >= NV) continue;
+        const int b = idx / COLS, col = idx - b * COLS;
+        const int c = col / A, a = col - c * A, i = i0 + a;
+        R xr = 0, pv = 0;
+        if (i < N) {
+            const size_t o0 = (size_t)c * G + S.g0 + i, o = o0 + (size_t)b * N;
+            const PS xb = X[o];
+            xold[u] = xb;
+            xr = (b == 0) ? R(0) : PosT<PM, R>::rel(xb, X[o0], S.box[c], S.fix_scale[c], S.fix_inv[c]);
+            pv = fma(hdt[d.typ[S.g0 + i]], F[o], V[o]);
+        }
+        xrel[u] = xr;
+        xs[idx] = xr;
+        ps[idx] = pv;
+    }
+    __syncthreads();
+    // phase 2: to modes, A O A per mode
+    const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
+    const R *eta = reinterpret_cast<const R *>(d.eta) + (size_t)j * d.Dtot + S.dof0;
+    const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
+    R qv[kNmPer], pvm[kNmPer];
+#pragma unroll
+    for (int u = 0; u < kNmPer; ++u) {
+        const int idx = threadIdx.x + u * kNmThreads;
+        qv[u] = pvm[u] = 0;
+        if (idx >= NV) continue;
+        const int k = idx / COLS, col = idx - k * COLS;
+        const int c = col / A, a = col - c * A, i = i0 + a;
+        R q = 0, p = 0;
+#pragma unroll 8
+        for (int b = 0; b < P; ++b) {
+            q = fma(Cs[b * P + k], xs[b * COLS + col], q);
+            p = fma(Cs[b * P + k], ps[b * COLS + col], p);
+        }
+        if (i < N) {
+            const int t = d.typ[S.g0 + i];
+            const R sig = reinterpret_cast<const R *>(d.osig)[s * kMaxTypes + t];
+            mode_aoa(q, p, rot[3 * k], rot[3 * k + 1], rot[3 * k + 2], c1, sig * eta[(size_t)(k * 3 + c) * N + i]);
+        }
+        qv[u] = q;
+        pvm[u] = p;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kNmPer; ++u) {
+        const int idx = threadIdx.x + u * kNmThreads;
+        if (idx < NV) {
+            xs[idx] = qv[u];
+            ps[idx] = pvm[u];
+        }
+    }
+    __syncthreads();
+    // phase 3: back to beads
+    R xnew[kNmPer];
+#pragma unroll
+    for (int u = 0; u < kNmPer; ++u) {
+        const int idx = threadIdx.x + u * kNmThreads;
+        xnew[u] = 0;
+        if (idx >= NV) continue;
+        const int b = idx / COLS, col = idx - b * COLS;
+        R x = 0, w = 0;
+#pragma unroll 8
+        for (int k = 0; k < P; ++k) {
+            x = fma(Cs[b * P + k], xs[k * COLS + col], x);
+            w = fma(Cs[b * P + k], ps[k * COLS + col], w);
+        }
+        xnew[u] = x;
+        qv[u] = w;
+    }
+    __syncthreads();
+    double spring = 0.0;
+#pragma unroll
+    for (int u = 0; u < kNmPer; ++u) {
+        const int idx = threadIdx.x + u * kNmThreads;
+        if (idx >= NV) continue;
+        const int b = idx / COLS, col = idx - b * COLS;
+        const int c = col / A, a = col - c * A, i = i0 + a;
+        xs[idx] = xnew[u];
+        R dsq = 0;
+        if (i < N) {
+            const size_t g = S.g0 + (size_t)b * N + i, o = (size_t)c * G + g;
+            V[o] = qv[u];
+            const PS xn = PosT<PM, R>::add(xold[u], xnew[u] - xrel[u], S.box[c], S.fix_scale[c], S.fix_inv[c]);
+            X[o] = xn;
+            if (PM != PM_FREE) {
+                reinterpret_cast<PS *>(d.pos[cur])[4 * g + c] = xn;
+                const R dc = PosT<PM, R>::diff(xn, reinterpret_cast<const PS *>(d.xref)[o], S.fix_scale[c]);
+                dsq = dc * dc;
+            }
+        }
+        dd[idx] = dsq;
+    }
+    __syncthreads();
+    bool moved = false;
+    const R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
+#pragma unroll
+    for (int u = 0; u < kNmPer; ++u) {
+        const int idx = threadIdx.x + u * kNmThreads;
+        if (idx >= NV) continue;
+        const int b = idx / COLS, col = idx - b * COLS;
+        const int c = col / A, a = col - c * A, i = i0 + a;
+        if (i >= N) continue;
+        const int bn = (b + 1) % P;
+        const R dx = xs[b * COLS + col] - xs[bn * COLS + col];
+        spring += 0.5 * d.mass_mvv[d.typ[S.g0 + i]] * S.wP * S.wP * (double)(dx * dx);
+        if (PM != PM_FREE && c == 0) {
+            const R tot = dd[b * COLS + a] + dd[b * COLS + A + a] + dd[b * COLS + 2 * A + a];
+            moved |= tot > lim;
+        }
+    }
+    if (PM != PM_FREE && __syncthreads_or(moved) && threadIdx.x == 0) atomicOr(&d.flag[cur], 1u);
+    double acc[kNQ];
+    for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+    acc[Q_SPRING] = warp_sum(spring);
+    cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
+}
+
 // ---------------------------------------------------------------------------
 // List rebuild: three phases of the cooperative step kernel, separated by grid
 // barriers, run only when flag[cur] is set.  bin_phase wraps the positions
@@ -1049,13 +1210,16 @@ __global__ void k_setclock(Dev d, long long b) { d.clock[0] = b; }
 
 bool md_supported_P(int P) { return (P >= 1 && P <= 6) || P == 8 || P == 16 || P == 32; }
 
+int integrate_atoms_per_cta(int P) { return P == 1 ? kIntAtomsPerCta : nm_values(P) / (3 * P); }
+
 template <int PM, class R>
 static void integrate_all(const Dev &d, const MdLaunch &m, int j, int cur, cudaStream_t st)
 {
     for (int u = 0; u < m.nP; ++u) {
         switch (m.Pvals[u]) {
-#define QTB_P(PP) case PP: k_integrate<PP, PM, R><<<m.n_icta, 128, 0, st>>>(d, j, cur); break;
-            QTB_P(1) QTB_P(2) QTB_P(3) QTB_P(4) QTB_P(5) QTB_P(6) QTB_P(8) QTB_P(16) QTB_P(32)
+            case 1: k_integrate<1, PM, R><<<m.n_icta, 128, 0, st>>>(d, j, cur); break;
+#define QTB_P(PP) case PP: k_integrate_nm<PP, PM, R><<<m.n_icta, nm_threads(PP), 0, st>>>(d, j, cur); break;
+            QTB_P(2) QTB_P(3) QTB_P(4) QTB_P(5) QTB_P(6) QTB_P(8) QTB_P(16) QTB_P(32)
 #undef QTB_P
             default: break;
         }

@@ -66,6 +66,8 @@ void launch_reduce(const Dev &d, const MdLaunch &m, int j, int record, cudaStrea
 void launch_tick(const Dev &d, cudaStream_t st);
 void launch_setclock(const Dev &d, long long blk, cudaStream_t st);
 bool md_supported_P(int P);
+// atoms per CTA of the integrator for bead count P
+int integrate_atoms_per_cta(int P);
 
 // filter_tc.cu
 cudaError_t filter_tc_prepare();
