@@ -129,7 +129,13 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-WORKLOADS = ("mgo8000", "lih_qtbpimd_p8", "lih_pimd_p32", "sweep64")
+WORKLOADS = ("mgo8000", "lih_qtbpimd_p8", "lih_pimd_p32", "sweep64", "lih_pimd_p32_big")
+
+# algorithmic bytes per bead-atom of one launch of the ring-polymer integrator
+# (k_integrate_nm): read x, v, f, xref and the coloured noise, write x, v and the
+# packed copy of the positions, 3 components each (4-byte values in the mixed
+# form, 8-byte in the FP64 form)
+INTEGRATOR_BYTES = {"mixed": 3 * (5 + 3) * 4, "fp64": 3 * (5 + 3) * 8}
 
 
 def workload(name, ncell, precision, filt):
@@ -139,6 +145,8 @@ def workload(name, ncell, precision, filt):
     lih_qtbpimd_p8: LiH 6^3 cells (1728 ions), QTB-PIMD P = 8 (kappa_P from the solver), 50 K,
         dt 0.25 fs, 2049 taps, w_max 0.6 rad/fs.
     lih_pimd_p32: the same crystal, standard PIMD P = 32 with a white Langevin bath.
+    lih_pimd_p32_big: LiH 20^3 cells (64000 ions) x 32 beads, white PIMD: the
+        integrator's stream (~200 MB per step) exceeds the 129 MB L2.
     sweep64: 64 MgO systems of 3..8 cells per side (216-4096 ions) at T_i = 10 150^(i/63) K,
         QTB-MD, one context (batched), dt 1 fs, 2049 taps, w_max 0.3 rad/fs.
     """
@@ -152,16 +160,18 @@ def workload(name, ncell, precision, filt):
         setup = (qtb.NOISE_QTB, 2049, 0.3)
         desc = (f"MgO rock salt {ncell}x{ncell}x{ncell} cells ({len(s['types'])} ions), QTB-MD 100 K, dt 1 fs, "
                 f"2049-tap {filt} noise filter, 256-step blocks")
-    elif name in ("lih_qtbpimd_p8", "lih_pimd_p32"):
+    elif name in ("lih_qtbpimd_p8", "lih_pimd_p32", "lih_pimd_p32_big"):
         P = 8 if name == "lih_qtbpimd_p8" else 32
-        s, pot = W.lih_system(6, 50.0, gamma=1e-3, n_beads=P)
+        nc = 20 if name == "lih_pimd_p32_big" else 6
+        s, pot = W.lih_system(nc, 50.0, gamma=1e-3, n_beads=P)
         systems = [s]
         dt = 0.25
         if P == 8:
             setup = (qtb.NOISE_QTB_PIMD, 2049, 0.6)
             desc = f"LiH rock salt 6x6x6 cells (1728 ions) x 8 beads, QTB-PIMD (kappa_P solver) 50 K, dt 0.25 fs, 2049-tap {filt} filter"
         else:
-            desc = "LiH rock salt 6x6x6 cells (1728 ions) x 32 beads, PIMD with white Langevin bath 50 K, dt 0.25 fs"
+            desc = (f"LiH rock salt {nc}x{nc}x{nc} cells ({len(s['types'])} ions) x 32 beads, PIMD with white "
+                    f"Langevin bath 50 K, dt 0.25 fs")
     elif name == "sweep64":
         systems, pot = W.sweep_systems(64, gamma=1e-3)
         setup = (qtb.NOISE_QTB, 2049, 0.3)
@@ -269,7 +279,9 @@ def run_ours(args):
     for k, (n, p) in enumerate(sizes):
         x, v = qtb.qtb_get_state(ctx, k, p, n)
         states.append((x, v))
-        pairs += sum(count_pairs(x[b], systems[k]["box"], pot["r_cut"]) for b in range(p))
+        # every bead of small systems; 4 evenly spaced beads of large ones, scaled to P
+        beads = range(p) if n * p <= 100000 else range(0, p, max(1, p // 4))
+        pairs += int(round(sum(count_pairs(x[b], systems[k]["box"], pot["r_cut"]) for b in beads) * p / len(beads)))
     force_ms = kernel_ms["force"] / max(kernel_n["force"], 1)
     achieved = PAIR_FLOPS * pairs / (force_ms * 1e-3) / 1e12 if force_ms > 0 else None
     peak = alu_peak_tflops()
@@ -304,6 +316,7 @@ def run_ours(args):
                      "frac": achieved / peak if achieved else None, "traffic": measured_traffic("k_step", args.workload),
                      "peak_source": "152 SM x 128 FP32 lanes x 2 flop x sm_max_mhz of MEASURED_PEAKS.json",
                      "flops_per_launch": PAIR_FLOPS * pairs, "pairs_per_launch": pairs, "mean_launch_ms": force_ms},
+        "roofline_integrator": integrator_roofline(kernel_ms, kernel_n, units, sizes, args.precision),
         "kernel_ms_per_bench_step": step_breakdown,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * units * 3 * 8),
@@ -339,6 +352,28 @@ def measured_traffic(kernel, workload_name):
         return rec["dram_bytes_per_launch"]
     except Exception:
         return None
+
+
+def hbm_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def integrator_roofline(kernel_ms, kernel_n, units, sizes, precision):
+    """HBM roofline of the ring-polymer integrator (systems with P > 1; for
+    one-bead systems it is fused into the step kernel)."""
+    if all(p == 1 for _, p in sizes) or kernel_n["integrate"] == 0:
+        return None
+    ms = kernel_ms["integrate"] / kernel_n["integrate"]
+    nbytes = INTEGRATOR_BYTES[precision] * units
+    peak, src = hbm_peak_gbs()
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "k_integrate_nm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": src, "bytes_per_launch": nbytes, "mean_launch_ms": ms,
+            "traffic": None}
 
 
 def alu_peak_tflops():

@@ -113,6 +113,10 @@ typedef struct {
                               once some bead-atom has moved skin/2 since the last
                               rebuild.  0 selects min(0.8, r_cut/4); < 0: no skin.
                               Forces do not depend on it (up to summation order). */
+    int nm_layout;         /* ring-polymer integrator (n_beads > 1): 0 auto, 1 compact
+                              (8-32 atoms per CTA, more CTAs; small contexts), 2 wide (32
+                              atoms per CTA, coalesced rows; large contexts).  Same
+                              arithmetic, bit-identical results. */
 } qtb_params;
 
 /* Observable record (FP64), one per recorded step and system:

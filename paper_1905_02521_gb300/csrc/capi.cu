@@ -678,6 +678,7 @@ int validate(const qtb_system *sys, int n_sys, const qtb_params *p)
     if (p->precision != QTB_FP64 && p->precision != QTB_MIXED) return fail(QTB_ERR_ARG, "unknown precision");
     if (p->filter_prec < 0 || p->filter_prec > 2) return fail(QTB_ERR_ARG, "unknown filter precision");
     if (p->obs_stride < 1 || p->max_records < 1) return fail(QTB_ERR_ARG, "obs_stride and max_records must be >= 1");
+    if (p->nm_layout < 0 || p->nm_layout > 2) return fail(QTB_ERR_ARG, "nm_layout must be 0, 1 or 2");
     if (p->potential == QTB_POT_PAIR) {
         if (!p->charge || !p->buck_A || !p->buck_rho || !p->buck_C) return fail(QTB_ERR_ARG, "pair tables missing");
         if (!(p->r_cut > 0)) return fail(QTB_ERR_ARG, "r_cut must be > 0");
@@ -840,6 +841,11 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         stage_cap = (int)std::max(512LL, std::min(roundup((long long)std::ceil(1.5 * kStencilCells * ecell) + 128, 64), 1024LL));
     }
     int nlcta = 0;
+    // ring-polymer integrator layout: 32 atoms per CTA (coalesced rows) for large
+    // contexts, fewer (more CTAs) for small ones
+    long long beads_total = 0;
+    for (int s = 0; s < n_sys; ++s) beads_total += (long long)sys[s].n_atoms * sys[s].n_beads;
+    const int nm_big = p->nm_layout == 2 ? 1 : p->nm_layout == 1 ? 0 : (beads_total >= (1LL << 18) ? 1 : 0);
     for (int s = 0; s < n_sys; ++s) {
         const qtb_system &q = sys[s];
         HSys &h = c->hs[s];
@@ -861,7 +867,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         G += (long long)h.N * h.P;
         D += S.dofp;
         S.icta0 = icta;
-        icta += (h.N + integrate_atoms_per_cta(h.P) - 1) / integrate_atoms_per_cta(h.P);
+        icta += (h.N + integrate_atoms_per_cta(h.P, nm_big) - 1) / integrate_atoms_per_cta(h.P, nm_big);
         S.icta1 = icta;
         for (int k = 0; k < 3; ++k) S.box[k] = q.box[k];
         S.T = q.T;
@@ -971,9 +977,12 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
             m.Pvals[m.nP++] = c->hs[s].P;
         }
     }
+    m.nm_big = nm_big;
     m.fused = c->pair ? 1 : 0;
     for (int s = 0; s < n_sys; ++s)
         if (c->hs[s].P != 1) m.fused = 0;
+    if (integrate_prepare(m) != cudaSuccess)
+        return bail(fail(QTB_ERR_CUDA, "cannot reserve shared memory for the ring-polymer integrator"));
 
     // tables
     std::vector<double> rot;

@@ -347,35 +347,43 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
 }
 
 // Ring-polymer integrator for P >= 2 with the normal-mode transforms in shared
-// memory.  A CTA takes A = nm_values(P) / (3 P) atoms of one system, i.e. 3 A
-// columns (component c, atom a; col = c A + a) of P beads.  Phase 1 (thread per
+// memory.  A CTA takes A atoms of one system, i.e. 3 A columns (component c,
+// atom a; col = c A + a) of P beads, V = 3 A P values.  Phase 1 (thread per
 // (bead b, column)): relative bead positions and half-kicked bead velocities
 // (B, dt/2) into shared memory.  Phase 2 (thread per (mode k, column)): the
 // forward transforms, A(dt/2) O(dt) A(dt/2) of mode k.  Phase 3 (thread per
 // (bead, column), the mapping of phase 1): back to beads, each bead moved
-// within its own periodic image, spring energy, displacement test of each
-// bead-atom against skin/2.
-// values per CTA and threads: small rings take fewer atoms per CTA (more CTAs)
-__host__ __device__ constexpr int nm_values(int P) { return P >= 16 ? 768 : 192; }
-__host__ __device__ constexpr int nm_threads(int P) { return P >= 16 ? 128 : 64; }
+// within its own periodic image.  Phase 4 (thread per (bead, column)): spring
+// energy; the threads of component 0 write the packed position and test the
+// bead-atom's displacement against skin/2.  Every thread issues all of its
+// global loads of a phase before it uses them.  BIG (large contexts): 32 atoms
+// per CTA, so that the 32 threads of a warp read 128 contiguous bytes.
+__host__ __device__ constexpr int nm_atoms(int P, int big) { return big ? 32 : (P >= 16 ? 768 : 192) / (3 * P); }
+__host__ __device__ constexpr int nm_threads(int P, int big) { return big ? (P >= 8 ? 256 : 128) : (P >= 16 ? 128 : 64); }
 
 template <int P, int PM, class R>
-__global__ void __launch_bounds__(nm_threads(P)) k_integrate_nm(Dev d, int j, int cur)
+__host__ __device__ constexpr size_t nm_smem(int big)
+{
+    return (size_t)3 * nm_atoms(P, big) * P * (2 * sizeof(R) + sizeof(typename PosT<PM, R>::S)) + (size_t)P * P * sizeof(R);
+}
+
+template <int P, int PM, class R, int BIG>
+__global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int j, int cur)
 {
     typedef typename PosT<PM, R>::S PS;
-    constexpr int kNmThreads = nm_threads(P), kNmPer = nm_values(P) / nm_threads(P);
-    constexpr int A = nm_values(P) / (3 * P);
-    constexpr int COLS = 3 * A, NV = COLS * P;
-    __shared__ R Cs[P * P];
-    __shared__ R xs[NV], ps[NV];  // [b or k][col]
-    __shared__ R dd[NV];          // squared displacement component per (b, col)
-    __shared__ double red[kNmThreads / 32][kNQ];
+    constexpr int NT = nm_threads(P, BIG), A = nm_atoms(P, BIG);
+    constexpr int COLS = 3 * A, NV = COLS * P, PER = (NV + NT - 1) / NT;
+    extern __shared__ __align__(16) unsigned char nsm[];
+    R *xs = reinterpret_cast<R *>(nsm);            // [b or k][col]
+    R *ps = xs + NV;
+    R *Cs = ps + NV;                               // [b][k]
+    PS *xn_s = reinterpret_cast<PS *>(Cs + P * P); // new positions [b][col]
+    __shared__ double red[NT / 32][kNQ];
     const int cta = blockIdx.x;
     const int s = d.icta_sys[cta];
     const DSys S = d.sys[s];
-    const bool mine = (S.P == P);  // another instantiation handles the other systems
-    if (!mine) return;             // uniform over the CTA; no grid-wide step in this kernel
-    for (int t = threadIdx.x; t < P * P; t += blockDim.x) Cs[t] = reinterpret_cast<const R *>(d.nmC)[S.nm0 + t];
+    if (S.P != P) return;  // another instantiation handles this system (uniform over the CTA)
+    for (int t = threadIdx.x; t < P * P; t += NT) Cs[t] = reinterpret_cast<const R *>(d.nmC)[S.nm0 + t];
     const int N = S.N;
     const int i0 = (cta - S.icta0) * A;
     const size_t G = (size_t)d.G;
@@ -383,71 +391,85 @@ __global__ void __launch_bounds__(nm_threads(P)) k_integrate_nm(Dev d, int j, in
     R *V = reinterpret_cast<R *>(d.v);
     const R *F = reinterpret_cast<const R *>(d.f);
     const R *hdt = reinterpret_cast<const R *>(d.hdt_m);
-    // phase 1: relative positions and B(dt/2) velocities, bead space
-    R xrel[kNmPer];
-    PS xold[kNmPer];
+    // phase 1: loads, then relative positions and B(dt/2) velocities, bead space
+    PS xold[PER], x0v[PER];
+    R vv[PER], fv[PER], xrel[PER];
+    int tt[PER];
 #pragma unroll
-    for (int u = 0; u < kNmPer; ++u) {
-        const int idx = threadIdx.x + u * kNmThreads;
-        xrel[u] = 0;
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NT;
+        const int b = idx / COLS, col = idx - b * COLS;
+        const int c = col / A, i = i0 + (col - c * A);
+        xold[u] = x0v[u] = PS(0);
+        vv[u] = fv[u] = R(0);
+        tt[u] = 0;
+        if (idx < NV && i < N) {
+            const size_t o0 = (size_t)c * G + S.g0 + i, o = o0 + (size_t)b * N;
+            xold[u] = X[o];
+            x0v[u] = X[o0];
+            vv[u] = V[o];
+            fv[u] = F[o];
+            tt[u] = d.typ[S.g0 + i];
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NT;
         if (idx >= NV) continue;
         const int b = idx / COLS, col = idx - b * COLS;
-        const int c = col / A, a = col - c * A, i = i0 + a;
-        R xr = 0, pv = 0;
-        if (i < N) {
-            const size_t o0 = (size_t)c * G + S.g0 + i, o = o0 + (size_t)b * N;
-            const PS xb = X[o];
-            xold[u] = xb;
-            xr = (b == 0) ? R(0) : PosT<PM, R>::rel(xb, X[o0], S.box[c], S.fix_scale[c], S.fix_inv[c]);
-            pv = fma(hdt[d.typ[S.g0 + i]], F[o], V[o]);
-        }
+        const int c = col / A;
+        const R xr = (b == 0) ? R(0) : PosT<PM, R>::rel(xold[u], x0v[u], S.box[c], S.fix_scale[c], S.fix_inv[c]);
         xrel[u] = xr;
         xs[idx] = xr;
-        ps[idx] = pv;
+        ps[idx] = fma(hdt[tt[u]], fv[u], vv[u]);
     }
     __syncthreads();
     // phase 2: to modes, A O A per mode
     const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
     const R *eta = reinterpret_cast<const R *>(d.eta) + (size_t)j * d.Dtot + S.dof0;
     const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
-    R qv[kNmPer], pvm[kNmPer];
+    R qv[PER], pm[PER], noise[PER];
 #pragma unroll
-    for (int u = 0; u < kNmPer; ++u) {
-        const int idx = threadIdx.x + u * kNmThreads;
-        qv[u] = pvm[u] = 0;
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NT;
+        const int k = idx / COLS, col = idx - k * COLS;
+        const int c = col / A, i = i0 + (col - c * A);
+        noise[u] = R(0);
+        if (idx < NV && i < N) {
+            const R sig = reinterpret_cast<const R *>(d.osig)[s * kMaxTypes + d.typ[S.g0 + i]];
+            noise[u] = sig * eta[(size_t)(k * 3 + c) * N + i];
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NT;
+        qv[u] = pm[u] = R(0);
         if (idx >= NV) continue;
         const int k = idx / COLS, col = idx - k * COLS;
-        const int c = col / A, a = col - c * A, i = i0 + a;
         R q = 0, p = 0;
 #pragma unroll 8
         for (int b = 0; b < P; ++b) {
             q = fma(Cs[b * P + k], xs[b * COLS + col], q);
             p = fma(Cs[b * P + k], ps[b * COLS + col], p);
         }
-        if (i < N) {
-            const int t = d.typ[S.g0 + i];
-            const R sig = reinterpret_cast<const R *>(d.osig)[s * kMaxTypes + t];
-            mode_aoa(q, p, rot[3 * k], rot[3 * k + 1], rot[3 * k + 2], c1, sig * eta[(size_t)(k * 3 + c) * N + i]);
-        }
+        mode_aoa(q, p, rot[3 * k], rot[3 * k + 1], rot[3 * k + 2], c1, noise[u]);
         qv[u] = q;
-        pvm[u] = p;
+        pm[u] = p;
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < kNmPer; ++u) {
-        const int idx = threadIdx.x + u * kNmThreads;
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NT;
         if (idx < NV) {
             xs[idx] = qv[u];
-            ps[idx] = pvm[u];
+            ps[idx] = pm[u];
         }
     }
     __syncthreads();
-    // phase 3: back to beads
-    R xnew[kNmPer];
+    // phase 3: back to beads (positions stay in each bead's own image)
 #pragma unroll
-    for (int u = 0; u < kNmPer; ++u) {
-        const int idx = threadIdx.x + u * kNmThreads;
-        xnew[u] = 0;
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NT;
         if (idx >= NV) continue;
         const int b = idx / COLS, col = idx - b * COLS;
         R x = 0, w = 0;
@@ -456,48 +478,58 @@ __global__ void __launch_bounds__(nm_threads(P)) k_integrate_nm(Dev d, int j, in
             x = fma(Cs[b * P + k], xs[k * COLS + col], x);
             w = fma(Cs[b * P + k], ps[k * COLS + col], w);
         }
-        xnew[u] = x;
-        qv[u] = w;
+        qv[u] = x;  // new relative position
+        pm[u] = w;  // new velocity
     }
     __syncthreads();
-    double spring = 0.0;
 #pragma unroll
-    for (int u = 0; u < kNmPer; ++u) {
-        const int idx = threadIdx.x + u * kNmThreads;
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NT;
         if (idx >= NV) continue;
         const int b = idx / COLS, col = idx - b * COLS;
-        const int c = col / A, a = col - c * A, i = i0 + a;
-        xs[idx] = xnew[u];
-        R dsq = 0;
+        const int c = col / A, i = i0 + (col - c * A);
+        xs[idx] = qv[u];
         if (i < N) {
-            const size_t g = S.g0 + (size_t)b * N + i, o = (size_t)c * G + g;
-            V[o] = qv[u];
-            const PS xn = PosT<PM, R>::add(xold[u], xnew[u] - xrel[u], S.box[c], S.fix_scale[c], S.fix_inv[c]);
+            const size_t o = (size_t)c * G + S.g0 + (size_t)b * N + i;
+            V[o] = pm[u];
+            const PS xn = PosT<PM, R>::add(xold[u], qv[u] - xrel[u], S.box[c], S.fix_scale[c], S.fix_inv[c]);
             X[o] = xn;
-            if (PM != PM_FREE) {
-                reinterpret_cast<PS *>(d.pos[cur])[4 * g + c] = xn;
-                const R dc = PosT<PM, R>::diff(xn, reinterpret_cast<const PS *>(d.xref)[o], S.fix_scale[c]);
-                dsq = dc * dc;
-            }
+            xn_s[idx] = xn;
         }
-        dd[idx] = dsq;
     }
     __syncthreads();
+    // phase 4: spring energy; packed positions and displacement test per bead-atom
+    double spring = 0.0;
     bool moved = false;
     const R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
 #pragma unroll
-    for (int u = 0; u < kNmPer; ++u) {
-        const int idx = threadIdx.x + u * kNmThreads;
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NT;
         if (idx >= NV) continue;
         const int b = idx / COLS, col = idx - b * COLS;
         const int c = col / A, a = col - c * A, i = i0 + a;
         if (i >= N) continue;
-        const int bn = (b + 1) % P;
-        const R dx = xs[b * COLS + col] - xs[bn * COLS + col];
-        spring += 0.5 * d.mass_mvv[d.typ[S.g0 + i]] * S.wP * S.wP * (double)(dx * dx);
+        const R dx = xs[idx] - xs[((b + 1) % P) * COLS + col];
+        spring += 0.5 * d.mass_mvv[tt[u]] * S.wP * S.wP * (double)(dx * dx);
         if (PM != PM_FREE && c == 0) {
-            const R tot = dd[b * COLS + a] + dd[b * COLS + A + a] + dd[b * COLS + 2 * A + a];
+            const size_t g = S.g0 + (size_t)b * N + i;
+            const PS *XR = reinterpret_cast<const PS *>(d.xref);
+            R tot = 0;
+            PS w3[3];
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                w3[cc] = xn_s[b * COLS + cc * A + a];
+                const R dc = PosT<PM, R>::diff(w3[cc], XR[(size_t)cc * G + g], S.fix_scale[cc]);
+                tot = fma(dc, dc, tot);
+            }
             moved |= tot > lim;
+            if (PM == PM_FIX) {
+                int4 *pk = reinterpret_cast<int4 *>(d.pos[cur]);
+                pk[g] = make_int4((int)w3[0], (int)w3[1], (int)w3[2], tt[u]);
+            } else {
+                D4 *pk = reinterpret_cast<D4 *>(d.pos[cur]);
+                pk[g] = D4{(double)w3[0], (double)w3[1], (double)w3[2], (double)tt[u]};
+            }
         }
     }
     if (PM != PM_FREE && __syncthreads_or(moved) && threadIdx.x == 0) atomicOr(&d.flag[cur], 1u);
@@ -1210,7 +1242,43 @@ __global__ void k_setclock(Dev d, long long b) { d.clock[0] = b; }
 
 bool md_supported_P(int P) { return (P >= 1 && P <= 6) || P == 8 || P == 16 || P == 32; }
 
-int integrate_atoms_per_cta(int P) { return P == 1 ? kIntAtomsPerCta : nm_values(P) / (3 * P); }
+int integrate_atoms_per_cta(int P, int big) { return P == 1 ? kIntAtomsPerCta : nm_atoms(P, big); }
+
+template <int P, int PM, class R>
+static void nm_launch(const Dev &d, const MdLaunch &m, int j, int cur, cudaStream_t st)
+{
+    if (m.nm_big) k_integrate_nm<P, PM, R, 1><<<m.n_icta, nm_threads(P, 1), nm_smem<P, PM, R>(1), st>>>(d, j, cur);
+    else k_integrate_nm<P, PM, R, 0><<<m.n_icta, nm_threads(P, 0), nm_smem<P, PM, R>(0), st>>>(d, j, cur);
+}
+
+template <int P, int PM, class R>
+static cudaError_t nm_prepare_one(int big)
+{
+    if (big) return cudaFuncSetAttribute(k_integrate_nm<P, PM, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nm_smem<P, PM, R>(1));
+    return cudaFuncSetAttribute(k_integrate_nm<P, PM, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nm_smem<P, PM, R>(0));
+}
+
+template <int PM, class R>
+static cudaError_t nm_prepare(const MdLaunch &m)
+{
+    for (int u = 0; u < m.nP; ++u) {
+        cudaError_t e = cudaSuccess;
+        switch (m.Pvals[u]) {
+#define QTB_P(PP) case PP: e = nm_prepare_one<PP, PM, R>(m.nm_big); break;
+            QTB_P(2) QTB_P(3) QTB_P(4) QTB_P(5) QTB_P(6) QTB_P(8) QTB_P(16) QTB_P(32)
+#undef QTB_P
+            default: break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t integrate_prepare(const MdLaunch &m)
+{
+    if (!m.pair) return m.mixed ? nm_prepare<PM_FREE, float>(m) : nm_prepare<PM_FREE, double>(m);
+    return m.mixed ? nm_prepare<PM_FIX, float>(m) : nm_prepare<PM_BOX64, double>(m);
+}
 
 template <int PM, class R>
 static void integrate_all(const Dev &d, const MdLaunch &m, int j, int cur, cudaStream_t st)
@@ -1218,7 +1286,7 @@ static void integrate_all(const Dev &d, const MdLaunch &m, int j, int cur, cudaS
     for (int u = 0; u < m.nP; ++u) {
         switch (m.Pvals[u]) {
             case 1: k_integrate<1, PM, R><<<m.n_icta, 128, 0, st>>>(d, j, cur); break;
-#define QTB_P(PP) case PP: k_integrate_nm<PP, PM, R><<<m.n_icta, nm_threads(PP), 0, st>>>(d, j, cur); break;
+#define QTB_P(PP) case PP: nm_launch<PP, PM, R>(d, m, j, cur, st); break;
             QTB_P(2) QTB_P(3) QTB_P(4) QTB_P(5) QTB_P(6) QTB_P(8) QTB_P(16) QTB_P(32)
 #undef QTB_P
             default: break;

@@ -45,6 +45,7 @@ struct MdLaunch {
     int Pvals[8];         // distinct bead counts
     int fused;            // all systems one-bead with a pair potential: the step kernel
                           // carries out the first half of the next step
+    int nm_big;           // ring-polymer integrator with 32 atoms per CTA (large contexts)
     int step_grid[4];     // resident CTAs of the step kernel, by (adv, rec)
     size_t step_smem;     // its dynamic shared memory (list build staging chunk)
 };
@@ -66,8 +67,10 @@ void launch_reduce(const Dev &d, const MdLaunch &m, int j, int record, cudaStrea
 void launch_tick(const Dev &d, cudaStream_t st);
 void launch_setclock(const Dev &d, long long blk, cudaStream_t st);
 bool md_supported_P(int P);
-// atoms per CTA of the integrator for bead count P
-int integrate_atoms_per_cta(int P);
+// atoms per CTA of the integrator for bead count P (big: large-context layout)
+int integrate_atoms_per_cta(int P, int big);
+// dynamic shared memory attributes of the ring-polymer integrator
+cudaError_t integrate_prepare(const MdLaunch &m);
 
 // filter_tc.cu
 cudaError_t filter_tc_prepare();

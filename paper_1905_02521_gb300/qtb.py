@@ -49,7 +49,7 @@ class qtb_params(C.Structure):
                 ("ext_V0", C.c_double), ("ext_a", C.c_double), ("dt", C.c_double), ("precision", C.c_int),
                 ("filter_prec", C.c_int), ("seed", C.c_ulonglong), ("obs_stride", C.c_int),
                 ("max_records", C.c_int), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
-                ("alloc_user", C.c_void_p), ("skin", C.c_double)]
+                ("alloc_user", C.c_void_p), ("skin", C.c_double), ("nm_layout", C.c_int)]
 
 
 _lib = None
@@ -190,6 +190,7 @@ def qtb_init(systems, params, stream=None):
     p.obs_stride = int(params.get("obs_stride", 1))
     p.max_records = int(params.get("max_records", 4096))
     p.skin = float(params.get("skin", 0.0))
+    p.nm_layout = int(params.get("nm_layout", 0))
     if params.get("torch_alloc", True):
         a, f = _torch_allocator()
         p.dev_alloc, p.dev_free = a, f

@@ -109,3 +109,23 @@ def test_pimd_beads_keep_their_images(qtb, oracle):
         qtb.qtb_destroy(ctx)
     print("P = 4 MgO, skin 0.4: %d list rebuilds in 600 steps" % nreb)
     assert 2 <= nreb < 150
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_integrator_layouts_are_bit_identical(qtb, precision):
+    # the compact and the wide layout of the ring-polymer integrator do the same
+    # arithmetic per value: identical trajectories, through graph blocks and
+    # direct launches
+    P = 8
+    s, pot = W.mgo_system(3, 300.0, n_beads=P, seed=6)
+    N = len(s["types"])
+    out = []
+    for layout in (1, 2):
+        ctx = gpu_ctx(qtb, [s], pot, 0.5, precision=precision, filter_prec=1, seed=4, nm_layout=layout)
+        try:
+            qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB_PIMD, 513, 0.6)
+            qtb.qtb_step_n(ctx, 256 + 37)
+            out.append(qtb.qtb_get_state(ctx, 0, P, N))
+        finally:
+            qtb.qtb_destroy(ctx)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
