@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--workload", default="mgo8000", choices=WORKLOADS)
     ap.add_argument("--ncell", type=int, default=10, help="cells per side of the mgo8000 workload")
     ap.add_argument("--skin", type=float, default=0.0, help="neighbour-list skin, A (0: library default)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="choose skin, lanes per bead-atom and integrator layout with qtb_autotune first (untimed)")
     ap.add_argument("--filter", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -221,6 +223,10 @@ def run_ours(args):
     systems, pot, params, setup, desc = workload(args.workload, args.ncell, args.precision, filt)
     params["seed"] = replica_seed(12345, rank)
     params["skin"] = args.skin
+    tuning = None
+    if args.autotune:
+        mode, n_taps, wmax = setup if setup is not None else (qtb.NOISE_WHITE, 1, 0.0)
+        params, tuning = qtb.qtb_autotune(systems, params, mode, n_taps, wmax, n_blocks=3)
     sizes = [(len(x["types"]), int(x["pos"].shape[0])) for x in systems]   # (N, P)
     units = sum(n * p for n, p in sizes)                                    # atom*bead per MD step
     stream = torch.cuda.Stream()
@@ -309,7 +315,9 @@ def run_ours(args):
         "config": {"workload": desc, "name": args.workload, "systems": len(systems),
                    "atom_beads_per_md_step": units, "md_steps_per_bench_step": BLOCK, "precision": args.precision,
                    "filter": filt if setup is not None else "none (white noise)", "parallelism": f"replicas x{ws}",
-                   "skin_A": args.skin if args.skin else "default",
+                   "skin_A": params["skin"] if params["skin"] else "default",
+                   "list_lanes": params.get("list_lanes") or "default (16)",
+                   "autotune": tuning,
                    "launch": "direct (2 x 128-step calls per block)" if args.direct else "CUDA graph per 256-step block",
                    "l2": "256 MB buffer written between timed steps (flush)"},
         "roofline": {"bound": "alu", "kernel": "k_step", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

@@ -117,6 +117,8 @@ typedef struct {
                               (8-32 atoms per CTA, more CTAs; small contexts), 2 wide (32
                               atoms per CTA, coalesced rows; large contexts).  Same
                               arithmetic, bit-identical results. */
+    int list_lanes;        /* PAIR: lanes per bead-atom of the force kernel, 8, 16 or 32
+                              (0: 16).  Changes the summation order only. */
 } qtb_params;
 
 /* Observable record (FP64), one per recorded step and system:
@@ -194,6 +196,31 @@ int qtb_kernel_times(qtb_ctx *c, double *mean_ms, int *counts, int n_classes);
 /* Number of neighbour-list rebuilds carried out so far (PAIR; 0 otherwise),
  * the one made by qtb_init / qtb_set_state included.  Synchronises. */
 int qtb_list_rebuilds(qtb_ctx *c, long long *count);
+
+/* Result of qtb_autotune. */
+typedef struct {
+    double skin;          /* chosen neighbour-list skin, A (0: the default) */
+    int nm_layout;        /* chosen ring-polymer integrator layout (1 compact, 2 wide; 0 if P = 1 only) */
+    int list_lanes;       /* chosen lanes per bead-atom of the force kernel (0: the default, 16) */
+    double ms_per_step;   /* mean device time of one MD step with that choice */
+    double default_ms_per_step;  /* the same with the defaults (skin 0, nm_layout 0, list_lanes 0) */
+    int n_tried;          /* configurations timed */
+} qtb_tuning;
+
+/* Autotuner of the launch shapes and the cell/neighbour-list batching.  For
+ * every candidate -- skin in {0.5, 0.8, 1.2, 1.6} A (those below r_cut/2),
+ * lanes per bead-atom in {8, 16, 32}, and for systems with beads the integrator
+ * layouts {1, 2} -- it creates a context for the given systems and parameters
+ * (qtb_init), applies the filter (noise_mode, n_taps, omega_max; as
+ * qtb_set_filter on every system), runs n_blocks 256-step warm-up blocks and
+ * then times n_blocks >= 1 blocks (so the list-rebuild rate of a system that has
+ * left its initial configuration is in the timing), and writes
+ * into *best a copy of *p with the fastest skin, nm_layout and list_lanes.  The
+ * candidates change the summation order and the rebuild schedule only, not the
+ * dynamics.  Pair potentials only (QTB_ERR_ARG otherwise).  stream: as qtb_init.
+ * Allocates and frees one context at a time; synchronises. */
+int qtb_autotune(const qtb_system *sys, int n_sys, const qtb_params *p, void *stream, int noise_mode, int n_taps,
+                 double omega_max, int n_blocks, qtb_params *best, qtb_tuning *result);
 
 /* Current step index (number of steps taken). */
 int qtb_get_step(qtb_ctx *c, long long *step);

@@ -19,9 +19,9 @@ OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libqtb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# md.cu writes every fused multiply-add out explicitly (the integrator and the
+# the MD sources (md_kernels.cuh) write every fused multiply-add out explicitly (the integrator and the
 # fused force epilogue must round alike): no automatic contraction there
-EXTRA = {"md.cu": ["--fmad=false"]}
+EXTRA = {f: ["--fmad=false"] for f in ("md.cu", "md_step8.cu", "md_step16.cu", "md_step32.cu")}
 
 
 def nvcc() -> str:

@@ -679,6 +679,8 @@ int validate(const qtb_system *sys, int n_sys, const qtb_params *p)
     if (p->filter_prec < 0 || p->filter_prec > 2) return fail(QTB_ERR_ARG, "unknown filter precision");
     if (p->obs_stride < 1 || p->max_records < 1) return fail(QTB_ERR_ARG, "obs_stride and max_records must be >= 1");
     if (p->nm_layout < 0 || p->nm_layout > 2) return fail(QTB_ERR_ARG, "nm_layout must be 0, 1 or 2");
+    if (p->list_lanes != 0 && p->list_lanes != 8 && p->list_lanes != 16 && p->list_lanes != 32)
+        return fail(QTB_ERR_ARG, "list_lanes must be 0, 8, 16 or 32");
     if (p->potential == QTB_POT_PAIR) {
         if (!p->charge || !p->buck_A || !p->buck_rho || !p->buck_C) return fail(QTB_ERR_ARG, "pair tables missing");
         if (!(p->r_cut > 0)) return fail(QTB_ERR_ARG, "r_cut must be > 0");
@@ -846,6 +848,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     long long beads_total = 0;
     for (int s = 0; s < n_sys; ++s) beads_total += (long long)sys[s].n_atoms * sys[s].n_beads;
     const int nm_big = p->nm_layout == 2 ? 1 : p->nm_layout == 1 ? 0 : (beads_total >= (1LL << 18) ? 1 : 0);
+    const int lanes = p->list_lanes ? p->list_lanes : 16;
     for (int s = 0; s < n_sys; ++s) {
         const qtb_system &q = sys[s];
         HSys &h = c->hs[s];
@@ -914,7 +917,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
                 R.cell0 = ncells;
                 ncells += cells;
                 R.fcta0 = nlcta;
-                const int nl = (h.N + kListAtoms - 1) / kListAtoms;
+                const int nl = (h.N + list_atoms(lanes) - 1) / list_atoms(lanes);
                 nlcta += nl;
                 c->dr.push_back(R);
                 for (int t = 0; t < cells; ++t) c->cell_rep.push_back(nrep);
@@ -928,6 +931,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     for (int s = 0; s < n_sys; ++s)
         for (int t = c->ds[s].icta0; t < c->ds[s].icta1; ++t) c->icta_sys.push_back(s);
     c->ml.mixed = c->mixed;
+    c->ml.lanes = lanes;
     if (c->pair && step_prepare(c->ml, stage_cap) != cudaSuccess)
         return bail(fail(QTB_ERR_CUDA, "cannot prepare the cooperative step kernel (shared memory, occupancy)"));
     int ext_gx = 0;
@@ -938,7 +942,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         if (c->pair) {
             // the system's replicas are consecutive, and so are their list force CTAs
             S.fcta0 = c->dr[S.rep0].fcta0;
-            S.fcta1 = c->dr[S.rep0 + c->hs[s].P - 1].fcta0 + (c->hs[s].N + kListAtoms - 1) / kListAtoms;
+            S.fcta1 = c->dr[S.rep0 + c->hs[s].P - 1].fcta0 + (c->hs[s].N + list_atoms(lanes) - 1) / list_atoms(lanes);
             nforce = S.fcta1;
         } else {
             S.fcta0 = s * ext_gx;

@@ -1,1175 +1,8 @@
-// md.cu -- cell lists, pair and external forces, the normal-mode BAOAB
-// integrator and the per-system reductions (sm_103a).
-//
-// Eq. 4: every bead feels -(1/P) grad V of its own replica plus the ring
-// springs; the springs are integrated exactly in normal-mode space (Sec. 2.3,
-// Eq. 11 with the physical force entering through the B kicks).  Eq. 8: the
-// Langevin O step carries the coloured random force.  Eq. 5: primitive energy
-// estimator, accumulated in FP64.
-//
-// Mixed form: positions in 30-bit fixed point per box edge (exact integer
-// displacements, periodic wrap by masking), FP32 arithmetic, per-atom forces
-// summed in float-float (error-free TwoSum per lane and across the warp), so
-// that the only FP32 errors left are those of the individual pair terms.
-//
-// Pair forces come from Verlet neighbour lists (every pair within r_cut +
-// skin at the last rebuild, with its periodic image).  Positions move
-// continuously between rebuilds and are wrapped into the box only when the
-// lists are rebuilt, which happens when some bead-atom has moved more than
-// skin/2 since the last one: then no pair outside a list can have come within
-// r_cut.  For one-bead systems the force kernel also carries out the first
-// half of the next step (B, A, O, A), so that a step is one launch.
-#include <algorithm>
-#include <climits>
-#include <type_traits>
-
-#include "qtb_dev.cuh"
-#include "qtb_kernels.cuh"
+// md.cu -- integrators, external potentials, reductions and the launchers of
+// the MD hot path (sm_103a); the device code is in md_kernels.cuh.
+#include "md_kernels.cuh"
 
 namespace qtb {
-
-struct alignas(32) D4 {  // packed FP64 position + type of one cell slot
-    double x, y, z, w;
-};
-
-// ---------------------------------------------------------------------------
-// position storage
-
-template <int PM, class R> struct PosT;
-
-// rel: minimum-image difference; add: move (no wrap, see above); diff: plain
-// difference in A (displacement since the last rebuild)
-template <class R> struct PosT<PM_BOX64, R> {  // FP64 A, in [0, L) at each rebuild
-    typedef double S;
-    __device__ static R rel(S a, S b, double L, float, float)
-    {
-        double d = a - b;
-        return (R)(d - L * rint(d / L));
-    }
-    __device__ static S add(S a, R delta, double, float, float) { return a + (double)delta; }
-    __device__ static R diff(S a, S b, float) { return (R)(a - b); }
-    __device__ static S wrap(S x, double L)
-    {
-        x -= L * floor(x / L);
-        return (x >= L || x < 0.0) ? 0.0 : x;
-    }
-};
-
-template <class R> struct PosT<PM_FIX, R> {  // 30-bit fixed point per box edge, in [0, 2^30) at each rebuild
-    typedef int S;
-    __device__ static R rel(S a, S b, double, float scale, float) { return (R)fix_minimg(a - b) * (R)scale; }
-    __device__ static S add(S a, R delta, double, float, float inv)
-    {
-        const int dq = __float2int_rn((float)delta * inv);
-        return (int)((unsigned)a + (unsigned)dq);
-    }
-    __device__ static R diff(S a, S b, float scale) { return (R)(int)((unsigned)a - (unsigned)b) * (R)scale; }
-    __device__ static S wrap(S x, double) { return x & (int)((1u << kFixBits) - 1u); }
-};
-
-template <class R> struct PosT<PM_FREE, R> {  // unbounded (external potentials)
-    typedef R S;
-    __device__ static R rel(S a, S b, double, float, float) { return a - b; }
-    __device__ static S add(S a, R delta, double, float, float) { return a + delta; }
-    __device__ static R diff(S a, S b, float) { return a - b; }
-    __device__ static S wrap(S x, double) { return x; }
-};
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ float warp_sum(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// error-free sum: s + e = a + b exactly (Knuth's TwoSum)
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    const float z = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
-}
-
-// float-float accumulator
-struct FF {
-    float hi, lo;
-    __device__ void add(float x)
-    {
-        float s, e;
-        two_sum(hi, x, s, e);
-        hi = s;
-        lo = __fadd_rn(lo, e);
-    }
-    __device__ void warp_reduce()
-    {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
-            float s, e;
-            two_sum(hi, oh, s, e);
-            hi = s;
-            lo = __fadd_rn(__fadd_rn(lo, ol), e);
-        }
-    }
-    // sum over aligned groups of W lanes (W a power of two <= 32)
-    template <int W> __device__ void group_reduce()
-    {
-#pragma unroll
-        for (int o = W / 2; o > 0; o >>= 1) {
-            const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
-            float s, e;
-            two_sum(hi, oh, s, e);
-            hi = s;
-            lo = __fadd_rn(__fadd_rn(lo, ol), e);
-        }
-    }
-    __device__ float value() const { return __fadd_rn(hi, lo); }
-};
-
-// plain accumulator with the same interface (FP64 form)
-struct DD {
-    double hi;
-    __device__ void add(double x) { hi += x; }
-    __device__ void warp_reduce() { hi = warp_sum(hi); }
-    template <int W> __device__ void group_reduce()
-    {
-#pragma unroll
-        for (int o = W / 2; o > 0; o >>= 1) hi += __shfl_xor_sync(0xffffffffu, hi, o);
-    }
-    __device__ double value() const { return hi; }
-};
-
-template <int W, class T> __device__ __forceinline__ T group_sum(T v)
-{
-#pragma unroll
-    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// CTA-wide sum of kNQ doubles held by lane 0 of each warp into out[0..kNQ)
-__device__ void cta_store_partials(const double *acc, double (*red)[kNQ], double *out)
-{
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (lane == 0)
-        for (int q = 0; q < kNQ; ++q) red[warp][q] = acc[q];
-    __syncthreads();
-    if (threadIdx.x < kNQ) {
-        double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
-        out[threadIdx.x] = s;
-    }
-}
-
-// Grid-wide barrier of a cooperative launch (all CTAs co-resident): arrival
-// counter bar[0] and generation bar[1].  The wait is bounded: after about a
-// second it records ERR_TIMEOUT_BAR and lets the CTA go on (the results of
-// that launch are then void, the host reports QTB_ERR_TIMEOUT).  Called by
-// all threads of every CTA.
-__device__ void grid_barrier(const Dev &d)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *gen = d.gbar + 1;
-        const unsigned g0 = *gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(d.gbar, 1u);
-        if (arrived == gridDim.x * gridDim.y - 1u) {
-            d.gbar[0] = 0u;
-            __threadfence();
-            atomicAdd(d.gbar + 1, 1u);
-        } else {
-            long long spins = 0;
-            while (*gen == g0) {
-                if (++spins > (1LL << 25)) {
-                    atomicOr(d.err, (unsigned)ERR_TIMEOUT_BAR);
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-}
-
-// One normal mode: A(dt/2) (exact free ring-polymer rotation, (cos, sin/w,
-// -w sin) = (cs, sw, ws); for the centroid (1, dt/2, 0) a drift), O(dt) with
-// the random kick `noise` = sqrt((1 - c1^2)/m) eta, A(dt/2).  (q, p) in place.
-// Shared by the integrator and the fused force epilogue, with every
-// multiply-add written out (this file is compiled without contraction), so
-// that both round alike.
-template <class R>
-__device__ __forceinline__ void mode_aoa(R &q, R &p, R cs, R sw, R ws, R c1, R noise)
-{
-    const R qn = fma(p, sw, q * cs);
-    R pn = fma(p, cs, q * ws);
-    pn = fma(c1, pn, noise);
-    q = fma(pn, sw, qn * cs);
-    p = fma(pn, cs, qn * ws);
-}
-
-// ---------------------------------------------------------------------------
-// Integrator: B(dt/2) in bead space, then A(dt/2) O A(dt/2) in normal-mode
-// space.  Lane 3a + c (a < 10) of a warp takes Cartesian component c of atom
-// i with all of its P beads, so that the three components of a bead-atom meet
-// in one warp for the neighbour-list displacement test.  Writes the new
-// positions to x and (pair potential) to the packed copy pos[cur] that the
-// force kernel gathers from, and requests a list rebuild (flag[cur]) when a
-// bead-atom has moved more than skin/2 since the last one.
-
-template <int P, int PM, class R>
-__global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
-{
-    constexpr int UN = (P <= 8) ? P : 1;  // full unroll only for small rings
-    typedef typename PosT<PM, R>::S PS;
-    __shared__ R Cs[P * P];
-    __shared__ double red[4][kNQ];
-    const int cta = blockIdx.x;
-    const int s = d.icta_sys[cta];
-    const DSys S = d.sys[s];
-    const bool mine = (S.P == P);  // another instantiation handles the other systems
-    if (mine)
-        for (int t = threadIdx.x; t < P * P; t += blockDim.x) Cs[t] = reinterpret_cast<const R *>(d.nmC)[S.nm0 + t];
-    __syncthreads();
-    const int N = S.N;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int aw = lane / 3, c = lane - 3 * aw;
-    const int i = (cta - S.icta0) * kIntAtomsPerCta + warp * kIntAtomsPerWarp + aw;
-    const bool act = mine && aw < kIntAtomsPerWarp && i < N;
-    double acc[kNQ];
-    for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
-    double spring = 0.0;
-    PS *X = reinterpret_cast<PS *>(d.x);
-    const size_t G = (size_t)d.G;
-    const size_t base = act ? (size_t)c * G + S.g0 + i : 0;
-    const float fsc = S.fix_scale[c], finv = S.fix_inv[c];
-    PS x0{};
-    R a[P], a0[P];  // bead positions relative to bead 0: new, old
-    if (act) {
-        R *V = reinterpret_cast<R *>(d.v);
-        const R *F = reinterpret_cast<const R *>(d.f);
-        const int t = d.typ[S.g0 + i];
-        const R hdtm = reinterpret_cast<const R *>(d.hdt_m)[t];
-        const R sig = reinterpret_cast<const R *>(d.osig)[s * kMaxTypes + t];
-        const double L = S.box[c];
-        x0 = X[base];
-        R q[P];
-        // relative bead positions -> modes
-#pragma unroll(UN)
-        for (int b = 0; b < P; ++b) {
-            a[b] = (b == 0) ? R(0) : PosT<PM, R>::rel(X[base + (size_t)b * N], x0, L, fsc, finv);
-            a0[b] = a[b];
-        }
-#pragma unroll(UN)
-        for (int k = 0; k < P; ++k) {
-            R u = 0;
-#pragma unroll(UN)
-            for (int b = 0; b < P; ++b) u = fma(Cs[b * P + k], a[b], u);
-            q[k] = u;
-        }
-        // B: half kick with the current forces, bead velocities -> modes
-#pragma unroll(UN)
-        for (int b = 0; b < P; ++b) a[b] = fma(hdtm, F[base + (size_t)b * N], V[base + (size_t)b * N]);
-        R p[P];
-#pragma unroll(UN)
-        for (int k = 0; k < P; ++k) {
-            R u = 0;
-#pragma unroll(UN)
-            for (int b = 0; b < P; ++b) u = fma(Cs[b * P + k], a[b], u);
-            p[k] = u;
-        }
-        const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
-        const R *eta = reinterpret_cast<const R *>(d.eta) + (size_t)j * d.Dtot + S.dof0;
-        const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
-#pragma unroll(UN)
-        for (int k = 0; k < P; ++k)
-            mode_aoa(q[k], p[k], rot[3 * k], rot[3 * k + 1], rot[3 * k + 2], c1, sig * eta[(size_t)(k * 3 + c) * N + i]);
-        // modes -> beads
-#pragma unroll(UN)
-        for (int b = 0; b < P; ++b) {
-            R u = 0, w = 0;
-#pragma unroll(UN)
-            for (int k = 0; k < P; ++k) {
-                u = fma(Cs[b * P + k], q[k], u);
-                w = fma(Cs[b * P + k], p[k], w);
-            }
-            a[b] = u;
-            V[base + (size_t)b * N] = w;
-        }
-        if (P > 1) {
-            R sp = 0;
-#pragma unroll(UN)
-            for (int b = 0; b < P; ++b) {
-                R dd = a[b] - a[(b + 1) % P];
-                sp = fma(dd, dd, sp);
-            }
-            spring = 0.5 * d.mass_mvv[t] * S.wP * S.wP * (double)sp;
-        }
-    }
-    // new bead positions: each bead moves by the change of its position relative
-    // to bead 0, so that it stays in its own periodic image (after a list rebuild
-    // the beads of an atom on the box boundary may be wrapped into different
-    // images); with a pair potential also the packed copy and the displacement
-    // test (the three components meet through shuffles)
-    bool moved = false;
-    const int l0 = 3 * aw;
-#pragma unroll(UN)
-    for (int b = 0; b < P; ++b) {
-        R dd = 0;
-        if (act) {
-            const size_t o = base + (size_t)b * N;
-            const PS xn = PosT<PM, R>::add(X[o], a[b] - a0[b], S.box[c], fsc, finv);
-            X[o] = xn;
-            if (PM != PM_FREE) {
-                const size_t g = S.g0 + (size_t)b * N + i;
-                reinterpret_cast<PS *>(d.pos[cur])[4 * g + c] = xn;
-                const R dc = PosT<PM, R>::diff(xn, reinterpret_cast<const PS *>(d.xref)[o], fsc);
-                dd = dc * dc;
-            }
-        }
-        if (PM != PM_FREE) {
-            const R tot = __shfl_sync(0xffffffffu, dd, l0 & 31) + __shfl_sync(0xffffffffu, dd, (l0 + 1) & 31) +
-                          __shfl_sync(0xffffffffu, dd, (l0 + 2) & 31);
-            const R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
-            moved |= act && c == 0 && tot > lim;
-        }
-    }
-    if (PM != PM_FREE && __any_sync(0xffffffffu, moved) && lane == 0) atomicOr(&d.flag[cur], 1u);
-    spring = warp_sum(spring);
-    acc[Q_SPRING] = spring;
-    if (mine) cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
-}
-
-// Ring-polymer integrator for P >= 2 with the normal-mode transforms in shared
-// memory.  A CTA takes A atoms of one system, i.e. 3 A columns (component c,
-// atom a; col = c A + a) of P beads, V = 3 A P values.  Phase 1 (thread per
-// (bead b, column)): relative bead positions and half-kicked bead velocities
-// (B, dt/2) into shared memory.  Phase 2 (thread per (mode k, column)): the
-// forward transforms, A(dt/2) O(dt) A(dt/2) of mode k.  Phase 3 (thread per
-// (bead, column), the mapping of phase 1): back to beads, each bead moved
-// within its own periodic image.  Phase 4 (thread per (bead, column)): spring
-// energy; the threads of component 0 write the packed position and test the
-// bead-atom's displacement against skin/2.  Every thread issues all of its
-// global loads of a phase before it uses them.  BIG (large contexts): 32 atoms
-// per CTA, so that the 32 threads of a warp read 128 contiguous bytes.
-__host__ __device__ constexpr int nm_atoms(int P, int big) { return big ? 32 : (P >= 16 ? 768 : 192) / (3 * P); }
-__host__ __device__ constexpr int nm_threads(int P, int big) { return big ? (P >= 8 ? 256 : 128) : (P >= 16 ? 128 : 64); }
-
-template <int P, int PM, class R>
-__host__ __device__ constexpr size_t nm_smem(int big)
-{
-    return (size_t)3 * nm_atoms(P, big) * P * (2 * sizeof(R) + sizeof(typename PosT<PM, R>::S)) + (size_t)P * P * sizeof(R);
-}
-
-template <int P, int PM, class R, int BIG>
-__global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int j, int cur)
-{
-    typedef typename PosT<PM, R>::S PS;
-    constexpr int NT = nm_threads(P, BIG), A = nm_atoms(P, BIG);
-    constexpr int COLS = 3 * A, NV = COLS * P, PER = (NV + NT - 1) / NT;
-    extern __shared__ __align__(16) unsigned char nsm[];
-    R *xs = reinterpret_cast<R *>(nsm);            // [b or k][col]
-    R *ps = xs + NV;
-    R *Cs = ps + NV;                               // [b][k]
-    PS *xn_s = reinterpret_cast<PS *>(Cs + P * P); // new positions [b][col]
-    __shared__ double red[NT / 32][kNQ];
-    const int cta = blockIdx.x;
-    const int s = d.icta_sys[cta];
-    const DSys S = d.sys[s];
-    if (S.P != P) return;  // another instantiation handles this system (uniform over the CTA)
-    for (int t = threadIdx.x; t < P * P; t += NT) Cs[t] = reinterpret_cast<const R *>(d.nmC)[S.nm0 + t];
-    const int N = S.N;
-    const int i0 = (cta - S.icta0) * A;
-    const size_t G = (size_t)d.G;
-    PS *X = reinterpret_cast<PS *>(d.x);
-    R *V = reinterpret_cast<R *>(d.v);
-    const R *F = reinterpret_cast<const R *>(d.f);
-    const R *hdt = reinterpret_cast<const R *>(d.hdt_m);
-    // phase 1: loads, then relative positions and B(dt/2) velocities, bead space
-    PS xold[PER], x0v[PER];
-    R vv[PER], fv[PER], xrel[PER];
-    int tt[PER];
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        const int b = idx / COLS, col = idx - b * COLS;
-        const int c = col / A, i = i0 + (col - c * A);
-        xold[u] = x0v[u] = PS(0);
-        vv[u] = fv[u] = R(0);
-        tt[u] = 0;
-        if (idx < NV && i < N) {
-            const size_t o0 = (size_t)c * G + S.g0 + i, o = o0 + (size_t)b * N;
-            xold[u] = X[o];
-            x0v[u] = X[o0];
-            vv[u] = V[o];
-            fv[u] = F[o];
-            tt[u] = d.typ[S.g0 + i];
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        if (idx >= NV) continue;
-        const int b = idx / COLS, col = idx - b * COLS;
-        const int c = col / A;
-        const R xr = (b == 0) ? R(0) : PosT<PM, R>::rel(xold[u], x0v[u], S.box[c], S.fix_scale[c], S.fix_inv[c]);
-        xrel[u] = xr;
-        xs[idx] = xr;
-        ps[idx] = fma(hdt[tt[u]], fv[u], vv[u]);
-    }
-    __syncthreads();
-    // phase 2: to modes, A O A per mode
-    const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
-    const R *eta = reinterpret_cast<const R *>(d.eta) + (size_t)j * d.Dtot + S.dof0;
-    const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
-    R qv[PER], pm[PER], noise[PER];
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        const int k = idx / COLS, col = idx - k * COLS;
-        const int c = col / A, i = i0 + (col - c * A);
-        noise[u] = R(0);
-        if (idx < NV && i < N) {
-            const R sig = reinterpret_cast<const R *>(d.osig)[s * kMaxTypes + d.typ[S.g0 + i]];
-            noise[u] = sig * eta[(size_t)(k * 3 + c) * N + i];
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        qv[u] = pm[u] = R(0);
-        if (idx >= NV) continue;
-        const int k = idx / COLS, col = idx - k * COLS;
-        R q = 0, p = 0;
-#pragma unroll 8
-        for (int b = 0; b < P; ++b) {
-            q = fma(Cs[b * P + k], xs[b * COLS + col], q);
-            p = fma(Cs[b * P + k], ps[b * COLS + col], p);
-        }
-        mode_aoa(q, p, rot[3 * k], rot[3 * k + 1], rot[3 * k + 2], c1, noise[u]);
-        qv[u] = q;
-        pm[u] = p;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        if (idx < NV) {
-            xs[idx] = qv[u];
-            ps[idx] = pm[u];
-        }
-    }
-    __syncthreads();
-    // phase 3: back to beads (positions stay in each bead's own image)
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        if (idx >= NV) continue;
-        const int b = idx / COLS, col = idx - b * COLS;
-        R x = 0, w = 0;
-#pragma unroll 8
-        for (int k = 0; k < P; ++k) {
-            x = fma(Cs[b * P + k], xs[k * COLS + col], x);
-            w = fma(Cs[b * P + k], ps[k * COLS + col], w);
-        }
-        qv[u] = x;  // new relative position
-        pm[u] = w;  // new velocity
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        if (idx >= NV) continue;
-        const int b = idx / COLS, col = idx - b * COLS;
-        const int c = col / A, i = i0 + (col - c * A);
-        xs[idx] = qv[u];
-        if (i < N) {
-            const size_t o = (size_t)c * G + S.g0 + (size_t)b * N + i;
-            V[o] = pm[u];
-            const PS xn = PosT<PM, R>::add(xold[u], qv[u] - xrel[u], S.box[c], S.fix_scale[c], S.fix_inv[c]);
-            X[o] = xn;
-            xn_s[idx] = xn;
-        }
-    }
-    __syncthreads();
-    // phase 4: spring energy; packed positions and displacement test per bead-atom
-    double spring = 0.0;
-    bool moved = false;
-    const R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        if (idx >= NV) continue;
-        const int b = idx / COLS, col = idx - b * COLS;
-        const int c = col / A, a = col - c * A, i = i0 + a;
-        if (i >= N) continue;
-        const R dx = xs[idx] - xs[((b + 1) % P) * COLS + col];
-        spring += 0.5 * d.mass_mvv[tt[u]] * S.wP * S.wP * (double)(dx * dx);
-        if (PM != PM_FREE && c == 0) {
-            const size_t g = S.g0 + (size_t)b * N + i;
-            const PS *XR = reinterpret_cast<const PS *>(d.xref);
-            R tot = 0;
-            PS w3[3];
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                w3[cc] = xn_s[b * COLS + cc * A + a];
-                const R dc = PosT<PM, R>::diff(w3[cc], XR[(size_t)cc * G + g], S.fix_scale[cc]);
-                tot = fma(dc, dc, tot);
-            }
-            moved |= tot > lim;
-            if (PM == PM_FIX) {
-                int4 *pk = reinterpret_cast<int4 *>(d.pos[cur]);
-                pk[g] = make_int4((int)w3[0], (int)w3[1], (int)w3[2], tt[u]);
-            } else {
-                D4 *pk = reinterpret_cast<D4 *>(d.pos[cur]);
-                pk[g] = D4{(double)w3[0], (double)w3[1], (double)w3[2], (double)tt[u]};
-            }
-        }
-    }
-    if (PM != PM_FREE && __syncthreads_or(moved) && threadIdx.x == 0) atomicOr(&d.flag[cur], 1u);
-    double acc[kNQ];
-    for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
-    acc[Q_SPRING] = warp_sum(spring);
-    cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
-}
-
-// ---------------------------------------------------------------------------
-// List rebuild: three phases of the cooperative step kernel, separated by grid
-// barriers, run only when flag[cur] is set.  bin_phase wraps the positions
-// into the box (x, its packed copy pos[cur] and the reference xref) and bins
-// them into cells >= (r_cut + skin)/2 with atomic slots; sort_phase puts each
-// cell's slots in bead-atom order (so that every list, and every later sum,
-// has a fixed order); build_cell scans the 5^3 stencil of one cell.
-
-__device__ __forceinline__ int rep_of(const Dev &d, long long g)  // replica holding bead-atom g
-{
-    int lo = 0, hi = d.nrep - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (d.rep[mid].g0 <= g) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-template <int PM>
-__device__ void bin_phase(const Dev &d, int cur)
-{
-    typedef typename PosT<PM, double>::S PS;
-    typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
-    const size_t G = (size_t)d.G;
-    PS *X = reinterpret_cast<PS *>(d.x);
-    PS *XR = reinterpret_cast<PS *>(d.xref);
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += (long long)gridDim.x * blockDim.x) {
-        const DRep &R = d.rep[rep_of(d, g)];
-        PS w[3];
-        int cc[3];
-        for (int c = 0; c < 3; ++c) {
-            const double L = R.box[c];
-            const int ncc = R.nc[c];
-            const PS xw = PosT<PM, double>::wrap(X[c * G + g], L);
-            X[c * G + g] = xw;
-            XR[c * G + g] = xw;
-            w[c] = xw;
-            int v;
-            if (PM == PM_FIX) v = (int)(((unsigned long long)(unsigned)xw * (unsigned)ncc) >> kFixBits);
-            else v = (int)floor((double)xw / L * ncc);
-            cc[c] = min(max(v, 0), ncc - 1);
-        }
-        E4 p;
-        p.x = w[0]; p.y = w[1]; p.z = w[2];
-        if (PM == PM_FIX) p.w = d.typ[g]; else p.w = (double)d.typ[g];
-        reinterpret_cast<E4 *>(d.pos[cur])[g] = p;
-        const int cell = R.cell0 + cc[0] + R.nc[0] * (cc[1] + R.nc[1] * cc[2]);
-        const int slot = atomicAdd(&d.cnt[cell], 1);
-        if (slot < d.cap)
-            d.cidx[(size_t)cell * d.cap + slot] = (int)g;
-        else
-            atomicOr(d.err, (unsigned)ERR_OVERFLOW);
-    }
-}
-
-// one warp per cell; keys: kMaxCellCap ints of shared memory per warp
-template <int PM>
-__device__ void sort_phase(const Dev &d, int *keys)
-{
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    int *kw = keys + warp * kMaxCellCap;
-    const size_t G = (size_t)d.G;
-    for (int cell = blockIdx.x * nw + warp; cell < d.ncells; cell += gridDim.x * nw) {
-        const int n = min(d.cnt[cell], d.cap);
-        for (int e = lane; e < n; e += 32) kw[e] = d.cidx[(size_t)cell * d.cap + e];
-        __syncwarp();
-        const int g0 = d.rep[d.cell_rep[cell]].g0;
-        for (int e = lane; e < n; e += 32) {
-            const int g = kw[e];
-            int rank = 0;
-            for (int t = 0; t < n; ++t) rank += (kw[t] < g) ? 1 : 0;
-            const size_t o = (size_t)cell * d.cap + rank;
-            d.cidx[o] = g;
-            if (PM == PM_FIX) {
-                const int *X = reinterpret_cast<const int *>(d.x);
-                reinterpret_cast<int4 *>(d.cpos)[o] = make_int4(X[g], X[G + g], X[2 * G + g], g - g0);
-            } else {
-                const double *X = reinterpret_cast<const double *>(d.x);
-                reinterpret_cast<D4 *>(d.cpos)[o] = D4{X[g], X[G + g], X[2 * G + g], (double)(g - g0)};
-            }
-        }
-        __syncwarp();
-        if (lane == 0) {
-            d.ccount[cell] = n;
-            d.cnt[cell] = 0;
-        }
-    }
-}
-
-// List build.  One CTA per home cell: its warps stage the stencil cells
-// (sorted slots; image shift added, fixed point + m 2^30 in wrapping int32
-// arithmetic; entry word = local index | image bits) chunk by chunk, and for
-// each chunk every warp takes one home bead-atom at a time, scans the flat
-// staged array and appends the entries within r_cut + skin to the bead-atom's
-// list, so that a list is in stencil scan order.
-constexpr int kStencilHalf = 2;
-constexpr int kStencil = (2 * kStencilHalf + 1) * (2 * kStencilHalf + 1) * (2 * kStencilHalf + 1);
-
-// shared memory of build_cell (besides the staging chunk)
-struct BuildSmem {
-    int soff[kStencil + 1], scell[kStencil], simg[kStencil][3];
-    int scount[kMaxCellCap];
-};
-
-template <int PM, class R>
-__device__ void build_cell(const Dev &d, R rc2, R rl2, int cell, void *stage_mem, BuildSmem &B)
-{
-    typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
-    constexpr int SH = kStencilHalf, SW = 2 * kStencilHalf + 1;
-    int *soff = B.soff, *scell = B.scell, *scount = B.scount;
-    int (*simg)[3] = B.simg;
-    E4 *stage = reinterpret_cast<E4 *>(stage_mem);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    __syncthreads();  // the previous cell of this CTA is done with the shared memory
-    const int cnt = d.ccount[cell];
-    if (cnt == 0) return;  // uniform over the CTA
-    const DRep RP = d.rep[d.cell_rep[cell]];
-    const int lc = cell - RP.cell0;
-    const int cx = lc % RP.nc[0], cy = (lc / RP.nc[0]) % RP.nc[1], cz = lc / (RP.nc[0] * RP.nc[1]);
-    for (int t = threadIdx.x; t < kStencil; t += blockDim.x) {
-        const int ox = t % SW - SH, oy = (t / SW) % SW - SH, oz = t / (SW * SW) - SH;
-        int ux = cx + ox, uy = cy + oy, uz = cz + oz;
-        const int mx = (int)floor_div(ux, RP.nc[0]), my = (int)floor_div(uy, RP.nc[1]), mz = (int)floor_div(uz, RP.nc[2]);
-        ux -= mx * RP.nc[0]; uy -= my * RP.nc[1]; uz -= mz * RP.nc[2];
-        const int nc = RP.cell0 + ux + RP.nc[0] * (uy + RP.nc[1] * uz);
-        scell[t] = nc;
-        simg[t][0] = mx; simg[t][1] = my; simg[t][2] = mz;
-        soff[t + 1] = d.ccount[nc];
-    }
-    __syncthreads();
-    if (warp == 0) {  // exclusive scan of the stencil counts (<= 128 entries)
-        int v[4], run = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int t = lane * 4 + k;
-            v[k] = (t < kStencil) ? soff[t + 1] : 0;
-            run += v[k];
-        }
-        int incl = run;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        int base = incl - run;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int t = lane * 4 + k;
-            if (t < kStencil) soff[t] = base;
-            base += v[k];
-            if (t == kStencil - 1) soff[kStencil] = base;
-        }
-    }
-    __syncthreads();
-    // the neighbourhood streams through shared memory in chunks of stage_cap
-    // entries (a multiple of 64); each home slot's list grows chunk by chunk
-    const int total = soff[kStencil];
-    const int CH = d.stage_cap;
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) scount[t] = 0;
-    const R sx = (R)RP.fix_scale[0], sy = (R)RP.fix_scale[1], sz = (R)RP.fix_scale[2];
-    const unsigned lt = (1u << lane) - 1u;
-    const int maxnb = d.maxnb;
-    // pass 0 lists the entries within r_cut, pass 1 those of the skin shell, so
-    // that the shell entries close every list (the force loop can skip them)
-    for (int pass = 0; pass < 2; ++pass)
-    for (int c0 = 0; c0 < total; c0 += CH) {
-        const int cn = min(CH, total - c0);
-        const int padded = (cn + 63) & ~63;
-        __syncthreads();  // the previous chunk is scanned
-        // flat staging: every thread first issues all of its (independent) loads,
-        // then shifts by the image and stores
-        constexpr int U = 4;
-        for (int base = 0; base < cn; base += U * (int)blockDim.x) {
-            E4 buf[U];
-            int tcell[U], dst[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int el = base + u * (int)blockDim.x + (int)threadIdx.x;
-                dst[u] = -1;
-                tcell[u] = 0;
-                if (el < cn) {
-                    const int e = c0 + el;
-                    int lo = 0, hi = kStencil - 1;  // stencil cell t with soff[t] <= e < soff[t+1]
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (soff[mid] <= e) lo = mid; else hi = mid - 1;
-                    }
-                    tcell[u] = lo;
-                    dst[u] = el;
-                    buf[u] = reinterpret_cast<const E4 *>(d.cpos)[(size_t)scell[lo] * d.cap + (e - soff[lo])];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (dst[u] < 0) continue;
-                E4 p = buf[u];
-                const int t = tcell[u];
-                const int mx = simg[t][0], my = simg[t][1], mz = simg[t][2];
-                const unsigned ib = ((unsigned)(mx & 3) << 26) | ((unsigned)(my & 3) << 28) | ((unsigned)(mz & 3) << 30);
-                if (PM == PM_FIX) {
-                    p.x = (int)((unsigned)p.x + (unsigned)mx * (1u << kFixBits));
-                    p.y = (int)((unsigned)p.y + (unsigned)my * (1u << kFixBits));
-                    p.z = (int)((unsigned)p.z + (unsigned)mz * (1u << kFixBits));
-                    p.w = (int)((unsigned)p.w | ib);
-                } else {
-                    p.x += mx * RP.box[0];
-                    p.y += my * RP.box[1];
-                    p.z += mz * RP.box[2];
-                    p.w = (double)((unsigned)p.w | ib);
-                }
-                stage[dst[u]] = p;
-            }
-        }
-        // sentinel entries far outside the list radius pad the scan to a multiple of 64
-        for (int e = cn + threadIdx.x; e < padded; e += blockDim.x) {
-            if (PM == PM_FIX) reinterpret_cast<int4 *>(stage)[e] = make_int4(-(1 << kFixBits), -(1 << kFixBits), -(1 << kFixBits), 0);
-            else reinterpret_cast<D4 *>(stage)[e] = D4{-1e30, -1e30, -1e30, 0.0};
-        }
-        __syncthreads();
-        for (int slot = warp; slot < cnt; slot += nwarp) {
-            // the home bead-atom: its own cell, image 0
-            const E4 hp = reinterpret_cast<const E4 *>(d.cpos)[(size_t)cell * d.cap + slot];
-            const int gi = d.cidx[(size_t)cell * d.cap + slot];
-            unsigned *row = d.nbr + (size_t)gi * maxnb;
-            int n = scount[slot];
-            auto test = [&](const E4 &pj) {
-                R dx, dy, dz;
-                if (PM == PM_FIX) {
-                    dx = (R)(int)((unsigned)pj.x - (unsigned)hp.x) * sx;
-                    dy = (R)(int)((unsigned)pj.y - (unsigned)hp.y) * sy;
-                    dz = (R)(int)((unsigned)pj.z - (unsigned)hp.z) * sz;
-                } else {
-                    dx = (R)(pj.x - hp.x);
-                    dy = (R)(pj.y - hp.y);
-                    dz = (R)(pj.z - hp.z);
-                }
-                const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                // the home bead-atom itself (r2 == 0) and the sentinels fail
-                const bool take = pass == 0 ? (r2 < rc2 && r2 > R(0)) : (r2 >= rc2 && r2 < rl2);
-                const unsigned m = __ballot_sync(0xffffffffu, take);
-                if (take) {
-                    const int k = n + __popc(m & lt);
-                    if (k < maxnb) row[k] = (unsigned)pj.w;
-                }
-                n += __popc(m);
-            };
-            for (int e0 = 0; e0 < padded; e0 += 64) {
-                const E4 pa = stage[e0 + lane], pb = stage[e0 + 32 + lane];
-                test(pa);
-                test(pb);
-            }
-            if (lane == 0) scount[slot] = n;
-        }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        const int gi = d.cidx[(size_t)cell * d.cap + t];
-        d.nnb[gi] = min(scount[t], maxnb);
-        if (scount[t] > maxnb) atomicOr(d.err, (unsigned)ERR_NBR_OVERFLOW);
-    }
-}
-
-
-// ---------------------------------------------------------------------------
-// Pair force: Buckingham (energy-shifted) + damped shifted force Coulomb.
-
-__device__ __forceinline__ float my_exp(float x) { return expf(x); }
-__device__ __forceinline__ double my_exp(double x) { return exp(x); }
-__device__ __forceinline__ float my_erfc(float x) { return erfcf(x); }
-__device__ __forceinline__ double my_erfc(double x) { return erfc(x); }
-__device__ __forceinline__ float my_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double my_sqrt(double x) { return sqrt(x); }
-
-// Coefficients of one type pair, staged in shared memory by the step kernel
-// (the pair type varies across the lanes of a warp).
-template <class R> struct alignas(8 * sizeof(R)) PairRow {
-    R inv_rho, A_over_rho, C6, qq, A, C, eshift, pad;
-};
-
-template <class R> __device__ __forceinline__ PairRow<R> pair_row(const PairTabT<R> &T, int t)
-{
-    PairRow<R> p;
-    p.inv_rho = T.inv_rho[t]; p.A_over_rho = T.A_over_rho[t]; p.C6 = T.C6[t]; p.qq = T.qq[t];
-    p.A = T.A[t]; p.C = T.C[t]; p.eshift = T.eshift[t]; p.pad = R(0);
-    return p;
-}
-
-// -dV/dr / r and V of one pair at squared distance r2 < rc^2, FP32 form:
-// branch-free, 1/r from rsqrt + one Newton step, the steep Buckingham
-// exponential by expf (its argument reaches ~50), exp(-alpha^2 r^2) (argument
-// < 3) through exp2, erfc(x) = exp(-x^2) P(u) with the fitted polynomial of the
-// table.  This file is compiled without automatic multiply-add contraction:
-// every fused multiply-add is written out, so that all kernels round alike.
-__device__ __forceinline__ void pair_eval(const PairTabT<float> &T, const PairRow<float> &P2, float r2, float &f_over_r,
-                                          float &e, bool energy = true)
-{
-    float rinv = rsqrtf(r2);
-    rinv = rinv * fmaf(-0.5f * r2, rinv * rinv, 1.5f);
-    const float r = r2 * rinv;
-    const float r2i = rinv * rinv;
-    const float r6i = r2i * r2i * r2i;
-    const float ex = expf(-r * P2.inv_rho);                  // exp(-r/rho); A = 0 rows give 0 below
-    const float gg = exp2f(-T.alpha2_l2e * r2);              // exp(-alpha^2 r^2)
-    const float u = fmaf(T.alpha * r, T.erfc_us, -1.0f);
-    float P = T.erfc_c[11];
-#pragma unroll
-    for (int k = 10; k >= 0; --k) P = fmaf(P, u, T.erfc_c[k]);
-    const float er = gg * P;                                  // erfc(alpha r)
-    const float qq = P2.qq;
-    // A/rho e^{-r/rho} - 6C/r^7 + qq (erfc/r^2 + 2a/sqrt(pi) e^{-a^2 r^2}/r - fshift), times 1/r
-    const float fb = fmaf(P2.A_over_rho, ex, -(P2.C6 * r6i * rinv));
-    const float fc = fmaf(er, r2i, fmaf(T.two_a_sqrtpi * gg, rinv, -T.fshift));
-    f_over_r = fmaf(qq, fc, fb) * rinv;
-    if (energy) {
-        const float ec = fmaf(er, rinv, fmaf(T.fshift, r - T.rc, -T.erfc_rc_over_rc));
-        e = fmaf(qq, ec, fmaf(P2.A, ex, fmaf(-P2.C, r6i, -P2.eshift)));
-    } else {
-        e = 0.0f;
-    }
-}
-
-// FP64 form: library exp / erfc / sqrt (the reference-accuracy path)
-template <class R>
-__device__ __forceinline__ void pair_eval(const PairTabT<R> &T, const PairRow<R> &P2, R r2, R &f_over_r, R &e,
-                                          bool energy = true)
-{
-    const R r = my_sqrt(r2);
-    const R rinv = R(1) / r;
-    R f = 0, en = 0;
-    const R A = P2.A, Cc = P2.C;
-    if (A != R(0)) {
-        const R ex = my_exp(-r * P2.inv_rho);
-        f = P2.A_over_rho * ex;
-        en = A * ex;
-    }
-    if (Cc != R(0)) {
-        const R r2i = rinv * rinv;
-        const R r6i = r2i * r2i * r2i;
-        f = fma(-P2.C6 * r6i, rinv, f);
-        en = fma(-Cc, r6i, en);
-    }
-    en -= P2.eshift;
-    const R qq = P2.qq;
-    if (qq != R(0)) {
-        const R er = my_erfc(T.alpha * r);
-        const R gg = my_exp(-T.alpha2 * r2);
-        f = fma(qq, fma(er * rinv, rinv, fma(T.two_a_sqrtpi * gg, rinv, -T.fshift)), f);
-        if (energy) en = fma(qq, fma(er, rinv, fma(T.fshift, r - T.rc, -T.erfc_rc_over_rc)), en);
-    }
-    f_over_r = f * rinv;
-    e = en;
-}
-
-// Per-system reduction of the CTA partials into the observable record
-// (fixed summation order, FP64).  Executed by one CTA; sh holds one row per warp.
-__device__ void reduce_system(const Dev &d, int s, long long step, int record, double (*sh)[kNQ + 1])
-{
-    const DSys S = d.sys[s];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    double acc[kNQ + 1];
-    for (int q = 0; q <= kNQ; ++q) acc[q] = 0.0;
-    for (int c = S.fcta0 + (int)threadIdx.x; c < S.fcta1; c += blockDim.x)
-        for (int q = 0; q < kNQ; ++q) acc[q] += d.part[(size_t)c * kNQ + q];
-    for (int c = S.icta0 + (int)threadIdx.x; c < S.icta1; c += blockDim.x) acc[kNQ] += d.ipart[(size_t)c * kNQ + Q_SPRING];
-    for (int q = 0; q <= kNQ; ++q) acc[q] = warp_sum(acc[q]);
-    if (lane == 0)
-        for (int q = 0; q <= kNQ; ++q) sh[warp][q] = acc[q];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double tot[kNQ + 1];
-        for (int q = 0; q <= kNQ; ++q) {
-            tot[q] = 0.0;
-            for (int w = 0; w < nw; ++w) tot[q] += sh[w][q];
-        }
-        const double invP = S.invP;
-        double rec[QTB_NREC];
-        for (int q = 0; q < QTB_NREC; ++q) rec[q] = 0.0;
-        const double K = tot[Q_K], V = tot[Q_V] * invP, sp = tot[kNQ];
-        rec[0] = (double)step;
-        rec[1] = K;
-        rec[2] = V;
-        rec[3] = sp;
-        rec[4] = K - sp + V;
-        const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};  // xx xy xz / yx yy yz / zx zy zz
-        for (int a = 0; a < 9; ++a) rec[5 + a] = tot[Q_VIR + map[a]] * invP;
-        for (int c = 0; c < 3; ++c) rec[14 + c] = tot[Q_MOM + c];
-        rec[17] = tot[Q_X2] * invP;
-        if (!isfinite(K) || !isfinite(V)) atomicOr(d.err, (unsigned)ERR_NONFINITE);
-        for (int q = 0; q < QTB_NREC; ++q) d.latest[(size_t)s * QTB_NREC + q] = rec[q];
-        if (record >= 0 && step % d.obs_stride == 0) {
-            long long r = step / d.obs_stride - 1;
-            int slot = (int)(r % d.max_records);
-            for (int q = 0; q < QTB_NREC; ++q) d.series[((size_t)slot * d.nsys + s) * QTB_NREC + q] = rec[q];
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Pair force from the neighbour lists: kListLanes lanes per home bead-atom
-// (two bead-atoms per warp), each lane strides through the list with two
-// independent entries per iteration and the next iteration's entries already
-// requested; every entry is evaluated and masked by r < r_cut (no divergent
-// branch).  Epilogue on the first three lanes of a group (one Cartesian
-// component each): force (times 1/P, Eq. 4), the closing B(dt/2) kick, the
-// observables of recorded steps and, with ADV (one-bead systems), the first
-// half of the next step: B(dt/2), A(dt/2) O(dt) A(dt/2) with the next step's
-// coloured noise, written to x and pos[cur ^ 1], and the rebuild test for the
-// next step.  Recorded steps: the last CTA of a system reduces its partials.
-
-template <int PM, class R, int ADV, int REC>
-__device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, const PairRow<R> *ptab, int kick,
-                                           int j, int cur, int u, double (*red)[kNQ], double (*rsh)[kNQ + 1],
-                                           int &s_last)
-{
-    typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
-    typedef typename std::conditional<sizeof(R) == 4, FF, DD>::type ACC;
-    typedef typename PosT<PM, R>::S PS;
-    constexpr int LPA = kListLanes, APW = 32 / kListLanes;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int sub = lane & (LPA - 1), grp = lane / LPA;
-    const DRep RP = d.rep[d.lcta_rep[u]];
-    const int i = (u - RP.fcta0) * kListAtoms + warp * APW + grp;
-    const bool act = i < RP.N;
-    const long long step = d.clock[0] * kBlockSteps + j + 1;
-    const bool rec = REC && ((kick == 0) || (step % d.obs_stride == 0));
-    const DSys &S = d.sys[RP.sys];
-    const size_t G = (size_t)d.G;
-    const long long gi = RP.g0 + (act ? i : 0);
-    const E4 *Pc = reinterpret_cast<const E4 *>(d.pos[cur]);
-    const E4 *Pr = Pc + RP.g0;
-    const E4 hp = Pc[gi];
-    int ti;
-    if (PM == PM_FIX) ti = hp.w; else ti = (int)hp.w;
-    const int n = act ? min(d.nnb[gi], d.maxnb) : 0;
-    const unsigned *row = d.nbr + (size_t)gi * d.maxnb;
-    const R sx = (R)RP.fix_scale[0], sy = (R)RP.fix_scale[1], sz = (R)RP.fix_scale[2];
-    const R rc2 = T.rc2;
-    ACC fx{}, fy{}, fz{};
-    R en = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
-    struct Geo {
-        R dx, dy, dz, r2;
-        int tj;
-    };
-    // r_j + image - r_i of one list entry
-    auto geo = [&](unsigned e) {
-        const E4 pj = Pr[e & kNbIdx];
-        Geo g;
-        if (PM == PM_FIX) {
-            // exact in wrapping 32-bit arithmetic
-            g.dx = (R)(int)((unsigned)pj.x + ((e << 4) & 0xC0000000u) - (unsigned)hp.x) * sx;
-            g.dy = (R)(int)((unsigned)pj.y + ((e << 2) & 0xC0000000u) - (unsigned)hp.y) * sy;
-            g.dz = (R)(int)((unsigned)pj.z + (e & 0xC0000000u) - (unsigned)hp.z) * sz;
-            g.tj = pj.w;
-        } else {
-            // image from m mod 4: code 2 is +2 or -2, told apart by the sign of
-            // the raw difference (the box exceeds r_cut/2 + skin)
-            const double pd[3] = {(double)pj.x - (double)hp.x, (double)pj.y - (double)hp.y, (double)pj.z - (double)hp.z};
-            R dv[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const int code = (int)((e >> (26 + 2 * c)) & 3u);
-                const int m = (code == 3) ? -1 : (code == 2) ? (pd[c] > 0.0 ? -2 : 2) : code;
-                dv[c] = (R)(pd[c] + m * RP.box[c]);
-            }
-            g.dx = dv[0]; g.dy = dv[1]; g.dz = dv[2];
-            g.tj = (int)pj.w;
-        }
-        g.r2 = fma(g.dx, g.dx, fma(g.dy, g.dy, g.dz * g.dz));
-        return g;
-    };
-    // force (and on recorded steps energy and virial) of one entry, masked by `in`
-    auto force = [&](const Geo &g, bool in) {
-        R fo, ee;
-        pair_eval(T, ptab[ti * kMaxTypes + g.tj], g.r2, fo, ee, REC && rec);
-        fo = in ? fo : R(0);
-        // stored displacement is r_j - r_i: the force on i is -fo (r_j - r_i)
-        fx.add(-fo * g.dx); fy.add(-fo * g.dy); fz.add(-fo * g.dz);
-        if (REC && rec) {
-            en += in ? ee : R(0);
-            w0 = fma(fo * g.dx, g.dx, w0); w1 = fma(fo * g.dy, g.dy, w1); w2 = fma(fo * g.dz, g.dz, w2);
-            w3 = fma(fo * g.dx, g.dy, w3); w4 = fma(fo * g.dx, g.dz, w4); w5 = fma(fo * g.dy, g.dz, w5);
-        }
-    };
-    {
-        // entries k + q LPA (q < NE) of this lane; the next NE are requested before
-        // the current ones are evaluated (slots past the end read entry 0, masked).
-        // The lists end with the skin-shell entries: a round in which no lane of
-        // the warp has an entry within r_cut skips the pair terms (they would add
-        // exact zeros).  The trip count is the warp's longest list, so the vote
-        // is uniform.
-        constexpr int NE = 4;
-        int nmax = n;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-        unsigned e[NE];
-#pragma unroll
-        for (int q = 0; q < NE; ++q) e[q] = (sub + q * LPA < n) ? row[sub + q * LPA] : 0u;
-        for (int k0 = 0; k0 < nmax; k0 += NE * LPA) {
-            const int k = k0 + sub, kn = k + NE * LPA;
-            unsigned e2[NE];
-#pragma unroll
-            for (int q = 0; q < NE; ++q) e2[q] = (kn + q * LPA < n) ? row[kn + q * LPA] : 0u;
-            Geo g[NE];
-            bool in[NE], any = false;
-#pragma unroll
-            for (int q = 0; q < NE; ++q) {
-                g[q] = geo(e[q]);
-                in[q] = (k + q * LPA < n) && (g[q].r2 < rc2);
-                any |= in[q];
-            }
-            if (__any_sync(0xffffffffu, any)) {
-#pragma unroll
-                for (int q = 0; q < NE; ++q) force(g[q], in[q]);
-            }
-#pragma unroll
-            for (int q = 0; q < NE; ++q) e[q] = e2[q];
-        }
-    }
-    fx.template group_reduce<LPA>(); fy.template group_reduce<LPA>(); fz.template group_reduce<LPA>();
-    double acc[kNQ];
-#pragma unroll
-    for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
-    if (REC && rec) {
-        en = group_sum<LPA>(en);
-        w0 = group_sum<LPA>(w0); w1 = group_sum<LPA>(w1); w2 = group_sum<LPA>(w2);
-        w3 = group_sum<LPA>(w3); w4 = group_sum<LPA>(w4); w5 = group_sum<LPA>(w5);
-        if (act && sub == 0) {
-            acc[Q_V] = 0.5 * (double)en;
-            acc[Q_VIR + 0] = 0.5 * (double)w0; acc[Q_VIR + 1] = 0.5 * (double)w1;
-            acc[Q_VIR + 2] = 0.5 * (double)w2; acc[Q_VIR + 3] = 0.5 * (double)w3;
-            acc[Q_VIR + 4] = 0.5 * (double)w4; acc[Q_VIR + 5] = 0.5 * (double)w5;
-        }
-    }
-    R dd = 0;  // squared displacement component since the last rebuild (ADV)
-    if (act && sub < 3) {
-        const int c = sub;
-        const R invP = sizeof(R) == 4 ? (R)S.invP_f : (R)S.invP;
-        const R fc = (R)(c == 0 ? fx.value() : c == 1 ? fy.value() : fz.value()) * invP;
-        R *Fo = reinterpret_cast<R *>(d.f);
-        R *V = reinterpret_cast<R *>(d.v);
-        const size_t o = (size_t)c * G + gi;
-        Fo[o] = fc;
-        const R hdtm = T.hdt_m[ti];
-        R v = V[o];
-        if (kick) v = fma(hdtm, fc, v);
-        if (REC && rec) {
-            acc[Q_K] += 0.5 * T.mass_mvv[ti] * (double)v * (double)v;
-            acc[Q_MOM + c] += T.mass[ti] * (double)v;
-        }
-        if (ADV) {
-            // next step, one bead (the mode is the bead): B(dt/2), A(dt/2) O(dt) A(dt/2)
-            const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
-            const R cs = rot[0], sw = rot[1], ws = rot[2];
-            const R sig = reinterpret_cast<const R *>(d.osig)[RP.sys * kMaxTypes + ti];
-            const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
-            const R eta = reinterpret_cast<const R *>(d.eta)[(size_t)(j + 1) * d.Dtot + S.dof0 + (size_t)c * S.N + i];
-            R pk = fma(hdtm, fc, v);
-            R qq = 0;
-            mode_aoa(qq, pk, cs, sw, ws, c1, sig * eta);
-            v = pk;
-            PS *X = reinterpret_cast<PS *>(d.x);
-            const float fsc = S.fix_scale[c];
-            const PS xn = PosT<PM, R>::add(X[o], qq, S.box[c], fsc, S.fix_inv[c]);
-            X[o] = xn;
-            reinterpret_cast<PS *>(d.pos[cur ^ 1])[4 * (size_t)gi + c] = xn;
-            const R dc = PosT<PM, R>::diff(xn, reinterpret_cast<const PS *>(d.xref)[o], fsc);
-            dd = dc * dc;
-        }
-        if (kick || ADV) V[o] = v;
-    }
-    if (ADV) {
-        const int b0 = grp * LPA;
-        const R tot = __shfl_sync(0xffffffffu, dd, b0) + __shfl_sync(0xffffffffu, dd, b0 + 1) +
-                      __shfl_sync(0xffffffffu, dd, b0 + 2);
-        const R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
-        if (__any_sync(0xffffffffu, act && sub == 0 && tot > lim) && lane == 0) atomicOr(&d.flag[cur ^ 1], 1u);
-    }
-    if (REC && rec) {
-#pragma unroll
-        for (int q = 0; q < kNQ; ++q) acc[q] = warp_sum(acc[q]);
-        cta_store_partials(acc, red, d.part + (size_t)u * kNQ);
-        // the CTA with the system's last unit reduces (partials made visible first)
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const unsigned prev = atomicAdd(&d.done[RP.sys], 1u);
-            s_last = (prev == (unsigned)(S.fcta1 - S.fcta0 - 1)) ? 1 : 0;
-        }
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            reduce_system(d, RP.sys, step, kick ? 1 : -1, rsh);
-            if (threadIdx.x == 0) d.done[RP.sys] = 0u;
-        }
-    }
-}
-
-// One step of the pair-potential systems, a cooperative launch whose CTAs
-// (at most one wave) loop over the force units (kListAtoms bead-atoms each).
-// When the producer of this step's positions requested a rebuild (flag[cur]),
-// the grid first bins, sorts and builds the lists, phases separated by grid
-// barriers.  Dynamic shared memory: the staging chunk of the list build
-// (stage_cap entries; also the sort keys).
-template <int PM, class R, int ADV, int REC>
-__global__ void __launch_bounds__(32 * kListWarps, sizeof(R) == 4 ? 8 : 4) k_step(Dev d, PairTabT<R> T, int kick, int j, int cur)
-{
-    extern __shared__ __align__(32) unsigned char fsm[];
-    __shared__ BuildSmem B;
-    __shared__ PairRow<R> ptab[kMaxTypes * kMaxTypes];
-    if (threadIdx.x < kMaxTypes * kMaxTypes) ptab[threadIdx.x] = pair_row(T, threadIdx.x);
-    __syncthreads();
-    __shared__ double red[kListWarps][kNQ];
-    __shared__ double rsh[kListWarps][kNQ + 1];
-    __shared__ int s_last;
-    // read by every thread before the flag can be cleared (after the first barrier)
-    const bool rebuild = *(volatile const unsigned *)&d.flag[cur] != 0u;
-    if (rebuild) {
-        bin_phase<PM>(d, cur);
-        grid_barrier(d);
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            d.flag[cur] = 0u;  // this step's rebuild request is consumed
-            atomicAdd(d.nrebuild, 1ull);
-        }
-        sort_phase<PM>(d, reinterpret_cast<int *>(fsm));
-        grid_barrier(d);
-        for (int cell = blockIdx.x; cell < d.ncells; cell += gridDim.x) build_cell<PM, R>(d, T.rc2, T.rl2, cell, fsm, B);
-        grid_barrier(d);
-    }
-    for (int u = blockIdx.x; u < d.nunits; u += gridDim.x)
-        force_unit<PM, R, ADV, REC>(d, T, ptab, kick, j, cur, u, red, rsh, s_last);
-}
 
 // External separable potentials, one thread per bead-atom.  grid = (gx, nsys)
 template <class R>
@@ -1305,74 +138,20 @@ void launch_integrate(const Dev &d, const MdLaunch &m, int j, int cur, cudaStrea
     }
 }
 
-template <int PM, class R, int ADV, int REC>
-static cudaError_t step_prepare_one(size_t smem, int nsm, int &grid)
-{
-    cudaError_t e = cudaFuncSetAttribute(k_step<PM, R, ADV, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<PM, R, ADV, REC>, 32 * kListWarps, smem);
-    grid = per_sm * nsm;
-    return e;
-}
-
 cudaError_t step_prepare(MdLaunch &m, int stage_entries)
 {
-    int dev = 0, nsm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    m.step_smem = (size_t)stage_entries * (m.mixed ? sizeof(int4) : sizeof(D4));
-    if (m.mixed) {
-        if ((e = step_prepare_one<PM_FIX, float, 0, 0>(m.step_smem, nsm, m.step_grid[0])) != cudaSuccess) return e;
-        if ((e = step_prepare_one<PM_FIX, float, 0, 1>(m.step_smem, nsm, m.step_grid[1])) != cudaSuccess) return e;
-        if ((e = step_prepare_one<PM_FIX, float, 1, 0>(m.step_smem, nsm, m.step_grid[2])) != cudaSuccess) return e;
-        e = step_prepare_one<PM_FIX, float, 1, 1>(m.step_smem, nsm, m.step_grid[3]);
-    } else {
-        if ((e = step_prepare_one<PM_BOX64, double, 0, 0>(m.step_smem, nsm, m.step_grid[0])) != cudaSuccess) return e;
-        if ((e = step_prepare_one<PM_BOX64, double, 0, 1>(m.step_smem, nsm, m.step_grid[1])) != cudaSuccess) return e;
-        if ((e = step_prepare_one<PM_BOX64, double, 1, 0>(m.step_smem, nsm, m.step_grid[2])) != cudaSuccess) return e;
-        e = step_prepare_one<PM_BOX64, double, 1, 1>(m.step_smem, nsm, m.step_grid[3]);
-    }
-    return e;
-}
-
-// cooperative launch: all CTAs resident at once (the grid barriers need it)
-template <int PM, class R, int ADV, int REC>
-static cudaError_t step_launch(const Dev &d, const MdLaunch &m, const PairTabT<R> &T, int kick, int j, int cur,
-                               cudaStream_t st)
-{
-    const int grid = std::min(d.nunits, m.step_grid[ADV * 2 + REC]);
-    if (grid < 1) return cudaErrorInvalidConfiguration;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(32 * kListWarps);
-    cfg.dynamicSmemBytes = m.step_smem;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeCooperative;
-    at[0].val.cooperative = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_step<PM, R, ADV, REC>, d, T, kick, j, cur);
-}
-
-template <int PM, class R>
-static cudaError_t step_any(const Dev &d, const MdLaunch &m, const PairTabT<R> &T, int kick, int j, int cur, int adv,
-                            int rec, cudaStream_t st)
-{
-    if (adv && rec) return step_launch<PM, R, 1, 1>(d, m, T, kick, j, cur, st);
-    if (adv) return step_launch<PM, R, 1, 0>(d, m, T, kick, j, cur, st);
-    if (rec) return step_launch<PM, R, 0, 1>(d, m, T, kick, j, cur, st);
-    return step_launch<PM, R, 0, 0>(d, m, T, kick, j, cur, st);
+    if (m.lanes == 8) return step_prepare_l8(m, stage_entries);
+    if (m.lanes == 32) return step_prepare_l32(m, stage_entries);
+    return step_prepare_l16(m, stage_entries);
 }
 
 cudaError_t launch_force(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,
                          int kick, int j, int cur, int adv, int rec, cudaStream_t st)
 {
     if (m.pair) {
-        if (m.mixed) return step_any<PM_FIX, float>(d, m, Tf, kick, j, cur, adv, rec, st);
-        return step_any<PM_BOX64, double>(d, m, Td, kick, j, cur, adv, rec, st);
+        if (m.lanes == 8) return step_force_l8(d, m, Tf, Td, kick, j, cur, adv, rec, st);
+        if (m.lanes == 32) return step_force_l32(d, m, Tf, Td, kick, j, cur, adv, rec, st);
+        return step_force_l16(d, m, Tf, Td, kick, j, cur, adv, rec, st);
     }
     dim3 g((unsigned)m.n_ecta, (unsigned)d.nsys);
     if (m.mixed) k_force_ext<float><<<g, 128, 0, st>>>(d, Tf, kick);

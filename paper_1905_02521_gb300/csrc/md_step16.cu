@@ -1,0 +1,16 @@
+// md_step16.cu -- the cooperative step kernel with 16 lanes per bead-atom
+// (instantiated in a translation unit of its own so that the variants compile in
+// parallel).
+#include "md_kernels.cuh"
+
+namespace qtb {
+
+cudaError_t step_prepare_l16(MdLaunch &m, int stage_entries) { return step_prepare_lanes<16>(m, stage_entries); }
+
+cudaError_t step_force_l16(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,
+                          int kick, int j, int cur, int adv, int rec, cudaStream_t st)
+{
+    return step_force_lanes<16>(d, m, Tf, Td, kick, j, cur, adv, rec, st);
+}
+
+}  // namespace qtb

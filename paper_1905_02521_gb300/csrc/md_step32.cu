@@ -1,0 +1,16 @@
+// md_step32.cu -- the cooperative step kernel with 32 lanes per bead-atom
+// (instantiated in a translation unit of its own so that the variants compile in
+// parallel).
+#include "md_kernels.cuh"
+
+namespace qtb {
+
+cudaError_t step_prepare_l32(MdLaunch &m, int stage_entries) { return step_prepare_lanes<32>(m, stage_entries); }
+
+cudaError_t step_force_l32(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,
+                          int kick, int j, int cur, int adv, int rec, cudaStream_t st)
+{
+    return step_force_lanes<32>(d, m, Tf, Td, kick, j, cur, adv, rec, st);
+}
+
+}  // namespace qtb

@@ -42,8 +42,9 @@ enum { ERR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_SOLVE = 4, ERR_TIMEOUT_TC = 8, E
 constexpr unsigned kNbIdx = (1u << 26) - 1u;
 constexpr int kMaxCellCap = 512;        // slots per cell of the cell list
 constexpr int kListWarps = 4;        // warps per CTA of the list force kernel
-constexpr int kListLanes = 16;       // lanes per home bead-atom
-constexpr int kListAtoms = kListWarps * 32 / kListLanes;  // home bead-atoms per CTA
+// lanes per home bead-atom of the step kernel: 8, 16 (default) or 32; a force
+// unit (one CTA's share of work) holds list_atoms(lanes) bead-atoms
+__host__ __device__ constexpr int list_atoms(int lanes) { return kListWarps * 32 / lanes; }
 
 struct DSys {
     int N, P;          // atoms, beads
@@ -74,7 +75,7 @@ struct DRep {          // one replica (system, bead) of a pair-potential system
     int nc[3];         // cells per edge
     int cell0;         // first cell
     int cta0;          // first binning CTA
-    int fcta0;         // first CTA of the list force kernel (kListAtoms bead-atoms each)
+    int fcta0;         // first force unit of the step kernel
     double box[3];
     float fix_scale[3];  // box / 2^30
 };
@@ -116,7 +117,7 @@ struct Dev {
     const DSys *sys;
     const DRep *rep;
     const int *cell_rep;  // [ncells]
-    const int *lcta_rep;  // [nunits] replica of each force unit (kListAtoms bead-atoms)
+    const int *lcta_rep;  // [nunits] replica of each force unit
     int nunits;           // force units
     const int *icta_sys;  // [integrator CTAs] system of each CTA
     const int *ext_cta_sys;

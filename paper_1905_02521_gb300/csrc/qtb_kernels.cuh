@@ -46,14 +46,25 @@ struct MdLaunch {
     int fused;            // all systems one-bead with a pair potential: the step kernel
                           // carries out the first half of the next step
     int nm_big;           // ring-polymer integrator with 32 atoms per CTA (large contexts)
+    int lanes;            // lanes per bead-atom of the step kernel (8, 16, 32)
     int step_grid[4];     // resident CTAs of the step kernel, by (adv, rec)
     size_t step_smem;     // its dynamic shared memory (list build staging chunk)
 };
 constexpr int kIntAtomsPerWarp = 10;                   // integrator: lanes 3a + c, a < 10
 constexpr int kIntAtomsPerCta = 4 * kIntAtomsPerWarp;  // 128 threads
 constexpr int kStencilCells = 125;                     // 5^3 stencil of (r_cut + skin)/2 cells
-// attributes and resident grid sizes of the cooperative step kernel
+// attributes and resident grid sizes of the cooperative step kernel (m.lanes)
 cudaError_t step_prepare(MdLaunch &m, int stage_entries);
+// per lane count, one translation unit each (md_step8.cu, md_step16.cu, md_step32.cu)
+cudaError_t step_prepare_l8(MdLaunch &m, int stage_entries);
+cudaError_t step_prepare_l16(MdLaunch &m, int stage_entries);
+cudaError_t step_prepare_l32(MdLaunch &m, int stage_entries);
+cudaError_t step_force_l8(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,
+                          int kick, int j, int cur, int adv, int rec, cudaStream_t st);
+cudaError_t step_force_l16(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,
+                           int kick, int j, int cur, int adv, int rec, cudaStream_t st);
+cudaError_t step_force_l32(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,
+                           int kick, int j, int cur, int adv, int rec, cudaStream_t st);
 // positions of step s: the integrator writes pos[cur], cur = s & 1, and
 // requests a list rebuild in flag[cur] when some bead-atom moved skin/2
 void launch_integrate(const Dev &d, const MdLaunch &m, int j, int cur, cudaStream_t st);

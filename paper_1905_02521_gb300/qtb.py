@@ -49,7 +49,8 @@ class qtb_params(C.Structure):
                 ("ext_V0", C.c_double), ("ext_a", C.c_double), ("dt", C.c_double), ("precision", C.c_int),
                 ("filter_prec", C.c_int), ("seed", C.c_ulonglong), ("obs_stride", C.c_int),
                 ("max_records", C.c_int), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
-                ("alloc_user", C.c_void_p), ("skin", C.c_double), ("nm_layout", C.c_int)]
+                ("alloc_user", C.c_void_p), ("skin", C.c_double), ("nm_layout", C.c_int),
+                ("list_lanes", C.c_int)]
 
 
 _lib = None
@@ -82,6 +83,7 @@ def lib():
             "qtb_get_noise": ([vp, i, vp, C.POINTER(ll)], i),
             "qtb_get_step": ([vp, C.POINTER(ll)], i),
             "qtb_list_rebuilds": ([vp, C.POINTER(ll)], i),
+            "qtb_autotune": ([vp, i, vp, vp, i, i, d, i, vp, vp], i),
             "qtb_set_profiling": ([vp, i], i),
             "qtb_kernel_times": ([vp, vp, vp, i], i),
             "qtb_kappa_solve": ([i, i, d, d, vp], i),
@@ -149,10 +151,9 @@ def torch_stream():
 
 # --- C-named entry points ---------------------------------------------------------
 
-def qtb_init(systems, params, stream=None):
-    """systems: list of dicts (pos [P,N,3], vel, types, box, T, gamma); params: dict.
-
-    Returns an opaque context handle (an integer)."""
+def _c_args(systems, params, stream):
+    """C structures (systems array, params) for qtb_init / qtb_autotune and the
+    host arrays they borrow (keep alive for the call)."""
     keep = []
     arr = (qtb_system * len(systems))()
     for k, s in enumerate(systems):
@@ -191,14 +192,41 @@ def qtb_init(systems, params, stream=None):
     p.max_records = int(params.get("max_records", 4096))
     p.skin = float(params.get("skin", 0.0))
     p.nm_layout = int(params.get("nm_layout", 0))
+    p.list_lanes = int(params.get("list_lanes", 0))
     if params.get("torch_alloc", True):
         a, f = _torch_allocator()
         p.dev_alloc, p.dev_free = a, f
     if stream is None and params.get("torch_stream", True):
         stream = torch_stream()
+    return arr, p, stream, keep
+
+
+def qtb_init(systems, params, stream=None):
+    """systems: list of dicts (pos [P,N,3], vel, types, box, T, gamma); params: dict.
+
+    Returns an opaque context handle (an integer)."""
+    arr, p, stream, keep = _c_args(systems, params, stream)
     h = C.c_void_p()
     _check(lib().qtb_init(C.byref(h), C.cast(arr, C.c_void_p), len(systems), C.addressof(p), stream))
     return h.value
+
+
+class qtb_tuning(C.Structure):
+    _fields_ = [("skin", C.c_double), ("nm_layout", C.c_int), ("list_lanes", C.c_int), ("ms_per_step", C.c_double),
+                ("default_ms_per_step", C.c_double), ("n_tried", C.c_int)]
+
+
+def qtb_autotune(systems, params, mode=0, n_taps=1, omega_max=0.0, n_blocks=2, stream=None):
+    """Times the candidate skins, lane counts and integrator layouts on these
+    systems (see qtb.h) and returns (params with the fastest choice, tuning dict)."""
+    arr, p, stream, keep = _c_args(systems, params, stream)
+    best = qtb_params()
+    res = qtb_tuning()
+    _check(lib().qtb_autotune(C.cast(arr, C.c_void_p), len(systems), C.addressof(p), stream, int(mode), int(n_taps),
+                              float(omega_max), int(n_blocks), C.addressof(best), C.byref(res)))
+    tuned = dict(params, skin=best.skin, nm_layout=best.nm_layout, list_lanes=best.list_lanes)
+    info = {k: getattr(res, k) for k, _ in qtb_tuning._fields_}
+    return tuned, info
 
 
 def qtb_set_filter(ctx, sys, mode, n_taps=1, omega_max=0.0):

@@ -129,3 +129,44 @@ def test_integrator_layouts_are_bit_identical(qtb, precision):
         finally:
             qtb.qtb_destroy(ctx)
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lane_counts_give_the_same_forces(qtb, oracle, precision):
+    # 8, 16 or 32 lanes per bead-atom: the same terms summed in another order
+    s, pot = W.mgo_system(3, 300.0, sigma=0.05, seed=12)
+    N = len(s["types"])
+    for lanes in (8, 16, 32):
+        ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=precision, seed=3, list_lanes=lanes)
+        try:
+            qtb.qtb_step_n(ctx, 40)
+            x, _ = qtb.qtb_get_state(ctx, 0, 1, N)
+            f = qtb.qtb_get_forces(ctx, 0, 1, N)[0]
+            fo, _, _ = oracle.pair_forces(x[0], s["types"], s["box"], pot)
+            if precision == 0:
+                assert rel_inf(f, fo) < 1e-12
+            else:
+                assert rel_l2(f, fo) < F32_L2 and rel_inf(f, fo) < F32_INF
+        finally:
+            qtb.qtb_destroy(ctx)
+
+
+def test_autotune_picks_a_valid_configuration(qtb, oracle):
+    from helpers import gpu_params
+    s, pot = W.mgo_system(4, 300.0)
+    params = gpu_params(pot, 1.0, precision=1, filter_prec=1, seed=5)
+    tuned, info = qtb.qtb_autotune([s], params, qtb.NOISE_QTB, 513, 0.3, n_blocks=1)
+    print("autotune:", info)
+    assert info["n_tried"] == 1 + 4 * 3
+    assert 0 < info["ms_per_step"] <= info["default_ms_per_step"]
+    assert tuned["list_lanes"] in (0, 8, 16, 32) and tuned["skin"] in (0.0, 0.5, 0.8, 1.2, 1.6)
+    N = len(s["types"])
+    ctx = qtb.qtb_init([s], tuned)
+    try:
+        qtb.qtb_step_n(ctx, 300)
+        x, _ = qtb.qtb_get_state(ctx, 0, 1, N)
+        f = qtb.qtb_get_forces(ctx, 0, 1, N)[0]
+        fo, _, _ = oracle.pair_forces(x[0], s["types"], s["box"], pot)
+        assert rel_l2(f, fo) < F32_L2 and rel_inf(f, fo) < F32_INF
+    finally:
+        qtb.qtb_destroy(ctx)
