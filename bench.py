@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--workload", default="mgo8000", choices=WORKLOADS)
     ap.add_argument("--ncell", type=int, default=10, help="cells per side of the mgo8000 workload")
     ap.add_argument("--skin", type=float, default=0.0, help="neighbour-list skin, A (0: library default)")
+    ap.add_argument("--generator", default="filter", choices=["filter", "fourier"],
+                    help="coloured noise: time-domain filter, or Fourier segments (Eq. 9)")
+    ap.add_argument("--segment-blocks", type=int, default=8, help="256-step blocks per Fourier segment")
     ap.add_argument("--autotune", action="store_true",
                     help="choose skin, lanes per bead-atom and integrator layout with qtb_autotune first (untimed)")
     ap.add_argument("--filter", default="auto", choices=["auto", "fp32", "bf16"])
@@ -234,6 +237,8 @@ def run_ours(args):
         ctx = qtb.qtb_init(systems, params, stream=stream.cuda_stream)
     if setup is not None:
         qtb.qtb_set_filter(ctx, -1, *setup)
+    if args.generator == "fourier":
+        qtb.qtb_set_generator(ctx, qtb.GEN_FOURIER, args.segment_blocks)
     qtb.qtb_set_profiling(ctx, not args.direct)
     flush = l2_flush_buffer(torch)
 
@@ -318,6 +323,8 @@ def run_ours(args):
                    "skin_A": params["skin"] if params["skin"] else "default",
                    "list_lanes": params.get("list_lanes") or "default (16)",
                    "autotune": tuning,
+                   "noise_generator": args.generator if args.generator == "filter" else
+                   f"fourier segments of {256 * args.segment_blocks} steps (Eq. 9)",
                    "launch": "direct (2 x 128-step calls per block)" if args.direct else "CUDA graph per 256-step block",
                    "l2": "256 MB buffer written between timed steps (flush)"},
         "roofline": {"bound": "alu", "kernel": "k_step", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

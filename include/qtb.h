@@ -146,6 +146,22 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
  * the filter in force at each step. */
 int qtb_set_filter(qtb_ctx *c, int sys, int mode, int n_taps, double omega_max);
 
+/* Generator of the coloured noise, for every system of the context.
+ *   QTB_GEN_FILTER  (default) the zero-phase time-domain filter of qtb_set_filter:
+ *                   stationary noise, no segment boundaries.
+ *   QTB_GEN_FOURIER the paper's own method (Eq. 9, Sec. 2.2): segments of
+ *                   n = 256 segment_blocks steps (segment_blocks in {1, 2, 4, 8}),
+ *                   each drawn in Fourier space on w_j = 2 pi j/(n dt) from the
+ *                   n normals of the white stream over the segment and brought to
+ *                   the time domain by an inverse FFT; discrete spectral density
+ *                   S = theta W (kappa_P W for QTB-PIMD, k_B T for WHITE), the
+ *                   mode and cutoff of qtb_set_filter (n_taps unused).  The noise
+ *                   is periodic within a segment and uncorrelated across segments.
+ * The learned kappa_P mode is not available with QTB_GEN_FOURIER (QTB_ERR_ARG).
+ * Takes effect from the next step. */
+typedef enum { QTB_GEN_FILTER = 0, QTB_GEN_FOURIER = 1 } qtb_generator;
+int qtb_set_generator(qtb_ctx *c, int generator, int segment_blocks);
+
 /* Advance every system by n_steps BAOAB steps (asynchronous).  Whole 256-step
  * noise blocks run as one CUDA-graph launch. */
 int qtb_step_n(qtb_ctx *c, long long n_steps);

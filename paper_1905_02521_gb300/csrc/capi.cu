@@ -78,6 +78,10 @@ struct qtb_ctx {
     long long ring_hi = LLONG_MIN; // highest white block in the ring
     long long ring_lo = LLONG_MIN; // lowest white block in the ring
     long long eta_blk = LLONG_MIN; // block whose coloured noise is in eta
+    // Fourier-segment generator (Eq. 9): segments of seg_blocks blocks
+    int gen = QTB_GEN_FILTER, seg_blocks = 1;
+    long long eta_seg = LLONG_MIN; // segment in eta
+    void *d_sq = nullptr, *d_tw = nullptr;  // sqrt(S_j/n) per system, twiddles
     int Kmax = 0;
     int max_dofp = 0, max_repN = 0;
     size_t ring_bytes = 0;
@@ -437,6 +441,17 @@ void ensure_ring(qtb_ctx *c, long long lo, long long hi)
 // make eta hold block b (ring then holds blocks b-Kb .. b+Kb)
 void ensure_eta(qtb_ctx *c, long long b)
 {
+    if (c->gen == QTB_GEN_FOURIER) {
+        const long long seg = floor_div(b, c->seg_blocks);
+        set_clock(c, b);
+        if (c->eta_seg != seg) {
+            launch_fourier(c->d, c->mixed ? 0 : 1, c->max_dofp, c->d.nsys, c->d_sq, c->d_tw,
+                           kBlockSteps * c->seg_blocks, 1, c->st);
+            c->eta_seg = seg;
+        }
+        c->eta_blk = b;
+        return;
+    }
     if (c->eta_blk == b) return;
     ensure_ring(c, b - c->d.Kb, b + c->d.Kb);
     set_clock(c, b);
@@ -524,8 +539,15 @@ int capture_block(qtb_ctx *c, cudaGraph_t *g)
     c->capturing = true;
     c->ev_used = 0;
     int rc;
-    { ProfMark m(c, KC_WHITE); gen_white(c, LLONG_MIN); }  // block clock + Kb
-    { ProfMark m(c, KC_FILTER); filter_block(c); }
+    if (c->gen == QTB_GEN_FOURIER) {
+        // a new segment at the first block of each segment (the kernel tests the block clock)
+        ProfMark m(c, KC_FILTER);
+        launch_fourier(c->d, c->mixed ? 0 : 1, c->max_dofp, c->d.nsys, c->d_sq, c->d_tw,
+                       kBlockSteps * c->seg_blocks, 0, c->st);
+    } else {
+        { ProfMark m(c, KC_WHITE); gen_white(c, LLONG_MIN); }  // block clock + Kb
+        { ProfMark m(c, KC_FILTER); filter_block(c); }
+    }
     rc = run_steps(c, 0, kBlockSteps, true);
     launch_tick(c->d, c->st);
     c->capturing = false;
@@ -574,6 +596,39 @@ int ensure_kappa(qtb_ctx *c, int P)
     c->release(M);
     if (rc) return rc;
     c->kappaF[P] = F;
+    return QTB_OK;
+}
+
+// Fourier-segment generator: sqrt(S_j/n) of every system on the segment grid
+// (spectra as for the filter) and the twiddles e^{+2 pi i k/n}, k < n/2
+int setup_fourier(qtb_ctx *c, const std::vector<DSpec> &spec)
+{
+    const int n = kBlockSteps * c->seg_blocks, ns = (int)c->hs.size();
+    for (int s = 0; s < ns; ++s)
+        if (spec[s].mode == QTB_NOISE_QTB_PIMD_MLP)
+            return fail(QTB_ERR_ARG, "system %d: the learned kappa_P mode needs the filter generator", s);
+    const size_t rs = c->mixed ? 4 : 8;
+    c->release(c->d_sq);
+    c->release(c->d_tw);
+    c->d_sq = c->alloc(rs * (size_t)ns * (n / 2 + 1));
+    c->d_tw = c->alloc(rs * (size_t)n);
+    if (!c->d_sq || !c->d_tw) return fail(QTB_ERR_OOM, "segment spectrum allocation failed");
+    launch_spectrum_seg(c->dspec, ns, n, c->d_sq, c->mixed ? 0 : 1, c->st);
+    std::vector<double> tw((size_t)n);
+    for (int k = 0; k < n / 2; ++k) {
+        tw[2 * k] = std::cos(2.0 * kPi * k / n);
+        tw[2 * k + 1] = std::sin(2.0 * kPi * k / n);
+    }
+    if (c->mixed) {
+        std::vector<float> tf(tw.begin(), tw.end());
+        CUDA_TRY(cudaMemcpyAsync(c->d_tw, tf.data(), 4 * tf.size(), cudaMemcpyHostToDevice, c->st));
+        CUDA_TRY(cudaStreamSynchronize(c->st));
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(c->d_tw, tw.data(), 8 * tw.size(), cudaMemcpyHostToDevice, c->st));
+        CUDA_TRY(cudaStreamSynchronize(c->st));
+    }
+    CUDA_TRY(fourier_prepare(n));
+    CUDA_TRY(cudaGetLastError());
     return QTB_OK;
 }
 
@@ -656,7 +711,12 @@ int rebuild_filters(qtb_ctx *c)
         int rc = setup_tc(c);
         if (rc) return rc;
     }
+    if (c->gen == QTB_GEN_FOURIER) {
+        int rc = setup_fourier(c, spec);
+        if (rc) return rc;
+    }
     c->eta_blk = LLONG_MIN;
+    c->eta_seg = LLONG_MIN;
     c->graph_dirty = true;
     return QTB_OK;
 }
@@ -1072,6 +1132,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     cudaMemsetAsync(d.flag, 0, 2 * sizeof(unsigned), c->st);
     cudaMemsetAsync(d.gbar, 0, 2 * sizeof(unsigned), c->st);
     d.eta = c->alloc(c->rsz * (size_t)kBlockSteps * (size_t)D);
+    d.eta_blocks = 1;
     d.part = (double *)c->alloc(sizeof(double) * kNQ * (size_t)std::max(nforce, 1LL));
     d.ipart = (double *)c->alloc(sizeof(double) * kNQ * (size_t)icta);
     d.latest = (double *)c->alloc(sizeof(double) * QTB_NREC * n_sys);
@@ -1138,8 +1199,13 @@ int qtb_step_n(qtb_ctx *c, long long n)
         const long long b = floor_div(c->step, kBlockSteps);
         const int j = (int)(c->step - b * kBlockSteps);
         if (j == 0 && n >= kBlockSteps) {
-            // the graph generates white block b + Kb and filters block b
-            ensure_ring(c, b - c->d.Kb, b + c->d.Kb - 1);
+            // the graph generates white block b + Kb and filters block b (filter), or
+            // generates a new segment when b starts one (Fourier segments)
+            if (c->gen == QTB_GEN_FOURIER) {
+                if (b % c->seg_blocks != 0) ensure_eta(c, b);  // the segment b lies in
+            } else {
+                ensure_ring(c, b - c->d.Kb, b + c->d.Kb - 1);
+            }
             set_clock(c, b);
             if (c->graph_dirty || !c->gexec) {
                 int rc = build_graph(c);
@@ -1150,6 +1216,7 @@ int qtb_step_n(qtb_ctx *c, long long n)
             c->ring_hi = b + c->d.Kb;
             c->ring_lo = c->ring_hi - c->d.nslots + 1;
             c->eta_blk = b;
+            c->eta_seg = floor_div(b, c->seg_blocks);
             c->dclock = b + 1;
             c->step += kBlockSteps;
             n -= kBlockSteps;
@@ -1168,6 +1235,38 @@ int qtb_step_n(qtb_ctx *c, long long n)
         CUDA_TRY(cudaGetLastError());
     }
     CUDA_TRY(cudaGetLastError());
+    return QTB_OK;
+}
+
+int qtb_set_generator(qtb_ctx *c, int generator, int segment_blocks)
+{
+    if (!c) return fail(QTB_ERR_ARG, "null context");
+    if (generator != QTB_GEN_FILTER && generator != QTB_GEN_FOURIER) return fail(QTB_ERR_ARG, "unknown generator");
+    const int M = generator == QTB_GEN_FOURIER ? segment_blocks : 1;
+    if (M != 1 && M != 2 && M != 4 && M != 8) return fail(QTB_ERR_ARG, "segment_blocks must be 1, 2, 4 or 8");
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+    if (M != c->seg_blocks) {
+        void *eta = c->alloc(c->rsz * (size_t)kBlockSteps * M * (size_t)c->d.Dtot);
+        if (!eta) return fail(QTB_ERR_OOM, "noise segment allocation failed");
+        CUDA_TRY(cudaMemsetAsync(eta, 0, c->rsz * (size_t)kBlockSteps * M * (size_t)c->d.Dtot, c->st));
+        c->release(c->d.eta);
+        c->d.eta = eta;
+    }
+    const int old_gen = c->gen, old_m = c->seg_blocks;
+    c->gen = generator;
+    c->seg_blocks = M;
+    c->d.eta_blocks = M;
+    int rc = rebuild_filters(c);
+    if (rc) {
+        c->gen = old_gen;
+        c->seg_blocks = c->d.eta_blocks = old_m;
+        if (old_m != M) {
+            c->release(c->d.eta);
+            c->d.eta = c->alloc(c->rsz * (size_t)kBlockSteps * old_m * (size_t)c->d.Dtot);
+        }
+        rebuild_filters(c);
+        return rc;
+    }
     return QTB_OK;
 }
 
@@ -1260,16 +1359,18 @@ int qtb_get_noise(qtb_ctx *c, int sys, double *out, long long *block_out)
     CUDA_TRY(cudaGetLastError());
     const DSys &S = c->ds[sys];
     const int D = 3 * S.N * S.P;
+    // rows of block b in the noise buffer (Fourier segments hold seg_blocks blocks)
+    const size_t r0 = (size_t)(b - floor_div(b, c->seg_blocks) * c->seg_blocks) * kBlockSteps;
     if (c->mixed) {
         std::vector<float> buf((size_t)kBlockSteps * D);
         for (int j = 0; j < kBlockSteps; ++j)
-            CUDA_TRY(cudaMemcpyAsync(buf.data() + (size_t)j * D, (const float *)c->d.eta + (size_t)j * c->d.Dtot + S.dof0,
+            CUDA_TRY(cudaMemcpyAsync(buf.data() + (size_t)j * D, (const float *)c->d.eta + (r0 + j) * c->d.Dtot + S.dof0,
                                      sizeof(float) * D, cudaMemcpyDeviceToHost, c->st));
         CUDA_TRY(cudaStreamSynchronize(c->st));
         for (size_t t = 0; t < buf.size(); ++t) out[t] = buf[t];
     } else {
         for (int j = 0; j < kBlockSteps; ++j)
-            CUDA_TRY(cudaMemcpyAsync(out + (size_t)j * D, (const double *)c->d.eta + (size_t)j * c->d.Dtot + S.dof0,
+            CUDA_TRY(cudaMemcpyAsync(out + (size_t)j * D, (const double *)c->d.eta + (r0 + j) * c->d.Dtot + S.dof0,
                                      sizeof(double) * D, cudaMemcpyDeviceToHost, c->st));
         CUDA_TRY(cudaStreamSynchronize(c->st));
     }

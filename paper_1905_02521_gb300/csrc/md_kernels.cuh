@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
             p[k] = u;
         }
         const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
-        const R *eta = reinterpret_cast<const R *>(d.eta) + (size_t)j * d.Dtot + S.dof0;
+        const R *eta = reinterpret_cast<const R *>(d.eta) + eta_row(d, j) * d.Dtot + S.dof0;
         const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
 #pragma unroll(UN)
         for (int k = 0; k < P; ++k)
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int 
     __syncthreads();
     // phase 2: to modes, A O A per mode
     const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
-    const R *eta = reinterpret_cast<const R *>(d.eta) + (size_t)j * d.Dtot + S.dof0;
+    const R *eta = reinterpret_cast<const R *>(d.eta) + eta_row(d, j) * d.Dtot + S.dof0;
     const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
     R qv[PER], pm[PER], noise[PER];
 #pragma unroll
@@ -1097,7 +1097,7 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
             const R cs = rot[0], sw = rot[1], ws = rot[2];
             const R sig = reinterpret_cast<const R *>(d.osig)[RP.sys * kMaxTypes + ti];
             const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
-            const R eta = reinterpret_cast<const R *>(d.eta)[(size_t)(j + 1) * d.Dtot + S.dof0 + (size_t)c * S.N + i];
+            const R eta = reinterpret_cast<const R *>(d.eta)[eta_row(d, j + 1) * d.Dtot + S.dof0 + (size_t)c * S.N + i];
             R pk = fma(hdtm, fc, v);
             R qq = 0;
             mode_aoa(qq, pk, cs, sw, ws, c1, sig * eta);

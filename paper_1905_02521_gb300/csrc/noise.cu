@@ -164,17 +164,12 @@ __device__ double kappa_eval_dev(const DSpec &sp, double y)
 }
 
 // S_j, j = 0..K, per system.  grid = (ceil((Kmax+1)/256), nsys)
-__global__ void k_spectrum(const DSpec *spec, double *S)
+// spectral density at w (rad/fs) of a system in a non-learned mode: k_B T
+// (white), theta (QTB, Eq. 7) or kappa_P (QTB-PIMD, Eq. 12), times the cutoff
+__device__ double spectrum_value(const DSpec &sp, double w)
 {
-    const DSpec sp = spec[blockIdx.y];
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j > sp.K) return;
-    int L = 2 * sp.K + 1;
-    double w = 2.0 * kPi * j / (L * sp.dt);
     double base;
-    if (sp.mode == QTB_NOISE_QTB_PIMD_MLP) {
-        return;  // filled by the learned model's spectrum kernel (mlp.cu)
-    } else if (sp.mode == QTB_NOISE_WHITE) {
+    if (sp.mode == QTB_NOISE_WHITE) {
         base = kBoltz * sp.T;
     } else if (sp.mode == QTB_NOISE_QTB) {
         base = theta_dev(w, sp.T);
@@ -185,10 +180,19 @@ __global__ void k_spectrum(const DSpec *spec, double *S)
     double W = 1.0;
     if (sp.mode != QTB_NOISE_WHITE && sp.omega_max > 0.0)
         W = 1.0 / (1.0 + exp((w - sp.omega_max) / (sp.omega_max / 50.0)));
-    S[sp.taps0 + j] = base * W;
+    return base * W;
 }
 
-// h_k = (1/L) [sqrt(S_0) + 2 sum_j sqrt(S_j) cos(2 pi j k / L)].  grid = (ceil((Kmax+1)/128), nsys)
+__global__ void k_spectrum(const DSpec *spec, double *S)
+{
+    const DSpec sp = spec[blockIdx.y];
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > sp.K) return;
+    if (sp.mode == QTB_NOISE_QTB_PIMD_MLP) return;  // filled by the learned model's spectrum kernel (mlp.cu)
+    int L = 2 * sp.K + 1;
+    S[sp.taps0 + j] = spectrum_value(sp, 2.0 * kPi * j / (L * sp.dt));
+}
+
 __global__ void k_taps(const DSpec *spec, const double *S, double *h64, float *h32)
 {
     const DSpec sp = spec[blockIdx.y];
@@ -323,6 +327,118 @@ __global__ void k_kappa_trsv(int n, const double *M, double *r)
 }
 
 // ---------------------------------------------------------------------------
+// Fourier-segment generator (Eq. 9): segments of n = 256 M steps per dof,
+// eta_t = (1/sqrt(n)) sum_j c_j e^{+2 pi i j t/n}, c_0 = sqrt(S_0) xi_0,
+// c_{n/2} = sqrt(S_{n/2}) xi_1, c_j = sqrt(S_j/2) (xi_2j + i xi_2j+1) and
+// c_{n-j} = conj(c_j), xi the white stream of the dof over the segment.
+
+// sqrt(S_j / n) on w_j = 2 pi j/(n dt), j = 0..n/2, per system
+template <class R>
+__global__ void k_spectrum_seg(const DSpec *spec, int n, R *sq)
+{
+    const DSpec sp = spec[blockIdx.y];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > n / 2) return;
+    sq[(size_t)blockIdx.y * (n / 2 + 1) + j] = (R)sqrt(spectrum_value(sp, 2.0 * kPi * j / (n * sp.dt)) / n);
+}
+
+constexpr int kSegPairs = 2;  // dof pairs per CTA of the segment generator
+
+// One CTA per kSegPairs pairs of dofs of one system: the n normals of each dof
+// (the white stream over the segment's steps), the spectrum W = Z_a + i Z_b of a
+// pair (both Z Hermitian, so the inverse transform of W carries the two real
+// sequences as its real and imaginary parts), a radix-2 Stockham inverse FFT
+// in shared memory (ping-pong between two buffers), eta rows t = 0..n-1.
+// Launched for every block; it generates only at the first block of a segment
+// unless `force`.  grid = (ceil(max dofp / (2 kSegPairs)), nsys), 256 threads,
+// dynamic smem 2 kSegPairs * 2 n * sizeof(R).
+template <class R, class C>
+__global__ void __launch_bounds__(256) k_fourier(Dev d, const R *sq, const R *tw, int n, int force)
+{
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const long long blk = d.clock[0];
+    const int M = n / kBlockSteps;
+    const long long seg = floor_div(blk, M);
+    if (!force && blk != seg * M) return;
+    const DSys S = d.sys[blockIdx.y];
+    const int dof_first = blockIdx.x * 2 * kSegPairs;
+    if (dof_first >= S.dofp) return;
+    const int nreal = 3 * S.N * S.P, h = n / 2;
+    const size_t span = (size_t)2 * n;  // one pair's complex sequence
+    R *bufA = reinterpret_cast<R *>(fsm);
+    R *bufB = bufA + kSegPairs * span;
+    // 1) normals: pair p, dof a (0) or b (1), step t -> bufB[p span + ab n + t]
+    const int nq = n / 4;
+    for (int w = threadIdx.x; w < kSegPairs * 2 * nq; w += blockDim.x) {
+        const int q = w % nq, ab = (w / nq) & 1, p = w / (2 * nq);
+        const int dofl = dof_first + 2 * p + ab;
+        C z0 = 0, z1 = 0, z2 = 0, z3 = 0;
+        if (dofl < nreal) {
+            const unsigned long long uq = (unsigned long long)(seg * nq + q);
+            uint4 ctr = make_uint4((uint32_t)uq, (uint32_t)dofl, 0u, (uint32_t)(uq >> 32));
+            uint4 r = philox4x32_10(ctr, (uint32_t)d.seed, (uint32_t)(d.seed >> 32) ^ (uint32_t)blockIdx.y);
+            bm_pair(r.x, r.y, z0, z1);
+            bm_pair(r.z, r.w, z2, z3);
+        }
+        R *dst = bufB + p * span + ab * n + 4 * q;
+        dst[0] = (R)z0; dst[1] = (R)z1; dst[2] = (R)z2; dst[3] = (R)z3;
+    }
+    __syncthreads();
+    // 2) W_j = Z_a,j + i Z_b,j (sq holds sqrt(S_j/n): the 1/sqrt(n) is folded in)
+    const R *sqs = sq + (size_t)blockIdx.y * (h + 1);
+    for (int w = threadIdx.x; w < kSegPairs * n; w += blockDim.x) {
+        const int j = w % n, p = w / n;
+        const R *xa = bufB + p * span, *xb = xa + n;
+        R re, im;
+        if (j == 0) {
+            re = sqs[0] * xa[0]; im = sqs[0] * xb[0];
+        } else if (j == h) {
+            re = sqs[h] * xa[1]; im = sqs[h] * xb[1];
+        } else {
+            const int jj = j < h ? j : n - j;
+            const R r = sqs[jj] * (R)0.70710678118654752440;
+            const R ar = xa[2 * jj], ai = xa[2 * jj + 1], br = xb[2 * jj], bi = xb[2 * jj + 1];
+            if (j < h) { re = r * (ar - bi); im = r * (ai + br); }  // r (a_re + i a_im) + i r (b_re + i b_im)
+            else { re = r * (ar + bi); im = r * (br - ai); }        // the conjugates
+        }
+        bufA[p * span + 2 * j] = re;
+        bufA[p * span + 2 * j + 1] = im;
+    }
+    __syncthreads();
+    // 3) sum_j W_j e^{+2 pi i j t/n}: stage (l, m) maps x[k + jj m], x[k + jj m + l m] to
+    //    y[k + 2 jj m] = sum, y[k + 2 jj m + m] = e^{+2 pi i jj m/n} (difference)
+    R *x = bufA, *y = bufB;
+    for (int l = h, m = 1; l >= 1; l >>= 1, m <<= 1) {
+        for (int w = threadIdx.x; w < kSegPairs * h; w += blockDim.x) {
+            const int b = w % h, p = w / h;
+            const int jj = b / m, k = b - jj * m;
+            const R wr = tw[2 * (jj * m)], wi = tw[2 * (jj * m) + 1];
+            const R *xp = x + p * span;
+            R *yp = y + p * span;
+            const int i0 = k + jj * m, i1 = i0 + l * m, o0 = k + 2 * jj * m, o1 = o0 + m;
+            const R c0r = xp[2 * i0], c0i = xp[2 * i0 + 1], c1r = xp[2 * i1], c1i = xp[2 * i1 + 1];
+            const R dr = c0r - c1r, di = c0i - c1i;
+            yp[2 * o0] = c0r + c1r;
+            yp[2 * o0 + 1] = c0i + c1i;
+            yp[2 * o1] = fma(wr, dr, -wi * di);
+            yp[2 * o1 + 1] = fma(wr, di, wi * dr);
+        }
+        __syncthreads();
+        R *t = x;
+        x = y;
+        y = t;
+    }
+    // 4) eta rows of the segment (padding dofs: 0)
+    R *eta = reinterpret_cast<R *>(d.eta);
+    for (int w = threadIdx.x; w < kSegPairs * 2 * n; w += blockDim.x) {
+        const int ab = w % 2, t = (w / 2) % n, p = w / (2 * n);
+        const int dofl = dof_first + 2 * p + ab;
+        if (dofl >= S.dofp) continue;
+        eta[(size_t)t * d.Dtot + S.dof0 + dofl] = (dofl < nreal) ? x[p * span + 2 * t + ab] : R(0);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 
 void launch_white(const Dev &d, int filter_kind, int max_dofp, int nsys, long long blk, cudaStream_t st)
@@ -375,6 +491,38 @@ void launch_kappa_solve(int P, int n, double ymax, double y0, double *A, double 
     k_kappa_normal<<<dim3((n + 31) / 32, (n + 31) / 32), 256, 0, st>>>(rows, n, A, b, M, r);
     k_kappa_chol<<<1, 1024, 0, st>>>(n, M, err);
     k_kappa_trsv<<<1, 1024, 0, st>>>(n, M, r);
+}
+
+
+size_t fourier_smem(int n, int fp64) { return (size_t)2 * kSegPairs * 2 * n * (fp64 ? 8 : 4); }
+
+cudaError_t fourier_prepare(int n)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_fourier<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fourier_smem(n, 0));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_fourier<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)fourier_smem(n, 1));
+}
+
+void launch_spectrum_seg(const DSpec *spec, int nsys, int n, void *sq, int fp64, cudaStream_t st)
+{
+    dim3 g((unsigned)((n / 2 + 1 + 255) / 256), (unsigned)nsys);
+    if (fp64) k_spectrum_seg<double><<<g, 256, 0, st>>>(spec, n, reinterpret_cast<double *>(sq));
+    else k_spectrum_seg<float><<<g, 256, 0, st>>>(spec, n, reinterpret_cast<float *>(sq));
+}
+
+void launch_fourier(const Dev &d, int fp64, int max_dofp, int nsys, const void *sq, const void *tw, int n, int force,
+                    cudaStream_t st)
+{
+    dim3 g((unsigned)((max_dofp + 2 * kSegPairs - 1) / (2 * kSegPairs)), (unsigned)nsys);
+    const size_t sm = fourier_smem(n, fp64);
+    if (fp64)
+        k_fourier<double, double><<<g, 256, sm, st>>>(d, reinterpret_cast<const double *>(sq),
+                                                      reinterpret_cast<const double *>(tw), n, force);
+    else
+        k_fourier<float, float><<<g, 256, sm, st>>>(d, reinterpret_cast<const float *>(sq),
+                                                    reinterpret_cast<const float *>(tw), n, force);
 }
 
 }  // namespace qtb

@@ -140,6 +140,7 @@ struct Dev {
     unsigned *flag;       // [2] rebuild requests; flag[s & 1] is set by whoever produces the positions of step s
     unsigned *gbar;       // [2] grid barrier of the cooperative step kernel: arrivals, generation
     unsigned long long *nrebuild;  // list rebuilds carried out
+    int eta_blocks;       // blocks per noise segment (1: time-domain filter)
     // noise
     void *ring;           // [nslots][Dtot][256] white noise (double, float or bf16)
     void *eta;            // [256][Dtot] coloured noise (R)
@@ -187,5 +188,14 @@ __host__ __device__ inline long long floor_div(long long a, long long b)
 
 // sign-extend a 30-bit fixed-point difference (minimum image)
 __device__ __forceinline__ int fix_minimg(int d) { return (d << (32 - kFixBits)) >> (32 - kFixBits); }
+
+// row of the coloured-noise buffer for step j of the current block: the
+// Fourier-segment generator keeps segments of eta_blocks blocks (256 rows each)
+__device__ __forceinline__ size_t eta_row(const Dev &d, int j)
+{
+    if (d.eta_blocks <= 1) return (size_t)j;
+    const long long b = d.clock[0];
+    return (size_t)(b - floor_div(b, d.eta_blocks) * d.eta_blocks) * kBlockSteps + j;
+}
 
 }  // namespace qtb

@@ -32,6 +32,14 @@ void launch_spectrum_taps(const DSpec *spec, int nsys, int Kmax, double *S, doub
 
 // mlp.cu: spectrum S_j = kT f(y_j) ratio_model(y_j, P) W(w_j) for systems in the learned mode
 void launch_spectrum_mlp(const DSpec *spec, int nsys, int Kmax, double *S, const float *w, cudaStream_t st);
+// Fourier-segment generator (Eq. 9), segments of n = 256 M <= 2048 steps:
+// sqrt(S_j / n) per system on the segment grid, then the segment of every dof
+// into eta rows 0..n-1 (only at a segment's first block unless force)
+size_t fourier_smem(int n, int fp64);
+cudaError_t fourier_prepare(int n);
+void launch_spectrum_seg(const DSpec *spec, int nsys, int n, void *sq, int fp64, cudaStream_t st);
+void launch_fourier(const Dev &d, int fp64, int max_dofp, int nsys, const void *sq, const void *tw, int n, int force,
+                    cudaStream_t st);
 void launch_kappa_solve(int P, int n, double ymax, double y0, double *A, double *b, double *M, double *r,
                         unsigned *err, cudaStream_t st);
 

@@ -25,6 +25,7 @@ FP64, MIXED = 0, 1
 FILTER_FP64, FILTER_FP32, FILTER_BF16 = 0, 1, 2
 NOISE_WHITE, NOISE_QTB, NOISE_QTB_PIMD, NOISE_QTB_PIMD_MLP = 0, 1, 2, 3
 POT_PAIR, POT_HARMONIC, POT_DOUBLEWELL = 0, 1, 2
+GEN_FILTER, GEN_FOURIER = 0, 1
 
 
 class QtbError(RuntimeError):
@@ -83,6 +84,7 @@ def lib():
             "qtb_get_noise": ([vp, i, vp, C.POINTER(ll)], i),
             "qtb_get_step": ([vp, C.POINTER(ll)], i),
             "qtb_list_rebuilds": ([vp, C.POINTER(ll)], i),
+            "qtb_set_generator": ([vp, i, i], i),
             "qtb_autotune": ([vp, i, vp, vp, i, i, d, i, vp, vp], i),
             "qtb_set_profiling": ([vp, i], i),
             "qtb_kernel_times": ([vp, vp, vp, i], i),
@@ -231,6 +233,10 @@ def qtb_autotune(systems, params, mode=0, n_taps=1, omega_max=0.0, n_blocks=2, s
 
 def qtb_set_filter(ctx, sys, mode, n_taps=1, omega_max=0.0):
     _check(lib().qtb_set_filter(ctx, sys, mode, n_taps, omega_max))
+
+
+def qtb_set_generator(ctx, generator, segment_blocks=1):
+    _check(lib().qtb_set_generator(ctx, int(generator), int(segment_blocks)))
 
 
 def qtb_step_n(ctx, n):
