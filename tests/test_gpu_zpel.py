@@ -1,0 +1,70 @@
+"""Quartic double wells (V = V0 (x^2/a^2 - 1)^2, V0 = 0.1 eV, a = 0.5 A, m = 1.008 u,
+T = 100 K; 32769 independent 1-D wells) against the exact quantum averages of a
+grid diagonalisation (oracle/wells.py):
+
+* standard PIMD converges to the exact <x^2> and <V> as P grows (P = 32 within
+  2 % / 5 %): checks the reference and the ring-polymer path;
+* QTB-PIMD (Eqs. 10-12) at P = 8 is as close as PIMD at P = 32 and much closer
+  in <V> than PIMD at P = 8;
+* QTB-MD (P = 1) corrects most of the classical error (classical <x^2> +21 %,
+  <V> -85 %; QTB within 6 % / 15 %), the remainder being the anharmonic error
+  of a harmonic-exact bath (zero-point energy leakage, Sec. 2.2).
+"""
+import numpy as np
+import pytest
+
+from helpers import gpu_ctx
+from oracle import wells as Wl
+from paper_1905_02521_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+V0, A, M, T, DT, NAT = 0.1, 0.5, 1.008, 100.0, 0.5, 10923
+
+
+@pytest.fixture(scope="module")
+def qtb():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1905_02521_gb300 import build
+    build.build()
+    from paper_1905_02521_gb300 import qtb as q
+    return q
+
+
+def _run(qtb, P, mode, gamma=0.004, nsteps=16384, neq=8192):
+    s, pot = W.oscillators(NAT, T, gamma, n_beads=P, x0=A, spread=0.05, mass=M)
+    ctx = gpu_ctx(qtb, [s], pot, DT, precision=1, filter_prec=1, seed=11, potential=qtb.POT_DOUBLEWELL,
+                  ext={"V0": V0, "a": A}, obs_stride=8, max_records=4096)
+    try:
+        if mode != qtb.NOISE_WHITE:
+            qtb.qtb_set_filter(ctx, 0, mode, 2049, 0.6)
+        qtb.qtb_step_n(ctx, neq)
+        qtb.qtb_step_n(ctx, nsteps)
+        ser = qtb.qtb_get_series(ctx, 0, nsteps // 8)
+    finally:
+        qtb.qtb_destroy(ctx)
+    nd = 3 * NAT
+    return ser[:, 17].mean() / nd, ser[:, 2].mean() / nd   # bead-averaged <x^2>, <V> per well
+
+
+def test_double_wells_against_exact_quantum_averages(qtb):
+    _, x2e, ve = Wl.thermal(Wl.double_well(V0, A), M, T, 1.6, with_v=True)
+    _, x2c, vc = Wl.classical(Wl.double_well(V0, A), M, T, 1.6)
+    err = lambda r: (r[0] / x2e - 1.0, r[1] / ve - 1.0)  # noqa: E731
+    res = {
+        "classical": err(_run(qtb, 1, qtb.NOISE_WHITE)),
+        "qtb": err(_run(qtb, 1, qtb.NOISE_QTB)),
+        "qtbpimd8": err(_run(qtb, 8, qtb.NOISE_QTB_PIMD)),
+        "pimd8": err(_run(qtb, 8, qtb.NOISE_WHITE)),
+        "pimd32": err(_run(qtb, 32, qtb.NOISE_WHITE)),
+    }
+    for k, (ex, ev) in res.items():
+        print("%-9s <x^2> %+.1f %%  <V> %+.1f %%" % (k, 100 * ex, 100 * ev))
+    # the classical run reproduces the classical averages (the bath at k_B T)
+    assert res["classical"][0] == pytest.approx(x2c / x2e - 1.0, abs=0.01)
+    assert res["classical"][1] == pytest.approx(vc / ve - 1.0, abs=0.02)
+    assert abs(res["pimd32"][0]) < 0.02 and abs(res["pimd32"][1]) < 0.05
+    assert abs(res["qtbpimd8"][0]) < 0.04 and abs(res["qtbpimd8"][1]) < 0.04
+    assert abs(res["qtbpimd8"][1]) < abs(res["pimd8"][1]) / 3
+    assert abs(res["qtb"][0]) < 0.06 and abs(res["qtb"][1]) < 0.15
