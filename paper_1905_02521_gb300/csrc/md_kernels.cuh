@@ -1012,13 +1012,14 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
         g.r2 = fma(g.dx, g.dx, fma(g.dy, g.dy, g.dz * g.dz));
         return g;
     };
-    // force (and on recorded steps energy and virial) of one entry, masked by `in`
-    auto force = [&](const Geo &g, bool in) {
+    // force (and on recorded steps energy and virial) of one entry, masked by `in`,
+    // added to the round's partial sums (px, py, pz)
+    auto force = [&](const Geo &g, bool in, R &px, R &py, R &pz) {
         R fo, ee;
         pair_eval(T, ptab[ti * kMaxTypes + g.tj], g.r2, fo, ee, REC && rec);
         fo = in ? fo : R(0);
         // stored displacement is r_j - r_i: the force on i is -fo (r_j - r_i)
-        fx.add(-fo * g.dx); fy.add(-fo * g.dy); fz.add(-fo * g.dz);
+        px = fma(-fo, g.dx, px); py = fma(-fo, g.dy, py); pz = fma(-fo, g.dz, pz);
         if (REC && rec) {
             en += in ? ee : R(0);
             w0 = fma(fo * g.dx, g.dx, w0); w1 = fma(fo * g.dy, g.dy, w1); w2 = fma(fo * g.dz, g.dz, w2);
@@ -1053,8 +1054,14 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
                 any |= in[q];
             }
             if (__any_sync(0xffffffffu, any)) {
+                // the round's NE terms are summed in R, the partial sum then added
+                // error-free (float-float): the extra roundings are those of NE - 1
+                // additions of terms of like size (modelled on the CPU: no change of
+                // the error budget)
+                R px = 0, py = 0, pz = 0;
 #pragma unroll
-                for (int q = 0; q < NE; ++q) force(g[q], in[q]);
+                for (int q = 0; q < NE; ++q) force(g[q], in[q], px, py, pz);
+                fx.add(px); fy.add(py); fz.add(pz);
             }
 #pragma unroll
             for (int q = 0; q < NE; ++q) e[q] = e2[q];
