@@ -16,6 +16,8 @@
  *           spectral density is 2 m gamma theta(w,T)  (kappa_P for QTB-PIMD,
  *           Eq. 12, applied to the ring-polymer normal modes, Sec. 2.3)
  *   Eq. 11  normal-mode frequencies of the free ring polymer
+ *   (Sec. 2.3) centroid-virial kinetic estimators of the ring polymer, which
+ *           the paper does not print (it gives the primitive one, Eq. 5)
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   - the coloured noise is a zero-phase time-domain filter of white noise,
@@ -427,6 +429,39 @@ static void observe(ora_sim *s, double *rec)
     for (int a = 0; a < 9; ++a) rec[5 + a] = s->vir[a];
     for (int c = 0; c < 3; ++c) rec[14 + c] = mom[c];
     rec[17] = x2 / P;
+    /* Centroid-virial kinetic estimators.  With the bead forces f_s = -(1/P)
+     * grad V(r_s) of Eq. 4 and the centroid rbar = (1/P) sum_s r_s of each atom,
+     *   K_cv   = 3N k_B T/2 - 1/2 sum_i sum_s (r_i,s - rbar_i) . f_i,s
+     * (PIMD: the centroid is classical at T), and, for a bath that is not
+     * classical (QTB-PIMD), the same virial term with the measured kinetic
+     * energy of the centroid mode, K_0 = sum_i m_i P |vbar_i|^2 / 2, in place of
+     * 3N k_B T/2.  Both are exact in expectation for a harmonic potential under
+     * their own bath.  Bead offsets are taken relative to bead 0, by minimum
+     * image in a periodic box (the beads of an atom lie within half a box). */
+    double cv = 0.0, K0 = 0.0;
+    for (int i = 0; i < N; ++i) {
+        double m = s->mass_t[s->type[i]];
+        for (int c = 0; c < 3; ++c) {
+            double L = (s->p.potential == 0) ? s->p.box[c] : 0.0;
+            double x0 = s->x[(size_t)i * 3 + c];
+            double dbar = 0.0, vs = 0.0;
+            for (int b = 0; b < P; ++b) {
+                double d = s->x[((size_t)b * N + i) * 3 + c] - x0;
+                if (L > 0.0) d -= L * round(d / L);
+                dbar += d;
+                vs += s->v[((size_t)b * N + i) * 3 + c];
+            }
+            dbar /= P;
+            for (int b = 0; b < P; ++b) {
+                double d = s->x[((size_t)b * N + i) * 3 + c] - x0;
+                if (L > 0.0) d -= L * round(d / L);
+                cv += (d - dbar) * s->f[((size_t)b * N + i) * 3 + c];
+            }
+            K0 += 0.5 * m * ORA_MVV2E * vs * vs / P;
+        }
+    }
+    rec[18] = 1.5 * N * ORA_KB * s->p.T - 0.5 * cv;
+    rec[19] = K0 - 0.5 * cv;
 }
 
 /* Advance nsteps BAOAB steps; if rec != NULL write one record per step. */

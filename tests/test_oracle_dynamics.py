@@ -9,7 +9,10 @@
 * PIMD on harmonic oscillators reproduces the finite-P closed form of the
   primitive estimator (Eqs. 3, 5, 11);
 * QTB-PIMD on harmonic oscillators gives the bead-averaged <x^2> = theta/(m w^2)
-  that Eq. 10 demands, again with the friction correction by quadrature.
+  that Eq. 10 demands, again with the friction correction by quadrature;
+* the centroid-virial kinetic estimators (slots 18, 19) match the same closed
+  forms: E_P/2 for PIMD, and for QTB-PIMD the centroid-mode estimator gives the
+  quantum theta/2 while the classical-centroid one does not.
 """
 import numpy as np
 import pytest
@@ -106,6 +109,13 @@ def test_pimd_harmonic_primitive_energy_closed_form(oracle):
         E_P = KB * T * np.sum(1.0 / (1.0 + (2 * P / 3.0) ** 2 * np.sin(k * np.pi / P) ** 2))
         sig = _block_sigma(E)
         assert abs(E.mean() - E_P) < 4 * sig + 3e-3 * E_P, (P, E.mean(), E_P, sig)
+        # centroid-virial estimators: <K_cv> = <V> = E_P/2 for a harmonic potential,
+        # with a variance that, unlike the primitive one, does not grow with P
+        for q in (18, 19):
+            Ecv = (rec[:, q] + rec[:, 2]) / 300.0
+            assert abs(Ecv.mean() - E_P) < 4 * _block_sigma(Ecv) + 3e-3 * E_P, (P, q, Ecv.mean(), E_P)
+        if P > 1:
+            assert rec[:, 18].std() < 0.5 * (rec[:, 4] - rec[:, 2]).std()
 
 
 @pytest.mark.slow
@@ -127,3 +137,16 @@ def test_qtb_pimd_harmonic_position_variance(oracle):
     assert abs(x2.mean() - x2_q) < 4 * sig + 5e-3 * x2_q
     # Eq. 10: without friction the bead average is the quantum theta/(m w0^2)
     assert x2_q == pytest.approx(S.theta(w0, T) / (m * MVV2E * w0 ** 2), rel=0.05)
+    # kinetic energy per oscillator: the centroid-mode kinetic energy plus the
+    # virial term (m w0^2/2P) sum_{k>0} <q_k^2>, each mode by quadrature; without
+    # friction theta/2.  The classical-centroid K_cv (k_B T/2 for the centroid)
+    # misses the centroid's quantum part.
+    v2_0 = _quad_x2_v2(dens, w0 / np.sqrt(P), gamma, m, np.pi / dt)[1]
+    vir = 0.5 * m * MVV2E * w0 ** 2 / P * np.sum(q2[1:])
+    K_q = 0.5 * m * MVV2E * v2_0 + vir
+    Kcv0 = rec[:, 19] / 150.0
+    assert abs(Kcv0.mean() - K_q) < 4 * _block_sigma(Kcv0) + 5e-3 * K_q
+    assert K_q == pytest.approx(0.5 * S.theta(w0, T), rel=0.05)
+    Kcv = rec[:, 18] / 150.0
+    assert abs(Kcv.mean() - (0.5 * KB * T + vir)) < 4 * _block_sigma(Kcv) + 5e-3 * K_q
+    assert Kcv.mean() < 0.9 * K_q
