@@ -311,6 +311,7 @@ def run_ours(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_value = ws * units * BLOCK * args.steps / (np.sum(e2e_ms) / 1e3)
     integ = 1 if all(p == 1 for _, p in sizes) else BLOCK * len({p for _, p in sizes})
+    cen = 1 if any(p > 1 for _, p in sizes) else 0  # centroid estimators, recorded step only
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -338,8 +339,9 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(len(systems) * qtb.NREC * 8)},
         # per block: white, filter, the integrator (once for one-bead systems, else every
         # step per distinct bead count), 256 step launches (a list rebuild runs inside the
-        # step launch that needs it), the block clock
-        "gpu_launches": 2 + integ + BLOCK + 1,
+        # step launch that needs it), the centroid estimators of the recorded step (ring
+        # polymers), the block clock
+        "gpu_launches": 2 + integ + BLOCK + cen + 1,
         "list_rebuilds_per_bench_step": rebuilds,
         "wall_s": wall,
         "observables": {"K_eV": float(obs[1]), "V_eV": float(obs[2]), "step": int(obs[0])},

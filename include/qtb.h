@@ -127,7 +127,13 @@ typedef struct {
  *   [4] E_prim = K - spring + V (Eq. 5)
  *   [5..13] virial (1/P) sum_s sum_pairs d (x) F, row-major 3x3 (eV)
  *   [14..16] total momentum (u A/fs)   [17] (1/P) sum_s sum_i |r_i^(s)|^2 (A^2)
- *   [18..19] reserved (0) */
+ *   [18] K_cv = 3N k_B T/2 - 1/2 sum_s sum_i (r_i^(s) - rbar_i) . f_i^(s), the
+ *        centroid-virial kinetic energy (f = -(1/P) grad V, Eq. 4; rbar the bead
+ *        centroid, bead offsets by minimum image); PIMD, classical centroid
+ *   [19] K_cv,0: the same with 3N k_B T/2 replaced by the centroid-mode kinetic
+ *        energy sum_i m_i P |vbar_i|^2/2 (a bath that does not hold the centroid
+ *        at k_B T: QTB-PIMD).  The paper prints neither (only Eq. 5).  One
+ *        bead: [18] = 3N k_B T/2, [19] = K. */
 #define QTB_NREC 20
 
 /* Create a context for n_sys independent systems sharing one parameter set.

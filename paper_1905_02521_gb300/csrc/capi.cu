@@ -68,7 +68,7 @@ struct qtb_ctx {
     std::vector<HSys> hs;
     std::vector<DSys> ds;
     std::vector<DRep> dr;
-    std::vector<int> cell_rep, icta_sys, lcta_rep;
+    std::vector<int> cell_rep, icta_sys, lcta_rep, ccta_sys;
     Dev d{};
     MdLaunch ml{};
     PairTab tab{};
@@ -344,6 +344,7 @@ int refresh_forces(qtb_ctx *c)
     }
     CUDA_TRY(launch_force(c->d, c->ml, c->tabf, c->tab, 0, j, cur, 0, 1, c->st));
     if (!c->pair) launch_reduce(c->d, c->ml, j, -1, c->st);  // the list force kernel reduces itself
+    launch_centroid(c->d, c->ml, j, -1, c->st);
     CUDA_TRY(cudaGetLastError());
     return QTB_OK;
 }
@@ -524,9 +525,10 @@ int run_steps(qtb_ctx *c, int j0, int count, bool graph)
             ProfMark pm(c, KC_FORCE);
             CUDA_TRY(launch_force(c->d, m, c->tabf, c->tab, 1, j, cur, adv, rec, c->st));
         }
-        if (!m.pair) {
+        if (!m.pair || (rec && m.n_ccta)) {
             ProfMark pm(c, KC_REDUCE);
-            launch_reduce(c->d, m, j, 1, c->st);
+            if (!m.pair) launch_reduce(c->d, m, j, 1, c->st);
+            if (rec) launch_centroid(c->d, m, j, 1, c->st);
         }
         c->capturing = keep;
     }
@@ -865,7 +867,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
 
     // ---- layout
     long long G = 0, D = 0;
-    int icta = 0, nrep = 0, ncells = 0, cap = 8;
+    int icta = 0, ccta = 0, nrep = 0, ncells = 0, cap = 8;
     int rot_tot = 0, nm_tot = 0;
     std::map<int, int> nm_off;
     std::vector<double> nmC_host;
@@ -932,6 +934,9 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         S.icta0 = icta;
         icta += (h.N + integrate_atoms_per_cta(h.P, nm_big) - 1) / integrate_atoms_per_cta(h.P, nm_big);
         S.icta1 = icta;
+        S.ccta0 = ccta;
+        if (h.P > 1) ccta += (h.N + kCenAtoms - 1) / kCenAtoms;
+        S.ccta1 = ccta;
         for (int k = 0; k < 3; ++k) S.box[k] = q.box[k];
         S.T = q.T;
         S.gamma = q.gamma;
@@ -990,6 +995,8 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         return bail(fail(QTB_ERR_ARG, "cell capacity %d > %d: box too dense for (r_cut + skin)/2 cells", cap, kMaxCellCap));
     for (int s = 0; s < n_sys; ++s)
         for (int t = c->ds[s].icta0; t < c->ds[s].icta1; ++t) c->icta_sys.push_back(s);
+    for (int s = 0; s < n_sys; ++s)
+        for (int t = c->ds[s].ccta0; t < c->ds[s].ccta1; ++t) c->ccta_sys.push_back(s);
     c->ml.mixed = c->mixed;
     c->ml.lanes = lanes;
     if (c->pair && step_prepare(c->ml, stage_cap) != cudaSuccess)
@@ -1031,6 +1038,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     m.mixed = c->mixed;
     m.pair = c->pair;
     m.n_icta = icta;
+    m.n_ccta = ccta;
     m.n_ecta = ext_gx;
     m.nP = 0;
     for (int s = 0; s < n_sys; ++s) {
@@ -1093,6 +1101,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     d.cell_rep = upload(c, c->cell_rep);
     d.lcta_rep = upload(c, c->lcta_rep);
     d.icta_sys = upload(c, c->icta_sys);
+    d.ccta_sys = ccta ? upload(c, c->ccta_sys) : nullptr;
     d.sys = upload(c, c->ds);
     const size_t psz = c->pair && c->mixed ? 4 : c->rsz;
     d.x = c->alloc(psz * 3 * (size_t)G);
@@ -1142,6 +1151,12 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     d.done = (unsigned *)c->alloc(sizeof(unsigned) * n_sys);
     if (!d.done) return bail(fail(QTB_ERR_OOM, "device allocation failed"));
     cudaMemsetAsync(d.done, 0, sizeof(unsigned) * n_sys, c->st);
+    if (ccta) {
+        d.cpart = (double *)c->alloc(sizeof(double) * 2 * (size_t)ccta);
+        d.cdone = (unsigned *)c->alloc(sizeof(unsigned) * n_sys);
+        if (!d.cpart || !d.cdone || !d.ccta_sys) return bail(fail(QTB_ERR_OOM, "device allocation failed"));
+        cudaMemsetAsync(d.cdone, 0, sizeof(unsigned) * n_sys, c->st);
+    }
     c->dspec = (DSpec *)c->alloc(sizeof(DSpec) * n_sys);
     if (!d.x || !d.v || !d.f || !d.cnt || !d.ccount || !d.cidx || !d.cpos || !d.eta || !d.part || !d.ipart ||
         !d.latest || !d.series || !d.clock || !d.err || !d.typ || !d.sys || !c->dspec)

@@ -67,6 +67,127 @@ __global__ void k_reduce(Dev d, int j, int record)
     reduce_system(d, blockIdx.x, step, record, sh);
 }
 
+// ---------------------------------------------------------------------------
+// Centroid-virial kinetic estimators of the ring-polymer systems (P > 1), on
+// the recorded steps, after the force kernel (positions and forces of the step,
+// velocities after the closing kick):
+//   slot 18: K_cv   = 3N k_B T/2 - 1/2 sum_i sum_s (r_i,s - rbar_i) . f_i,s
+//   slot 19: K_cv,0 = K_0        - 1/2 sum_i sum_s (r_i,s - rbar_i) . f_i,s,
+// f = -(1/P) grad V (Eq. 4), rbar the atom's bead centroid, K_0 = sum_i m_i P
+// |vbar_i|^2 / 2 the kinetic energy of the centroid mode (the form for a bath
+// that does not hold the centroid at k_B T, QTB-PIMD).  A CTA takes kCenAtoms
+// atoms (lane = atom, coalesced rows); its 8 warps split the beads.  Per atom and
+// component, with d_b the offset of bead b from bead 0 (minimum image), the
+// sums over beads of d_b f_b, d_b, f_b and v_b give
+//   sum_b (d_b - dbar) f_b = sum d_b f_b - (sum d_b)(sum f_b)/P,
+// FP64.  The last CTA of a system completes the record (fixed order).
+constexpr int kCenWarps = 8;
+
+template <int PM, class R>
+__global__ void __launch_bounds__(32 * kCenWarps) k_centroid(Dev d, int j, int record)
+{
+    typedef typename PosT<PM, R>::S PS;
+    __shared__ double sh[kCenWarps][12][kCenAtoms];
+    __shared__ double fin[kCenWarps][2];
+    __shared__ int last;
+    const long long step = d.clock[0] * kBlockSteps + j + 1;  // steps completed
+    if (record >= 0 && step % d.obs_stride != 0) return;
+    const int cta = blockIdx.x, s = d.ccta_sys[cta];
+    const DSys S = d.sys[s];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N = S.N, P = S.P;
+    const int i = (cta - S.ccta0) * kCenAtoms + lane;
+    const size_t G = (size_t)d.G;
+    const PS *X = reinterpret_cast<const PS *>(d.x);
+    const R *F = reinterpret_cast<const R *>(d.f);
+    const R *V = reinterpret_cast<const R *>(d.v);
+    double a[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) a[q] = 0.0;
+    if (i < N) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t o0 = (size_t)c * G + S.g0 + i;
+            const PS x0 = X[o0];
+            double sdf = 0.0, sd = 0.0, sf = 0.0, sv = 0.0;
+            for (int b = warp; b < P; b += kCenWarps) {
+                const size_t o = o0 + (size_t)b * N;
+                const double dd = (double)PosT<PM, R>::rel(X[o], x0, S.box[c], S.fix_scale[c], S.fix_inv[c]);
+                const double f = (double)F[o];
+                sdf = fma(dd, f, sdf);
+                sd += dd;
+                sf += f;
+                sv += (double)V[o];
+            }
+            a[4 * c] = sdf; a[4 * c + 1] = sd; a[4 * c + 2] = sf; a[4 * c + 3] = sv;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 12; ++q) sh[warp][q][lane] = a[q];
+    __syncthreads();
+    if (warp == 0) {
+        double cv = 0.0, k0 = 0.0;
+        if (i < N) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double sdf = 0.0, sd = 0.0, sf = 0.0, sv = 0.0;
+                for (int w = 0; w < kCenWarps; ++w) {
+                    sdf += sh[w][4 * c][lane];
+                    sd += sh[w][4 * c + 1][lane];
+                    sf += sh[w][4 * c + 2][lane];
+                    sv += sh[w][4 * c + 3][lane];
+                }
+                cv += sdf - sd * sf / P;
+                k0 += sv * sv;
+            }
+            k0 *= 0.5 * d.mass_mvv[d.typ[S.g0 + i]] / P;
+        }
+        cv = warp_sum(cv);
+        k0 = warp_sum(k0);
+        if (lane == 0) {
+            d.cpart[2 * (size_t)cta] = cv;
+            d.cpart[2 * (size_t)cta + 1] = k0;
+        }
+    }
+    // the CTA that finishes a system last completes its record
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(&d.cdone[s], 1u) == (unsigned)(S.ccta1 - S.ccta0 - 1)) ? 1 : 0;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double cv = 0.0, k0 = 0.0;
+    for (int c = S.ccta0 + (int)threadIdx.x; c < S.ccta1; c += blockDim.x) {
+        cv += __ldcg(d.cpart + 2 * (size_t)c);
+        k0 += __ldcg(d.cpart + 2 * (size_t)c + 1);
+    }
+    cv = warp_sum(cv);
+    k0 = warp_sum(k0);
+    if (lane == 0) {
+        fin[warp][0] = cv;
+        fin[warp][1] = k0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cv = 0.0;
+        k0 = 0.0;
+        for (int w = 0; w < kCenWarps; ++w) {
+            cv += fin[w][0];
+            k0 += fin[w][1];
+        }
+        const double r18 = 1.5 * N * kBoltz * S.T - 0.5 * cv, r19 = k0 - 0.5 * cv;
+        d.latest[(size_t)s * QTB_NREC + 18] = r18;
+        d.latest[(size_t)s * QTB_NREC + 19] = r19;
+        if (record >= 0) {
+            const long long r = step / d.obs_stride - 1;
+            const int slot = (int)(r % d.max_records);
+            d.series[((size_t)slot * d.nsys + s) * QTB_NREC + 18] = r18;
+            d.series[((size_t)slot * d.nsys + s) * QTB_NREC + 19] = r19;
+        }
+        d.cdone[s] = 0u;
+    }
+}
+
 __global__ void k_tick(Dev d) { d.clock[0] += 1; }
 __global__ void k_setclock(Dev d, long long b) { d.clock[0] = b; }
 
@@ -162,6 +283,19 @@ cudaError_t launch_force(const Dev &d, const MdLaunch &m, const PairTabT<float> 
 void launch_reduce(const Dev &d, const MdLaunch &m, int j, int record, cudaStream_t st)
 {
     k_reduce<<<d.nsys, 128, 0, st>>>(d, j, record);
+}
+
+void launch_centroid(const Dev &d, const MdLaunch &m, int j, int record, cudaStream_t st)
+{
+    if (m.n_ccta == 0) return;
+    const int g = m.n_ccta, nt = 32 * kCenWarps;
+    if (!m.pair) {
+        if (m.mixed) k_centroid<PM_FREE, float><<<g, nt, 0, st>>>(d, j, record);
+        else k_centroid<PM_FREE, double><<<g, nt, 0, st>>>(d, j, record);
+    } else {
+        if (m.mixed) k_centroid<PM_FIX, float><<<g, nt, 0, st>>>(d, j, record);
+        else k_centroid<PM_BOX64, double><<<g, nt, 0, st>>>(d, j, record);
+    }
 }
 
 void launch_tick(const Dev &d, cudaStream_t st) { k_tick<<<1, 1, 0, st>>>(d); }

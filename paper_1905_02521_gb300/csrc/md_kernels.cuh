@@ -929,6 +929,12 @@ static __device__ void reduce_system(const Dev &d, int s, long long step, int re
         for (int a = 0; a < 9; ++a) rec[5 + a] = tot[Q_VIR + map[a]] * invP;
         for (int c = 0; c < 3; ++c) rec[14 + c] = tot[Q_MOM + c];
         rec[17] = tot[Q_X2] * invP;
+        // centroid-virial estimators: for one bead 3N k_B T/2 and K; ring
+        // polymers get them from the centroid kernel that follows
+        if (S.P == 1) {
+            rec[18] = 1.5 * S.N * kBoltz * S.T;
+            rec[19] = K;
+        }
         if (!isfinite(K) || !isfinite(V)) atomicOr(d.err, (unsigned)ERR_NONFINITE);
         for (int q = 0; q < QTB_NREC; ++q) d.latest[(size_t)s * QTB_NREC + q] = rec[q];
         if (record >= 0 && step % d.obs_stride == 0) {

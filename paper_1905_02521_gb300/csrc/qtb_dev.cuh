@@ -56,6 +56,7 @@ struct DSys {
     int rep0;          // first replica (pair potential)
     int icta0, icta1;  // integrator CTA range
     int fcta0, fcta1;  // force CTA range
+    int ccta0, ccta1;  // centroid-estimator CTA range (empty for one bead)
     int rot0;          // offset of this system's mode rotation table
     int nm0;           // offset of this system's normal-mode matrix
     double box[3];
@@ -159,6 +160,9 @@ struct Dev {
     long long *clock;     // [0] = current noise block
     unsigned *err;        // error word
     unsigned *done;       // [nsys] CTAs finished (last-CTA reduction), reset by the last one
+    double *cpart;        // [centroid CTAs][2] virial term, centroid kinetic energy
+    const int *ccta_sys;  // [centroid CTAs] system of each CTA
+    unsigned *cdone;      // [nsys] centroid CTAs finished, reset by the last one
     int stage_cap;        // staged neighbourhood entries per CTA of the list build kernel
     unsigned long long seed;
     double mass_mvv[kMaxTypes];  // m * mvv2e per type (eV fs^2 / A^2)

@@ -48,6 +48,7 @@ struct MdLaunch {
     int mixed;            // 0: FP64 form, 1: mixed form
     int pair;             // pair potential (else external)
     int n_icta;           // integrator CTAs
+    int n_ccta;           // centroid-estimator CTAs (0: no ring polymer)
     int n_ecta;           // external-force CTAs per system
     int nP;               // number of distinct bead counts
     int Pvals[8];         // distinct bead counts
@@ -83,6 +84,10 @@ void launch_integrate(const Dev &d, const MdLaunch &m, int j, int cur, cudaStrea
 cudaError_t launch_force(const Dev &d, const MdLaunch &m, const PairTabT<float> &Tf, const PairTabT<double> &Td,
                          int kick, int j, int cur, int adv, int rec, cudaStream_t st);
 void launch_reduce(const Dev &d, const MdLaunch &m, int j, int record, cudaStream_t st);
+// centroid-virial estimators of the ring-polymer systems (record slots 18, 19),
+// after the force launch of a step that may be recorded (record < 0: latest only)
+constexpr int kCenAtoms = 32;  // atoms per CTA of the centroid estimator
+void launch_centroid(const Dev &d, const MdLaunch &m, int j, int record, cudaStream_t st);
 void launch_tick(const Dev &d, cudaStream_t st);
 void launch_setclock(const Dev &d, long long blk, cudaStream_t st);
 bool md_supported_P(int P);
