@@ -1,0 +1,160 @@
+"""QTB-MD of the 64-ion MgO crystal at 20 K against its harmonic lattice
+dynamics (oracle/lattice.py: modes of the finite-difference Hessian of the
+oracle's forces at the rock-salt sites).
+
+At 20 K the crystal's vibrations are almost purely zero-point motion
+(hbar w/2 ~ 17-60 meV per mode against k_B T = 1.7 meV), weakly anharmonic:
+
+* the QTB energy <K + V> - V(x0) is the harmonic sum over modes of the
+  Langevin response to the filter's own noise density (friction included),
+  ~ sum_m theta(w_m, T) (Eq. 1), eight times the classical 3N k_B T;
+* the kinetic-energy spectrum from the velocities (phonon density of states
+  weighted by the bath) carries the quantum theta in every band of the
+  harmonic spectrum;
+* a larger friction broadens the vibrational peaks and adds a high-frequency
+  tail above the top phonon (the drawback of a large gamma, Sec. 3): the
+  weight of that tail follows the Langevin prediction and grows with gamma.
+"""
+import numpy as np
+import pytest
+
+from helpers import gpu_ctx
+from oracle import lattice as L
+from oracle import spectra as S
+from paper_1905_02521_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+MVV2E, KB = 103.64269652680505, 8.617333262e-5
+T, DT, NTAPS, WMAX = 20.0, 1.0, 2049, 0.3
+STRIDE, SEG = 2, 4096                        # velocity samples every 2 fs, 4096-sample segments
+BANDS = [(0.03, 0.10), (0.10, 0.14), (0.14, 0.17), (0.17, 0.20)]
+TAIL = 0.20                                  # above the top phonon (0.182 rad/fs)
+
+
+@pytest.fixture(scope="module")
+def qtb():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1905_02521_gb300 import build
+    build.build()
+    from paper_1905_02521_gb300 import qtb as q
+    return q
+
+
+@pytest.fixture(scope="module")
+def lattice(oracle):
+    pot = W.mgo_potential()
+    x, t, box = W.rocksalt(2, 4.21, 0.0)
+    H = L.hessian(lambda y: oracle.pair_forces(y, t, box, pot)[0], x)
+    w, _ = L.modes(H, pot["mass"][t])
+    w[:3] = 0.0                              # the free translations
+    V0 = oracle.pair_forces(x, t, box, pot)[1]
+    # the discrete density of the filtered noise, |h_0 + 2 sum_k h_k cos(w k dt)|^2, on a
+    # 2^20-point grid of [0, 2 pi/dt) (FFT of the cosine series), linearly interpolated
+    h = S.taps(NTAPS, DT, T, WMAX)
+    a = np.zeros(1 << 20)
+    a[0], a[1:len(h)] = h[0], 2.0 * h[1:]
+    Hw = np.fft.rfft(a).real
+    wg = 2.0 * np.pi * np.arange(len(Hw)) / (len(a) * DT)
+
+    def dens(om):
+        return np.interp(np.atleast_1d(om), wg, Hw ** 2)
+    return dict(pot=pot, x=x, t=t, box=box, w=w, V0=V0, dens=dens)
+
+
+def run(qtb, lat, gamma, nsamp, nequil=4000, seed=5):
+    s = W.system(lat["x"], lat["t"], lat["box"], lat["pot"], T, gamma)
+    N = len(lat["t"])
+    ctx = gpu_ctx(qtb, [s], lat["pot"], DT, precision=1, filter_prec=1, seed=seed, obs_stride=STRIDE,
+                  max_records=nsamp)
+    try:
+        qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB, NTAPS, WMAX)
+        qtb.qtb_step_n(ctx, nequil)
+        vs = np.empty((nsamp, N, 3))
+        for i in range(nsamp):
+            qtb.qtb_step_n(ctx, STRIDE)
+            vs[i] = qtb.qtb_get_state(ctx, 0, 1, N)[1][0]
+        ser = qtb.qtb_get_series(ctx, 0, nsamp)
+    finally:
+        qtb.qtb_destroy(ctx)
+    return vs, ser
+
+
+def kinetic_spectrum(vs, masses):
+    """One-sided spectral density of the kinetic energy (eV per rad/fs), Hann-windowed
+    periodograms of 50 %-overlapping segments; int g dw = <K>."""
+    u = (vs * np.sqrt(0.5 * masses * MVV2E)[None, :, None]).reshape(len(vs), -1)
+    win = np.hanning(SEG)
+    acc, nseg = 0.0, 0
+    for s0 in range(0, len(u) - SEG + 1, SEG // 2):
+        acc = acc + (np.abs(np.fft.rfft(u[s0:s0 + SEG] * win[:, None], axis=0)) ** 2).sum(1)
+        nseg += 1
+    tau = STRIDE * DT
+    g = tau * acc / nseg / (win ** 2).sum() / np.pi
+    om = 2.0 * np.pi * np.arange(len(g)) / (SEG * tau)
+    return om, g, om[1]
+
+
+def predicted(lat, gamma, lo, hi, n=40001):
+    grid = np.linspace(lo, hi, n)
+    return float(np.trapezoid(L.langevin_kinetic_density(lat["w"], gamma, lat["dens"], grid), grid))
+
+
+def band(om, g, dw, lo, hi):
+    sel = (om >= lo) & (om < hi)
+    return float(g[sel].sum() * dw)
+
+
+def harmonic_qtb_energy(lat, gamma):
+    """sum over modes of <K_m> + <U_m> under the Langevin response (friction included)."""
+    tot = 0.0
+    for wm in lat["w"]:
+        grid = np.unique(np.concatenate([np.linspace(0.0, 0.5, 20001),
+                                         np.linspace(max(wm - 40 * gamma, 0.0), wm + 40 * gamma, 20001)]))
+        if wm > 0:   # kinetic w^2 and potential w_m^2 parts of the response
+            r = (grid ** 2 + wm ** 2) / ((wm ** 2 - grid ** 2) ** 2 + (gamma * grid) ** 2)
+        else:        # free translation: kinetic only
+            r = 1.0 / (grid ** 2 + gamma ** 2)
+        tot += float(np.trapezoid((gamma / np.pi) * r * lat["dens"](grid), grid))
+    return tot
+
+
+def test_qtb_energy_and_bands_follow_the_quantum_harmonic_crystal(qtb, lattice):
+    gamma = 0.02
+    vs, ser = run(qtb, lattice, gamma, 32768)
+    N = len(lattice["t"])
+    E = (ser[:, 1] + ser[:, 2]).mean() - lattice["V0"]
+    E_h = harmonic_qtb_energy(lattice, gamma)
+    E_q = L.harmonic_energy(0.0, lattice["w"], T)
+    print("E - V0: MD %.4f  harmonic Langevin %.4f  sum theta %.4f  classical %.4f eV"
+          % (E, E_h, E_q, (3 * N - 3) * KB * T))
+    assert E == pytest.approx(E_h, rel=0.02)      # anharmonicity at zero-point amplitudes
+    assert E_h == pytest.approx(E_q, rel=0.01)    # friction correction at gamma = 0.02 /fs
+    assert E > 5 * (3 * N - 3) * KB * T
+    om, g, dw = kinetic_spectrum(vs, lattice["pot"]["mass"][lattice["t"]])
+    for lo, hi in BANDS:
+        meas, pred = band(om, g, dw, lo, hi), predicted(lattice, gamma, lo, hi)
+        nm = int(((lattice["w"] >= lo) & (lattice["w"] < hi)).sum())
+        print("band %.2f-%.2f: %3d modes, K measured %.4f predicted %.4f (classical %.4f) eV"
+              % (lo, hi, nm, meas, pred, 0.5 * nm * KB * T))
+        assert meas == pytest.approx(pred, rel=0.05)
+        assert meas > 4 * 0.5 * nm * KB * T
+
+
+def test_friction_broadens_the_spectrum(qtb, lattice):
+    tails, preds = [], []
+    for gamma in (0.005, 0.02, 0.08):
+        vs, _ = run(qtb, lattice, gamma, 16384, seed=9)
+        om, g, dw = kinetic_spectrum(vs, lattice["pot"]["mass"][lattice["t"]])
+        tot = band(om, g, dw, 0.0, om[-1] + dw)
+        meas = band(om, g, dw, TAIL, om[-1] + dw) / tot
+        pred = predicted(lattice, gamma, TAIL, 0.6) / predicted(lattice, gamma, 0.0, 0.6)
+        print("gamma %.3f: kinetic-energy fraction above %.2f rad/fs: measured %.4f predicted %.4f"
+              % (gamma, TAIL, meas, pred))
+        tails.append(meas)
+        preds.append(pred)
+    assert tails[0] < tails[1] < tails[2]
+    assert preds[2] > 5 * preds[0]
+    for m, p in zip(tails, preds):
+        assert m == pytest.approx(p, rel=0.1)
