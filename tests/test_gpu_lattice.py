@@ -158,3 +158,61 @@ def test_friction_broadens_the_spectrum(qtb, lattice):
     assert preds[2] > 5 * preds[0]
     for m, p in zip(tails, preds):
         assert m == pytest.approx(p, rel=0.1)
+
+
+def _taps_density(Tk):
+    h = S.taps(NTAPS, DT, Tk, WMAX)
+    a = np.zeros(1 << 20)
+    a[0], a[1:len(h)] = h[0], 2.0 * h[1:]
+    Hw = np.fft.rfft(a).real
+    wg = 2.0 * np.pi * np.arange(len(Hw)) / (len(a) * DT)
+    return lambda om: np.interp(np.atleast_1d(om), wg, Hw ** 2)
+
+
+def test_heat_capacity_follows_the_quantum_harmonic_crystal(qtb, lattice):
+    """E(T) of QTB-MD over 25-800 K (one batched context, one system per temperature)
+    against the harmonic Langevin energy at each T; the finite-difference heat capacity
+    rises from far below the classical 3 k_B per ion towards it (the MgO heat-capacity
+    behaviour of Sec. 2.2), while white-noise (classical) Langevin gives ~3 k_B at 100 K."""
+    Ts = [25.0, 50.0, 100.0, 200.0, 400.0, 800.0]
+    gamma, neq, nrun, stride = 0.01, 4096, 49152, 8
+    N = len(lattice["t"])
+    systems = [W.system(lattice["x"], lattice["t"], lattice["box"], lattice["pot"], Tk, gamma, vel_seed=40 + i)
+               for i, Tk in enumerate(Ts + [100.0, 200.0])]
+    ctx = gpu_ctx(qtb, systems, lattice["pot"], DT, precision=1, filter_prec=1, seed=77, obs_stride=stride,
+                  max_records=nrun // stride)
+    try:
+        for i in range(len(Ts)):
+            qtb.qtb_set_filter(ctx, i, qtb.NOISE_QTB, NTAPS, WMAX)
+        qtb.qtb_step_n(ctx, neq)
+        qtb.qtb_step_n(ctx, nrun)
+        E = []
+        for i in range(len(systems)):
+            ser = qtb.qtb_get_series(ctx, i, nrun // stride)
+            e = ser[:, 1] + ser[:, 2] - lattice["V0"]
+            nb = 16
+            blocks = np.array([b.mean() for b in np.array_split(e, nb)])
+            E.append((e.mean(), blocks.std(ddof=1) / np.sqrt(nb)))
+    finally:
+        qtb.qtb_destroy(ctx)
+    Eh = [harmonic_qtb_energy(dict(w=lattice["w"], dens=_taps_density(Tk)), gamma) for Tk in Ts]
+    dof = 3 * N - 3
+    for k, Tk in enumerate(Ts):
+        print("T %5.0f K: E - V0 QTB %.4f +- %.4f, harmonic %.4f eV" % (Tk, E[k][0], E[k][1], Eh[k]))
+        assert E[k][0] == pytest.approx(Eh[k], rel=0.02 + 0.02 * Tk / 800.0)
+    cv, cvh = [], []
+    for k in range(len(Ts) - 1):
+        dT = Ts[k + 1] - Ts[k]
+        c = (E[k + 1][0] - E[k][0]) / dT / (dof * KB)
+        ch = (Eh[k + 1] - Eh[k]) / dT / (dof * KB)
+        sc = np.hypot(E[k + 1][1], E[k][1]) / dT / (dof * KB)
+        print("C_v / 3 k_B per ion, %3.0f-%3.0f K: QTB %.3f +- %.3f, harmonic %.3f"
+              % (Ts[k], Ts[k + 1], c, sc, ch))
+        cv.append(c)
+        cvh.append(ch)
+        assert abs(c - ch) < 4 * sc + 0.05
+    cl = (E[-1][0] - E[-2][0]) / 100.0 / (dof * KB)
+    print("C_v / 3 k_B per ion, classical Langevin 100-200 K: %.3f" % cl)
+    # quantum at 100-200 K (harmonic 0.29), near Dulong-Petit at 400-800 K; classical ~1 at 100-200 K
+    assert cv[2] < 0.45 and cv[-1] > 0.8
+    assert cl == pytest.approx(1.0, abs=0.1)
