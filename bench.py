@@ -293,8 +293,12 @@ def run_ours(args):
         # every bead of small systems; 4 evenly spaced beads of large ones, scaled to P
         beads = range(p) if n * p <= 100000 else range(0, p, max(1, p // 4))
         pairs += int(round(sum(count_pairs(x[b], systems[k]["box"], pot["r_cut"]) for b in beads) * p / len(beads)))
-    force_ms = kernel_ms["force"] / max(kernel_n["force"], 1)
-    achieved = PAIR_FLOPS * pairs / (force_ms * 1e-3) / 1e12 if force_ms > 0 else None
+    sampled = {k: kernel_ms[k] / kernel_n[k] for k in kernel_ms if kernel_n[k]}
+    launch_ms = in_graph_launch_ms(sampled, kernel_n, np.mean(step_ms), args.steps, sizes)
+    force_ms = launch_ms.get("force", 0.0)
+    fused = all(p == 1 for _, p in sizes)
+    flops_per_launch = PAIR_FLOPS * pairs
+    achieved = flops_per_launch / (force_ms * 1e-3) / 1e12 if force_ms > 0 else None
     peak = alu_peak_tflops()
     step_breakdown = {k: round(kernel_ms[k] / max(args.steps, 1), 4) for k in kernel_ms}
 
@@ -310,7 +314,7 @@ def run_ours(args):
             qtb.qtb_observables(ctx, k)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_value = ws * units * BLOCK * args.steps / (np.sum(e2e_ms) / 1e3)
-    integ = 1 if all(p == 1 for _, p in sizes) else BLOCK * len({p for _, p in sizes})
+    integ = 1 if fused else BLOCK * len({p for _, p in sizes})
     cen = 1 if any(p > 1 for _, p in sizes) else 0  # centroid estimators, recorded step only
 
     line = {
@@ -329,10 +333,15 @@ def run_ours(args):
                    "launch": "direct (2 x 128-step calls per block)" if args.direct else "CUDA graph per 256-step block",
                    "l2": "256 MB buffer written between timed steps (flush)"},
         "roofline": {"bound": "alu", "kernel": "k_step", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if achieved else None, "traffic": measured_traffic("k_step", args.workload),
+                     "frac": achieved / peak if achieved else None,
+                     "traffic": measured_traffic("k_step", args.workload),
                      "peak_source": "152 SM x 128 FP32 lanes x 2 flop x sm_max_mhz of MEASURED_PEAKS.json",
-                     "flops_per_launch": PAIR_FLOPS * pairs, "pairs_per_launch": pairs, "mean_launch_ms": force_ms},
-        "roofline_integrator": integrator_roofline(kernel_ms, kernel_n, units, sizes, args.precision),
+                     "flops_per_launch": flops_per_launch, "pairs_per_launch": pairs, "mean_launch_ms": force_ms,
+                     "duration_method": "in-graph: event-timed block minus its once-per-block kernels, "
+                                        "shared between the per-step kernels in the ratio of their event-timed "
+                                        "samples (every 64th step)",
+                     "sampled_launch_ms": sampled.get("force")},
+        "roofline_integrator": integrator_roofline(launch_ms, units, sizes, args.precision),
         "kernel_ms_per_bench_step": step_breakdown,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * units * 3 * 8),
@@ -379,12 +388,39 @@ def hbm_peak_gbs():
         return 6800.0, "fallback"
 
 
-def integrator_roofline(kernel_ms, kernel_n, units, sizes, precision):
+def in_graph_launch_ms(sampled, kernel_n, block_ms, nblocks, sizes):
+    """Mean duration of one launch of each kernel class inside the captured block.
+
+    An event pair around a launch exposes that launch's dispatch latency (the
+    graph can no longer overlap it with the previous kernel), so the sampled
+    durations overstate the in-graph ones.  The event-timed block length minus
+    the kernels launched once per block (white noise, filter, and the
+    integrator when it is fused into the step kernel) is the time of the
+    per-step launches; it is shared between them in the ratio of their
+    samples."""
+    if "force" not in sampled:
+        return dict(sampled)
+    fused = all(p == 1 for _, p in sizes)
+    n_p = len({p for _, p in sizes})
+    per_step = {"force": 1}
+    if not fused:
+        per_step["integrate"] = n_p
+    once = sum(sampled[k] * kernel_n[k] / nblocks for k in sampled if k not in per_step)
+    rest = (block_ms - once) / BLOCK
+    w = sum(sampled[k] * c for k, c in per_step.items() if k in sampled)
+    out = dict(sampled)
+    for k, c in per_step.items():
+        if k in sampled:
+            out[k] = rest * sampled[k] / w
+    return out
+
+
+def integrator_roofline(launch_ms, units, sizes, precision):
     """HBM roofline of the ring-polymer integrator (systems with P > 1; for
     one-bead systems it is fused into the step kernel)."""
-    if all(p == 1 for _, p in sizes) or kernel_n["integrate"] == 0:
+    if all(p == 1 for _, p in sizes) or "integrate" not in launch_ms:
         return None
-    ms = kernel_ms["integrate"] / kernel_n["integrate"]
+    ms = launch_ms["integrate"]
     nbytes = INTEGRATOR_BYTES[precision] * units
     peak, src = hbm_peak_gbs()
     achieved = nbytes / (ms * 1e-3) / 1e9

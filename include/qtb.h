@@ -203,7 +203,7 @@ int qtb_get_taps(qtb_ctx *c, int sys, double *h, int max, int *n_out);
 int qtb_get_noise(qtb_ctx *c, int sys, double *out, long long *block_out);
 
 /* Profiling of whole 256-step blocks: when enabled, the captured block records
- * a CUDA event pair around the launches of every 16th step and around the
+ * a CUDA event pair around the launches of every 64th step and around the
  * per-block noise launches (classes: 0 white noise, 1 filter, 2 integrator,
  * 3 unused (list rebuilds run inside the force launch), 4 force (pair
  * potential: the step kernel, with a list rebuild when one is due and, for

@@ -501,7 +501,7 @@ ProfMark::~ProfMark()
 // Positions of step s are in pos[s & 1].  Unfused: integrate, force.  Fused
 // (one-bead systems): integrate once, then one force launch per step, each but
 // the last also doing the first half of the next step.  A list rebuild, when
-// requested, runs inside the force launch.  Profiling samples every 16th step
+// requested, runs inside the force launch.  Profiling samples every 64th step
 // of a captured block (event nodes cost about a microsecond each, so they are
 // not put on every launch).
 int run_steps(qtb_ctx *c, int j0, int count, bool graph)
@@ -511,7 +511,7 @@ int run_steps(qtb_ctx *c, int j0, int count, bool graph)
     for (int t = 0; t < count; ++t) {
         const int j = j0 + t, cur = j & 1;
         const bool keep = c->capturing;
-        if (j % 16 != 0) c->capturing = false;
+        if (j % 64 != 0) c->capturing = false;
         if (!m.fused || t == 0) {
             ProfMark pm(c, KC_INTEGRATE);
             launch_integrate(c->d, m, j, cur, c->st);

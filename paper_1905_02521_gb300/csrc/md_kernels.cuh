@@ -189,7 +189,9 @@ static __device__ void grid_barrier(const Dev &d)
         } else {
             long long spins = 0;
             while (*gen == g0) {
-                if (++spins > (1LL << 25)) {
+                // bounded; after one timeout every later barrier of the launch gives up at once
+                if (++spins > (1LL << 25) ||
+                    ((spins & 1023) == 0 && (*(volatile const unsigned *)d.err & (unsigned)ERR_TIMEOUT_BAR))) {
                     atomicOr(d.err, (unsigned)ERR_TIMEOUT_BAR);
                     break;
                 }
