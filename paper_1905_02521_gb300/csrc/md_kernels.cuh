@@ -353,42 +353,79 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
 
 // Ring-polymer integrator for P >= 2 with the normal-mode transforms in shared
 // memory.  A CTA takes A atoms of one system, i.e. 3 A columns (component c,
-// atom a; col = c A + a) of P beads, V = 3 A P values.  Phase 1 (thread per
-// (bead b, column)): relative bead positions and half-kicked bead velocities
-// (B, dt/2) into shared memory.  Phase 2 (thread per (mode k, column)): the
-// forward transforms, A(dt/2) O(dt) A(dt/2) of mode k.  Phase 3 (thread per
-// (bead, column), the mapping of phase 1): back to beads, each bead moved
-// within its own periodic image.  Phase 4 (thread per (bead, column)): spring
-// energy; the threads of component 0 write the packed position and test the
-// bead-atom's displacement against skin/2.  Every thread issues all of its
-// global loads of a phase before it uses them.  BIG (large contexts): 32 atoms
-// per CTA, so that the 32 threads of a warp read 128 contiguous bytes.
+// atom a; col = c A + a) of P beads, V = 3 A P values.  A thread task is MT
+// consecutive rows (beads or modes) of one column (register tiling: one shared
+// load of a value feeds MT multiply-adds; MT = 1 for small rings).  Phase 1
+// (task = beads): relative bead positions and half-kicked bead velocities
+// (B, dt/2) into shared memory.  Phase 2 (task = modes): the forward
+// transforms, A(dt/2) O(dt) A(dt/2) of each mode.  Phase 3 (task = beads, the
+// mapping of phase 1): back to beads, each bead moved within its own periodic
+// image.  Phase 4: spring energy; the tasks of component 0 write the packed
+// positions and test each bead-atom's displacement against skin/2.  Every sum
+// over beads or modes runs in ascending order, whatever the tiling, so that
+// every layout rounds alike.  BIG (large contexts): 32 atoms per CTA, so that
+// the 32 threads of a warp read 128 contiguous bytes.
+__host__ __device__ constexpr int nm_rows(int P) { return P >= 16 ? 4 : 1; }
 __host__ __device__ constexpr int nm_atoms(int P, int big) { return big ? 32 : (P >= 16 ? 768 : 192) / (3 * P); }
-__host__ __device__ constexpr int nm_threads(int P, int big) { return big ? (P >= 8 ? 256 : 128) : (P >= 16 ? 128 : 64); }
+// compact layout: one thread per task (the transforms are latency-bound chains
+// of P multiply-adds; few CTAs per SM at these sizes)
+__host__ __device__ constexpr int nm_threads(int P, int big)
+{
+    return big ? (P >= 8 ? 256 : 128) : (3 * nm_atoms(P, 0) * P / nm_rows(P) + 31) / 32 * 32;
+}
 
 template <int P, int PM, class R>
 __host__ __device__ constexpr size_t nm_smem(int big)
 {
-    return (size_t)3 * nm_atoms(P, big) * P * (2 * sizeof(R) + sizeof(typename PosT<PM, R>::S)) + (size_t)P * P * sizeof(R);
+    return (size_t)3 * nm_atoms(P, big) * P * (2 * sizeof(R) + sizeof(typename PosT<PM, R>::S)) +
+           (size_t)P * P * sizeof(R) * (nm_rows(P) > 1 ? 2 : 1);
+}
+
+// MT consecutive coefficients from shared memory (16-byte aligned when MT = 4)
+template <int MT> __device__ __forceinline__ void nm_row(const float *p, float (&c)[MT])
+{
+    if constexpr (MT == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+    } else {
+#pragma unroll
+        for (int m = 0; m < MT; ++m) c[m] = p[m];
+    }
+}
+template <int MT> __device__ __forceinline__ void nm_row(const double *p, double (&c)[MT])
+{
+    if constexpr (MT == 4) {
+        const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+        c[0] = a.x; c[1] = a.y; c[2] = b.x; c[3] = b.y;
+    } else {
+#pragma unroll
+        for (int m = 0; m < MT; ++m) c[m] = p[m];
+    }
 }
 
 template <int P, int PM, class R, int BIG>
 __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int j, int cur)
 {
     typedef typename PosT<PM, R>::S PS;
-    constexpr int NT = nm_threads(P, BIG), A = nm_atoms(P, BIG);
-    constexpr int COLS = 3 * A, NV = COLS * P, PER = (NV + NT - 1) / NT;
+    constexpr int NT = nm_threads(P, BIG), A = nm_atoms(P, BIG), MT = nm_rows(P), NG = P / MT;
+    constexpr int COLS = 3 * A, NV = COLS * P, NTASK = NG * COLS, PER = (NTASK + NT - 1) / NT;
+    static_assert(P % MT == 0, "rows per task must divide P");
     extern __shared__ __align__(16) unsigned char nsm[];
     R *xs = reinterpret_cast<R *>(nsm);            // [b or k][col]
     R *ps = xs + NV;
     R *Cs = ps + NV;                               // [b][k]
-    PS *xn_s = reinterpret_cast<PS *>(Cs + P * P); // new positions [b][col]
+    R *CsT = Cs + P * P;                           // [k][b] (MT > 1)
+    PS *xn_s = reinterpret_cast<PS *>(CsT + (MT > 1 ? P * P : 0));  // new positions [b][col]
     __shared__ double red[NT / 32][kNQ];
     const int cta = blockIdx.x;
     const int s = d.icta_sys[cta];
     const DSys S = d.sys[s];
     if (S.P != P) return;  // another instantiation handles this system (uniform over the CTA)
-    for (int t = threadIdx.x; t < P * P; t += NT) Cs[t] = reinterpret_cast<const R *>(d.nmC)[S.nm0 + t];
+    for (int t = threadIdx.x; t < P * P; t += NT) {
+        const R cv = reinterpret_cast<const R *>(d.nmC)[S.nm0 + t];
+        Cs[t] = cv;
+        if (MT > 1) CsT[(t % P) * P + t / P] = cv;  // t = b P + k
+    }
     const int N = S.N;
     const int i0 = (cta - S.icta0) * A;
     const size_t G = (size_t)d.G;
@@ -397,109 +434,159 @@ __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int 
     const R *F = reinterpret_cast<const R *>(d.f);
     const R *hdt = reinterpret_cast<const R *>(d.hdt_m);
     // phase 1: loads, then relative positions and B(dt/2) velocities, bead space
-    PS xold[PER], x0v[PER];
-    R vv[PER], fv[PER], xrel[PER];
+    PS xold[PER][MT], x0v[PER];
+    R vv[PER][MT], fv[PER][MT], xrel[PER][MT];
     int tt[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int idx = threadIdx.x + u * NT;
-        const int b = idx / COLS, col = idx - b * COLS;
+        const int g = idx / COLS, col = idx - g * COLS;
         const int c = col / A, i = i0 + (col - c * A);
-        xold[u] = x0v[u] = PS(0);
-        vv[u] = fv[u] = R(0);
+        x0v[u] = PS(0);
         tt[u] = 0;
-        if (idx < NV && i < N) {
-            const size_t o0 = (size_t)c * G + S.g0 + i, o = o0 + (size_t)b * N;
-            xold[u] = X[o];
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+            xold[u][m] = PS(0);
+            vv[u][m] = fv[u][m] = R(0);
+        }
+        if (idx < NTASK && i < N) {
+            const size_t o0 = (size_t)c * G + S.g0 + i;
             x0v[u] = X[o0];
-            vv[u] = V[o];
-            fv[u] = F[o];
             tt[u] = d.typ[S.g0 + i];
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                const size_t o = o0 + (size_t)(g * MT + m) * N;
+                xold[u][m] = X[o];
+                vv[u][m] = V[o];
+                fv[u][m] = F[o];
+            }
         }
     }
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int idx = threadIdx.x + u * NT;
-        if (idx >= NV) continue;
-        const int b = idx / COLS, col = idx - b * COLS;
+        if (idx >= NTASK) continue;
+        const int g = idx / COLS, col = idx - g * COLS;
         const int c = col / A;
-        const R xr = (b == 0) ? R(0) : PosT<PM, R>::rel(xold[u], x0v[u], S.box[c], S.fix_scale[c], S.fix_inv[c]);
-        xrel[u] = xr;
-        xs[idx] = xr;
-        ps[idx] = fma(hdt[tt[u]], fv[u], vv[u]);
+        const R hd = hdt[tt[u]];
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+            const int b = g * MT + m;
+            const R xr = (b == 0) ? R(0) : PosT<PM, R>::rel(xold[u][m], x0v[u], S.box[c], S.fix_scale[c], S.fix_inv[c]);
+            xrel[u][m] = xr;
+            xs[b * COLS + col] = xr;
+            ps[b * COLS + col] = fma(hd, fv[u][m], vv[u][m]);
+        }
     }
     __syncthreads();
     // phase 2: to modes, A O A per mode
     const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
     const R *eta = reinterpret_cast<const R *>(d.eta) + eta_row(d, j) * d.Dtot + S.dof0;
     const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
-    R qv[PER], pm[PER], noise[PER];
+    R qv[PER][MT], pm[PER][MT];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int idx = threadIdx.x + u * NT;
-        const int k = idx / COLS, col = idx - k * COLS;
+        const int g = idx / COLS, col = idx - g * COLS;
         const int c = col / A, i = i0 + (col - c * A);
-        noise[u] = R(0);
-        if (idx < NV && i < N) {
-            const R sig = reinterpret_cast<const R *>(d.osig)[s * kMaxTypes + d.typ[S.g0 + i]];
-            noise[u] = sig * eta[(size_t)(k * 3 + c) * N + i];
-        }
-    }
+        R noise[MT];
 #pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        qv[u] = pm[u] = R(0);
-        if (idx >= NV) continue;
-        const int k = idx / COLS, col = idx - k * COLS;
-        R q = 0, p = 0;
-#pragma unroll 8
-        for (int b = 0; b < P; ++b) {
-            q = fma(Cs[b * P + k], xs[b * COLS + col], q);
-            p = fma(Cs[b * P + k], ps[b * COLS + col], p);
+        for (int m = 0; m < MT; ++m) noise[m] = R(0);
+        if (idx < NTASK && i < N) {
+            const R sig = reinterpret_cast<const R *>(d.osig)[s * kMaxTypes + tt[u]];
+#pragma unroll
+            for (int m = 0; m < MT; ++m) noise[m] = sig * eta[(size_t)((g * MT + m) * 3 + c) * N + i];
         }
-        mode_aoa(q, p, rot[3 * k], rot[3 * k + 1], rot[3 * k + 2], c1, noise[u]);
-        qv[u] = q;
-        pm[u] = p;
+        R q[MT], p[MT];
+#pragma unroll
+        for (int m = 0; m < MT; ++m) q[m] = p[m] = R(0);
+        if (idx < NTASK) {
+#pragma unroll 8
+            for (int b = 0; b < P; ++b) {
+                const R xv = xs[b * COLS + col], pv = ps[b * COLS + col];
+                R cf[MT];
+                nm_row<MT>(Cs + b * P + g * MT, cf);
+#pragma unroll
+                for (int m = 0; m < MT; ++m) {
+                    q[m] = fma(cf[m], xv, q[m]);
+                    p[m] = fma(cf[m], pv, p[m]);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                const int k = g * MT + m;
+                mode_aoa(q[m], p[m], rot[3 * k], rot[3 * k + 1], rot[3 * k + 2], c1, noise[m]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+            qv[u][m] = q[m];
+            pm[u][m] = p[m];
+        }
     }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int idx = threadIdx.x + u * NT;
-        if (idx < NV) {
-            xs[idx] = qv[u];
-            ps[idx] = pm[u];
+        if (idx >= NTASK) continue;
+        const int g = idx / COLS, col = idx - g * COLS;
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+            xs[(g * MT + m) * COLS + col] = qv[u][m];
+            ps[(g * MT + m) * COLS + col] = pm[u][m];
         }
     }
     __syncthreads();
     // phase 3: back to beads (positions stay in each bead's own image)
+    const R *Cb = (MT > 1) ? CsT : Cs;  // C[b][k] at CsT[k P + b] (tiled) or Cs[b P + k]
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int idx = threadIdx.x + u * NT;
-        if (idx >= NV) continue;
-        const int b = idx / COLS, col = idx - b * COLS;
-        R x = 0, w = 0;
+        if (idx >= NTASK) continue;
+        const int g = idx / COLS, col = idx - g * COLS;
+        R x[MT], w[MT];
+#pragma unroll
+        for (int m = 0; m < MT; ++m) x[m] = w[m] = R(0);
 #pragma unroll 8
         for (int k = 0; k < P; ++k) {
-            x = fma(Cs[b * P + k], xs[k * COLS + col], x);
-            w = fma(Cs[b * P + k], ps[k * COLS + col], w);
+            const R qk = xs[k * COLS + col], pk = ps[k * COLS + col];
+            R cf[MT];
+            if (MT > 1) {
+                nm_row<MT>(Cb + k * P + g * MT, cf);
+            } else {
+#pragma unroll
+                for (int m = 0; m < MT; ++m) cf[m] = Cb[(g * MT + m) * P + k];
+            }
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                x[m] = fma(cf[m], qk, x[m]);
+                w[m] = fma(cf[m], pk, w[m]);
+            }
         }
-        qv[u] = x;  // new relative position
-        pm[u] = w;  // new velocity
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+            qv[u][m] = x[m];  // new relative position
+            pm[u][m] = w[m];  // new velocity
+        }
     }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int idx = threadIdx.x + u * NT;
-        if (idx >= NV) continue;
-        const int b = idx / COLS, col = idx - b * COLS;
+        if (idx >= NTASK) continue;
+        const int g = idx / COLS, col = idx - g * COLS;
         const int c = col / A, i = i0 + (col - c * A);
-        xs[idx] = qv[u];
-        if (i < N) {
-            const size_t o = (size_t)c * G + S.g0 + (size_t)b * N + i;
-            V[o] = pm[u];
-            const PS xn = PosT<PM, R>::add(xold[u], qv[u] - xrel[u], S.box[c], S.fix_scale[c], S.fix_inv[c]);
-            X[o] = xn;
-            xn_s[idx] = xn;
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+            const int b = g * MT + m;
+            xs[b * COLS + col] = qv[u][m];
+            if (i < N) {
+                const size_t o = (size_t)c * G + S.g0 + (size_t)b * N + i;
+                V[o] = pm[u][m];
+                const PS xn = PosT<PM, R>::add(xold[u][m], qv[u][m] - xrel[u][m], S.box[c], S.fix_scale[c], S.fix_inv[c]);
+                X[o] = xn;
+                xn_s[b * COLS + col] = xn;
+            }
         }
     }
     __syncthreads();
@@ -510,30 +597,34 @@ __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int 
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int idx = threadIdx.x + u * NT;
-        if (idx >= NV) continue;
-        const int b = idx / COLS, col = idx - b * COLS;
+        if (idx >= NTASK) continue;
+        const int g = idx / COLS, col = idx - g * COLS;
         const int c = col / A, a = col - c * A, i = i0 + a;
         if (i >= N) continue;
-        const R dx = xs[idx] - xs[((b + 1) % P) * COLS + col];
-        spring += 0.5 * d.mass_mvv[tt[u]] * S.wP * S.wP * (double)(dx * dx);
-        if (PM != PM_FREE && c == 0) {
-            const size_t g = S.g0 + (size_t)b * N + i;
-            const PS *XR = reinterpret_cast<const PS *>(d.xref);
-            R tot = 0;
-            PS w3[3];
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                w3[cc] = xn_s[b * COLS + cc * A + a];
-                const R dc = PosT<PM, R>::diff(w3[cc], XR[(size_t)cc * G + g], S.fix_scale[cc]);
-                tot = fma(dc, dc, tot);
-            }
-            moved |= tot > lim;
-            if (PM == PM_FIX) {
-                int4 *pk = reinterpret_cast<int4 *>(d.pos[cur]);
-                pk[g] = make_int4((int)w3[0], (int)w3[1], (int)w3[2], tt[u]);
-            } else {
-                D4 *pk = reinterpret_cast<D4 *>(d.pos[cur]);
-                pk[g] = D4{(double)w3[0], (double)w3[1], (double)w3[2], (double)tt[u]};
+        for (int m = 0; m < MT; ++m) {
+            const int b = g * MT + m;
+            const R dx = xs[b * COLS + col] - xs[((b + 1) % P) * COLS + col];
+            spring += 0.5 * d.mass_mvv[tt[u]] * S.wP * S.wP * (double)(dx * dx);
+            if (PM != PM_FREE && c == 0) {
+                const size_t gg = S.g0 + (size_t)b * N + i;
+                const PS *XR = reinterpret_cast<const PS *>(d.xref);
+                R tot = 0;
+                PS w3[3];
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    w3[cc] = xn_s[b * COLS + cc * A + a];
+                    const R dc = PosT<PM, R>::diff(w3[cc], XR[(size_t)cc * G + gg], S.fix_scale[cc]);
+                    tot = fma(dc, dc, tot);
+                }
+                moved |= tot > lim;
+                if (PM == PM_FIX) {
+                    int4 *pk = reinterpret_cast<int4 *>(d.pos[cur]);
+                    pk[gg] = make_int4((int)w3[0], (int)w3[1], (int)w3[2], tt[u]);
+                } else {
+                    D4 *pk = reinterpret_cast<D4 *>(d.pos[cur]);
+                    pk[gg] = D4{(double)w3[0], (double)w3[1], (double)w3[2], (double)tt[u]};
+                }
             }
         }
     }

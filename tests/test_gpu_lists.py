@@ -112,11 +112,11 @@ def test_pimd_beads_keep_their_images(qtb, oracle):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_integrator_layouts_are_bit_identical(qtb, precision):
+@pytest.mark.parametrize("P", [8, 32])
+def test_integrator_layouts_are_bit_identical(qtb, precision, P):
     # the compact and the wide layout of the ring-polymer integrator do the same
     # arithmetic per value: identical trajectories, through graph blocks and
-    # direct launches
-    P = 8
+    # direct launches (P = 32: four rows per thread task in both layouts)
     s, pot = W.mgo_system(3, 300.0, n_beads=P, seed=6)
     N = len(s["types"])
     out = []

@@ -141,14 +141,16 @@ def test_fp64_qtb_trajectory_matches_oracle(qtb, oracle):
     _traj_compare(qtb, oracle, s, pot, 1.0, qtb.NOISE_QTB, 513, 0.3, 100, 10, 1e-12)
 
 
-def test_fp64_pimd_trajectory_matches_oracle(qtb, oracle):
-    # white-noise PIMD, P = 4: normal-mode integrator and per-bead forces
-    s, pot = W.mgo_system(2, 300.0, n_beads=4)
+@pytest.mark.parametrize("P", [4, 16])
+def test_fp64_pimd_trajectory_matches_oracle(qtb, oracle, P):
+    # white-noise PIMD: normal-mode integrator (P = 16: register-tiled transforms)
+    # and per-bead forces
+    s, pot = W.mgo_system(2, 300.0, n_beads=P)
     rng = np.random.default_rng(5)
     s["pos"] = s["pos"] + rng.normal(0, 0.01, s["pos"].shape)
     # (rounding-order differences of 1e-16 grow along the stiff ring-polymer
     # trajectory to ~1e-12 after 60 steps: state compared at 1e-11)
-    _traj_compare(qtb, oracle, s, pot, 0.5, qtb.NOISE_WHITE, 1, 0.0, 60, 20, 1e-11, P=4)
+    _traj_compare(qtb, oracle, s, pot, 0.5, qtb.NOISE_WHITE, 1, 0.0, 60, 20, 1e-11, P=P)
 
 
 def test_mixed_forces_on_own_configuration_first_100_steps(qtb, oracle):
