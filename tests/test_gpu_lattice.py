@@ -143,7 +143,10 @@ def test_qtb_energy_and_bands_follow_the_quantum_harmonic_crystal(qtb, lattice):
 
 
 def test_friction_broadens_the_spectrum(qtb, lattice):
-    tails, preds = [], []
+    """Friction sweep at 20 K: the high-frequency tail follows the Langevin prediction, and
+    the zero-point energy leakage of Sec. 2.2 (kinetic energy moved from the high- to the
+    low-frequency modes, against the harmonic share of each band) shrinks as gamma grows."""
+    tails, preds, dev = [], [], []
     for gamma in (0.005, 0.02, 0.08):
         vs, _ = run(qtb, lattice, gamma, 16384, seed=9)
         om, g, dw = kinetic_spectrum(vs, lattice["pot"]["mass"][lattice["t"]])
@@ -152,12 +155,22 @@ def test_friction_broadens_the_spectrum(qtb, lattice):
         pred = predicted(lattice, gamma, TAIL, 0.6) / predicted(lattice, gamma, 0.0, 0.6)
         print("gamma %.3f: kinetic-energy fraction above %.2f rad/fs: measured %.4f predicted %.4f"
               % (gamma, TAIL, meas, pred))
+        dev.append([])
+        for lo, hi in BANDS:
+            bm, bp = band(om, g, dw, lo, hi), predicted(lattice, gamma, lo, hi)
+            dev[-1].append(bm / bp - 1.0)
+            print("    band %.2f-%.2f: measured/predicted - 1 = %+.3f" % (lo, hi, bm / bp - 1.0))
         tails.append(meas)
         preds.append(pred)
     assert tails[0] < tails[1] < tails[2]
     assert preds[2] > 5 * preds[0]
     for m, p in zip(tails, preds):
         assert m == pytest.approx(p, rel=0.1)
+    # leakage: low band in excess, the 0.14-0.17 band in deficit, both shrinking with gamma
+    low, high = [dv[0] for dv in dev], [dv[2] for dv in dev]
+    assert low[0] > low[1] > low[2] > -0.01 and low[0] > 0.04
+    assert high[0] < high[1] < high[2] < 0.01 and high[0] < -0.1
+    assert max(abs(x) for x in dev[2]) < 0.02
 
 
 def _taps_density(Tk):
