@@ -19,7 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libqtb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# the MD sources (md_kernels.cuh) write every fused multiply-add out explicitly (the integrator and the
+# the MD sources (md_kernels.cuh, md_integrate.cuh) write every fused multiply-add out explicitly (the integrator and the
 # fused force epilogue must round alike): no automatic contraction there
 EXTRA = {f: ["--fmad=false"] for f in ("md.cu", "md_step8.cu", "md_step16.cu", "md_step32.cu")}
 

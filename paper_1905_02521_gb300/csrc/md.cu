@@ -1,6 +1,7 @@
 // md.cu -- integrators, external potentials, reductions and the launchers of
-// the MD hot path (sm_103a); the device code is in md_kernels.cuh.
-#include "md_kernels.cuh"
+// the MD hot path (sm_103a); the device code is in md_kernels.cuh and
+// md_integrate.cuh.
+#include "md_integrate.cuh"
 
 namespace qtb {
 

@@ -1,7 +1,8 @@
-// md_kernels.cuh -- device code of the MD hot path (sm_103a), included by md.cu
-// (integrators, external forces, launchers) and by md_step8.cu, md_step16.cu and
-// md_step32.cu (the step kernel for 8, 16 and 32 lanes per bead-atom, compiled in
-// parallel).
+// md_kernels.cuh -- device code of the MD hot path (sm_103a) shared by the
+// integrators (md_integrate.cuh, md.cu) and the step kernel (md_step8.cu,
+// md_step16.cu and md_step32.cu: 8, 16 and 32 lanes per bead-atom, compiled in
+// parallel): position representations, reductions, the grid barrier, the mode
+// propagator, the list rebuild, the pair force and the step kernel itself.
 //
 // Eq. 4: every bead feels -(1/P) grad V of its own replica plus the ring
 // springs; the springs are integrated exactly in normal-mode space (Sec. 2.3,
@@ -217,422 +218,6 @@ __device__ __forceinline__ void mode_aoa(R &q, R &p, R cs, R sw, R ws, R c1, R n
     pn = fma(c1, pn, noise);
     q = fma(pn, sw, qn * cs);
     p = fma(pn, cs, qn * ws);
-}
-
-// ---------------------------------------------------------------------------
-// Integrator: B(dt/2) in bead space, then A(dt/2) O A(dt/2) in normal-mode
-// space.  Lane 3a + c (a < 10) of a warp takes Cartesian component c of atom
-// i with all of its P beads, so that the three components of a bead-atom meet
-// in one warp for the neighbour-list displacement test.  Writes the new
-// positions to x and (pair potential) to the packed copy pos[cur] that the
-// force kernel gathers from, and requests a list rebuild (flag[cur]) when a
-// bead-atom has moved more than skin/2 since the last one.
-
-template <int P, int PM, class R>
-__global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
-{
-    constexpr int UN = (P <= 8) ? P : 1;  // full unroll only for small rings
-    typedef typename PosT<PM, R>::S PS;
-    __shared__ R Cs[P * P];
-    __shared__ double red[4][kNQ];
-    const int cta = blockIdx.x;
-    const int s = d.icta_sys[cta];
-    const DSys S = d.sys[s];
-    const bool mine = (S.P == P);  // another instantiation handles the other systems
-    if (mine)
-        for (int t = threadIdx.x; t < P * P; t += blockDim.x) Cs[t] = reinterpret_cast<const R *>(d.nmC)[S.nm0 + t];
-    __syncthreads();
-    const int N = S.N;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int aw = lane / 3, c = lane - 3 * aw;
-    const int i = (cta - S.icta0) * kIntAtomsPerCta + warp * kIntAtomsPerWarp + aw;
-    const bool act = mine && aw < kIntAtomsPerWarp && i < N;
-    double acc[kNQ];
-    for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
-    double spring = 0.0;
-    PS *X = reinterpret_cast<PS *>(d.x);
-    const size_t G = (size_t)d.G;
-    const size_t base = act ? (size_t)c * G + S.g0 + i : 0;
-    const float fsc = S.fix_scale[c], finv = S.fix_inv[c];
-    PS x0{};
-    R a[P], a0[P];  // bead positions relative to bead 0: new, old
-    if (act) {
-        R *V = reinterpret_cast<R *>(d.v);
-        const R *F = reinterpret_cast<const R *>(d.f);
-        const int t = d.typ[S.g0 + i];
-        const R hdtm = reinterpret_cast<const R *>(d.hdt_m)[t];
-        const R sig = reinterpret_cast<const R *>(d.osig)[s * kMaxTypes + t];
-        const double L = S.box[c];
-        x0 = X[base];
-        R q[P];
-        // relative bead positions -> modes
-#pragma unroll(UN)
-        for (int b = 0; b < P; ++b) {
-            a[b] = (b == 0) ? R(0) : PosT<PM, R>::rel(X[base + (size_t)b * N], x0, L, fsc, finv);
-            a0[b] = a[b];
-        }
-#pragma unroll(UN)
-        for (int k = 0; k < P; ++k) {
-            R u = 0;
-#pragma unroll(UN)
-            for (int b = 0; b < P; ++b) u = fma(Cs[b * P + k], a[b], u);
-            q[k] = u;
-        }
-        // B: half kick with the current forces, bead velocities -> modes
-#pragma unroll(UN)
-        for (int b = 0; b < P; ++b) a[b] = fma(hdtm, F[base + (size_t)b * N], V[base + (size_t)b * N]);
-        R p[P];
-#pragma unroll(UN)
-        for (int k = 0; k < P; ++k) {
-            R u = 0;
-#pragma unroll(UN)
-            for (int b = 0; b < P; ++b) u = fma(Cs[b * P + k], a[b], u);
-            p[k] = u;
-        }
-        const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
-        const R *eta = reinterpret_cast<const R *>(d.eta) + eta_row(d, j) * d.Dtot + S.dof0;
-        const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
-#pragma unroll(UN)
-        for (int k = 0; k < P; ++k)
-            mode_aoa(q[k], p[k], rot[3 * k], rot[3 * k + 1], rot[3 * k + 2], c1, sig * eta[(size_t)(k * 3 + c) * N + i]);
-        // modes -> beads
-#pragma unroll(UN)
-        for (int b = 0; b < P; ++b) {
-            R u = 0, w = 0;
-#pragma unroll(UN)
-            for (int k = 0; k < P; ++k) {
-                u = fma(Cs[b * P + k], q[k], u);
-                w = fma(Cs[b * P + k], p[k], w);
-            }
-            a[b] = u;
-            V[base + (size_t)b * N] = w;
-        }
-        if (P > 1) {
-            R sp = 0;
-#pragma unroll(UN)
-            for (int b = 0; b < P; ++b) {
-                R dd = a[b] - a[(b + 1) % P];
-                sp = fma(dd, dd, sp);
-            }
-            spring = 0.5 * d.mass_mvv[t] * S.wP * S.wP * (double)sp;
-        }
-    }
-    // new bead positions: each bead moves by the change of its position relative
-    // to bead 0, so that it stays in its own periodic image (after a list rebuild
-    // the beads of an atom on the box boundary may be wrapped into different
-    // images); with a pair potential also the packed copy and the displacement
-    // test (the three components meet through shuffles)
-    bool moved = false;
-    const int l0 = 3 * aw;
-#pragma unroll(UN)
-    for (int b = 0; b < P; ++b) {
-        R dd = 0;
-        if (act) {
-            const size_t o = base + (size_t)b * N;
-            const PS xn = PosT<PM, R>::add(X[o], a[b] - a0[b], S.box[c], fsc, finv);
-            X[o] = xn;
-            if (PM != PM_FREE) {
-                const size_t g = S.g0 + (size_t)b * N + i;
-                reinterpret_cast<PS *>(d.pos[cur])[4 * g + c] = xn;
-                const R dc = PosT<PM, R>::diff(xn, reinterpret_cast<const PS *>(d.xref)[o], fsc);
-                dd = dc * dc;
-            }
-        }
-        if (PM != PM_FREE) {
-            const R tot = __shfl_sync(0xffffffffu, dd, l0 & 31) + __shfl_sync(0xffffffffu, dd, (l0 + 1) & 31) +
-                          __shfl_sync(0xffffffffu, dd, (l0 + 2) & 31);
-            const R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
-            moved |= act && c == 0 && tot > lim;
-        }
-    }
-    if (PM != PM_FREE && __any_sync(0xffffffffu, moved) && lane == 0) atomicOr(&d.flag[cur], 1u);
-    spring = warp_sum(spring);
-    acc[Q_SPRING] = spring;
-    if (mine) cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
-}
-
-// Ring-polymer integrator for P >= 2 with the normal-mode transforms in shared
-// memory.  A CTA takes A atoms of one system, i.e. 3 A columns (component c,
-// atom a; col = c A + a) of P beads, V = 3 A P values.  A thread task is MT
-// consecutive rows (beads or modes) of one column (register tiling: one shared
-// load of a value feeds MT multiply-adds; MT = 1 for small rings).  Phase 1
-// (task = beads): relative bead positions and half-kicked bead velocities
-// (B, dt/2) into shared memory.  Phase 2 (task = modes): the forward
-// transforms, A(dt/2) O(dt) A(dt/2) of each mode.  Phase 3 (task = beads, the
-// mapping of phase 1): back to beads, each bead moved within its own periodic
-// image.  Phase 4: spring energy; the tasks of component 0 write the packed
-// positions and test each bead-atom's displacement against skin/2.  Every sum
-// over beads or modes runs in ascending order, whatever the tiling, so that
-// every layout rounds alike.  BIG (large contexts): 32 atoms per CTA, so that
-// the 32 threads of a warp read 128 contiguous bytes.
-__host__ __device__ constexpr int nm_rows(int P) { return P >= 16 ? 4 : 1; }
-__host__ __device__ constexpr int nm_atoms(int P, int big) { return big ? 32 : (P >= 16 ? 768 : 192) / (3 * P); }
-// compact layout: one thread per task (the transforms are latency-bound chains
-// of P multiply-adds; few CTAs per SM at these sizes)
-__host__ __device__ constexpr int nm_threads(int P, int big)
-{
-    return big ? (P >= 8 ? 256 : 128) : (3 * nm_atoms(P, 0) * P / nm_rows(P) + 31) / 32 * 32;
-}
-
-template <int P, int PM, class R>
-__host__ __device__ constexpr size_t nm_smem(int big)
-{
-    return (size_t)3 * nm_atoms(P, big) * P * (2 * sizeof(R) + sizeof(typename PosT<PM, R>::S)) +
-           (size_t)P * P * sizeof(R) * (nm_rows(P) > 1 ? 2 : 1);
-}
-
-// MT consecutive coefficients from shared memory (16-byte aligned when MT = 4)
-template <int MT> __device__ __forceinline__ void nm_row(const float *p, float (&c)[MT])
-{
-    if constexpr (MT == 4) {
-        const float4 v = *reinterpret_cast<const float4 *>(p);
-        c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
-    } else {
-#pragma unroll
-        for (int m = 0; m < MT; ++m) c[m] = p[m];
-    }
-}
-template <int MT> __device__ __forceinline__ void nm_row(const double *p, double (&c)[MT])
-{
-    if constexpr (MT == 4) {
-        const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
-        c[0] = a.x; c[1] = a.y; c[2] = b.x; c[3] = b.y;
-    } else {
-#pragma unroll
-        for (int m = 0; m < MT; ++m) c[m] = p[m];
-    }
-}
-
-template <int P, int PM, class R, int BIG>
-__global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int j, int cur)
-{
-    typedef typename PosT<PM, R>::S PS;
-    constexpr int NT = nm_threads(P, BIG), A = nm_atoms(P, BIG), MT = nm_rows(P), NG = P / MT;
-    constexpr int COLS = 3 * A, NV = COLS * P, NTASK = NG * COLS, PER = (NTASK + NT - 1) / NT;
-    static_assert(P % MT == 0, "rows per task must divide P");
-    extern __shared__ __align__(16) unsigned char nsm[];
-    R *xs = reinterpret_cast<R *>(nsm);            // [b or k][col]
-    R *ps = xs + NV;
-    R *Cs = ps + NV;                               // [b][k]
-    R *CsT = Cs + P * P;                           // [k][b] (MT > 1)
-    PS *xn_s = reinterpret_cast<PS *>(CsT + (MT > 1 ? P * P : 0));  // new positions [b][col]
-    __shared__ double red[NT / 32][kNQ];
-    const int cta = blockIdx.x;
-    const int s = d.icta_sys[cta];
-    const DSys S = d.sys[s];
-    if (S.P != P) return;  // another instantiation handles this system (uniform over the CTA)
-    for (int t = threadIdx.x; t < P * P; t += NT) {
-        const R cv = reinterpret_cast<const R *>(d.nmC)[S.nm0 + t];
-        Cs[t] = cv;
-        if (MT > 1) CsT[(t % P) * P + t / P] = cv;  // t = b P + k
-    }
-    const int N = S.N;
-    const int i0 = (cta - S.icta0) * A;
-    const size_t G = (size_t)d.G;
-    PS *X = reinterpret_cast<PS *>(d.x);
-    R *V = reinterpret_cast<R *>(d.v);
-    const R *F = reinterpret_cast<const R *>(d.f);
-    const R *hdt = reinterpret_cast<const R *>(d.hdt_m);
-    // phase 1: loads, then relative positions and B(dt/2) velocities, bead space
-    PS xold[PER][MT], x0v[PER];
-    R vv[PER][MT], fv[PER][MT], xrel[PER][MT];
-    int tt[PER];
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        const int g = idx / COLS, col = idx - g * COLS;
-        const int c = col / A, i = i0 + (col - c * A);
-        x0v[u] = PS(0);
-        tt[u] = 0;
-#pragma unroll
-        for (int m = 0; m < MT; ++m) {
-            xold[u][m] = PS(0);
-            vv[u][m] = fv[u][m] = R(0);
-        }
-        if (idx < NTASK && i < N) {
-            const size_t o0 = (size_t)c * G + S.g0 + i;
-            x0v[u] = X[o0];
-            tt[u] = d.typ[S.g0 + i];
-#pragma unroll
-            for (int m = 0; m < MT; ++m) {
-                const size_t o = o0 + (size_t)(g * MT + m) * N;
-                xold[u][m] = X[o];
-                vv[u][m] = V[o];
-                fv[u][m] = F[o];
-            }
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        if (idx >= NTASK) continue;
-        const int g = idx / COLS, col = idx - g * COLS;
-        const int c = col / A;
-        const R hd = hdt[tt[u]];
-#pragma unroll
-        for (int m = 0; m < MT; ++m) {
-            const int b = g * MT + m;
-            const R xr = (b == 0) ? R(0) : PosT<PM, R>::rel(xold[u][m], x0v[u], S.box[c], S.fix_scale[c], S.fix_inv[c]);
-            xrel[u][m] = xr;
-            xs[b * COLS + col] = xr;
-            ps[b * COLS + col] = fma(hd, fv[u][m], vv[u][m]);
-        }
-    }
-    __syncthreads();
-    // phase 2: to modes, A O A per mode
-    const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
-    const R *eta = reinterpret_cast<const R *>(d.eta) + eta_row(d, j) * d.Dtot + S.dof0;
-    const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
-    R qv[PER][MT], pm[PER][MT];
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        const int g = idx / COLS, col = idx - g * COLS;
-        const int c = col / A, i = i0 + (col - c * A);
-        R noise[MT];
-#pragma unroll
-        for (int m = 0; m < MT; ++m) noise[m] = R(0);
-        if (idx < NTASK && i < N) {
-            const R sig = reinterpret_cast<const R *>(d.osig)[s * kMaxTypes + tt[u]];
-#pragma unroll
-            for (int m = 0; m < MT; ++m) noise[m] = sig * eta[(size_t)((g * MT + m) * 3 + c) * N + i];
-        }
-        R q[MT], p[MT];
-#pragma unroll
-        for (int m = 0; m < MT; ++m) q[m] = p[m] = R(0);
-        if (idx < NTASK) {
-#pragma unroll 8
-            for (int b = 0; b < P; ++b) {
-                const R xv = xs[b * COLS + col], pv = ps[b * COLS + col];
-                R cf[MT];
-                nm_row<MT>(Cs + b * P + g * MT, cf);
-#pragma unroll
-                for (int m = 0; m < MT; ++m) {
-                    q[m] = fma(cf[m], xv, q[m]);
-                    p[m] = fma(cf[m], pv, p[m]);
-                }
-            }
-#pragma unroll
-            for (int m = 0; m < MT; ++m) {
-                const int k = g * MT + m;
-                mode_aoa(q[m], p[m], rot[3 * k], rot[3 * k + 1], rot[3 * k + 2], c1, noise[m]);
-            }
-        }
-#pragma unroll
-        for (int m = 0; m < MT; ++m) {
-            qv[u][m] = q[m];
-            pm[u][m] = p[m];
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        if (idx >= NTASK) continue;
-        const int g = idx / COLS, col = idx - g * COLS;
-#pragma unroll
-        for (int m = 0; m < MT; ++m) {
-            xs[(g * MT + m) * COLS + col] = qv[u][m];
-            ps[(g * MT + m) * COLS + col] = pm[u][m];
-        }
-    }
-    __syncthreads();
-    // phase 3: back to beads (positions stay in each bead's own image)
-    const R *Cb = (MT > 1) ? CsT : Cs;  // C[b][k] at CsT[k P + b] (tiled) or Cs[b P + k]
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        if (idx >= NTASK) continue;
-        const int g = idx / COLS, col = idx - g * COLS;
-        R x[MT], w[MT];
-#pragma unroll
-        for (int m = 0; m < MT; ++m) x[m] = w[m] = R(0);
-#pragma unroll 8
-        for (int k = 0; k < P; ++k) {
-            const R qk = xs[k * COLS + col], pk = ps[k * COLS + col];
-            R cf[MT];
-            if (MT > 1) {
-                nm_row<MT>(Cb + k * P + g * MT, cf);
-            } else {
-#pragma unroll
-                for (int m = 0; m < MT; ++m) cf[m] = Cb[(g * MT + m) * P + k];
-            }
-#pragma unroll
-            for (int m = 0; m < MT; ++m) {
-                x[m] = fma(cf[m], qk, x[m]);
-                w[m] = fma(cf[m], pk, w[m]);
-            }
-        }
-#pragma unroll
-        for (int m = 0; m < MT; ++m) {
-            qv[u][m] = x[m];  // new relative position
-            pm[u][m] = w[m];  // new velocity
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        if (idx >= NTASK) continue;
-        const int g = idx / COLS, col = idx - g * COLS;
-        const int c = col / A, i = i0 + (col - c * A);
-#pragma unroll
-        for (int m = 0; m < MT; ++m) {
-            const int b = g * MT + m;
-            xs[b * COLS + col] = qv[u][m];
-            if (i < N) {
-                const size_t o = (size_t)c * G + S.g0 + (size_t)b * N + i;
-                V[o] = pm[u][m];
-                const PS xn = PosT<PM, R>::add(xold[u][m], qv[u][m] - xrel[u][m], S.box[c], S.fix_scale[c], S.fix_inv[c]);
-                X[o] = xn;
-                xn_s[b * COLS + col] = xn;
-            }
-        }
-    }
-    __syncthreads();
-    // phase 4: spring energy; packed positions and displacement test per bead-atom
-    double spring = 0.0;
-    bool moved = false;
-    const R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * NT;
-        if (idx >= NTASK) continue;
-        const int g = idx / COLS, col = idx - g * COLS;
-        const int c = col / A, a = col - c * A, i = i0 + a;
-        if (i >= N) continue;
-#pragma unroll
-        for (int m = 0; m < MT; ++m) {
-            const int b = g * MT + m;
-            const R dx = xs[b * COLS + col] - xs[((b + 1) % P) * COLS + col];
-            spring += 0.5 * d.mass_mvv[tt[u]] * S.wP * S.wP * (double)(dx * dx);
-            if (PM != PM_FREE && c == 0) {
-                const size_t gg = S.g0 + (size_t)b * N + i;
-                const PS *XR = reinterpret_cast<const PS *>(d.xref);
-                R tot = 0;
-                PS w3[3];
-#pragma unroll
-                for (int cc = 0; cc < 3; ++cc) {
-                    w3[cc] = xn_s[b * COLS + cc * A + a];
-                    const R dc = PosT<PM, R>::diff(w3[cc], XR[(size_t)cc * G + gg], S.fix_scale[cc]);
-                    tot = fma(dc, dc, tot);
-                }
-                moved |= tot > lim;
-                if (PM == PM_FIX) {
-                    int4 *pk = reinterpret_cast<int4 *>(d.pos[cur]);
-                    pk[gg] = make_int4((int)w3[0], (int)w3[1], (int)w3[2], tt[u]);
-                } else {
-                    D4 *pk = reinterpret_cast<D4 *>(d.pos[cur]);
-                    pk[gg] = D4{(double)w3[0], (double)w3[1], (double)w3[2], (double)tt[u]};
-                }
-            }
-        }
-    }
-    if (PM != PM_FREE && __syncthreads_or(moved) && threadIdx.x == 0) atomicOr(&d.flag[cur], 1u);
-    double acc[kNQ];
-    for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
-    acc[Q_SPRING] = warp_sum(spring);
-    cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
 }
 
 // ---------------------------------------------------------------------------
