@@ -341,7 +341,7 @@ def run_ours(args):
                                         "shared between the per-step kernels in the ratio of their event-timed "
                                         "samples (every 64th step)",
                      "sampled_launch_ms": sampled.get("force")},
-        "roofline_integrator": integrator_roofline(launch_ms, units, sizes, args.precision),
+        "roofline_integrator": integrator_roofline(launch_ms, units, sizes, args.precision, args.workload),
         "kernel_ms_per_bench_step": step_breakdown,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * units * 3 * 8),
@@ -415,7 +415,7 @@ def in_graph_launch_ms(sampled, kernel_n, block_ms, nblocks, sizes):
     return out
 
 
-def integrator_roofline(launch_ms, units, sizes, precision):
+def integrator_roofline(launch_ms, units, sizes, precision, workload_name=None):
     """HBM roofline of the ring-polymer integrator (systems with P > 1; for
     one-bead systems it is fused into the step kernel)."""
     if all(p == 1 for _, p in sizes) or "integrate" not in launch_ms:
@@ -426,7 +426,7 @@ def integrator_roofline(launch_ms, units, sizes, precision):
     achieved = nbytes / (ms * 1e-3) / 1e9
     return {"bound": "hbm", "kernel": "k_integrate_nm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": src, "bytes_per_launch": nbytes, "mean_launch_ms": ms,
-            "traffic": None}
+            "traffic": measured_traffic("k_integrate_nm", workload_name) if workload_name else None}
 
 
 def alu_peak_tflops():
@@ -476,12 +476,15 @@ def oracle_sample(name, ncell, n_sample):
     return one, len(sel), n
 
 
-def cpu_baseline(name, sample_atoms=64, steps=1):
-    """The FP64 oracle timed on a bounded sample of the workload (see oracle_sample)."""
+def cpu_baseline(name, sample_atoms=64, min_seconds=10.0):
+    """The FP64 oracle timed on a bounded sample of the workload (see oracle_sample):
+    as many steps of the sample as fit in about min_seconds of host time."""
     one, k, n = oracle_sample(name, 10, sample_atoms)
     t0 = time.perf_counter()
-    for st in range(steps):
-        one(st)
+    steps = 0
+    while steps == 0 or time.perf_counter() - t0 < min_seconds:
+        one(steps)
+        steps += 1
     dt = time.perf_counter() - t0
     return {"value": k * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{k} of {n} bead-atoms x {steps} step(s): brute-force periodic forces + "
@@ -492,7 +495,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    one, k, n = oracle_sample(args.workload, args.ncell, 32)
+    one, k, n = oracle_sample(args.workload, args.ncell, 512)   # ~0.4 s of host time per step
     for i in range(args.warmup):
         one(i)
     t0 = time.perf_counter()
