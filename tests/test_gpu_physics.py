@@ -7,7 +7,10 @@
   friction correction (quadrature of the Langevin response with the filter's
   own spectral density, Eqs. 6-8), in both forms and with the tensor-core filter.
 * QTB-PIMD on harmonic oscillators gives the bead-averaged <x^2> that Eq. 10
-  demands, theta/(m w0^2), for P = 2, 4, 8.
+  demands, theta/(m w0^2), for P = 2, 4, 8, and the centroid-mode virial
+  estimator (record slot 19) gives the quantum kinetic energy theta/2;
+* standard PIMD: the centroid-virial estimator (slot 18) averages to the
+  finite-P closed form E_P/2 with a smaller fluctuation than the primitive one.
 """
 import numpy as np
 import pytest
@@ -121,3 +124,32 @@ def test_qtb_pimd_harmonic_bead_variance_eq10(qtb, oracle, P):
     assert abs(x2.mean() - x2_q) < 4 * _block_sigma(x2, 16) + 5e-3 * x2_q
     # Eq. 10: without friction the bead average is the quantum value theta/(m w0^2)
     assert x2_q == pytest.approx(S.theta(w0, T) / (m * MVV2E * w0 ** 2), rel=0.05)
+    # centroid-mode estimator (slot 19): the centroid's kinetic energy plus the virial
+    # term (m w0^2 / 2P) sum_{k>0} <q_k^2>, each mode by quadrature; ~theta/2
+    q2 = [_quad_x2_v2(dens, np.sqrt(w0 ** 2 / P + wk[k] ** 2), gamma, m, np.pi / dt)[0] for k in range(P)]
+    v2_0 = _quad_x2_v2(dens, w0 / np.sqrt(P), gamma, m, np.pi / dt)[1]
+    K_q = 0.5 * m * MVV2E * v2_0 + 0.5 * m * MVV2E * w0 ** 2 / P * np.sum(q2[1:])
+    Kcv0 = ser[:, 19] / (3 * 1000)
+    assert abs(Kcv0.mean() - K_q) < 4 * _block_sigma(Kcv0, 16) + 5e-3 * K_q, (Kcv0.mean(), K_q)
+    assert K_q == pytest.approx(0.5 * float(S.theta(w0, T)), rel=0.05)
+
+
+@pytest.mark.parametrize("P", [4, 8])
+def test_pimd_harmonic_centroid_virial_closed_form(qtb, P):
+    # standard PIMD (white bath): <K_cv> = <V> = E_P / 2 per dof (Eqs. 3, 5, 11), with a
+    # fluctuation well below that of the primitive estimator
+    w0, gamma, dt, m = 0.1, 0.01, 0.5, 1.008
+    T = HBAR * w0 / (3.0 * KB)                       # beta hbar w0 = 3
+    sysd, pot = W.oscillators(1000, T, gamma, n_beads=P, mass=m)
+    ctx = gpu_ctx(qtb, [sysd], pot, dt, precision=0, seed=78, potential=qtb.POT_HARMONIC, ext={"omega": w0},
+                  max_records=20000)
+    try:
+        qtb.qtb_step_n(ctx, 4096 + 16384)
+        ser = qtb.qtb_get_series(ctx, 0, 20000)[-16384:]
+    finally:
+        qtb.qtb_destroy(ctx)
+    k = np.arange(P)
+    E_P = KB * T * np.sum(1.0 / (1.0 + (2 * P / 3.0) ** 2 * np.sin(k * np.pi / P) ** 2))
+    Kcv = ser[:, 18] / 3000.0
+    assert abs(Kcv.mean() - 0.5 * E_P) < 4 * _block_sigma(Kcv, 16) + 3e-3 * E_P, (Kcv.mean(), 0.5 * E_P)
+    assert ser[:, 18].std() < 0.5 * (ser[:, 4] - ser[:, 2]).std()
