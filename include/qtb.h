@@ -186,8 +186,12 @@ int qtb_get_series(qtb_ctx *c, int sys, double *out, int max, int *n_out);
  * are wrapped into the box for PAIR systems.  Either pointer may be NULL. */
 int qtb_get_state(qtb_ctx *c, int sys, double *pos, double *vel);
 
-/* Replace positions/velocities of system sys (either may be NULL = keep) and
- * recompute its forces at the current step index. */
+/* Replace positions/velocities of system sys (either may be NULL = keep).  The
+ * forces and the observable record at the current step index are recomputed
+ * once, at the next call that needs them (qtb_step_n, qtb_sync,
+ * qtb_observables, qtb_get_series, qtb_get_state, qtb_get_forces,
+ * qtb_list_rebuilds), so that setting several systems costs one force
+ * evaluation; an error of that evaluation is returned by that call. */
 int qtb_set_state(qtb_ctx *c, int sys, const double *pos, const double *vel);
 
 /* Forces [P][N][3] (eV/A) of system sys at the current positions, including the

@@ -75,6 +75,7 @@ struct qtb_ctx {
     PairTabT<float> tabf{};
     long long step = 0;
     long long dclock = 0;          // host mirror of the device clock
+    bool stale = false;            // a state was set since the last force evaluation
     long long ring_hi = LLONG_MIN; // highest white block in the ring
     long long ring_lo = LLONG_MIN; // lowest white block in the ring
     long long eta_blk = LLONG_MIN; // block whose coloured noise is in eta
@@ -1206,10 +1207,20 @@ int qtb_set_filter(qtb_ctx *c, int sys, int mode, int n_taps, double omega_max)
     return rebuild_filters(c);
 }
 
+// one force evaluation (lists rebuilt, record of the current step) for all the
+// states set since the last one
+static int ensure_fresh(qtb_ctx *c)
+{
+    if (!c->stale) return QTB_OK;
+    c->stale = false;
+    return refresh_forces(c);
+}
+
 int qtb_step_n(qtb_ctx *c, long long n)
 {
     if (!c) return fail(QTB_ERR_ARG, "null context");
     if (n < 0) return fail(QTB_ERR_ARG, "n_steps < 0");
+    if (int rc = ensure_fresh(c)) return rc;
     while (n > 0) {
         const long long b = floor_div(c->step, kBlockSteps);
         const int j = (int)(c->step - b * kBlockSteps);
@@ -1288,6 +1299,7 @@ int qtb_set_generator(qtb_ctx *c, int generator, int segment_blocks)
 int qtb_sync(qtb_ctx *c)
 {
     if (!c) return fail(QTB_ERR_ARG, "null context");
+    if (int rc0 = ensure_fresh(c)) return rc0;
     return check_err_word(c);
 }
 
@@ -1295,6 +1307,7 @@ int qtb_observables(qtb_ctx *c, int sys, double *out)
 {
     if (!c || !out) return fail(QTB_ERR_ARG, "null argument");
     if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
+    if (int rc0 = ensure_fresh(c)) return rc0;
     int rc = check_err_word(c);
     if (rc) return rc;
     CUDA_TRY(cudaMemcpyAsync(out, c->d.latest + (size_t)sys * QTB_NREC, sizeof(double) * QTB_NREC,
@@ -1307,6 +1320,7 @@ int qtb_get_series(qtb_ctx *c, int sys, double *out, int max, int *n_out)
 {
     if (!c || !out || !n_out) return fail(QTB_ERR_ARG, "null argument");
     if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
+    if (int rc0 = ensure_fresh(c)) return rc0;
     int rc = check_err_word(c);
     if (rc) return rc;
     const long long total = c->step / c->p.obs_stride;
@@ -1328,6 +1342,7 @@ int qtb_get_state(qtb_ctx *c, int sys, double *pos, double *vel)
 {
     if (!c) return fail(QTB_ERR_ARG, "null context");
     if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
+    if (int rc0 = ensure_fresh(c)) return rc0;
     int rc = check_err_word(c);
     if (rc) return rc;
     if (pos && (rc = download(c, sys, 0, pos))) return rc;
@@ -1341,13 +1356,15 @@ int qtb_set_state(qtb_ctx *c, int sys, const double *pos, const double *vel)
     if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
     int rc = upload_state(c, sys, pos, vel);
     if (rc) return rc;
-    return refresh_forces(c);
+    c->stale = true;  // forces and the record follow at the next call that needs them
+    return QTB_OK;
 }
 
 int qtb_get_forces(qtb_ctx *c, int sys, double *f)
 {
     if (!c || !f) return fail(QTB_ERR_ARG, "null argument");
     if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
+    if (int rc0 = ensure_fresh(c)) return rc0;
     int rc = check_err_word(c);
     if (rc) return rc;
     return download(c, sys, 2, f);
@@ -1442,6 +1459,7 @@ int qtb_filter_source(qtb_ctx *c, int sys, int *source)
 int qtb_list_rebuilds(qtb_ctx *c, long long *count)
 {
     if (!c || !count) return fail(QTB_ERR_ARG, "null argument");
+    if (int rc0 = ensure_fresh(c)) return rc0;
     unsigned long long n = 0;
     if (c->pair) {
         CUDA_TRY(cudaMemcpyAsync(&n, c->d.nrebuild, sizeof n, cudaMemcpyDeviceToHost, c->st));
