@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--workload", default="mgo8000", choices=WORKLOADS)
     ap.add_argument("--ncell", type=int, default=10, help="cells per side of the mgo8000 workload")
     ap.add_argument("--skin", type=float, default=0.0, help="neighbour-list skin, A (0: library default)")
+    ap.add_argument("--rebuild-scope", type=int, default=0, choices=[0, 1],
+                    help="0: a list rebuild covers the requesting systems; 1: all systems of the context")
     ap.add_argument("--generator", default="filter", choices=["filter", "fourier"],
                     help="coloured noise: time-domain filter, or Fourier segments (Eq. 9)")
     ap.add_argument("--segment-blocks", type=int, default=8, help="256-step blocks per Fourier segment")
@@ -226,6 +228,7 @@ def run_ours(args):
     systems, pot, params, setup, desc = workload(args.workload, args.ncell, args.precision, filt)
     params["seed"] = replica_seed(12345, rank)
     params["skin"] = args.skin
+    params["rebuild_scope"] = args.rebuild_scope
     tuning = None
     if args.autotune:
         mode, n_taps, wmax = setup if setup is not None else (qtb.NOISE_WHITE, 1, 0.0)
@@ -327,6 +330,7 @@ def run_ours(args):
                    "filter": filt if setup is not None else "none (white noise)", "parallelism": f"replicas x{ws}",
                    "skin_A": params["skin"] if params["skin"] else "default",
                    "list_lanes": params.get("list_lanes") or "default (16)",
+                   "rebuild_scope": "all systems" if params.get("rebuild_scope") else "requesting systems",
                    "autotune": tuning,
                    "noise_generator": args.generator if args.generator == "filter" else
                    f"fourier segments of {256 * args.segment_blocks} steps (Eq. 9)",

@@ -119,6 +119,11 @@ typedef struct {
                               arithmetic, bit-identical results. */
     int list_lanes;        /* PAIR: lanes per bead-atom of the force kernel, 8, 16 or 32
                               (0: 16).  Changes the summation order only. */
+    int rebuild_scope;     /* PAIR: 0 a list rebuild covers the systems one of whose
+                              bead-atoms moved skin/2 (each system of a batch then runs
+                              bit for bit as it would alone); 1 every system of the
+                              context (fewer, larger rebuilds for batches of hot and
+                              cold systems; results change at the rounding level). */
 } qtb_params;
 
 /* Observable record (FP64), one per recorded step and system:
@@ -228,20 +233,23 @@ typedef struct {
     double skin;          /* chosen neighbour-list skin, A (0: the default) */
     int nm_layout;        /* chosen ring-polymer integrator layout (1 compact, 2 wide; 0 if P = 1 only) */
     int list_lanes;       /* chosen lanes per bead-atom of the force kernel (0: the default, 16) */
+    int rebuild_scope;    /* chosen rebuild scope (0 requesting systems, 1 all; 0 for one system) */
     double ms_per_step;   /* mean device time of one MD step with that choice */
-    double default_ms_per_step;  /* the same with the defaults (skin 0, nm_layout 0, list_lanes 0) */
+    double default_ms_per_step;  /* the same with the defaults (skin 0, nm_layout 0, list_lanes 0,
+                                    rebuild_scope 0) */
     int n_tried;          /* configurations timed */
 } qtb_tuning;
 
 /* Autotuner of the launch shapes and the cell/neighbour-list batching.  For
  * every candidate -- skin in {0.5, 0.8, 1.2, 1.6} A (those below r_cut/2),
- * lanes per bead-atom in {8, 16, 32}, and for systems with beads the integrator
- * layouts {1, 2} -- it creates a context for the given systems and parameters
+ * lanes per bead-atom in {8, 16, 32}, for systems with beads the integrator
+ * layouts {1, 2}, and for several systems the rebuild scopes {0, 1} -- it creates a context for the given systems and parameters
  * (qtb_init), applies the filter (noise_mode, n_taps, omega_max; as
  * qtb_set_filter on every system), runs n_blocks 256-step warm-up blocks and
  * then times n_blocks >= 1 blocks (so the list-rebuild rate of a system that has
  * left its initial configuration is in the timing), and writes
- * into *best a copy of *p with the fastest skin, nm_layout and list_lanes.  The
+ * into *best a copy of *p with the fastest skin, nm_layout, list_lanes and
+ * rebuild_scope.  The
  * candidates change the summation order and the rebuild schedule only, not the
  * dynamics.  Pair potentials only (QTB_ERR_ARG otherwise).  stream: as qtb_init.
  * Allocates and frees one context at a time; synchronises. */

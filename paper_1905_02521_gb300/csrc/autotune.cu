@@ -60,12 +60,14 @@ extern "C" int qtb_autotune(const qtb_system *sys, int n_sys, const qtb_params *
     const double skins[] = {0.5, 0.8, 1.2, 1.6};
     const int lanes[] = {8, 16, 32};
     const int layouts[] = {1, 2};
+    const int n_scope = n_sys > 1 ? 2 : 1;
     double best_ms = -1.0;
     int tried = 0, rc = QTB_OK;
     qtb_params q = *p;
     q.skin = 0.0;
     q.nm_layout = 0;
     q.list_lanes = 0;
+    q.rebuild_scope = 0;
     const double def_ms = time_config(sys, n_sys, &q, stream, noise_mode, n_taps, omega_max, n_blocks, &rc);
     if (rc != QTB_OK) return rc;
     *best = q;
@@ -73,23 +75,26 @@ extern "C" int qtb_autotune(const qtb_system *sys, int n_sys, const qtb_params *
     for (double sk : skins) {
         if (!(sk < 0.5 * p->r_cut)) continue;
         for (int ln : lanes)
-            for (int li = 0; li < (beads ? 2 : 1); ++li) {
-                q = *p;
-                q.skin = sk;
-                q.list_lanes = ln;
-                q.nm_layout = beads ? layouts[li] : 0;
-                const double ms = time_config(sys, n_sys, &q, stream, noise_mode, n_taps, omega_max, n_blocks, &rc);
-                ++tried;
-                if (rc != QTB_OK) return rc;
-                if (ms > 0.0 && ms < best_ms) {
-                    best_ms = ms;
-                    *best = q;
+            for (int li = 0; li < (beads ? 2 : 1); ++li)
+                for (int sc = 0; sc < n_scope; ++sc) {
+                    q = *p;
+                    q.skin = sk;
+                    q.list_lanes = ln;
+                    q.nm_layout = beads ? layouts[li] : 0;
+                    q.rebuild_scope = sc;
+                    const double ms = time_config(sys, n_sys, &q, stream, noise_mode, n_taps, omega_max, n_blocks, &rc);
+                    ++tried;
+                    if (rc != QTB_OK) return rc;
+                    if (ms > 0.0 && ms < best_ms) {
+                        best_ms = ms;
+                        *best = q;
+                    }
                 }
-            }
     }
     result->skin = best->skin;
     result->nm_layout = best->nm_layout;
     result->list_lanes = best->list_lanes;
+    result->rebuild_scope = best->rebuild_scope;
     result->ms_per_step = best_ms;
     result->default_ms_per_step = def_ms;
     result->n_tried = tried + 1;

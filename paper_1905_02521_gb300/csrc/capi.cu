@@ -342,6 +342,9 @@ int refresh_forces(qtb_ctx *c)
     if (c->pair) {
         CUDA_TRY(cudaMemsetAsync(c->d.flag, 0, 2 * sizeof(unsigned), c->st));
         CUDA_TRY(cudaMemsetAsync(c->d.flag + cur, 1, 1, c->st));
+        // every system rebuilds (a nonzero word per system)
+        CUDA_TRY(cudaMemsetAsync(c->d.rflag, 0, 2 * sizeof(unsigned) * c->d.nsys, c->st));
+        CUDA_TRY(cudaMemsetAsync(c->d.rflag + (size_t)cur * c->d.nsys, 1, sizeof(unsigned) * c->d.nsys, c->st));
     }
     CUDA_TRY(launch_force(c->d, c->ml, c->tabf, c->tab, 0, j, cur, 0, 1, c->st));
     if (!c->pair) launch_reduce(c->d, c->ml, j, -1, c->st);  // the list force kernel reduces itself
@@ -744,6 +747,7 @@ int validate(const qtb_system *sys, int n_sys, const qtb_params *p)
     if (p->nm_layout < 0 || p->nm_layout > 2) return fail(QTB_ERR_ARG, "nm_layout must be 0, 1 or 2");
     if (p->list_lanes != 0 && p->list_lanes != 8 && p->list_lanes != 16 && p->list_lanes != 32)
         return fail(QTB_ERR_ARG, "list_lanes must be 0, 8, 16 or 32");
+    if (p->rebuild_scope != 0 && p->rebuild_scope != 1) return fail(QTB_ERR_ARG, "rebuild_scope must be 0 or 1");
     if (p->potential == QTB_POT_PAIR) {
         if (!p->charge || !p->buck_A || !p->buck_rho || !p->buck_C) return fail(QTB_ERR_ARG, "pair tables missing");
         if (!(p->r_cut > 0)) return fail(QTB_ERR_ARG, "r_cut must be > 0");
@@ -963,6 +967,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         }
         S.nm0 = nm_off[h.P];
         S.rep0 = nrep;
+        S.cell0 = S.cell1 = ncells;
         c->max_dofp = std::max(c->max_dofp, S.dofp);
         if (c->pair) {
             int nc[3];
@@ -990,6 +995,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
                 for (int t = 0; t < nl; ++t) c->lcta_rep.push_back(nrep);
                 ++nrep;
             }
+            S.cell1 = ncells;
         }
     }
     if (cap > kMaxCellCap)
@@ -1030,6 +1036,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     d.G = G;
     d.Dtot = D;
     d.obs_stride = p->obs_stride;
+    d.rebuild_all = p->rebuild_scope;
     d.max_records = p->max_records;
     d.dt = p->dt;
     d.seed = p->seed;
@@ -1135,6 +1142,9 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         cudaMemsetAsync(d.nnb, 0, sizeof(int) * (size_t)G, c->st);
     }
     d.flag = (unsigned *)c->alloc(2 * sizeof(unsigned));
+    d.rflag = (unsigned *)c->alloc(2 * sizeof(unsigned) * n_sys);
+    if (!d.rflag) return bail(fail(QTB_ERR_OOM, "device allocation failed"));
+    cudaMemsetAsync(d.rflag, 0, 2 * sizeof(unsigned) * n_sys, c->st);
     d.gbar = (unsigned *)c->alloc(2 * sizeof(unsigned));
     d.nrebuild = (unsigned long long *)c->alloc(sizeof(unsigned long long));
     if (!d.flag || !d.gbar || !d.nrebuild) return bail(fail(QTB_ERR_OOM, "device allocation failed"));

@@ -132,7 +132,10 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
             moved |= act && c == 0 && tot > lim;
         }
     }
-    if (PM != PM_FREE && __any_sync(0xffffffffu, moved) && lane == 0) atomicOr(&d.flag[cur], 1u);
+    if (PM != PM_FREE && __any_sync(0xffffffffu, moved) && lane == 0) {
+        atomicOr(&d.rflag[cur * d.nsys + s], 1u);
+        atomicOr(&d.flag[cur], 1u);
+    }
     spring = warp_sum(spring);
     acc[Q_SPRING] = spring;
     if (mine) cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
@@ -415,7 +418,10 @@ __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int 
             }
         }
     }
-    if (PM != PM_FREE && __syncthreads_or(moved) && threadIdx.x == 0) atomicOr(&d.flag[cur], 1u);
+    if (PM != PM_FREE && __syncthreads_or(moved) && threadIdx.x == 0) {
+        atomicOr(&d.rflag[cur * d.nsys + s], 1u);
+        atomicOr(&d.flag[cur], 1u);
+    }
     double acc[kNQ];
     for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
     acc[Q_SPRING] = warp_sum(spring);

@@ -222,90 +222,112 @@ __device__ __forceinline__ void mode_aoa(R &q, R &p, R cs, R sw, R ws, R c1, R n
 
 // ---------------------------------------------------------------------------
 // List rebuild: three phases of the cooperative step kernel, separated by grid
-// barriers, run only when flag[cur] is set.  bin_phase wraps the positions
-// into the box (x, its packed copy pos[cur] and the reference xref) and bins
-// them into cells >= (r_cut + skin)/2 with atomic slots; sort_phase puts each
-// cell's slots in bead-atom order (so that every list, and every later sum,
-// has a fixed order); build_cell scans the 5^3 stencil of one cell.
+// barriers, run only when flag[cur] is set, and then only for the systems
+// whose own request is set (rflag[cur]; every system with rebuild scope 1):
+// each system rebuilds on its own schedule, so that a system of a batch runs
+// exactly as it would alone.
+// bin_phase wraps the positions into the box (x, its packed copy pos[cur] and
+// the reference xref) and bins them into cells >= (r_cut + skin)/2 with atomic
+// slots; sort_phase puts each cell's slots in bead-atom order (so that every
+// list, and every later sum, has a fixed order); build_cell scans the 5^3
+// stencil of one cell.
 
-__device__ __forceinline__ int rep_of(const Dev &d, long long g)  // replica holding bead-atom g
-{
-    int lo = 0, hi = d.nrep - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (d.rep[mid].g0 <= g) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
+// one bead-atom g of replica R: wrap, pack, bin
 template <int PM>
-__device__ void bin_phase(const Dev &d, int cur)
+__device__ __forceinline__ void bin_one(const Dev &d, int cur, long long g, const DRep &R)
 {
     typedef typename PosT<PM, double>::S PS;
     typedef typename std::conditional<PM == PM_FIX, int4, D4>::type E4;
     const size_t G = (size_t)d.G;
     PS *X = reinterpret_cast<PS *>(d.x);
     PS *XR = reinterpret_cast<PS *>(d.xref);
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += (long long)gridDim.x * blockDim.x) {
-        const DRep &R = d.rep[rep_of(d, g)];
-        PS w[3];
-        int cc[3];
-        for (int c = 0; c < 3; ++c) {
-            const double L = R.box[c];
-            const int ncc = R.nc[c];
-            const PS xw = PosT<PM, double>::wrap(X[c * G + g], L);
-            X[c * G + g] = xw;
-            XR[c * G + g] = xw;
-            w[c] = xw;
-            int v;
-            if (PM == PM_FIX) v = (int)(((unsigned long long)(unsigned)xw * (unsigned)ncc) >> kFixBits);
-            else v = (int)floor((double)xw / L * ncc);
-            cc[c] = min(max(v, 0), ncc - 1);
-        }
-        E4 p;
-        p.x = w[0]; p.y = w[1]; p.z = w[2];
-        if (PM == PM_FIX) p.w = d.typ[g]; else p.w = (double)d.typ[g];
-        reinterpret_cast<E4 *>(d.pos[cur])[g] = p;
-        const int cell = R.cell0 + cc[0] + R.nc[0] * (cc[1] + R.nc[1] * cc[2]);
-        const int slot = atomicAdd(&d.cnt[cell], 1);
-        if (slot < d.cap)
-            d.cidx[(size_t)cell * d.cap + slot] = (int)g;
-        else
-            atomicOr(d.err, (unsigned)ERR_OVERFLOW);
+    PS w[3];
+    int cc[3];
+    for (int c = 0; c < 3; ++c) {
+        const double L = R.box[c];
+        const int ncc = R.nc[c];
+        const PS xw = PosT<PM, double>::wrap(X[c * G + g], L);
+        X[c * G + g] = xw;
+        XR[c * G + g] = xw;
+        w[c] = xw;
+        int v;
+        if (PM == PM_FIX) v = (int)(((unsigned long long)(unsigned)xw * (unsigned)ncc) >> kFixBits);
+        else v = (int)floor((double)xw / L * ncc);
+        cc[c] = min(max(v, 0), ncc - 1);
+    }
+    E4 p;
+    p.x = w[0]; p.y = w[1]; p.z = w[2];
+    if (PM == PM_FIX) p.w = d.typ[g]; else p.w = (double)d.typ[g];
+    reinterpret_cast<E4 *>(d.pos[cur])[g] = p;
+    const int cell = R.cell0 + cc[0] + R.nc[0] * (cc[1] + R.nc[1] * cc[2]);
+    const int slot = atomicAdd(&d.cnt[cell], 1);
+    if (slot < d.cap)
+        d.cidx[(size_t)cell * d.cap + slot] = (int)g;
+    else
+        atomicOr(d.err, (unsigned)ERR_OVERFLOW);
+}
+
+// the bead-atoms of the systems that requested a rebuild (rflag[cur]); the
+// others keep their lists, positions and reference positions
+template <int PM>
+__device__ void bin_phase(const Dev &d, int cur)
+{
+    const unsigned *rf = d.rflag + cur * d.nsys;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x, nth = (long long)gridDim.x * blockDim.x;
+    for (int s = 0; s < d.nsys; ++s) {
+        if (!d.rebuild_all && rf[s] == 0u) continue;
+        const DSys &S = d.sys[s];
+        const long long gn = (long long)S.N * S.P;
+        // the grid-stride mapping of all bead-atoms, restricted to this system's range
+        // (consecutive systems land on different threads)
+        for (long long l = ((tid - S.g0) % nth + nth) % nth; l < gn; l += nth)
+            bin_one<PM>(d, cur, S.g0 + l, d.rep[S.rep0 + (int)(l / S.N)]);
     }
 }
 
-// one warp per cell; keys: kMaxCellCap ints of shared memory per warp
+// one cell by one warp: slots in bead-atom order, packed positions
 template <int PM>
-__device__ void sort_phase(const Dev &d, int *keys)
+__device__ __forceinline__ void sort_cell(const Dev &d, int cell, int *kw, int lane)
+{
+    const size_t G = (size_t)d.G;
+    const int n = min(d.cnt[cell], d.cap);
+    for (int e = lane; e < n; e += 32) kw[e] = d.cidx[(size_t)cell * d.cap + e];
+    __syncwarp();
+    const int g0 = d.rep[d.cell_rep[cell]].g0;
+    for (int e = lane; e < n; e += 32) {
+        const int g = kw[e];
+        int rank = 0;
+        for (int t = 0; t < n; ++t) rank += (kw[t] < g) ? 1 : 0;
+        const size_t o = (size_t)cell * d.cap + rank;
+        d.cidx[o] = g;
+        if (PM == PM_FIX) {
+            const int *X = reinterpret_cast<const int *>(d.x);
+            reinterpret_cast<int4 *>(d.cpos)[o] = make_int4(X[g], X[G + g], X[2 * G + g], g - g0);
+        } else {
+            const double *X = reinterpret_cast<const double *>(d.x);
+            reinterpret_cast<D4 *>(d.cpos)[o] = D4{X[g], X[G + g], X[2 * G + g], (double)(g - g0)};
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        d.ccount[cell] = n;
+        d.cnt[cell] = 0;
+    }
+}
+
+// one warp per cell of the requesting systems; keys: kMaxCellCap ints of shared
+// memory per warp
+template <int PM>
+__device__ void sort_phase(const Dev &d, int cur, int *keys)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     int *kw = keys + warp * kMaxCellCap;
-    const size_t G = (size_t)d.G;
-    for (int cell = blockIdx.x * nw + warp; cell < d.ncells; cell += gridDim.x * nw) {
-        const int n = min(d.cnt[cell], d.cap);
-        for (int e = lane; e < n; e += 32) kw[e] = d.cidx[(size_t)cell * d.cap + e];
-        __syncwarp();
-        const int g0 = d.rep[d.cell_rep[cell]].g0;
-        for (int e = lane; e < n; e += 32) {
-            const int g = kw[e];
-            int rank = 0;
-            for (int t = 0; t < n; ++t) rank += (kw[t] < g) ? 1 : 0;
-            const size_t o = (size_t)cell * d.cap + rank;
-            d.cidx[o] = g;
-            if (PM == PM_FIX) {
-                const int *X = reinterpret_cast<const int *>(d.x);
-                reinterpret_cast<int4 *>(d.cpos)[o] = make_int4(X[g], X[G + g], X[2 * G + g], g - g0);
-            } else {
-                const double *X = reinterpret_cast<const double *>(d.x);
-                reinterpret_cast<D4 *>(d.cpos)[o] = D4{X[g], X[G + g], X[2 * G + g], (double)(g - g0)};
-            }
-        }
-        __syncwarp();
-        if (lane == 0) {
-            d.ccount[cell] = n;
-            d.cnt[cell] = 0;
-        }
+    const unsigned *rf = d.rflag + cur * d.nsys;
+    const int wg = blockIdx.x * nw + warp, W = gridDim.x * nw;
+    for (int s = 0; s < d.nsys; ++s) {
+        if (!d.rebuild_all && rf[s] == 0u) continue;  // uniform over the grid
+        const int c0 = d.sys[s].cell0;
+        for (int cell = c0 + ((wg - c0) % W + W) % W; cell < d.sys[s].cell1; cell += W) sort_cell<PM>(d, cell, kw, lane);
     }
 }
 
@@ -808,7 +830,10 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
         const R tot = __shfl_sync(0xffffffffu, dd, b0) + __shfl_sync(0xffffffffu, dd, b0 + 1) +
                       __shfl_sync(0xffffffffu, dd, b0 + 2);
         const R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
-        if (__any_sync(0xffffffffu, act && sub == 0 && tot > lim) && lane == 0) atomicOr(&d.flag[cur ^ 1], 1u);
+        if (__any_sync(0xffffffffu, act && sub == 0 && tot > lim) && lane == 0) {
+            atomicOr(&d.rflag[(cur ^ 1) * d.nsys + RP.sys], 1u);
+            atomicOr(&d.flag[cur ^ 1], 1u);
+        }
     }
     if (REC && rec) {
 #pragma unroll
@@ -859,10 +884,19 @@ __global__ void __launch_bounds__(32 * kListWarps, sizeof(R) == 4 ? 7 : 4) k_ste
             d.flag[cur] = 0u;  // this step's rebuild request is consumed
             atomicAdd(d.nrebuild, 1ull);
         }
-        sort_phase<PM>(d, reinterpret_cast<int *>(fsm));
+        sort_phase<PM>(d, cur, reinterpret_cast<int *>(fsm));
         grid_barrier(d);
-        for (int cell = blockIdx.x; cell < d.ncells; cell += gridDim.x) build_cell<PM, R>(d, T.rc2, T.rl2, cell, fsm, B);
+        for (int s = 0; s < d.nsys; ++s) {  // the cells of the requesting systems
+            if (!d.rebuild_all && d.rflag[cur * d.nsys + s] == 0u) continue;  // uniform over the grid
+            const int c0 = d.sys[s].cell0, c1 = d.sys[s].cell1, nb = (int)gridDim.x;
+            for (int cell = c0 + (((int)blockIdx.x - c0) % nb + nb) % nb; cell < c1; cell += nb)
+                build_cell<PM, R>(d, T.rc2, T.rl2, cell, fsm, B);
+        }
         grid_barrier(d);
+        // the per-system requests were read by every phase: consumed now (their
+        // next producer, of step s + 2, runs in a later launch)
+        if (blockIdx.x == 0)
+            for (int t = threadIdx.x; t < d.nsys; t += blockDim.x) d.rflag[cur * d.nsys + t] = 0u;
     }
     for (int u = blockIdx.x; u < d.nunits; u += gridDim.x)
         force_unit<PM, R, ADV, REC, LPA>(d, T, ptab, kick, j, cur, u, red, rsh, s_last);

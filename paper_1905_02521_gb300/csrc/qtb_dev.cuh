@@ -57,6 +57,7 @@ struct DSys {
     int icta0, icta1;  // integrator CTA range
     int fcta0, fcta1;  // force CTA range
     int ccta0, ccta1;  // centroid-estimator CTA range (empty for one bead)
+    int cell0, cell1;  // cells of all its replicas (pair potential)
     int rot0;          // offset of this system's mode rotation table
     int nm0;           // offset of this system's normal-mode matrix
     double box[3];
@@ -139,6 +140,8 @@ struct Dev {
     int *nnb;             // [G] entries per bead-atom
     int maxnb;
     unsigned *flag;       // [2] rebuild requests; flag[s & 1] is set by whoever produces the positions of step s
+    unsigned *rflag;      // [2][nsys] the same per system: a rebuild covers the requesting systems
+    int rebuild_all;      // ... or every system (rebuild scope 1)
     unsigned *gbar;       // [2] grid barrier of the cooperative step kernel: arrivals, generation
     unsigned long long *nrebuild;  // list rebuilds carried out
     int eta_blocks;       // blocks per noise segment (1: time-domain filter)

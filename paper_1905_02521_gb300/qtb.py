@@ -51,7 +51,7 @@ class qtb_params(C.Structure):
                 ("filter_prec", C.c_int), ("seed", C.c_ulonglong), ("obs_stride", C.c_int),
                 ("max_records", C.c_int), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_user", C.c_void_p), ("skin", C.c_double), ("nm_layout", C.c_int),
-                ("list_lanes", C.c_int)]
+                ("list_lanes", C.c_int), ("rebuild_scope", C.c_int)]
 
 
 _lib = None
@@ -195,6 +195,7 @@ def _c_args(systems, params, stream):
     p.skin = float(params.get("skin", 0.0))
     p.nm_layout = int(params.get("nm_layout", 0))
     p.list_lanes = int(params.get("list_lanes", 0))
+    p.rebuild_scope = int(params.get("rebuild_scope", 0))
     if params.get("torch_alloc", True):
         a, f = _torch_allocator()
         p.dev_alloc, p.dev_free = a, f
@@ -214,19 +215,22 @@ def qtb_init(systems, params, stream=None):
 
 
 class qtb_tuning(C.Structure):
-    _fields_ = [("skin", C.c_double), ("nm_layout", C.c_int), ("list_lanes", C.c_int), ("ms_per_step", C.c_double),
+    _fields_ = [("skin", C.c_double), ("nm_layout", C.c_int), ("list_lanes", C.c_int), ("rebuild_scope", C.c_int),
+                ("ms_per_step", C.c_double),
                 ("default_ms_per_step", C.c_double), ("n_tried", C.c_int)]
 
 
 def qtb_autotune(systems, params, mode=0, n_taps=1, omega_max=0.0, n_blocks=2, stream=None):
-    """Times the candidate skins, lane counts and integrator layouts on these
-    systems (see qtb.h) and returns (params with the fastest choice, tuning dict)."""
+    """Times the candidate skins, lane counts, integrator layouts and rebuild
+    scopes on these systems (see qtb.h) and returns (params with the fastest
+    choice, tuning dict)."""
     arr, p, stream, keep = _c_args(systems, params, stream)
     best = qtb_params()
     res = qtb_tuning()
     _check(lib().qtb_autotune(C.cast(arr, C.c_void_p), len(systems), C.addressof(p), stream, int(mode), int(n_taps),
                               float(omega_max), int(n_blocks), C.addressof(best), C.byref(res)))
-    tuned = dict(params, skin=best.skin, nm_layout=best.nm_layout, list_lanes=best.list_lanes)
+    tuned = dict(params, skin=best.skin, nm_layout=best.nm_layout, list_lanes=best.list_lanes,
+                 rebuild_scope=best.rebuild_scope)
     info = {k: getattr(res, k) for k, _ in qtb_tuning._fields_}
     return tuned, info
 

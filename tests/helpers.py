@@ -4,11 +4,11 @@ import numpy as np
 
 
 def gpu_params(pot, dt, precision=0, filter_prec=1, seed=12345, potential=0, ext=None, obs_stride=1,
-               max_records=4096, skin=0.0, nm_layout=0, list_lanes=0):
+               max_records=4096, skin=0.0, nm_layout=0, list_lanes=0, rebuild_scope=0):
     p = {k: pot[k] for k in ("mass", "charge", "buck_A", "buck_rho", "buck_C")}
     p.update(dsf_alpha=pot["dsf_alpha"], r_cut=pot["r_cut"], dt=dt, precision=precision, filter_prec=filter_prec,
              seed=seed, potential=potential, obs_stride=obs_stride, max_records=max_records, skin=skin,
-             nm_layout=nm_layout, list_lanes=list_lanes)
+             nm_layout=nm_layout, list_lanes=list_lanes, rebuild_scope=rebuild_scope)
     ext = ext or {}
     p["ext_omega"] = ext.get("omega", 0.0)
     p["ext_V0"] = ext.get("V0", 0.0)

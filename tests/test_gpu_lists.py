@@ -160,6 +160,7 @@ def test_autotune_picks_a_valid_configuration(qtb, oracle):
     assert info["n_tried"] == 1 + 4 * 3
     assert 0 < info["ms_per_step"] <= info["default_ms_per_step"]
     assert tuned["list_lanes"] in (0, 8, 16, 32) and tuned["skin"] in (0.0, 0.5, 0.8, 1.2, 1.6)
+    assert tuned["rebuild_scope"] == 0          # one system: the scope is not a candidate
     N = len(s["types"])
     ctx = qtb.qtb_init([s], tuned)
     try:
