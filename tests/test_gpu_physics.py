@@ -61,10 +61,20 @@ def test_equilibrium_observables_within_2sigma(qtb, oracle_mgo_series, precision
     finally:
         qtb.qtb_destroy(ctx)
     assert len(ser) == 2000 and ser[-1, 0] == 2000
-    for k in (1, 2):  # kinetic and potential energy, second half (equilibrated)
-        o = rec[1000:, k]
-        g = ser[1000:, k]
-        assert abs(g.mean() - o.mean()) <= 2 * _block_sigma(o), (k, g.mean(), o.mean(), _block_sigma(o))
+    # second half (equilibrated): kinetic and potential energy, their sum, the virial
+    # trace (pressure work) and the total momentum, against the oracle's block error
+    obs = {"K": lambda r: r[:, 1], "V": lambda r: r[:, 2], "E": lambda r: r[:, 1] + r[:, 2],
+           "W": lambda r: r[:, 5] + r[:, 9] + r[:, 13], "|p|": lambda r: np.linalg.norm(r[:, 14:17], axis=1)}
+    form = {(0, 0): "FP64", (1, 1): "mixed, FP32 filter", (1, 2): "mixed, BF16 tensor-core filter"}[(precision, filt)]
+    for name, f in obs.items():
+        o, g = f(rec[1000:]), f(ser[1000:])
+        sig = _block_sigma(o)
+        print("%-30s %-4s GPU %.6g  oracle %.6g +- %.2g  (%+.2f sigma)"
+              % (form, name, g.mean(), o.mean(), sig, (g.mean() - o.mean()) / sig))
+        if name in ("K", "V"):
+            assert abs(g.mean() - o.mean()) <= 2 * sig, (name, g.mean(), o.mean(), sig)
+        else:
+            assert abs(g.mean() - o.mean()) <= 3 * sig, (name, g.mean(), o.mean(), sig)
 
 
 def _quad_x2_v2(dens, w0, gamma, m, wmax):
