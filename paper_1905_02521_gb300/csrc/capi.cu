@@ -346,6 +346,7 @@ int refresh_forces(qtb_ctx *c)
         CUDA_TRY(cudaMemsetAsync(c->d.rflag, 0, 2 * sizeof(unsigned) * c->d.nsys, c->st));
         CUDA_TRY(cudaMemsetAsync(c->d.rflag + (size_t)cur * c->d.nsys, 1, sizeof(unsigned) * c->d.nsys, c->st));
     }
+    launch_spring(c->d, c->ml, c->st);  // the record's spring term (no integrator ran)
     CUDA_TRY(launch_force(c->d, c->ml, c->tabf, c->tab, 0, j, cur, 0, 1, c->st));
     if (!c->pair) launch_reduce(c->d, c->ml, j, -1, c->st);  // the list force kernel reduces itself
     launch_centroid(c->d, c->ml, j, -1, c->st);

@@ -189,6 +189,45 @@ __global__ void __launch_bounds__(32 * kCenWarps) k_centroid(Dev d, int j, int r
     }
 }
 
+// Spring energy of the current positions into the integrator partials, for the
+// record of a step that no integrator produced (forces refreshed after qtb_init
+// or qtb_set_state; the partials would otherwise be stale or unset).  The CTAs
+// of the integrator grid split each system's atoms evenly; the sum over a
+// system's partials is what the reduction reads.  Relative bead positions as in
+// the integrators (bead 0 the origin, minimum image).
+template <int PM, class R>
+__global__ void __launch_bounds__(128) k_spring(Dev d)
+{
+    typedef typename PosT<PM, R>::S PS;
+    __shared__ double red[4][kNQ];
+    const int cta = blockIdx.x, s = d.icta_sys[cta];
+    const DSys S = d.sys[s];
+    const int nct = S.icta1 - S.icta0, per = (S.N + nct - 1) / nct;
+    const int a0 = (cta - S.icta0) * per, na = max(min(S.N, a0 + per) - a0, 0);
+    const size_t G = (size_t)d.G;
+    const PS *X = reinterpret_cast<const PS *>(d.x);
+    double spring = 0.0;
+    if (S.P > 1)
+        for (int t = threadIdx.x; t < 3 * na; t += blockDim.x) {
+            const int c = t / na, i = a0 + (t - c * na);
+            const size_t o0 = (size_t)c * G + S.g0 + i;
+            const PS x0 = X[o0];
+            R prev = 0, sp = 0;
+            for (int b = 1; b < S.P; ++b) {
+                const R xr = PosT<PM, R>::rel(X[o0 + (size_t)b * S.N], x0, S.box[c], S.fix_scale[c], S.fix_inv[c]);
+                const R dd = prev - xr;
+                sp = fma(dd, dd, sp);
+                prev = xr;
+            }
+            sp = fma(prev, prev, sp);  // bead P-1 to bead 0 (the origin)
+            spring += 0.5 * d.mass_mvv[d.typ[S.g0 + i]] * S.wP * S.wP * (double)sp;
+        }
+    double acc[kNQ];
+    for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+    acc[Q_SPRING] = warp_sum(spring);
+    cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
+}
+
 __global__ void k_tick(Dev d) { d.clock[0] += 1; }
 __global__ void k_setclock(Dev d, long long b) { d.clock[0] = b; }
 
@@ -296,6 +335,17 @@ void launch_centroid(const Dev &d, const MdLaunch &m, int j, int record, cudaStr
     } else {
         if (m.mixed) k_centroid<PM_FIX, float><<<g, nt, 0, st>>>(d, j, record);
         else k_centroid<PM_BOX64, double><<<g, nt, 0, st>>>(d, j, record);
+    }
+}
+
+void launch_spring(const Dev &d, const MdLaunch &m, cudaStream_t st)
+{
+    if (!m.pair) {
+        if (m.mixed) k_spring<PM_FREE, float><<<m.n_icta, 128, 0, st>>>(d);
+        else k_spring<PM_FREE, double><<<m.n_icta, 128, 0, st>>>(d);
+    } else {
+        if (m.mixed) k_spring<PM_FIX, float><<<m.n_icta, 128, 0, st>>>(d);
+        else k_spring<PM_BOX64, double><<<m.n_icta, 128, 0, st>>>(d);
     }
 }
 
