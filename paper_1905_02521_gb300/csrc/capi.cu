@@ -915,6 +915,9 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     // contexts, fewer (more CTAs) for small ones
     long long beads_total = 0;
     for (int s = 0; s < n_sys; ++s) beads_total += (long long)sys[s].n_atoms * sys[s].n_beads;
+    // bead-atom and dof indices are 32-bit on the device (3 dofs per bead-atom)
+    if (beads_total > (long long)INT_MAX / 4)
+        return bail(fail(QTB_ERR_ARG, "%lld bead-atoms in one context: at most %d", beads_total, INT_MAX / 4));
     const int nm_big = p->nm_layout == 2 ? 1 : p->nm_layout == 1 ? 0 : (beads_total >= (1LL << 18) ? 1 : 0);
     const int lanes = p->list_lanes ? p->list_lanes : 16;
     for (int s = 0; s < n_sys; ++s) {
