@@ -43,7 +43,7 @@ PAIR_FLOPS = 64
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=48)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mgo8000", choices=WORKLOADS)
@@ -107,22 +107,32 @@ class ClockSampler:
         self._t = None
 
     def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
-                if out.returncode == 0 and out.stdout.strip():
-                    self.samples.append([x.strip() for x in out.stdout.strip().split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+        # one long-lived nvidia-smi in loop mode (a sample every 50 ms), read line by line
+        try:
+            self._p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                        "--format=csv,noheader,nounits", "-lms", "50"],
+                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            return
+        for line in self._p.stdout:
+            if self._stop.is_set():
+                break
+            if line.strip():
+                self.samples.append([x.strip() for x in line.strip().split(",")])
 
     def start(self):
+        self._p = None
         self._t = threading.Thread(target=self._run, daemon=True)
         self._t.start()
 
     def stop(self):
         self._stop.set()
+        if self._p is not None:
+            self._p.terminate()      # the child this sampler started
+            try:
+                self._p.wait(timeout=5)
+            except Exception:
+                self._p.kill()
         if self._t:
             self._t.join(timeout=10)
         if not self.samples:
