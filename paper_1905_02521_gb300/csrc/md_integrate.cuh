@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
 // memory.  A CTA takes A atoms of one system, i.e. 3 A columns (component c,
 // atom a; col = c A + a) of P beads, V = 3 A P values.  A thread task is MT
 // consecutive rows (beads or modes) of one column (register tiling: one shared
-// load of a value feeds MT multiply-adds; MT = 1 for small rings).  Phase 1
+// load of a value feeds MT multiply-adds; MT = 1 for P < 8).  Phase 1
 // (task = beads): relative bead positions and half-kicked bead velocities
 // (B, dt/2) into shared memory.  Phase 2 (task = modes): the forward
 // transforms, A(dt/2) O(dt) A(dt/2) of each mode.  Phase 3 (task = beads, the
@@ -155,7 +155,8 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
 // over beads or modes runs in ascending order, whatever the tiling, so that
 // every layout rounds alike.  BIG (large contexts): 32 atoms per CTA, so that
 // the 32 threads of a warp read 128 contiguous bytes.
-__host__ __device__ constexpr int nm_rows(int P) { return P >= 16 ? 4 : 1; }
+// rows per task (measured on GB300: P = 32 best at 4 rows, 2 or 8 slower; P = 8 at 2)
+__host__ __device__ constexpr int nm_rows(int P) { return P >= 16 ? 4 : (P >= 8 ? 2 : 1); }
 __host__ __device__ constexpr int nm_atoms(int P, int big) { return big ? 32 : (P >= 16 ? 768 : 192) / (3 * P); }
 // compact layout: one thread per task (the transforms are latency-bound chains
 // of P multiply-adds; few CTAs per SM at these sizes)
