@@ -228,6 +228,16 @@ int qtb_kernel_times(qtb_ctx *c, double *mean_ms, int *counts, int n_classes);
  * the one made by qtb_init / qtb_set_state included.  Synchronises. */
 int qtb_list_rebuilds(qtb_ctx *c, long long *count);
 
+/* Self-test of the device's bounded waits (no counterpart in the paper; the
+ * grid barriers of the step kernel and the list rebuild use them).  One device
+ * thread waits, through the same bounded wait, on a flag that nothing sets; the
+ * wait gives up after about one second of device time and records that in a
+ * status word of its own, not in the context's error word, so the context stays
+ * usable.  Outputs: *gave_up = 1 when the wait gave up (the expected outcome),
+ * *ms = the kernel's duration.  Returns QTB_OK when the kernel ran.
+ * Synchronises. */
+int qtb_wait_selftest(qtb_ctx *c, int *gave_up, double *ms);
+
 /* Result of qtb_autotune. */
 typedef struct {
     double skin;          /* chosen neighbour-list skin, A (0: the default) */

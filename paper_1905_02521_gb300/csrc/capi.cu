@@ -76,6 +76,7 @@ struct qtb_ctx {
     long long step = 0;
     long long dclock = 0;          // host mirror of the device clock
     bool stale = false;            // a state was set since the last force evaluation
+    unsigned *d_selftest = nullptr;  // [2] words of qtb_wait_selftest
     long long ring_hi = LLONG_MIN; // highest white block in the ring
     long long ring_lo = LLONG_MIN; // lowest white block in the ring
     long long eta_blk = LLONG_MIN; // block whose coloured noise is in eta
@@ -1480,6 +1481,34 @@ int qtb_list_rebuilds(qtb_ctx *c, long long *count)
         CUDA_TRY(cudaStreamSynchronize(c->st));
     }
     *count = (long long)n;
+    return QTB_OK;
+}
+
+int qtb_wait_selftest(qtb_ctx *c, int *gave_up, double *ms)
+{
+    if (!c || !gave_up || !ms) return fail(QTB_ERR_ARG, "null argument");
+    if (int rc = check_err_word(c)) return rc;
+    if (!c->d_selftest) {
+        c->d_selftest = (unsigned *)c->alloc(2 * sizeof(unsigned));
+        if (!c->d_selftest) return fail(QTB_ERR_OOM, "device allocation failed");
+    }
+    CUDA_TRY(cudaMemsetAsync(c->d_selftest, 0, 2 * sizeof(unsigned), c->st));
+    cudaEvent_t a, b;
+    CUDA_TRY(cudaEventCreate(&a));
+    CUDA_TRY(cudaEventCreate(&b));
+    cudaEventRecord(a, c->st);
+    launch_wait_selftest(c->d_selftest, c->st);
+    cudaEventRecord(b, c->st);
+    unsigned h[2] = {0u, 0u};
+    cudaError_t e = cudaMemcpyAsync(h, c->d_selftest, sizeof h, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return fail(QTB_ERR_CUDA, "wait self-test: %s", cudaGetErrorString(e));
+    *gave_up = h[1] != 0u;
+    *ms = t;
     return QTB_OK;
 }
 

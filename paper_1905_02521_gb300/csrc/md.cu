@@ -228,6 +228,14 @@ __global__ void __launch_bounds__(128) k_spring(Dev d)
     cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
 }
 
+// Self-test of the bounded waits: one thread waits on words[0], which nothing
+// sets, through the wait of the grid barriers; it gives up after about a second
+// and records that in words[1] (not in the context's error word).
+__global__ void k_wait_selftest(unsigned *words)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) bounded_wait(words, 0u, words + 1, 1u);
+}
+
 __global__ void k_tick(Dev d) { d.clock[0] += 1; }
 __global__ void k_setclock(Dev d, long long b) { d.clock[0] = b; }
 
@@ -348,6 +356,8 @@ void launch_spring(const Dev &d, const MdLaunch &m, cudaStream_t st)
         else k_spring<PM_BOX64, double><<<m.n_icta, 128, 0, st>>>(d);
     }
 }
+
+void launch_wait_selftest(unsigned *words, cudaStream_t st) { k_wait_selftest<<<1, 32, 0, st>>>(words); }
 
 void launch_tick(const Dev &d, cudaStream_t st) { k_tick<<<1, 1, 0, st>>>(d); }
 void launch_setclock(const Dev &d, long long b, cudaStream_t st) { k_setclock<<<1, 1, 0, st>>>(d, b); }

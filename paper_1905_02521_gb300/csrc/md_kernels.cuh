@@ -175,6 +175,32 @@ static __device__ void cta_store_partials(const double *acc, double (*red)[kNQ],
 // second it records ERR_TIMEOUT_BAR and lets the CTA go on (the results of
 // that launch are then void, the host reports QTB_ERR_TIMEOUT).  Called by
 // all threads of every CTA.
+// Bounded wait: spin while *word == value, for at most about a second of
+// device time (%globaltimer, ns; a spin count as a second bound).  Gives up at
+// once when another wait of the launch already gave up (timeout bit `bit` set in
+// *err).  Returns false when it gave up, after setting that bit.
+__device__ __forceinline__ unsigned long long device_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+static __device__ bool bounded_wait(volatile const unsigned *word, unsigned value, unsigned *err, unsigned bit)
+{
+    const unsigned long long t0 = device_ns();
+    long long spins = 0;
+    while (*word == value) {
+        ++spins;
+        if ((spins & 255) == 0 &&
+            (device_ns() - t0 > 1000000000ull || spins > (1LL << 26) || (*(volatile const unsigned *)err & bit))) {
+            atomicOr(err, bit);
+            return false;
+        }
+        __nanosleep(32);
+    }
+    return true;
+}
+
 static __device__ void grid_barrier(const Dev &d)
 {
     __syncthreads();
@@ -188,16 +214,8 @@ static __device__ void grid_barrier(const Dev &d)
             __threadfence();
             atomicAdd(d.gbar + 1, 1u);
         } else {
-            long long spins = 0;
-            while (*gen == g0) {
-                // bounded; after one timeout every later barrier of the launch gives up at once
-                if (++spins > (1LL << 25) ||
-                    ((spins & 1023) == 0 && (*(volatile const unsigned *)d.err & (unsigned)ERR_TIMEOUT_BAR))) {
-                    atomicOr(d.err, (unsigned)ERR_TIMEOUT_BAR);
-                    break;
-                }
-                __nanosleep(32);
-            }
+            // bounded; after one timeout every later barrier of the launch gives up at once
+            bounded_wait(gen, g0, d.err, (unsigned)ERR_TIMEOUT_BAR);
         }
         __threadfence();
     }

@@ -91,6 +91,8 @@ void launch_centroid(const Dev &d, const MdLaunch &m, int j, int record, cudaStr
 // spring energy of the current positions into the integrator partials (the
 // record of a refreshed step, which no integrator produced)
 void launch_spring(const Dev &d, const MdLaunch &m, cudaStream_t st);
+// words[0]: a flag nothing sets; words[1]: set to 1 when the bounded wait gives up
+void launch_wait_selftest(unsigned *words, cudaStream_t st);
 void launch_tick(const Dev &d, cudaStream_t st);
 void launch_setclock(const Dev &d, long long blk, cudaStream_t st);
 bool md_supported_P(int P);

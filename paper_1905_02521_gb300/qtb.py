@@ -84,6 +84,7 @@ def lib():
             "qtb_get_noise": ([vp, i, vp, C.POINTER(ll)], i),
             "qtb_get_step": ([vp, C.POINTER(ll)], i),
             "qtb_list_rebuilds": ([vp, C.POINTER(ll)], i),
+            "qtb_wait_selftest": ([vp, C.POINTER(i), C.POINTER(d)], i),
             "qtb_set_generator": ([vp, i, i], i),
             "qtb_autotune": ([vp, i, vp, vp, i, i, d, i, vp, vp], i),
             "qtb_set_profiling": ([vp, i], i),
@@ -301,6 +302,13 @@ def qtb_list_rebuilds(ctx):
     n = C.c_longlong()
     _check(lib().qtb_list_rebuilds(ctx, C.byref(n)))
     return int(n.value)
+
+
+def qtb_wait_selftest(ctx):
+    """Runs the bounded-wait self-test (see qtb.h); returns (gave_up, ms)."""
+    g, ms = C.c_int(0), C.c_double(0.0)
+    _check(lib().qtb_wait_selftest(ctx, C.byref(g), C.byref(ms)))
+    return bool(g.value), ms.value
 
 
 def qtb_get_step(ctx):

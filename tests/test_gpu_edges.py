@@ -8,7 +8,9 @@
 * thermostat off (gamma = 0): the step conserves the total energy (one bead) or
   the ring-polymer Hamiltonian, and the total momentum, in both forms;
 * qtb_step_n with zero steps changes nothing; a run split at every step equals
-  one call bit for bit (one-bead and ring-polymer paths).
+  one call bit for bit (one-bead and ring-polymer paths);
+* the bounded device wait of the grid barriers gives up after about a second on
+  a flag that nothing sets, reports it, and leaves the context usable.
 """
 import numpy as np
 import pytest
@@ -132,3 +134,17 @@ def test_zero_steps_and_step_by_step_splitting(qtb, P):
         finally:
             qtb.qtb_destroy(ctx)
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(qtb):
+    s, pot = W.mgo_system(2, 300.0)
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=1, seed=7)
+    try:
+        gave_up, ms = qtb.qtb_wait_selftest(ctx)
+        assert gave_up and 500.0 < ms < 5000.0, (gave_up, ms)
+        qtb.qtb_step_n(ctx, 20)
+        qtb.qtb_sync(ctx)                              # no error recorded in the context
+        obs = qtb.qtb_observables(ctx, 0)
+        assert obs[0] == 20 and np.all(np.isfinite(obs))
+    finally:
+        qtb.qtb_destroy(ctx)
