@@ -302,7 +302,7 @@ def run_ours(args):
     states = []
     for k, (n, p) in enumerate(sizes):
         x, v = qtb.qtb_get_state(ctx, k, p, n)
-        states.append((x, v))
+        states.append((pinned(torch, x), pinned(torch, v)))   # the end-to-end leg uploads from pinned memory
         # every bead of small systems; 4 evenly spaced beads of large ones, scaled to P
         beads = range(p) if n * p <= 100000 else range(0, p, max(1, p // 4))
         pairs += int(round(sum(count_pairs(x[b], systems[k]["box"], pot["r_cut"]) for b in beads) * p / len(beads)))
@@ -320,7 +320,8 @@ def run_ours(args):
     for i in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for k, (x, v) in enumerate(states):
+        for k, (xt, vt) in enumerate(states):
+            x, v = xt.numpy(), vt.numpy()
             qtb.qtb_set_state(ctx, k, x, v)
         qtb.qtb_step_n(ctx, BLOCK)
         for k in range(len(systems)):
@@ -400,6 +401,13 @@ def hbm_peak_gbs():
             return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
     except Exception:
         return 6800.0, "fallback"
+
+
+def pinned(torch, a):
+    """A page-locked host copy of array a (a torch tensor; .numpy() views its memory)."""
+    t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+    t.numpy()[...] = a
+    return t
 
 
 def in_graph_launch_ms(sampled, kernel_n, block_ms, nblocks, sizes):

@@ -77,6 +77,8 @@ struct qtb_ctx {
     long long dclock = 0;          // host mirror of the device clock
     bool stale = false;            // a state was set since the last force evaluation
     unsigned *d_selftest = nullptr;  // [2] words of qtb_wait_selftest
+    double *d_stage = nullptr;       // state upload staging: positions, velocities [P][N][3]
+    size_t stage_n = 0;              // its size in doubles
     long long ring_hi = LLONG_MIN; // highest white block in the ring
     long long ring_lo = LLONG_MIN; // lowest white block in the ring
     long long eta_blk = LLONG_MIN; // block whose coloured noise is in eta
@@ -226,59 +228,23 @@ int check_err_word(qtb_ctx *c)
 
 int upload_state(qtb_ctx *c, int s, const double *pos, const double *vel)
 {
+    // one copy per array into a staging buffer, the conversion on the device
+    // (k_load_state), one synchronisation: the caller's arrays are borrowed
+    // for the call only (pinned host memory makes the copies plain DMA)
+    if (!pos && !vel) return QTB_OK;
     const HSys &h = c->hs[s];
-    const DSys &S = c->ds[s];
-    const size_t G = (size_t)c->d.G, NP = (size_t)h.N * h.P;
-    for (int comp = 0; comp < 3; ++comp) {
-        if (pos) {
-            if (c->pair && c->mixed) {
-                std::vector<int> buf(NP);
-                const double L = h.box[comp];
-                for (size_t t = 0; t < NP; ++t) {
-                    double u = pos[t * 3 + comp] / L;
-                    u -= std::floor(u);
-                    long long q = std::llround(u * (double)(1 << kFixBits));
-                    buf[t] = (int)(q & ((1LL << kFixBits) - 1));
-                }
-                CUDA_TRY(cudaMemcpyAsync((int *)c->d.x + comp * G + S.g0, buf.data(), NP * 4, cudaMemcpyHostToDevice, c->st));
-                CUDA_TRY(cudaStreamSynchronize(c->st));
-            } else if (c->pair) {
-                std::vector<double> buf(NP);
-                const double L = h.box[comp];
-                for (size_t t = 0; t < NP; ++t) {
-                    double x = pos[t * 3 + comp];
-                    x -= L * std::floor(x / L);
-                    if (x >= L || x < 0) x = 0;
-                    buf[t] = x;
-                }
-                CUDA_TRY(cudaMemcpyAsync((double *)c->d.x + comp * G + S.g0, buf.data(), NP * 8, cudaMemcpyHostToDevice, c->st));
-                CUDA_TRY(cudaStreamSynchronize(c->st));
-            } else if (c->mixed) {
-                std::vector<float> buf(NP);
-                for (size_t t = 0; t < NP; ++t) buf[t] = (float)pos[t * 3 + comp];
-                CUDA_TRY(cudaMemcpyAsync((float *)c->d.x + comp * G + S.g0, buf.data(), NP * 4, cudaMemcpyHostToDevice, c->st));
-                CUDA_TRY(cudaStreamSynchronize(c->st));
-            } else {
-                std::vector<double> buf(NP);
-                for (size_t t = 0; t < NP; ++t) buf[t] = pos[t * 3 + comp];
-                CUDA_TRY(cudaMemcpyAsync((double *)c->d.x + comp * G + S.g0, buf.data(), NP * 8, cudaMemcpyHostToDevice, c->st));
-                CUDA_TRY(cudaStreamSynchronize(c->st));
-            }
-        }
-        if (vel) {
-            if (c->mixed) {
-                std::vector<float> buf(NP);
-                for (size_t t = 0; t < NP; ++t) buf[t] = (float)vel[t * 3 + comp];
-                CUDA_TRY(cudaMemcpyAsync((float *)c->d.v + comp * G + S.g0, buf.data(), NP * 4, cudaMemcpyHostToDevice, c->st));
-                CUDA_TRY(cudaStreamSynchronize(c->st));
-            } else {
-                std::vector<double> buf(NP);
-                for (size_t t = 0; t < NP; ++t) buf[t] = vel[t * 3 + comp];
-                CUDA_TRY(cudaMemcpyAsync((double *)c->d.v + comp * G + S.g0, buf.data(), NP * 8, cudaMemcpyHostToDevice, c->st));
-                CUDA_TRY(cudaStreamSynchronize(c->st));
-            }
-        }
+    const size_t n3 = 3 * (size_t)h.N * h.P;
+    if (c->stage_n < 2 * n3) {
+        c->d_stage = (double *)c->alloc(sizeof(double) * 2 * n3);  // freed with the context
+        if (!c->d_stage) return fail(QTB_ERR_OOM, "device allocation failed");
+        c->stage_n = 2 * n3;
     }
+    double *dp = pos ? c->d_stage : nullptr, *dv = vel ? c->d_stage + n3 : nullptr;
+    if (pos) CUDA_TRY(cudaMemcpyAsync(dp, pos, sizeof(double) * n3, cudaMemcpyHostToDevice, c->st));
+    if (vel) CUDA_TRY(cudaMemcpyAsync(dv, vel, sizeof(double) * n3, cudaMemcpyHostToDevice, c->st));
+    launch_load_state(c->d, c->ml, s, (long long)n3, dp, dv, c->st);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(c->st));
     return QTB_OK;
 }
 

@@ -228,6 +228,52 @@ __global__ void __launch_bounds__(128) k_spring(Dev d)
     cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
 }
 
+// State upload: positions / velocities of system s from the caller's AoS layout
+// [P][N][3] (FP64, copied as is into a staging buffer) to the SoA state, one
+// thread per value.  Pair potentials: positions wrapped into the box (mixed
+// form: 30-bit fixed point, u = x/L - floor(x/L) rounded half away from zero to
+// a multiple of 2^-30); external potentials: as given (FP32 in the mixed form).
+template <int PM, class R>
+__global__ void k_load_state(Dev d, int s, const double *pos, const double *vel)
+{
+    const DSys S = d.sys[s];
+    const long long n3 = 3LL * S.N * S.P, G = d.G;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n3; t += (long long)gridDim.x * blockDim.x) {
+        const long long a = t / 3;
+        const int comp = (int)(t - 3 * a);
+        const size_t o = (size_t)comp * G + S.g0 + a;
+        if (pos) {
+            const double x = pos[t], L = S.box[comp];
+            if (PM == PM_FIX) {
+                double u = x / L;
+                u -= floor(u);
+                const long long q = (long long)round(u * (double)(1 << kFixBits));
+                reinterpret_cast<int *>(d.x)[o] = (int)(q & ((1LL << kFixBits) - 1));
+            } else if (PM == PM_BOX64) {
+                double w = x - L * floor(x / L);
+                if (w >= L || w < 0.0) w = 0.0;
+                reinterpret_cast<double *>(d.x)[o] = w;
+            } else {
+                reinterpret_cast<R *>(d.x)[o] = (R)x;
+            }
+        }
+        if (vel) reinterpret_cast<R *>(d.v)[o] = (R)vel[t];
+    }
+}
+
+void launch_load_state(const Dev &d, const MdLaunch &m, int s, long long n3, const double *pos, const double *vel,
+                       cudaStream_t st)
+{
+    const int grid = (int)std::min<long long>((n3 + 255) / 256, 4096);
+    if (!m.pair) {
+        if (m.mixed) k_load_state<PM_FREE, float><<<grid, 256, 0, st>>>(d, s, pos, vel);
+        else k_load_state<PM_FREE, double><<<grid, 256, 0, st>>>(d, s, pos, vel);
+    } else {
+        if (m.mixed) k_load_state<PM_FIX, float><<<grid, 256, 0, st>>>(d, s, pos, vel);
+        else k_load_state<PM_BOX64, double><<<grid, 256, 0, st>>>(d, s, pos, vel);
+    }
+}
+
 // Self-test of the bounded waits: one thread waits on words[0], which nothing
 // sets, through the wait of the grid barriers; it gives up after about a second
 // and records that in words[1] (not in the context's error word).

@@ -91,6 +91,10 @@ void launch_centroid(const Dev &d, const MdLaunch &m, int j, int record, cudaStr
 // spring energy of the current positions into the integrator partials (the
 // record of a refreshed step, which no integrator produced)
 void launch_spring(const Dev &d, const MdLaunch &m, cudaStream_t st);
+// positions / velocities (either may be null) of system s, [P][N][3] FP64 in device
+// memory (n3 = 3 N P values), into the state (wrapped / fixed point as the form needs)
+void launch_load_state(const Dev &d, const MdLaunch &m, int s, long long n3, const double *pos, const double *vel,
+                       cudaStream_t st);
 // words[0]: a flag nothing sets; words[1]: set to 1 when the bounded wait gives up
 void launch_wait_selftest(unsigned *words, cudaStream_t st);
 void launch_tick(const Dev &d, cudaStream_t st);
