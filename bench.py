@@ -470,12 +470,14 @@ def _tc_filter_available():
         return False
 
 
-def oracle_sample(name, ncell, n_sample):
+def oracle_sample(name, ncell, n_sample, part=0, parts=1):
     """A bounded sample of one MD step of the workload for the FP64 oracle:
     forces on `n_sample` bead-atoms of bead 0 of the first system (brute force
     over all ions and images) and the random force of their 3 dofs (2049-tap
-    direct convolution; white noise for standard PIMD).  Returns a callable
-    one(n) for step n and the number of bead-atoms it covers."""
+    direct convolution; white noise for standard PIMD).  With `parts` workers,
+    worker `part` takes its own n_sample of n_sample * parts evenly spaced
+    bead-atoms.  Returns a callable one(n) for step n, the number of
+    bead-atoms it covers and the system size."""
     import oracle
     from oracle import spectra as S
     systems, pot, params, setup, desc = workload(name, ncell, "fp64", "fp32")
@@ -488,7 +490,8 @@ def oracle_sample(name, ncell, n_sample):
         P = int(s["pos"].shape[0]) if mode == 2 else 1
         h = S.taps(L, dt, T, wmax, P=P, sol=S.kappa_solve(P) if P > 1 else None)
     n = len(s["types"])
-    sel = np.arange(0, n, max(1, n // n_sample))[:n_sample]
+    tot = min(n, n_sample * parts)
+    sel = np.arange(0, n, max(1, n // tot))[:tot][part::parts]
     oracle.build()
 
     def one(step):
@@ -498,39 +501,63 @@ def oracle_sample(name, ncell, n_sample):
     return one, len(sel), n
 
 
-def cpu_baseline(name, sample_atoms=64, min_seconds=10.0):
-    """The FP64 oracle timed on a bounded sample of the workload (see oracle_sample):
-    as many steps of the sample as fit in about min_seconds of host time."""
-    one, k, n = oracle_sample(name, 10, sample_atoms)
+def _oracle_worker(task):
+    """One process of the host-core pool: its slice of the sample, either for at
+    least `seconds` of host time or for `warmup` untimed then `steps` timed steps.
+    Returns (bead-atoms per step, timed steps, seconds, system size)."""
+    name, ncell, n_sample, part, parts, seconds, warmup, steps = task
+    one, k, n = oracle_sample(name, ncell, n_sample, part, parts)
+    for i in range(warmup):
+        one(i)
     t0 = time.perf_counter()
-    steps = 0
-    while steps == 0 or time.perf_counter() - t0 < min_seconds:
-        one(steps)
-        steps += 1
-    dt = time.perf_counter() - t0
-    return {"value": k * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{k} of {n} bead-atoms x {steps} step(s): brute-force periodic forces + "
-                      f"random force of their dofs, single thread, {dt:.1f} s"}
+    done = 0
+    while (seconds is not None and (done == 0 or time.perf_counter() - t0 < seconds)) or \
+            (seconds is None and done < steps):
+        one(warmup + done)
+        done += 1
+    return k, done, time.perf_counter() - t0, n
+
+
+def oracle_pool_run(name, ncell, n_sample, seconds=None, warmup=0, steps=0):
+    """The oracle on every host core: one spawned process per core (spawn, so that
+    no process inherits a CUDA context), each on its own slice of the sample.
+    Returns (bead-atom-steps per second over the slowest worker's time, workers,
+    bead-atoms per step, seconds, system size)."""
+    import multiprocessing as mp
+    workers = max(1, os.cpu_count() or 1)
+    tasks = [(name, ncell, n_sample, w, workers, seconds, warmup, steps) for w in range(workers)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        res = pool.map(_oracle_worker, tasks)
+    units = sum(k * d for k, d, _, _ in res)
+    t = max(dt for _, _, dt, _ in res)
+    return units / t, workers, sum(k for k, _, _, _ in res), t, res[0][3], res[0][1]
+
+
+def cpu_baseline(name, sample_atoms=64, min_seconds=10.0):
+    """The FP64 oracle, as it stands, on every host core (see oracle_pool_run):
+    each process runs its slice for about min_seconds."""
+    value, workers, k, dt, n, steps = oracle_pool_run(name, 10, sample_atoms, seconds=min_seconds)
+    return {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"{k} of {n} bead-atoms ({sample_atoms} per process, {workers} processes), "
+                      f"~{steps} step(s) each: brute-force periodic forces + random force of their dofs, "
+                      f"{dt:.1f} s"}
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    one, k, n = oracle_sample(args.workload, args.ncell, 512)   # ~0.4 s of host time per step
-    for i in range(args.warmup):
-        one(i)
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        one(args.warmup + i)
-    dt = time.perf_counter() - t0
-    value = k * args.steps / dt
+    # every host core, 64 bead-atoms per process and step (~50 ms of host time per step)
+    value, workers, k, dt, n, _ = oracle_pool_run(args.workload, args.ncell, 64, warmup=args.warmup,
+                                                  steps=args.steps)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: FP64 oracle on {k} of {n} bead-atoms per step", "name": args.workload},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{k} bead-atoms per step: forces + random force of the FP64 oracle"},
+            "config": {"workload": f"{args.workload}: FP64 oracle on {k} of {n} bead-atoms per step",
+                       "name": args.workload},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "sample": f"{k} bead-atoms per step over {workers} processes: forces + random "
+                                       f"force of the FP64 oracle"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
