@@ -251,42 +251,18 @@ int upload_state(qtb_ctx *c, int s, const double *pos, const double *vel)
 // which: 0 positions, 1 velocities, 2 forces
 int download(qtb_ctx *c, int s, int which, double *out)
 {
+    // converted on the device into the staging buffer, one copy, one synchronisation
     const HSys &h = c->hs[s];
-    const DSys &S = c->ds[s];
-    const size_t G = (size_t)c->d.G, NP = (size_t)h.N * h.P;
-    for (int comp = 0; comp < 3; ++comp) {
-        if (which == 0 && c->pair && c->mixed) {
-            std::vector<int> buf(NP);
-            CUDA_TRY(cudaMemcpyAsync(buf.data(), (int *)c->d.x + comp * G + S.g0, NP * 4, cudaMemcpyDeviceToHost, c->st));
-            CUDA_TRY(cudaStreamSynchronize(c->st));
-            // positions move unwrapped between list rebuilds: report them in [0, L)
-            const double sc = h.box[comp] / (double)(1 << kFixBits);
-            for (size_t t = 0; t < NP; ++t) out[t * 3 + comp] = (double)(buf[t] & ((1 << kFixBits) - 1)) * sc;
-        } else {
-            const void *src = (which == 0) ? c->d.x : (which == 1) ? c->d.v : c->d.f;
-            const bool f32 = c->mixed;  // positions of PAIR+MIXED handled above
-            if (f32) {
-                std::vector<float> buf(NP);
-                CUDA_TRY(cudaMemcpyAsync(buf.data(), (const float *)src + comp * G + S.g0, NP * 4, cudaMemcpyDeviceToHost, c->st));
-                CUDA_TRY(cudaStreamSynchronize(c->st));
-                for (size_t t = 0; t < NP; ++t) out[t * 3 + comp] = buf[t];
-            } else {
-                std::vector<double> buf(NP);
-                CUDA_TRY(cudaMemcpyAsync(buf.data(), (const double *)src + comp * G + S.g0, NP * 8, cudaMemcpyDeviceToHost, c->st));
-                CUDA_TRY(cudaStreamSynchronize(c->st));
-                const double L = h.box[comp];
-                const bool wrap = (which == 0 && c->pair);
-                for (size_t t = 0; t < NP; ++t) {
-                    double x = buf[t];
-                    if (wrap) {
-                        x -= L * std::floor(x / L);
-                        if (x >= L || x < 0) x = 0;
-                    }
-                    out[t * 3 + comp] = x;
-                }
-            }
-        }
+    const size_t n3 = 3 * (size_t)h.N * h.P;
+    if (c->stage_n < n3) {
+        c->d_stage = (double *)c->alloc(sizeof(double) * 2 * n3);  // freed with the context
+        if (!c->d_stage) return fail(QTB_ERR_OOM, "device allocation failed");
+        c->stage_n = 2 * n3;
     }
+    launch_store_state(c->d, c->ml, s, (long long)n3, which, c->d_stage, c->st);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(out, c->d_stage, sizeof(double) * n3, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(cudaStreamSynchronize(c->st));
     return QTB_OK;
 }
 

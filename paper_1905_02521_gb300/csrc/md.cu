@@ -274,6 +274,47 @@ void launch_load_state(const Dev &d, const MdLaunch &m, int s, long long n3, con
     }
 }
 
+// State download: positions (which 0, reported in [0, L) for pair potentials:
+// they move unwrapped between list rebuilds), velocities (1) or forces (2) of
+// system s into the caller's AoS layout [P][N][3], FP64, one thread per value.
+template <int PM, class R>
+__global__ void k_store_state(Dev d, int s, int which, double *out)
+{
+    const DSys S = d.sys[s];
+    const long long n3 = 3LL * S.N * S.P, G = d.G;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n3; t += (long long)gridDim.x * blockDim.x) {
+        const long long a = t / 3;
+        const int comp = (int)(t - 3 * a);
+        const size_t o = (size_t)comp * G + S.g0 + a;
+        double x;
+        if (which == 0 && PM == PM_FIX) {
+            const double sc = S.box[comp] / (double)(1 << kFixBits);
+            x = (double)(reinterpret_cast<const int *>(d.x)[o] & ((1 << kFixBits) - 1)) * sc;
+        } else if (which == 0 && PM == PM_BOX64) {
+            const double L = S.box[comp];
+            x = reinterpret_cast<const double *>(d.x)[o];
+            x = x - L * floor(x / L);
+            if (x >= L || x < 0.0) x = 0.0;
+        } else {
+            const void *src = (which == 0) ? d.x : (which == 1) ? d.v : d.f;
+            x = (double)reinterpret_cast<const R *>(src)[o];
+        }
+        out[t] = x;
+    }
+}
+
+void launch_store_state(const Dev &d, const MdLaunch &m, int s, long long n3, int which, double *out, cudaStream_t st)
+{
+    const int grid = (int)std::min<long long>((n3 + 255) / 256, 4096);
+    if (!m.pair) {
+        if (m.mixed) k_store_state<PM_FREE, float><<<grid, 256, 0, st>>>(d, s, which, out);
+        else k_store_state<PM_FREE, double><<<grid, 256, 0, st>>>(d, s, which, out);
+    } else {
+        if (m.mixed) k_store_state<PM_FIX, float><<<grid, 256, 0, st>>>(d, s, which, out);
+        else k_store_state<PM_BOX64, double><<<grid, 256, 0, st>>>(d, s, which, out);
+    }
+}
+
 // Self-test of the bounded waits: one thread waits on words[0], which nothing
 // sets, through the wait of the grid barriers; it gives up after about a second
 // and records that in words[1] (not in the context's error word).

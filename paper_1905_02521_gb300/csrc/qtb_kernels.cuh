@@ -95,6 +95,9 @@ void launch_spring(const Dev &d, const MdLaunch &m, cudaStream_t st);
 // memory (n3 = 3 N P values), into the state (wrapped / fixed point as the form needs)
 void launch_load_state(const Dev &d, const MdLaunch &m, int s, long long n3, const double *pos, const double *vel,
                        cudaStream_t st);
+// positions (which 0, wrapped for pair potentials), velocities (1) or forces (2) of
+// system s into out[P][N][3] (FP64, device memory, n3 = 3 N P values)
+void launch_store_state(const Dev &d, const MdLaunch &m, int s, long long n3, int which, double *out, cudaStream_t st);
 // words[0]: a flag nothing sets; words[1]: set to 1 when the bounded wait gives up
 void launch_wait_selftest(unsigned *words, cudaStream_t st);
 void launch_tick(const Dev &d, cudaStream_t st);
