@@ -1,8 +1,9 @@
 """The N > 1 path of bench.py on CPU: two gloo ranks.
 
 The method shards by independent replicas (no exchange step), so the only
-multi-rank logic is the replica seeding, the max-over-ranks time and the
-whole-job throughput; these run here with world_size 2 over gloo."""
+multi-rank logic is the replica seeding, the max-over-ranks time, the
+whole-job throughput and the oracle arm run by rank 0 alone; these run here
+with world_size 2 over gloo."""
 import os
 import sys
 
@@ -48,3 +49,45 @@ def test_two_gloo_ranks_max_time_and_replica_seeds():
     assert t0 == t1 == pytest.approx(15.0)           # max over ranks
     assert s0 != s1                                    # independent replicas
     assert v0 == v1 == pytest.approx(2 * 8000 * 256 * 4 / 0.015)
+
+
+def _ref_worker(rank, world, port, q):
+    import contextlib
+    import io
+    import types
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    buf = io.StringIO()
+    args = types.SimpleNamespace(workload="mgo8000", ncell=10, steps=1, warmup=0)
+    with contextlib.redirect_stdout(buf):
+        bench.run_reference(args)
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, buf.getvalue()))
+
+
+def test_reference_arm_prints_on_rank_zero_only():
+    # under torchrun the oracle arm runs on rank 0 alone; the other ranks exit without work
+    import json
+    import socket
+
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_ref_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = dict(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert out[1] == ""
+    line = json.loads(out[0].strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["cores"] >= 1
