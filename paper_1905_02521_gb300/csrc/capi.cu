@@ -106,7 +106,7 @@ struct qtb_ctx {
     size_t ev_used = 0, ev_pairs = 0;
     bool prof_launched = false;
     // tensor-core filter
-    alignas(64) CUtensorMap tmA, tmB;
+    CUtensorMap tmA, tmB;  // the type carries the alignment TMA descriptors need
     void *d_Bt = nullptr;
     size_t Bt_bytes = 0;
     int *d_tiles = nullptr;

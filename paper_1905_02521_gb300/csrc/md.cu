@@ -415,7 +415,7 @@ cudaError_t launch_force(const Dev &d, const MdLaunch &m, const PairTabT<float> 
     return cudaGetLastError();
 }
 
-void launch_reduce(const Dev &d, const MdLaunch &m, int j, int record, cudaStream_t st)
+void launch_reduce(const Dev &d, const MdLaunch &, int j, int record, cudaStream_t st)
 {
     k_reduce<<<d.nsys, 128, 0, st>>>(d, j, record);
 }
