@@ -370,7 +370,7 @@ def run_ours(args):
         "wall_s": wall,
         "observables": {"K_eV": float(obs[1]), "V_eV": float(obs[2]), "step": int(obs[0])},
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    if ws == 1 and not args.no_cpu_baseline:   # the host baseline belongs to the one-GPU line only
         line["cpu_baseline"] = cpu_baseline(args.workload, sample_atoms=64)
     qtb.qtb_destroy(ctx)
     if ws > 1:
