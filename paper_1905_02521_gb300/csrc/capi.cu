@@ -3,8 +3,8 @@
 // Owns the device layout of every system (bead-major SoA state, noise dofs
 // padded to tensor-core tiles, cell and neighbour lists per bead replica), the
 // noise pipeline (white blocks in a ring, coloured block per 256 steps) and the
-// CUDA graph that replays one 256-step block, with the neighbour-list rebuild
-// of each step as a conditional node decided on the device.
+// CUDA graph that replays one 256-step block; a neighbour-list rebuild, when a
+// system requests one, runs inside that step's cooperative force launch.
 #include <cuda.h>
 #include <dlfcn.h>
 

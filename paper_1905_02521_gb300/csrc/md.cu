@@ -1,6 +1,7 @@
-// md.cu -- integrators, external potentials, reductions and the launchers of
-// the MD hot path (sm_103a); the device code is in md_kernels.cuh and
-// md_integrate.cuh.
+// md.cu -- the launchers of the MD hot path (sm_103a) and its smaller kernels:
+// external potentials, reductions, centroid-virial estimators, the spring term
+// of refreshed records, state upload and download, the bounded-wait self-test.
+// The step kernel and the integrators are in md_kernels.cuh and md_integrate.cuh.
 #include "md_integrate.cuh"
 
 namespace qtb {
