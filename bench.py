@@ -55,12 +55,13 @@ def parse():
                     help="coloured noise: time-domain filter, or Fourier segments (Eq. 9)")
     ap.add_argument("--segment-blocks", type=int, default=8, help="256-step blocks per Fourier segment")
     ap.add_argument("--autotune", action="store_true",
-                    help="choose skin, lanes per bead-atom and integrator layout with qtb_autotune first (untimed)")
+                    help="choose skin, lanes per bead-atom, integrator layout and rebuild scope with qtb_autotune "
+                         "first (untimed)")
     ap.add_argument("--filter", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # direct launches (two 128-step calls per block) instead of the captured
-    # graph: for profilers that cannot see kernels of graphs with conditional nodes
+    # graph (for tools that profile launches outside graphs)
     ap.add_argument("--direct", action="store_true")
     return ap.parse_args()
 

@@ -1,7 +1,7 @@
 """Verlet neighbour lists on the GPU.
 
-* rebuilds decided and carried out on the device (conditional graph node
-  inside the captured block, flag-tested launches outside it) keep the forces
+* rebuilds decided and carried out on the device (inside the cooperative step
+  launch, when the producer of the positions requested one) keep the forces
   equal to the oracle's brute force on the GPU's own configuration, in small
   boxes (several periodic images per pair) and larger ones, FP64 and mixed;
 * the skin changes nothing but the summation order (FP64 trajectories with
