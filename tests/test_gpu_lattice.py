@@ -13,7 +13,8 @@ At 20 K the crystal's vibrations are almost purely zero-point motion
   harmonic spectrum;
 * a larger friction broadens the vibrational peaks and adds a high-frequency
   tail above the top phonon (the drawback of a large gamma, Sec. 3): the
-  weight of that tail follows the Langevin prediction and grows with gamma.
+  weight of that tail follows the Langevin prediction and grows with gamma;
+* 7LiH against 7LiD: the isotope shift of the zero-point energy.
 """
 import numpy as np
 import pytest
@@ -229,3 +230,47 @@ def test_heat_capacity_follows_the_quantum_harmonic_crystal(qtb, lattice):
     # quantum at 100-200 K (harmonic 0.29), near Dulong-Petit at 400-800 K; classical ~1 at 100-200 K
     assert cv[2] < 0.45 and cv[-1] > 0.8
     assert cl == pytest.approx(1.0, abs=0.1)
+
+
+def _lattice_of(oracle, pot, x, t, box, Tk, wmax, dt):
+    H = L.hessian(lambda y: oracle.pair_forces(y, t, box, pot)[0], x)
+    w, _ = L.modes(H, pot["mass"][t])
+    w[:3] = 0.0
+    h = S.taps(NTAPS, dt, Tk, wmax)
+    a = np.zeros(1 << 20)
+    a[0], a[1:len(h)] = h[0], 2.0 * h[1:]
+    Hw = np.fft.rfft(a).real
+    wg = 2.0 * np.pi * np.arange(len(Hw)) / (len(a) * dt)
+    return dict(w=w, dens=lambda om: np.interp(np.atleast_1d(om), wg, Hw ** 2),
+                V0=oracle.pair_forces(x, t, box, pot)[1])
+
+
+def test_isotope_shift_of_the_zero_point_energy(qtb, oracle):
+    """7LiH against 7LiD (the same Born-Oppenheimer surface, Sec. 2.2), 64 ions at 20 K:
+    QTB-MD gives each crystal its quantum harmonic energy and hence the isotope shift of
+    the zero-point energy, which classical MD (equipartition) misses entirely."""
+    Tk, dt, wmax, gamma = 20.0, 0.25, 0.6, 0.01
+    x, t, box = W.rocksalt(2, 4.08, 0.0)
+    E, Eh = {}, {}
+    for iso in ("H", "D"):
+        pot = W.lih_potential(iso)
+        lat = _lattice_of(oracle, pot, x, t, box, Tk, wmax, dt)
+        s = W.system(x, t, box, pot, Tk, gamma)
+        ctx = gpu_ctx(qtb, [s], pot, dt, precision=1, filter_prec=1, seed=13, obs_stride=8, max_records=4096)
+        try:
+            qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB, NTAPS, wmax)
+            qtb.qtb_step_n(ctx, 8192)
+            qtb.qtb_step_n(ctx, 32768)
+            ser = qtb.qtb_get_series(ctx, 0, 4096)
+        finally:
+            qtb.qtb_destroy(ctx)
+        E[iso] = (ser[:, 1] + ser[:, 2]).mean() - lat["V0"]
+        Eh[iso] = harmonic_qtb_energy(lat, gamma)
+        print("Li%s: E - V0 QTB %.4f eV, harmonic Langevin %.4f eV" % (iso, E[iso], Eh[iso]))
+    shift, shift_h = E["H"] - E["D"], Eh["H"] - Eh["D"]
+    print("isotope shift of E - V0: QTB %.4f eV, harmonic %.4f eV, classical 0" % (shift, shift_h))
+    for iso in ("H", "D"):
+        assert E[iso] == pytest.approx(Eh[iso], rel=0.05)
+    # measured: LiH +3.8 %, LiD +2.7 % above harmonic (anharmonicity at zero-point
+    # amplitudes, larger for the lighter isotope), shift +8 %
+    assert shift == pytest.approx(shift_h, rel=0.15) and shift_h > 1.5
