@@ -5,7 +5,9 @@
   FP64 form, 1e-5 in the mixed form (FP32 transform), for segments of one and of
   four blocks and for consecutive segments;
 * QTB harmonic oscillators driven by segments of 2048 steps reproduce
-  theta(w0, T) as with the time-domain filter.
+  theta(w0, T) as with the time-domain filter;
+* QTB-PIMD segments (density kappa_P W, one stream per normal-mode dof) equal
+  the oracle's.
 """
 import numpy as np
 import pytest
@@ -70,3 +72,24 @@ def test_oscillators_with_fourier_segments_reproduce_theta(qtb):
         qtb.qtb_destroy(ctx)
     E = (ser[:, 1] + ser[:, 2]) / (3 * 2000)
     assert E.mean() == pytest.approx(S.theta(w0, T), rel=0.05), (E.mean(), S.theta(w0, T))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_qtb_pimd_segments_match_oracle(qtb, oracle, precision):
+    # QTB-PIMD (Eq. 12): segments drawn with the density kappa_P W, one stream per
+    # normal-mode dof.  The GPU's kappa_P (normal equations) and the oracle's (LAPACK)
+    # agree to ~1e-6, hence 1e-5 here in both forms.
+    T, dt, wmax, seed, P = 100.0, 0.5, 0.6, 778, 4
+    s, pot = W.mgo_system(2, T, n_beads=P)
+    D = 3 * len(s["types"]) * P
+    ctx = gpu_ctx(qtb, [s], pot, dt, precision=precision, filter_prec=1, seed=seed)
+    try:
+        qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB_PIMD, 513, wmax)
+        qtb.qtb_set_generator(ctx, qtb.GEN_FOURIER, 1)
+        eta, blk = qtb.qtb_get_noise(ctx, 0, D)
+        assert blk == 0
+    finally:
+        qtb.qtb_destroy(ctx)
+    Sj = F.segment_spectrum(256, dt, T, wmax, P=P, sol=S.kappa_solve(P))
+    ref = F.eq9_segment(seed, 0, D, 0, 256, Sj)
+    assert rel_inf(eta.T, ref) < 1e-5, rel_inf(eta.T, ref)
