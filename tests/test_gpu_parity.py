@@ -89,6 +89,26 @@ def test_colored_noise_block_matches_oracle(qtb, oracle, precision, tol):
         qtb.qtb_destroy(ctx)
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-14), (1, 1e-5)])
+def test_white_noise_block_matches_oracle(qtb, oracle, precision, tol):
+    # white Langevin bath: eta = sqrt(k_B T) xi, the Philox + Box-Muller stream of every
+    # dof, all dofs of a ring-polymer system, blocks 0 and 2.  FP64 form: the normals to
+    # a few ulp (library log/sin/cos on either side); mixed form: Box-Muller in FP32
+    # (measured 2.7e-6 norm-wise), within the FP32 noise criterion
+    s, pot = W.mgo_system(2, 250.0, n_beads=2)
+    D = 3 * len(s["types"]) * 2
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=precision, filter_prec=1, seed=4242)
+    try:
+        for blk_want, n0 in ((0, 0), (2, 512)):
+            qtb.qtb_step_n(ctx, n0 - qtb.qtb_get_step(ctx))
+            eta, blk = qtb.qtb_get_noise(ctx, 0, D)
+            assert blk == blk_want
+            ref = np.sqrt(8.617333262e-5 * 250.0) * oracle.white_block(4242, 0, D, n0, 256)   # [dof][step]
+            assert rel_inf(eta, ref.T) < tol, (blk, rel_inf(eta, ref.T))
+    finally:
+        qtb.qtb_destroy(ctx)
+
+
 @pytest.mark.parametrize("ncell", [2, 3, 4])
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
 def test_forces_match_oracle(qtb, oracle, ncell, precision, tol):
