@@ -13,7 +13,11 @@ import pytest
 
 from helpers import gpu_ctx, minimg, oracle_sim, rel_inf, rel_l2
 
+from oracle import spectra as S
+from paper_1905_02521_gb300 import workloads as W
 from tolerances import F32_INF, F32_L2  # FP32 criterion and its max-norm guard (see tolerances.py)
+
+pytestmark = pytest.mark.gpu
 
 
 def assert_force_parity(f, fo, tol):
@@ -22,10 +26,6 @@ def assert_force_parity(f, fo, tol):
         assert rel_inf(f, fo) < F32_INF, (rel_l2(f, fo), rel_inf(f, fo))
     else:
         assert rel_inf(f, fo) < tol
-from oracle import spectra as S
-from paper_1905_02521_gb300 import workloads as W
-
-pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
