@@ -318,6 +318,7 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers: H2D state, 256 steps, D2H observables
     e2e_ms = []
+    rebuilds_e2e0 = qtb.qtb_list_rebuilds(ctx)
     for i in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -329,6 +330,7 @@ def run_ours(args):
             qtb.qtb_observables(ctx, k)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_value = ws * units * BLOCK * args.steps / (np.sum(e2e_ms) / 1e3)
+    rebuilds_e2e = (qtb.qtb_list_rebuilds(ctx) - rebuilds_e2e0) / args.steps
     integ = 1 if fused else BLOCK * len({p for _, p in sizes})
     cen = 1 if any(p > 1 for _, p in sizes) else 0  # centroid estimators, recorded step only
 
@@ -361,7 +363,7 @@ def run_ours(args):
         "kernel_ms_per_bench_step": step_breakdown,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * units * 3 * 8),
-                "d2h_bytes_per_step": int(len(systems) * qtb.NREC * 8)},
+                "d2h_bytes_per_step": int(len(systems) * qtb.NREC * 8), "list_rebuilds_per_step": rebuilds_e2e},
         # per block: white, filter, the integrator (once for one-bead systems, else every
         # step per distinct bead count), 256 step launches (a list rebuild runs inside the
         # step launch that needs it), the centroid estimators of the recorded step (ring

@@ -40,7 +40,7 @@ typedef enum {
     QTB_ERR_ARG = -1,       /* invalid argument (message says which)           */
     QTB_ERR_CUDA = -2,      /* a CUDA runtime/driver call failed                */
     QTB_ERR_OOM = -3,       /* device allocation failed                         */
-    QTB_ERR_TIMEOUT = -4,   /* reserved: a bounded device wait gave up          */
+    QTB_ERR_TIMEOUT = -4,   /* a bounded device wait gave up (barrier, mbarrier) */
     QTB_ERR_NONFINITE = -5, /* a force or velocity became NaN/Inf               */
     QTB_ERR_SOLVE = -6,     /* kappa_P solve failed (non-positive pivot or PSD) */
     QTB_ERR_OVERFLOW = -7,  /* a cell or a neighbour list overflowed its capacity */
@@ -196,7 +196,10 @@ int qtb_get_state(qtb_ctx *c, int sys, double *pos, double *vel);
  * once, at the next call that needs them (qtb_step_n, qtb_sync,
  * qtb_observables, qtb_get_series, qtb_get_state, qtb_get_forces,
  * qtb_list_rebuilds), so that setting several systems costs one force
- * evaluation; an error of that evaluation is returned by that call. */
+ * evaluation; an error of that evaluation is returned by that call.  PAIR: a
+ * system's neighbour lists are rebuilt then only if one of its bead-atoms lies
+ * more than skin/2 from its position at the last rebuild (the criterion of the
+ * steps); otherwise they stay valid and are kept. */
 int qtb_set_state(qtb_ctx *c, int sys, const double *pos, const double *vel);
 
 /* Forces [P][N][3] (eV/A) of system sys at the current positions, including the
@@ -225,7 +228,8 @@ int qtb_set_profiling(qtb_ctx *c, int enable);
 int qtb_kernel_times(qtb_ctx *c, double *mean_ms, int *counts, int n_classes);
 
 /* Number of neighbour-list rebuilds carried out so far (PAIR; 0 otherwise),
- * the one made by qtb_init / qtb_set_state included.  Synchronises. */
+ * the one made by qtb_init included (and those an uploaded state needed; see
+ * qtb_set_state).  Synchronises. */
 int qtb_list_rebuilds(qtb_ctx *c, long long *count);
 
 /* Self-test of the device's bounded waits (no counterpart in the paper; the

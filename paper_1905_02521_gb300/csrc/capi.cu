@@ -76,6 +76,7 @@ struct qtb_ctx {
     long long step = 0;
     long long dclock = 0;          // host mirror of the device clock
     bool stale = false;            // a state was set since the last force evaluation
+    bool lists_built = false;      // the neighbour lists of every system exist
     unsigned *d_selftest = nullptr;  // [2] words of qtb_wait_selftest
     double *d_stage = nullptr;       // state upload staging: positions, velocities [P][N][3]
     size_t stage_n = 0;              // its size in doubles
@@ -284,10 +285,17 @@ int refresh_forces(qtb_ctx *c)
     const int cur = (int)(c->step & 1);  // positions of step s live in pos[s & 1]
     if (c->pair) {
         CUDA_TRY(cudaMemsetAsync(c->d.flag, 0, 2 * sizeof(unsigned), c->st));
-        CUDA_TRY(cudaMemsetAsync(c->d.flag + cur, 1, 1, c->st));
-        // every system rebuilds (a nonzero word per system)
         CUDA_TRY(cudaMemsetAsync(c->d.rflag, 0, 2 * sizeof(unsigned) * c->d.nsys, c->st));
-        CUDA_TRY(cudaMemsetAsync(c->d.rflag + (size_t)cur * c->d.nsys, 1, sizeof(unsigned) * c->d.nsys, c->st));
+        if (!c->lists_built) {
+            // the first evaluation builds every system's lists (a nonzero word per system)
+            CUDA_TRY(cudaMemsetAsync(c->d.flag + cur, 1, 1, c->st));
+            CUDA_TRY(cudaMemsetAsync(c->d.rflag + (size_t)cur * c->d.nsys, 1, sizeof(unsigned) * c->d.nsys, c->st));
+            c->lists_built = true;
+        } else {
+            // later ones (uploaded states) rebuild only the systems whose bead-atoms left
+            // the skin/2 sphere around their positions at the last rebuild
+            launch_refresh_check(c->d, c->ml, cur, c->st);
+        }
     }
     launch_spring(c->d, c->ml, c->st);  // the record's spring term (no integrator ran)
     CUDA_TRY(launch_force(c->d, c->ml, c->tabf, c->tab, 0, j, cur, 0, 1, c->st));

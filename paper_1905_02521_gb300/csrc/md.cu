@@ -316,6 +316,52 @@ void launch_store_state(const Dev &d, const MdLaunch &m, int s, long long n3, in
     }
 }
 
+// Before the forces of an uploaded state are computed (pair potentials): the
+// packed gather copy pos[cur] of every bead-atom, and a rebuild request for each
+// system one of whose bead-atoms lies more than skin/2 from its position at the
+// last rebuild -- the test of the integrators; otherwise the lists stay valid.
+template <int PM, class R>
+__global__ void k_refresh_check(Dev d, int cur)
+{
+    typedef typename PosT<PM, R>::S PS;
+    const size_t G = (size_t)d.G;
+    const PS *X = reinterpret_cast<const PS *>(d.x);
+    const PS *XR = reinterpret_cast<const PS *>(d.xref);
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x, nth = (long long)gridDim.x * blockDim.x;
+    for (int s = 0; s < d.nsys; ++s) {
+        const DSys &S = d.sys[s];
+        const long long gn = (long long)S.N * S.P;
+        const R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
+        bool moved = false;
+        for (long long l = ((tid - S.g0) % nth + nth) % nth; l < gn; l += nth) {
+            const size_t g = (size_t)(S.g0 + l);
+            PS w[3];
+            R tot = 0;
+            for (int c = 0; c < 3; ++c) {
+                w[c] = X[c * G + g];
+                const R dc = PosT<PM, R>::diff(w[c], XR[c * G + g], S.fix_scale[c]);
+                tot = fma(dc, dc, tot);
+            }
+            moved |= tot > lim;
+            const int t = d.typ[g];
+            if (PM == PM_FIX) reinterpret_cast<int4 *>(d.pos[cur])[g] = make_int4((int)w[0], (int)w[1], (int)w[2], t);
+            else reinterpret_cast<D4 *>(d.pos[cur])[g] = D4{(double)w[0], (double)w[1], (double)w[2], (double)t};
+        }
+        if (moved) {
+            atomicOr(&d.rflag[cur * d.nsys + s], 1u);
+            atomicOr(&d.flag[cur], 1u);
+        }
+    }
+}
+
+void launch_refresh_check(const Dev &d, const MdLaunch &m, int cur, cudaStream_t st)
+{
+    if (!m.pair) return;
+    const int grid = (int)std::min<long long>(((long long)d.G + 255) / 256, 4096);
+    if (m.mixed) k_refresh_check<PM_FIX, float><<<grid, 256, 0, st>>>(d, cur);
+    else k_refresh_check<PM_BOX64, double><<<grid, 256, 0, st>>>(d, cur);
+}
+
 // Self-test of the bounded waits: one thread waits on words[0], which nothing
 // sets, through the wait of the grid barriers; it gives up after about a second
 // and records that in words[1] (not in the context's error word).

@@ -98,6 +98,10 @@ void launch_load_state(const Dev &d, const MdLaunch &m, int s, long long n3, con
 // positions (which 0, wrapped for pair potentials), velocities (1) or forces (2) of
 // system s into out[P][N][3] (FP64, device memory, n3 = 3 N P values)
 void launch_store_state(const Dev &d, const MdLaunch &m, int s, long long n3, int which, double *out, cudaStream_t st);
+// pair potentials, before the forces of an uploaded state: packed positions of
+// every bead-atom into pos[cur]; rebuild requests (flag, rflag[cur]) for the
+// systems with a bead-atom more than skin/2 from its position at the last rebuild
+void launch_refresh_check(const Dev &d, const MdLaunch &m, int cur, cudaStream_t st);
 // words[0]: a flag nothing sets; words[1]: set to 1 when the bounded wait gives up
 void launch_wait_selftest(unsigned *words, cudaStream_t st);
 void launch_tick(const Dev &d, cudaStream_t st);

@@ -171,3 +171,32 @@ def test_autotune_picks_a_valid_configuration(qtb, oracle):
         assert rel_l2(f, fo) < F32_L2 and rel_inf(f, fo) < F32_INF
     finally:
         qtb.qtb_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_uploaded_states_rebuild_only_when_needed(qtb, oracle, precision):
+    # qtb_set_state keeps a system's lists while every uploaded bead-atom lies within
+    # skin/2 of its position at the last rebuild (the stepping criterion), rebuilds
+    # otherwise; the forces match the oracle either way
+    s, pot = W.mgo_system(3, 300.0, seed=21)
+    N = len(s["types"])
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=precision, seed=9)     # default skin 0.8 A
+    try:
+        x0, v0 = qtb.qtb_get_state(ctx, 0, 1, N)
+        r0 = qtb.qtb_list_rebuilds(ctx)
+        tol = 1e-12 if precision == 0 else None
+        for shift, rebuilt in ((0.0, 0), (0.1, 0), (0.5, 1)):
+            x = x0.copy()
+            x[0, 7, 0] += shift                        # one ion, inside or outside skin/2 = 0.4 A
+            qtb.qtb_set_state(ctx, 0, x, v0)
+            f = qtb.qtb_get_forces(ctx, 0, 1, N)[0]
+            assert qtb.qtb_list_rebuilds(ctx) - r0 == rebuilt, shift
+            r0 += rebuilt
+            xg, _ = qtb.qtb_get_state(ctx, 0, 1, N)
+            fo, _, _ = oracle.pair_forces(xg[0], s["types"], s["box"], pot)
+            if tol:
+                assert rel_inf(f, fo) < tol
+            else:
+                assert rel_l2(f, fo) < F32_L2 and rel_inf(f, fo) < F32_INF
+    finally:
+        qtb.qtb_destroy(ctx)
