@@ -9,10 +9,11 @@ import numpy as np
 import pytest
 from scipy.special import erfc
 
+from golden_values import units, values
 from paper_1905_02521_gb300 import workloads as W
 
-MADELUNG_ROCKSALT = 1.747564594633
-KE = 14.3996454784
+MADELUNG_ROCKSALT = values("lattice_sums.txt")["madelung_rocksalt"]   # Borwein, Borwein & Taylor 1985
+KE = units()["k_e"]                                                   # CODATA 2018
 
 
 @pytest.fixture(scope="module")

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 from scipy import stats
 
+from golden_values import philox_kat
 from oracle import spectra as S
 
 HBAR, KB = 0.6582119569, 8.617333262e-5
@@ -40,13 +41,8 @@ def test_theta_limits_and_fig3_shape():
     assert e[-1] - t[-1] == pytest.approx(1.0 / (12 * t[-1]) - 1.0 / (720 * t[-1] ** 3), rel=1e-4)
 
 
-# Published known-answer vectors of Philox4x32-10 (Salmon et al., SC'11).
-KAT = [
-    ([0, 0, 0, 0], [0, 0], [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]),
-    ([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2, [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]),
-    ([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0],
-     [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]),
-]
+# Published known-answer vectors of Philox4x32-10 (Salmon et al., SC'11), tests/golden/.
+KAT = philox_kat()
 
 
 @pytest.mark.parametrize("ctr,key,expect", KAT)

@@ -6,11 +6,14 @@
 * at high temperature the double well tends to the classical averages, at low
   temperature its energy lies well above the classical one (zero point);
 * the double well of the study (V0 = 0.1 eV, a = 0.5 A, m = 1.008 u) has its
-  ground state below the barrier: hbar^2/(2 m V0 a^2) = 0.083 < 0.1.
+  ground state below the barrier, and its anharmonicity parameter of Eq. 13,
+  hbar^2/(2 m V0 a^2) = 0.083, lies below the double-well critical value the
+  paper prints in Sec. 3 (tests/golden/paper_values.txt): weakly anharmonic.
 """
 import numpy as np
 import pytest
 
+from golden_values import values
 from oracle import spectra as S
 from oracle import wells as Wl
 
@@ -49,4 +52,6 @@ def test_double_well_limits():
     assert 0.0 < cold[2] < cold[0]
     E, _ = Wl.levels(V, M, 1.6)
     assert E[0] < 0.1                             # ground state below the barrier
-    assert S.HBAR ** 2 / (2 * M * Wl.MVV2E * 0.1 * 0.25) == pytest.approx(0.083, abs=0.002)
+    C = S.HBAR ** 2 / (2 * M * Wl.MVV2E * 0.1 * 0.25)   # Eq. 13 with V0 = 0.1 eV, d = a = 0.5 A
+    assert C == pytest.approx(0.083, abs=0.002)
+    assert C < values("paper_values.txt")["C_crit_double_well"]
