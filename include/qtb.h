@@ -232,6 +232,16 @@ int qtb_kernel_times(qtb_ctx *c, double *mean_ms, int *counts, int n_classes);
  * qtb_set_state).  Synchronises. */
 int qtb_list_rebuilds(qtb_ctx *c, long long *count);
 
+/* Rebuild the neighbour lists of every system (PAIR; a no-op otherwise) on the
+ * current positions, at the next call that needs the forces (as after
+ * qtb_set_state); the forces and the record of the current step are evaluated
+ * again.  Changes no state: lists are otherwise rebuilt only when a bead-atom
+ * has moved skin/2.  Use: lists built on the initial, nearly perfect lattice
+ * hold the same number of entries for every ion and are traversed faster than
+ * any later lists; rebuilding them on a thermalised configuration gives the
+ * steady state of a long trajectory.  No counterpart in the paper. */
+int qtb_rebuild_lists(qtb_ctx *c);
+
 /* Self-test of the device's bounded waits (no counterpart in the paper; the
  * grid barriers of the step kernel and the list rebuild use them).  One device
  * thread waits, through the same bounded wait, on a flag that nothing sets; the

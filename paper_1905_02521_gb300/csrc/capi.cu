@@ -243,7 +243,10 @@ int upload_state(qtb_ctx *c, int s, const double *pos, const double *vel)
     double *dp = pos ? c->d_stage : nullptr, *dv = vel ? c->d_stage + n3 : nullptr;
     if (pos) CUDA_TRY(cudaMemcpyAsync(dp, pos, sizeof(double) * n3, cudaMemcpyHostToDevice, c->st));
     if (vel) CUDA_TRY(cudaMemcpyAsync(dv, vel, sizeof(double) * n3, cudaMemcpyHostToDevice, c->st));
-    launch_load_state(c->d, c->ml, s, (long long)n3, dp, dv, c->st);
+    // once the lists exist, an uploaded position is stored as its periodic copy
+    // nearest the reference of the last rebuild (positions are not wrapped between
+    // rebuilds): an unchanged state then keeps its lists
+    launch_load_state(c->d, c->ml, s, (long long)n3, dp, dv, (c->pair && c->lists_built) ? 1 : 0, c->st);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(c->st));
     return QTB_OK;
@@ -1418,6 +1421,17 @@ int qtb_filter_source(qtb_ctx *c, int sys, int *source)
     if (!c || !source) return fail(QTB_ERR_ARG, "null argument");
     if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
     *source = c->ksrc[sys];
+    return QTB_OK;
+}
+
+int qtb_rebuild_lists(qtb_ctx *c)
+{
+    if (!c) return fail(QTB_ERR_ARG, "null context");
+    if (!c->pair) return QTB_OK;
+    // the next call that needs the forces rebuilds every system's lists, the
+    // way the first evaluation after qtb_init does
+    c->lists_built = false;
+    c->stale = true;
     return QTB_OK;
 }
 

@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(128) k_spring(Dev d)
 // form: 30-bit fixed point, u = x/L - floor(x/L) rounded half away from zero to
 // a multiple of 2^-30); external potentials: as given (FP32 in the mixed form).
 template <int PM, class R>
-__global__ void k_load_state(Dev d, int s, const double *pos, const double *vel)
+__global__ void k_load_state(Dev d, int s, const double *pos, const double *vel, int near_ref)
 {
     const DSys S = d.sys[s];
     const long long n3 = 3LL * S.N * S.P, G = d.G;
@@ -245,14 +245,29 @@ __global__ void k_load_state(Dev d, int s, const double *pos, const double *vel)
         const size_t o = (size_t)comp * G + S.g0 + a;
         if (pos) {
             const double x = pos[t], L = S.box[comp];
+            // near_ref (the lists exist): between rebuilds a position moves on without
+            // wrapping, so that the periodic images of the lists stay valid; the
+            // uploaded position is stored as its periodic copy nearest the reference
+            // xref, which makes an unchanged state reproduce the stored one and the
+            // rebuild test measure the true displacement
             if (PM == PM_FIX) {
                 double u = x / L;
                 u -= floor(u);
                 const long long q = (long long)round(u * (double)(1 << kFixBits));
-                reinterpret_cast<int *>(d.x)[o] = (int)(q & ((1LL << kFixBits) - 1));
+                int qm = (int)(q & ((1LL << kFixBits) - 1));
+                if (near_ref) {
+                    const int xr = reinterpret_cast<const int *>(d.xref)[o];
+                    qm = (int)((unsigned)xr + (unsigned)fix_minimg((int)((unsigned)qm - (unsigned)xr)));
+                }
+                reinterpret_cast<int *>(d.x)[o] = qm;
             } else if (PM == PM_BOX64) {
                 double w = x - L * floor(x / L);
                 if (w >= L || w < 0.0) w = 0.0;
+                if (near_ref) {   // w itself unless the reference lies a box length away
+                    const double xr = reinterpret_cast<const double *>(d.xref)[o];
+                    const double k = rint((xr - w) / L);
+                    if (k != 0.0) w += k * L;
+                }
                 reinterpret_cast<double *>(d.x)[o] = w;
             } else {
                 reinterpret_cast<R *>(d.x)[o] = (R)x;
@@ -263,15 +278,15 @@ __global__ void k_load_state(Dev d, int s, const double *pos, const double *vel)
 }
 
 void launch_load_state(const Dev &d, const MdLaunch &m, int s, long long n3, const double *pos, const double *vel,
-                       cudaStream_t st)
+                       int near_ref, cudaStream_t st)
 {
     const int grid = (int)std::min<long long>((n3 + 255) / 256, 4096);
     if (!m.pair) {
-        if (m.mixed) k_load_state<PM_FREE, float><<<grid, 256, 0, st>>>(d, s, pos, vel);
-        else k_load_state<PM_FREE, double><<<grid, 256, 0, st>>>(d, s, pos, vel);
+        if (m.mixed) k_load_state<PM_FREE, float><<<grid, 256, 0, st>>>(d, s, pos, vel, 0);
+        else k_load_state<PM_FREE, double><<<grid, 256, 0, st>>>(d, s, pos, vel, 0);
     } else {
-        if (m.mixed) k_load_state<PM_FIX, float><<<grid, 256, 0, st>>>(d, s, pos, vel);
-        else k_load_state<PM_BOX64, double><<<grid, 256, 0, st>>>(d, s, pos, vel);
+        if (m.mixed) k_load_state<PM_FIX, float><<<grid, 256, 0, st>>>(d, s, pos, vel, near_ref);
+        else k_load_state<PM_BOX64, double><<<grid, 256, 0, st>>>(d, s, pos, vel, near_ref);
     }
 }
 

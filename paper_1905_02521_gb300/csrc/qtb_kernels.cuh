@@ -92,9 +92,11 @@ void launch_centroid(const Dev &d, const MdLaunch &m, int j, int record, cudaStr
 // record of a refreshed step, which no integrator produced)
 void launch_spring(const Dev &d, const MdLaunch &m, cudaStream_t st);
 // positions / velocities (either may be null) of system s, [P][N][3] FP64 in device
-// memory (n3 = 3 N P values), into the state (wrapped / fixed point as the form needs)
+// memory (n3 = 3 N P values), into the state (wrapped / fixed point as the form needs;
+// near_ref, pair potentials with lists built: each position as its periodic copy
+// nearest the reference position of the last rebuild)
 void launch_load_state(const Dev &d, const MdLaunch &m, int s, long long n3, const double *pos, const double *vel,
-                       cudaStream_t st);
+                       int near_ref, cudaStream_t st);
 // positions (which 0, wrapped for pair potentials), velocities (1) or forces (2) of
 // system s into out[P][N][3] (FP64, device memory, n3 = 3 N P values)
 void launch_store_state(const Dev &d, const MdLaunch &m, int s, long long n3, int which, double *out, cudaStream_t st);

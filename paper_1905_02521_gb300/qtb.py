@@ -84,6 +84,7 @@ def lib():
             "qtb_get_noise": ([vp, i, vp, C.POINTER(ll)], i),
             "qtb_get_step": ([vp, C.POINTER(ll)], i),
             "qtb_list_rebuilds": ([vp, C.POINTER(ll)], i),
+            "qtb_rebuild_lists": ([vp], i),
             "qtb_wait_selftest": ([vp, C.POINTER(i), C.POINTER(d)], i),
             "qtb_set_generator": ([vp, i, i], i),
             "qtb_autotune": ([vp, i, vp, vp, i, i, d, i, vp, vp], i),
@@ -302,6 +303,11 @@ def qtb_list_rebuilds(ctx):
     n = C.c_longlong()
     _check(lib().qtb_list_rebuilds(ctx, C.byref(n)))
     return int(n.value)
+
+
+def qtb_rebuild_lists(ctx):
+    """Rebuild every system's neighbour lists at the next force evaluation (see qtb.h)."""
+    _check(lib().qtb_rebuild_lists(ctx))
 
 
 def qtb_wait_selftest(ctx):

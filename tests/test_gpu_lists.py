@@ -6,7 +6,10 @@
   boxes (several periodic images per pair) and larger ones, FP64 and mixed;
 * the skin changes nothing but the summation order (FP64 trajectories with
   and without a skin agree to rounding);
-* a cold crystal with the default skin rebuilds (almost) never.
+* a cold crystal with the default skin rebuilds (almost) never;
+* uploaded states: the state qtb_get_state reports (wrapped into the box) goes
+  back without a rebuild, a moved ion forces one, and qtb_rebuild_lists
+  rebuilds on demand without touching the state.
 Bit-identical fused (graph) and unfused (single-step) stepping is checked by
 test_gpu_parity.py::test_stepping_is_deterministic_and_split_invariant.
 """
@@ -169,6 +172,71 @@ def test_autotune_picks_a_valid_configuration(qtb, oracle):
         f = qtb.qtb_get_forces(ctx, 0, 1, N)[0]
         fo, _, _ = oracle.pair_forces(x[0], s["types"], s["box"], pot)
         assert rel_l2(f, fo) < F32_L2 and rel_inf(f, fo) < F32_INF
+    finally:
+        qtb.qtb_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_state_round_trip_keeps_lists(qtb, oracle, precision):
+    # between rebuilds positions move on without wrapping (the lists' periodic images
+    # stay valid), while qtb_get_state reports them wrapped into the box: uploading
+    # that state again must reproduce the stored one and keep the lists (ions on the
+    # box-edge planes cross the edge within a few steps of every rebuild)
+    s, pot = W.mgo_system(3, 300.0, seed=23)
+    N = len(s["types"])
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=precision, seed=5)     # default skin 0.8 A
+    try:
+        for _ in range(3):
+            qtb.qtb_step_n(ctx, 300)
+            x0, v0 = qtb.qtb_get_state(ctx, 0, 1, N)
+            f0 = qtb.qtb_get_forces(ctx, 0, 1, N)[0]
+            r0 = qtb.qtb_list_rebuilds(ctx)
+            qtb.qtb_set_state(ctx, 0, x0, v0)
+            f1 = qtb.qtb_get_forces(ctx, 0, 1, N)[0]
+            assert qtb.qtb_list_rebuilds(ctx) == r0
+            x1, v1 = qtb.qtb_get_state(ctx, 0, 1, N)
+            assert np.array_equal(v1, v0)
+            if precision == 0:   # an ion across the box edge: one rounding of x -/+ L
+                assert np.abs(minimg(x1 - x0, s["box"])).max() < 1e-12
+            else:                # fixed point: exact
+                assert np.array_equal(x1, x0)
+            fo, _, _ = oracle.pair_forces(x1[0], s["types"], s["box"], pot)
+            if precision == 0:
+                assert rel_inf(f1, f0) < 1e-12 and rel_inf(f1, fo) < 1e-12
+            else:
+                assert rel_inf(f1, f0) < F32_INF
+                assert rel_l2(f1, fo) < F32_L2 and rel_inf(f1, fo) < F32_INF
+    finally:
+        qtb.qtb_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_forced_rebuild_keeps_the_state(qtb, oracle, precision):
+    # qtb_rebuild_lists: one rebuild of every list on the current positions at the next
+    # force evaluation; the state is unchanged, the forces and the steps that follow
+    # match the oracle
+    s, pot = W.mgo_system(3, 300.0, seed=29)
+    N = len(s["types"])
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=precision, seed=6)
+    try:
+        qtb.qtb_step_n(ctx, 300)
+        x0, v0 = qtb.qtb_get_state(ctx, 0, 1, N)
+        r0 = qtb.qtb_list_rebuilds(ctx)
+        qtb.qtb_rebuild_lists(ctx)
+        f = qtb.qtb_get_forces(ctx, 0, 1, N)[0]
+        assert qtb.qtb_list_rebuilds(ctx) == r0 + 1
+        x1, v1 = qtb.qtb_get_state(ctx, 0, 1, N)
+        assert np.array_equal(v1, v0)
+        assert np.abs(minimg(x1 - x0, s["box"])).max() < 1e-12
+        for step in (0, 256):
+            qtb.qtb_step_n(ctx, step)
+            x, _ = qtb.qtb_get_state(ctx, 0, 1, N)
+            f = qtb.qtb_get_forces(ctx, 0, 1, N)[0]
+            fo, _, _ = oracle.pair_forces(x[0], s["types"], s["box"], pot)
+            if precision == 0:
+                assert rel_inf(f, fo) < 1e-12
+            else:
+                assert rel_l2(f, fo) < F32_L2 and rel_inf(f, fo) < F32_INF
     finally:
         qtb.qtb_destroy(ctx)
 
