@@ -58,6 +58,10 @@ def test_host_validation_rejects_bad_arguments(qtb):
         qtb.qtb_init([s], dict(base, dt=0.0))
     with pytest.raises(qtb.QtbError):
         qtb.qtb_kappa_solve(0)
+    for call in (qtb.qtb_rebuild_lists, qtb.qtb_list_rebuilds, qtb.qtb_sync):   # null context
+        with pytest.raises(qtb.QtbError) as e:
+            call(None)
+        assert e.value.code == qtb.ERR_ARG
 
 
 def test_binding_fails_loudly_without_library(monkeypatch):
