@@ -280,7 +280,8 @@ void set_clock(qtb_ctx *c, long long b)
     }
 }
 
-// forces (and energies) at the current positions, lists rebuilt; no velocity kick
+// forces (and energies) at the current positions, the lists rebuilt where needed
+// (all of them at the first evaluation); no velocity kick
 int refresh_forces(qtb_ctx *c)
 {
     set_clock(c, floor_div(c->step, kBlockSteps));
@@ -1175,8 +1176,8 @@ int qtb_set_filter(qtb_ctx *c, int sys, int mode, int n_taps, double omega_max)
     return rebuild_filters(c);
 }
 
-// one force evaluation (lists rebuilt, record of the current step) for all the
-// states set since the last one
+// one force evaluation (lists rebuilt where needed, record of the current step)
+// for all the states set since the last one
 static int ensure_fresh(qtb_ctx *c)
 {
     if (!c->stale) return QTB_OK;
