@@ -3,6 +3,8 @@
 * thermostat off (gamma = 0): energy conservation, time reversibility and
   momentum conservation of the Langevin/BAOAB integrator (Eq. 8 without bath,
   Eq. 4 for the ring polymer);
+* white bath on harmonic oscillators at a large step: the stationary covariance
+  of the B A O A B splitting, solved exactly as a discrete Lyapunov equation;
 * QTB on harmonic oscillators reproduces theta(w0, T) of Eq. 1 up to the
   friction correction, computed independently by quadrature of the Langevin
   response with the filter's own spectral density (Eqs. 6-8);
@@ -57,6 +59,38 @@ def test_ring_polymer_nve_conserves_effective_hamiltonian(oracle):
     rec = sim.step(300)
     H = rec[:, 1] + rec[:, 3] + rec[:, 2]
     assert np.abs(H - (r0[1] + r0[3] + r0[2])).max() < 2e-3 * r0[1]
+
+
+@pytest.mark.slow
+def test_baoab_harmonic_stationary_covariance(oracle):
+    # White bath at omega dt = 0.5, far from the continuous-time limit.  One step
+    # B A O A B is a linear map of (x, v) plus Gaussian noise injected at O, so its
+    # stationary covariance solves a discrete Lyapunov equation.  For this splitting
+    # it is k_B T/(m w^2) in x at any stable step (Leimkuhler & Matthews 2013) and
+    # (k_B T/m)(1 - (w dt/2)^2) in v at the full step; another order of the same
+    # steps (A B O B A: 1/(1 - (w dt/2)^2)) or a wrong noise amplitude misses it by
+    # percents, against a statistical error of ~0.2 % here.
+    from scipy.linalg import solve_discrete_lyapunov
+    w0, T, gamma, dt, m = 0.1, 300.0, 0.02, 5.0, 1.008
+    mk, kT = m * MVV2E, KB * T
+    c = np.exp(-gamma * dt)
+    Bk = np.array([[1.0, 0.0], [-0.5 * dt * w0 ** 2, 1.0]])
+    Ad = np.array([[1.0, 0.5 * dt], [0.0, 1.0]])
+    Ou = np.array([[1.0, 0.0], [0.0, c]])
+    M = Bk @ Ad @ Ou @ Ad @ Bk
+    n = Bk @ Ad @ np.array([0.0, np.sqrt((1.0 - c * c) * kT / mk)])
+    cov = solve_discrete_lyapunov(M, np.outer(n, n))
+    assert cov[0, 0] == pytest.approx(kT / (mk * w0 ** 2), rel=1e-12)
+    assert cov[1, 1] == pytest.approx(kT / mk * (1.0 - (0.5 * w0 * dt) ** 2), rel=1e-12)
+    sysd, pot = W.oscillators(100, T, gamma, mass=m)           # 300 independent oscillators
+    sim = oracle.Sim(sysd["pos"], sysd["vel"], sysd["types"], pot, None, T, gamma, dt, seed=11,
+                     potential=oracle.POT_HARMONIC, ext={"omega": w0})
+    sim.step(500, record=False)
+    rec = sim.step(20000)
+    K, V = rec[:, 1] / 300.0, rec[:, 2] / 300.0                # per oscillator
+    assert abs(K.mean() - 0.5 * mk * cov[1, 1]) < 4 * _block_sigma(K)
+    assert abs(V.mean() - 0.5 * mk * w0 ** 2 * cov[0, 0]) < 4 * _block_sigma(V)
+    assert K.mean() < 0.5 * kT * 0.97                          # the splitting's kinetic bias is resolved
 
 
 def _quad_x2_v2(wgrid_S, w0, gamma, m, wmax):
