@@ -4,7 +4,8 @@
   momentum conservation of the Langevin/BAOAB integrator (Eq. 8 without bath,
   Eq. 4 for the ring polymer);
 * white bath on harmonic oscillators at a large step: the stationary covariance
-  of the B A O A B splitting, solved exactly as a discrete Lyapunov equation;
+  of the B A O A B splitting, solved exactly as a discrete Lyapunov equation,
+  for one bead and per normal mode of a ring polymer (exact free rotation);
 * QTB on harmonic oscillators reproduces theta(w0, T) of Eq. 1 up to the
   friction correction, computed independently by quadrature of the Langevin
   response with the filter's own spectral density (Eqs. 6-8);
@@ -91,6 +92,62 @@ def test_baoab_harmonic_stationary_covariance(oracle):
     assert abs(K.mean() - 0.5 * mk * cov[1, 1]) < 4 * _block_sigma(K)
     assert abs(V.mean() - 0.5 * mk * w0 ** 2 * cov[0, 0]) < 4 * _block_sigma(V)
     assert K.mean() < 0.5 * kT * 0.97                          # the splitting's kinetic bias is resolved
+
+
+def _rp_mode_covariances(w0, P, T, gamma, dt, m, wk):
+    """Stationary (q, v) covariance of each ring-polymer normal mode under one step
+    B(dt/2) A(dt/2) O(dt) A(dt/2) B(dt/2): B kicks with the external force
+    -(m w0^2/P) q (Eq. 4), A is the exact free rotation at w_k (Eq. 11), O the white
+    bath at k_B T; the noise enters at O."""
+    from scipy.linalg import solve_discrete_lyapunov
+    mk, kT, c = m * MVV2E, KB * T, np.exp(-gamma * dt)
+    out = []
+    for w in wk:
+        Bk = np.array([[1.0, 0.0], [-0.5 * dt * w0 ** 2 / P, 1.0]])
+        if w == 0.0:
+            Ar = np.array([[1.0, 0.5 * dt], [0.0, 1.0]])
+        else:
+            cs, sn = np.cos(0.5 * dt * w), np.sin(0.5 * dt * w)
+            Ar = np.array([[cs, sn / w], [-w * sn, cs]])
+        Ou = np.array([[1.0, 0.0], [0.0, c]])
+        n = Bk @ Ar @ np.array([0.0, np.sqrt((1.0 - c * c) * kT / mk)])
+        out.append(solve_discrete_lyapunov(Bk @ Ar @ Ou @ Ar @ Bk, np.outer(n, n)))
+    return out
+
+
+@pytest.mark.slow
+def test_ring_polymer_baoab_stationary_covariance(oracle):
+    # P = 4 ring polymers in a harmonic well at beta hbar w0 = 3 with a 5 fs step:
+    # every normal mode is a linear system, so the exact stationary averages of the
+    # discrete scheme follow from one Lyapunov solve per mode.  The bead-averaged
+    # <x^2>, the kinetic energy and the spring energy of the oracle's trajectory must
+    # match them; a drift in place of the exact free rotation, a missing 1/P on the
+    # external force or a mode transform that is not orthogonal would not.
+    w0, gamma, dt, m, P = 0.1, 0.02, 5.0, 1.008, 4
+    T = HBAR * w0 / (3.0 * KB)
+    mk, kT = m * MVV2E, KB * T
+    wP = np.sqrt(P) * KB * T / HBAR
+    wk = 2 * wP * np.sin(np.arange(P) * np.pi / P)
+    # the construction itself: at a small step the continuous-time ring polymer
+    for w, cov in zip(wk, _rp_mode_covariances(w0, P, T, gamma, 0.01, m, wk)):
+        assert cov[0, 0] == pytest.approx(kT / (mk * (w0 ** 2 / P + w ** 2)), rel=1e-4)
+        assert cov[1, 1] == pytest.approx(kT / mk, rel=1e-4)
+    covs = _rp_mode_covariances(w0, P, T, gamma, dt, m, wk)
+    x2_ex = np.mean([cv[0, 0] for cv in covs])                      # (1/P) sum_k <q_k^2>
+    K_ex = 0.5 * mk * sum(cv[1, 1] for cv in covs)
+    spring_ex = 0.5 * mk * sum(w * w * cv[0, 0] for w, cv in zip(wk, covs))
+    sysd, pot = W.oscillators(100, T, gamma, n_beads=P, mass=m)
+    sim = oracle.Sim(sysd["pos"], sysd["vel"], sysd["types"], pot, None, T, gamma, dt, seed=17,
+                     potential=oracle.POT_HARMONIC, ext={"omega": w0})
+    sim.step(1000, record=False)
+    rec = sim.step(20000)
+    for q, ex in ((17, x2_ex), (1, K_ex), (3, spring_ex)):
+        y = rec[:, q] / 300.0                                         # per 1-D oscillator
+        assert abs(y.mean() - ex) < 4 * _block_sigma(y), (q, y.mean(), ex)
+    # the step is large enough for the discrete scheme to differ from the continuous
+    # limit (kinetic energy P k_B T/2 per oscillator) by more than the tolerance above
+    y = rec[:, 1] / 300.0
+    assert P * kT / 2 - K_ex > 4 * _block_sigma(y) + abs(y.mean() - K_ex)
 
 
 def _quad_x2_v2(wgrid_S, w0, gamma, m, wmax):
