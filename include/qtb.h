@@ -196,10 +196,13 @@ int qtb_get_state(qtb_ctx *c, int sys, double *pos, double *vel);
  * once, at the next call that needs them (qtb_step_n, qtb_sync,
  * qtb_observables, qtb_get_series, qtb_get_state, qtb_get_forces,
  * qtb_list_rebuilds), so that setting several systems costs one force
- * evaluation; an error of that evaluation is returned by that call.  PAIR: a
- * system's neighbour lists are rebuilt then only if one of its bead-atoms lies
- * more than skin/2 from its position at the last rebuild (the criterion of the
- * steps); otherwise they stay valid and are kept. */
+ * evaluation; an error of that evaluation is returned by that call.  PAIR:
+ * positions may lie in any periodic image (each is taken modulo the box, as the
+ * copy nearest its position at the last list rebuild, so the state that
+ * qtb_get_state reports goes back unchanged); a system's neighbour lists are
+ * rebuilt then only if one of its bead-atoms lies more than skin/2 from its
+ * position at the last rebuild (the criterion of the steps); otherwise they
+ * stay valid and are kept. */
 int qtb_set_state(qtb_ctx *c, int sys, const double *pos, const double *vel);
 
 /* Forces [P][N][3] (eV/A) of system sys at the current positions, including the
