@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--filter", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-blocks", type=int, default=3,
+                    help="timed 256-step blocks of the FP64 form of the same workload (0: skip that leg)")
+    ap.add_argument("--matched-blocks", type=int, default=8,
+                    help="256-step blocks of the matched-error run of both forms (0: skip it)")
     # direct launches (two 128-step calls per block) instead of the captured
     # graph (for tools that profile launches outside graphs)
     ap.add_argument("--direct", action="store_true")
@@ -328,9 +332,12 @@ def run_ours(args):
     peak = alu_peak_tflops()
     step_breakdown = {k: round(kernel_ms[k] / max(args.steps, 1), 4) for k in kernel_ms}
 
-    # end to end through the C ABI with host buffers: H2D state, 256 steps, D2H observables
+    # end to end through the C ABI with host buffers: H2D state, 256 steps, D2H
+    # observables and the state reached
     e2e_ms = []
     rebuilds_e2e0 = qtb.qtb_list_rebuilds(ctx)
+    outs = [(pinned(torch, np.zeros_like(xt.numpy())), pinned(torch, np.zeros_like(vt.numpy())))
+            for xt, vt in states]
     for i in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -338,8 +345,9 @@ def run_ours(args):
             x, v = xt.numpy(), vt.numpy()
             qtb.qtb_set_state(ctx, k, x, v)
         qtb.qtb_step_n(ctx, BLOCK)
-        for k in range(len(systems)):
+        for k, (n, p) in enumerate(sizes):
             qtb.qtb_observables(ctx, k)
+            qtb.qtb_get_state_into(ctx, k, outs[k][0].numpy(), outs[k][1].numpy())
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_value = ws * units * BLOCK * args.steps / (np.sum(e2e_ms) / 1e3)
     rebuilds_e2e = (qtb.qtb_list_rebuilds(ctx) - rebuilds_e2e0) / args.steps
@@ -377,7 +385,9 @@ def run_ours(args):
         "kernel_ms_per_bench_step": step_breakdown,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * units * 3 * 8),
-                "d2h_bytes_per_step": int(len(systems) * qtb.NREC * 8), "list_rebuilds_per_step": rebuilds_e2e},
+                "d2h_bytes_per_step": int(len(systems) * qtb.NREC * 8 + 2 * units * 3 * 8),
+                "list_rebuilds_per_step": rebuilds_e2e,
+                "per_step": "state uploaded from pinned host memory, 256 steps, observables and state read back"},
         # per block: white, filter, the integrator (once for one-bead systems, else every
         # step per distinct bead count), 256 step launches (a list rebuild runs inside the
         # step launch that needs it), the centroid estimators of the recorded step (ring
@@ -387,13 +397,107 @@ def run_ours(args):
         "wall_s": wall,
         "observables": {"K_eV": float(obs[1]), "V_eV": float(obs[2]), "step": int(obs[0])},
     }
+    qtb.qtb_destroy(ctx)
+    del flush
+    if args.precision == "mixed" and setup is not None and args.fp64_blocks > 0:
+        # the metric compares the mixed form with the FP64 form at matched error:
+        # the FP64 form of the same workload, timed from the same steady state
+        fp64 = fp64_form_leg(qtb, torch, systems, params, setup, states, units, args.fp64_blocks)
+        fp64["mixed_over_fp64"] = value / fp64["value"]
+        line["fp64_form"] = fp64
+    if args.precision == "mixed" and setup is not None and args.matched_blocks > 0 and len(systems) == 1:
+        line["matched_error"] = matched_error(qtb, systems, params, setup, states[0], args.matched_blocks)
     if ws == 1 and not args.no_cpu_baseline:   # the host baseline belongs to the one-GPU line only
         line["cpu_baseline"] = cpu_baseline(args.workload, sample_atoms=64)
-    qtb.qtb_destroy(ctx)
     if ws > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def fp64_form_leg(qtb, torch, systems, params, setup, states, units, n_blocks):
+    """The FP64 form (every step in FP64, FP64 filter) of the same workload: the
+    mixed form's steady state uploaded, lists rebuilt on it, one warm-up block,
+    then n_blocks device-timed 256-step blocks with an L2 flush between them."""
+    p64 = dict(params, precision=qtb.FP64, filter_prec=qtb.FILTER_FP64)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = qtb.qtb_init(systems, p64, stream=stream.cuda_stream)
+    try:
+        qtb.qtb_set_filter(ctx, -1, *setup)
+        for k, (xt, vt) in enumerate(states):
+            qtb.qtb_set_state(ctx, k, xt.numpy(), vt.numpy())
+        qtb.qtb_rebuild_lists(ctx)
+        qtb.qtb_step_n(ctx, BLOCK)
+        qtb.qtb_sync(ctx)
+        flush = l2_flush_buffer(torch)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_blocks)]
+        torch.cuda.synchronize()
+        for i, (a, b) in enumerate(ev):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+                a.record(stream)
+            qtb.qtb_step_n(ctx, BLOCK)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+    finally:
+        qtb.qtb_destroy(ctx)
+    t = float(np.sum(ms))
+    return {"value": units * BLOCK * n_blocks / (t / 1e3), "unit": UNIT, "ms_per_step": t / n_blocks,
+            "steps": n_blocks, "dtype": "f64", "filter": "fp64 (direct convolution)",
+            "start": "the mixed form's steady state, lists rebuilt, one warm-up block"}
+
+
+# record slots: K, V, E = K + V, virial trace
+MATCHED_OBS = (("K_eV", lambda r: r[:, 1]), ("V_eV", lambda r: r[:, 2]), ("E_eV", lambda r: r[:, 1] + r[:, 2]),
+               ("virial_trace_eV", lambda r: r[:, 5] + r[:, 9] + r[:, 13]))
+
+
+def block_sigma(x, n_blocks=16):
+    """Standard error of the mean of a correlated series by block averaging."""
+    x = np.asarray(x, np.float64)
+    m = len(x) // n_blocks
+    b = x[:m * n_blocks].reshape(n_blocks, m).mean(1)
+    return float(b.std(ddof=1) / np.sqrt(n_blocks))
+
+
+def matched_error(qtb, systems, params, setup, state, n_blocks, stride=4):
+    """Error of the mixed form against the FP64 form at the bench's own size.
+
+    Both forms start from the same steady state (the mixed form's, uploaded to
+    both) at step 0 with the same seed, so they draw the same Philox stream,
+    and run n_blocks 256-step blocks recording every `stride` steps.  The FP64
+    form stands in for the FP64 oracle, to which it is parity-pinned at 1e-12
+    on the configurations the oracle can run.  For each observable: the mean of
+    each form, the FP64 form's block-averaged standard error sigma, and the
+    mixed form's deviation in units of sigma."""
+    nrec = n_blocks * BLOCK // stride
+    x, v = state[0].numpy(), state[1].numpy()
+    series = {}
+    for form, prec, fp in (("fp64", qtb.FP64, qtb.FILTER_FP64), ("mixed", qtb.MIXED, params["filter_prec"])):
+        p = dict(params, precision=prec, filter_prec=fp, obs_stride=stride, max_records=nrec)
+        ctx = qtb.qtb_init(systems, p)
+        try:
+            qtb.qtb_set_filter(ctx, -1, *setup)
+            qtb.qtb_set_state(ctx, 0, x, v)
+            qtb.qtb_step_n(ctx, n_blocks * BLOCK)
+            series[form] = qtb.qtb_get_series(ctx, 0, nrec)
+        finally:
+            qtb.qtb_destroy(ctx)
+    out = {"steps": n_blocks * BLOCK, "record_stride": stride, "reference": "FP64 GPU form (parity-pinned to the "
+           "FP64 oracle at 1e-12)", "sigma": "block average, 16 blocks", "observables": {}}
+    worst = 0.0
+    for name, get in MATCHED_OBS:
+        a, b = get(series["fp64"]), get(series["mixed"])
+        sig = block_sigma(a)
+        dev = (b.mean() - a.mean()) / sig if sig > 0 else 0.0
+        worst = max(worst, abs(dev))
+        out["observables"][name] = {"fp64": float(a.mean()), "mixed": float(b.mean()), "sigma": sig,
+                                    "mixed_minus_fp64_in_sigma": float(dev)}
+    out["max_abs_deviation_in_sigma"] = worst
+    out["matched"] = bool(worst <= 2.0)
+    return out
 
 
 def measured_traffic(kernel, workload_name):

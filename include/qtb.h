@@ -173,14 +173,26 @@ int qtb_set_filter(qtb_ctx *c, int sys, int mode, int n_taps, double omega_max);
 typedef enum { QTB_GEN_FILTER = 0, QTB_GEN_FOURIER = 1 } qtb_generator;
 int qtb_set_generator(qtb_ctx *c, int generator, int segment_blocks);
 
-/* Advance every system by n_steps BAOAB steps (asynchronous).  Whole 256-step
- * noise blocks run as one CUDA-graph launch. */
+/* Advance every system by n_steps steps of the Langevin equation of motion
+ * (asynchronous): Eq. 8 for one bead (QTB-MD, the random force of Eqs. 6-7) and
+ * Eq. 4 with the ring-polymer springs of Eq. 3 for P beads (PIMD; QTB-PIMD
+ * with the random force of Eq. 12 on the normal modes of Eq. 11).  The paper
+ * does not fix the integrator; the reading used is BAOAB: a half kick by the
+ * forces (B), the exact free ring-polymer motion for dt/2 per normal mode (A),
+ * the friction and random force over dt (O: v <- c1 v + sqrt((1 - c1^2)/m) eta,
+ * c1 = exp(-gamma dt)), A, new forces, B.  Whole 256-step noise blocks run as
+ * one CUDA-graph launch.  n_steps >= 0 (0: no-op). */
 int qtb_step_n(qtb_ctx *c, long long n_steps);
 
 /* Wait for the stream; report device-side errors of earlier steps. */
 int qtb_sync(qtb_ctx *c);
 
-/* Latest observable record of system sys (QTB_NREC doubles, host). */
+/* Latest observable record of system sys (QTB_NREC doubles, host; layout
+ * above): the kinetic and potential energies and the primitive energy
+ * estimator of Eq. 5 (E = K - spring + V, with the spring term of Eq. 3 and
+ * V/P per replica of Eq. 4), the virial, the total momentum, the mean square
+ * position and the centroid-virial kinetic estimators.  Synchronises; returns
+ * a device-side error of an earlier step if one was raised. */
 int qtb_observables(qtb_ctx *c, int sys, double *out);
 
 /* All records kept for system sys, oldest first: out[max][QTB_NREC]; *n_out =
@@ -342,17 +354,19 @@ int qtb_set_kappa_model(qtb_ctx *c, const qtb_kappa_model *model);
 int qtb_filter_source(qtb_ctx *c, int sys, int *source);
 
 /* Same solve as qtb_kappa_solve for callers that cannot allocate device
- * memory (no counterpart in the paper; an interface convenience).  Callers in
- * a stream-capture region, processes whose device memory is all reserved by
- * another allocator, or latency-critical loops cannot call cudaMalloc; this
- * entry point allocates nothing: its scratch is a static __device__ array of
- * 6.3 MB in the library, present on every device that loads the library until
- * the process exits.
+ * memory (no counterpart in the paper; an interface convenience).  A process
+ * whose device memory is all reserved by another allocator (a caching pool
+ * that owns the device, an MPS client with a fixed memory limit) cannot get a
+ * cudaMalloc through, and a latency-critical loop must not call it, since an
+ * allocation can block and synchronise the device.  This entry point
+ * allocates nothing: its scratch is a static __device__ array of 6.3 MB in the
+ * library, present on every device that loads the library until the process
+ * exits.
  *   n        collocation nodes, 8 <= n <= 512 (QTB_ERR_ARG beyond: the scratch
  *            is sized for 512)
  *   F_dev    [n] DEVICE output buffer owned by the caller (F_P at the nodes)
- *   stream   cudaStream_t to run on (NULL = legacy default stream); the call
- *            synchronises it before returning.
+ *   stream   cudaStream_t to run on (NULL = legacy default stream); every call,
+ *            P = 1 included, synchronises it before returning.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
  * any stream capture.  All calls share the one array and it keeps the last

@@ -549,13 +549,15 @@ int ensure_kappa(qtb_ctx *c, int P)
     double *A = (double *)c->alloc(sizeof(double) * (size_t)rows * n);
     double *b = (double *)c->alloc(sizeof(double) * rows);
     double *M = (double *)c->alloc(sizeof(double) * (size_t)n * n);
-    if (!F || !A || !b || !M) return fail(QTB_ERR_OOM, "kappa_P solve: device allocation failed");
-    launch_kappa_solve(P, n, ymax, y0, A, b, M, F, c->d.err, c->st);
+    double *work = (double *)c->alloc(sizeof(double) * (size_t)(rows + n));
+    if (!F || !A || !b || !M || !work) return fail(QTB_ERR_OOM, "kappa_P solve: device allocation failed");
+    launch_kappa_solve(P, n, ymax, y0, A, b, M, F, work, c->d.err, c->st);
     CUDA_TRY(cudaGetLastError());
     int rc = check_err_word(c);
     c->release(A);
     c->release(b);
     c->release(M);
+    c->release(work);
     if (rc) return rc;
     c->kappaF[P] = F;
     return QTB_OK;
@@ -1498,16 +1500,17 @@ int qtb_kappa_solve(int P, int n, double y_max, double y0, double *F)
     const int rows = 2 * n - 1;
     double *A = nullptr, *b = nullptr, *M = nullptr, *r = nullptr;
     unsigned *err = nullptr;
-    size_t need = sizeof(double) * ((size_t)rows * n + rows + (size_t)n * n + n) + 16;
+    size_t need = sizeof(double) * ((size_t)rows * n + rows + (size_t)n * n + n + rows + n) + 16;
     char *base = nullptr;
     CUDA_TRY(cudaMalloc(&base, need));
     A = (double *)base;
     b = A + (size_t)rows * n;
     M = b + rows;
     r = M + (size_t)n * n;
-    err = (unsigned *)(r + n);
+    double *work = r + n;
+    err = (unsigned *)(work + rows + n);
     cudaMemset(err, 0, sizeof(unsigned));
-    launch_kappa_solve(P, n, y_max, y0, A, b, M, r, err, 0);
+    launch_kappa_solve(P, n, y_max, y0, A, b, M, r, work, err, 0);
     unsigned e = 0;
     cudaError_t ce = cudaGetLastError();
     if (ce == cudaSuccess) ce = cudaMemcpy(F, r, sizeof(double) * n, cudaMemcpyDeviceToHost);

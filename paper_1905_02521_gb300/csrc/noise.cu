@@ -326,6 +326,40 @@ __global__ void k_kappa_trsv(int n, const double *M, double *r)
     }
 }
 
+// Refinement of the least-squares solution (corrected semi-normal equations,
+// Bjorck): s = b - A x, g = A^T s, solve L L^T d = g with the Cholesky factor
+// already in M, x += d.  The normal equations alone leave an error of order
+// cond(A)^2 eps; each refinement step brings it towards cond(A) eps, the
+// accuracy of an orthogonal-factorisation solve.
+
+// s[m] = b[m] - A[m,:] x; one warp per row
+__global__ void k_kappa_resid(int rows, int n, const double *A, const double *b, const double *x, double *s)
+{
+    const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (m >= rows) return;
+    const double *Ar = A + (size_t)m * n;
+    double acc = 0.0;
+    for (int i = lane; i < n; i += 32) acc += Ar[i] * x[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) s[m] = b[m] - acc;
+}
+
+// g[i] = sum_m A[m,i] s[m]; one thread per column
+__global__ void k_kappa_atv(int rows, int n, const double *A, const double *s, double *g)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = 0.0;
+    for (int m = 0; m < rows; ++m) acc += A[(size_t)m * n + i] * s[m];
+    g[i] = acc;
+}
+
+__global__ void k_kappa_add(int n, double *x, const double *d)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] += d[i];
+}
+
 // ---------------------------------------------------------------------------
 // Fourier-segment generator (Eq. 9): segments of n = 256 M steps per dof,
 // eta_t = (1/sqrt(n)) sum_j c_j e^{+2 pi i j t/n}, c_0 = sqrt(S_0) xi_0,
@@ -483,7 +517,7 @@ void launch_spectrum_taps(const DSpec *spec, int nsys, int Kmax, double *S, doub
 }
 
 void launch_kappa_solve(int P, int n, double ymax, double y0, double *A, double *b, double *M, double *r,
-                        unsigned *err, cudaStream_t st)
+                        double *work, unsigned *err, cudaStream_t st)
 {
     int rows = 2 * n - 1;
     cudaMemsetAsync(A, 0, sizeof(double) * (size_t)rows * n, st);
@@ -491,6 +525,13 @@ void launch_kappa_solve(int P, int n, double ymax, double y0, double *A, double 
     k_kappa_normal<<<dim3((n + 31) / 32, (n + 31) / 32), 256, 0, st>>>(rows, n, A, b, M, r);
     k_kappa_chol<<<1, 1024, 0, st>>>(n, M, err);
     k_kappa_trsv<<<1, 1024, 0, st>>>(n, M, r);
+    double *s = work, *g = work + rows;
+    for (int it = 0; it < kKappaRefine; ++it) {
+        k_kappa_resid<<<(rows * 32 + 255) / 256, 256, 0, st>>>(rows, n, A, b, r, s);
+        k_kappa_atv<<<(n + 127) / 128, 128, 0, st>>>(rows, n, A, s, g);
+        k_kappa_trsv<<<1, 1024, 0, st>>>(n, M, g);
+        k_kappa_add<<<(n + 255) / 256, 256, 0, st>>>(n, r, g);
+    }
 }
 
 

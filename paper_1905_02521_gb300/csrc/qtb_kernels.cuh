@@ -40,8 +40,11 @@ cudaError_t fourier_prepare(int n);
 void launch_spectrum_seg(const DSpec *spec, int nsys, int n, void *sq, int fp64, cudaStream_t st);
 void launch_fourier(const Dev &d, int fp64, int max_dofp, int nsys, const void *sq, const void *tw, int n, int force,
                     cudaStream_t st);
+// kappa_P solve on the collocation grid (Eq. 10): A [(2n-1) x n], b [2n-1], M [n x n]
+// scratch, work [(2n-1) + n] scratch of the refinement steps, r [n] the solution
+constexpr int kKappaRefine = 1;  // corrected semi-normal-equation refinement steps
 void launch_kappa_solve(int P, int n, double ymax, double y0, double *A, double *b, double *M, double *r,
-                        unsigned *err, cudaStream_t st);
+                        double *work, unsigned *err, cudaStream_t st);
 
 // md.cu
 struct MdLaunch {

@@ -273,6 +273,16 @@ def qtb_get_state(ctx, sys, n_beads, n_atoms):
     return pos, vel
 
 
+def qtb_get_state_into(ctx, sys, pos, vel):
+    """qtb_get_state into caller-owned C-contiguous float64 arrays [P][N][3]
+    (e.g. views of page-locked host memory); either may be None."""
+    for a in (pos, vel):
+        if a is not None:
+            assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    _check(lib().qtb_get_state(ctx, sys, None if pos is None else pos.ctypes.data,
+                               None if vel is None else vel.ctypes.data))
+
+
 def qtb_set_state(ctx, sys, pos=None, vel=None):
     pos = None if pos is None else np.ascontiguousarray(pos, np.float64)
     vel = None if vel is None else np.ascontiguousarray(vel, np.float64)

@@ -4,9 +4,11 @@ same seeded inputs.  Tolerances:
 * FP64 form: 1e-12 norm-wise (max |diff| / RMS) on forces, states and noise;
 * mixed form: forces within 1e-5 norm-wise of the oracle evaluated on the GPU's
   own configuration (per step, first 100 steps); FP32 noise within 1e-5;
-* kappa_P: the GPU solves the same least-squares problem by normal equations +
-  Cholesky, the oracle by LAPACK; both agree to cond(A)^2 eps ~ 1e-8, so 1e-6
-  relative is required.
+* kappa_P: the GPU solves the same least-squares problem (Eq. 10 on the
+  collocation grid) by normal equations + Cholesky followed by one step of
+  corrected semi-normal-equation refinement, the oracle by LAPACK; both reach
+  cond(A) eps (cond <= 7e3 for P <= 32), so 1e-10 relative is required per
+  node and for the taps.
 """
 import numpy as np
 import pytest
@@ -42,7 +44,7 @@ def qtb():
 def test_kappa_solve_matches_oracle(qtb, P):
     Fg = qtb.qtb_kappa_solve(P, n=1024, y_max=1000.0, y0=1.0)
     sol = S.kappa_solve(P, n=1024, ymax=1000.0, y0=1.0)
-    assert np.allclose(Fg, sol.F, rtol=1e-6, atol=0)
+    assert np.allclose(Fg, sol.F, rtol=1e-10, atol=0), np.abs(Fg / sol.F - 1).max()
 
 
 def test_taps_match_oracle(qtb):
@@ -67,7 +69,7 @@ def test_kappa_taps_match_oracle(qtb):
         qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB_PIMD, 257, 0.6)
         h = qtb.qtb_get_taps(ctx, 0)
         ho = S.taps(257, 0.25, 50.0, 0.6, P=4, sol=S.kappa_solve(4))
-        assert rel_inf(h, ho) < 1e-6
+        assert rel_inf(h, ho) < 1e-10
     finally:
         qtb.qtb_destroy(ctx)
 
@@ -126,13 +128,21 @@ def test_forces_match_oracle(qtb, oracle, ncell, precision, tol):
         qtb.qtb_destroy(ctx)
 
 
+def _oracle_taps(qtb, mode, n_taps, dt, T, omega_max, P):
+    """The oracle's taps of a noise mode: theta (Eq. 7) or kappa_P (Eqs. 10, 12)."""
+    if mode == qtb.NOISE_QTB:
+        return S.taps(n_taps, dt, T, omega_max)
+    if mode == qtb.NOISE_QTB_PIMD:
+        return S.taps(n_taps, dt, T, omega_max, P=P, sol=S.kappa_solve(P))
+    return None
+
+
 def _traj_compare(qtb, oracle, s, pot, dt, mode, n_taps, omega_max, nsteps, check_every, tol, P=1):
     ctx = gpu_ctx(qtb, [s], pot, dt, precision=0, seed=4321)
     try:
-        taps = None
-        if mode == qtb.NOISE_QTB:
+        taps = _oracle_taps(qtb, mode, n_taps, dt, s["T"], omega_max, P)
+        if taps is not None:
             qtb.qtb_set_filter(ctx, 0, mode, n_taps, omega_max)
-            taps = S.taps(n_taps, dt, s["T"], omega_max)
         sim = oracle_sim(oracle, s, pot, dt, seed=4321, taps=taps)
         N = len(s["types"])
         done = 0
@@ -156,9 +166,26 @@ def _traj_compare(qtb, oracle, s, pot, dt, mode, n_taps, omega_max, nsteps, chec
 
 
 def test_fp64_qtb_trajectory_matches_oracle(qtb, oracle):
-    # 64-ion MgO, QTB-MD, 513 taps: per-step state and forces over 100 steps
+    # 64-ion MgO, QTB-MD, 513 taps: state and forces after every one of the
+    # first 100 steps
     s, pot = W.mgo_system(2, 300.0)
-    _traj_compare(qtb, oracle, s, pot, 1.0, qtb.NOISE_QTB, 513, 0.3, 100, 10, 1e-12)
+    _traj_compare(qtb, oracle, s, pot, 1.0, qtb.NOISE_QTB, 513, 0.3, 100, 1, 1e-12)
+
+
+@pytest.mark.parametrize("P", [4, 8])
+def test_fp64_qtb_pimd_trajectory_matches_oracle(qtb, oracle, P):
+    # QTB-PIMD (Sec. 2.3): kappa_P of Eq. 10 in the taps (Eq. 12), the time-domain
+    # filter over all 3 N P normal-mode dofs (dof = (k 3 + c) N + i), the O step
+    # in mode space, per-bead forces with the 1/P of Eq. 4.  64-ion LiH at 50 K,
+    # dt 0.25 fs, gamma 0.01/fs (so that the coloured force moves the state
+    # visibly each step), 257 taps; state, velocities and forces after every one
+    # of the first 100 steps.  (Rounding-order differences grow along the stiff
+    # ring-polymer trajectory as in the white PIMD test: 1e-11.)
+    s, pot = W.lih_system(2, 50.0, gamma=1e-2, n_beads=P)
+    s["box"] = np.array([8.16] * 3)
+    rng = np.random.default_rng(11)
+    s["pos"] = s["pos"] + rng.normal(0, 0.01, s["pos"].shape)
+    _traj_compare(qtb, oracle, s, pot, 0.25, qtb.NOISE_QTB_PIMD, 257, 0.6, 100, 1, 1e-11, P=P)
 
 
 @pytest.mark.parametrize("P", [4, 16])
@@ -179,9 +206,8 @@ def test_mixed_forces_on_own_configuration_first_100_steps(qtb, oracle):
     ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=1, filter_prec=1)
     try:
         qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB, 513, 0.3)
-        worst = 0.0
-        for _ in range(10):
-            qtb.qtb_step_n(ctx, 10)
+        for _ in range(100):   # after every one of the first 100 steps
+            qtb.qtb_step_n(ctx, 1)
             x, _ = qtb.qtb_get_state(ctx, 0, 1, N)
             f = qtb.qtb_get_forces(ctx, 0, 1, N)[0]
             fo, _, _ = oracle.pair_forces(x[0], s["types"], s["box"], pot)
@@ -207,6 +233,46 @@ def test_mixed_single_step_matches_oracle_step(qtb, oracle):
         xo, vo, _, _ = sim.state()
         assert np.abs(minimg(x1 - xo, s["box"])).max() < 1e-5
         assert rel_inf(v1, vo) < 1e-5
+    finally:
+        qtb.qtb_destroy(ctx)
+
+
+@pytest.mark.parametrize("filter_prec", [1, 2])
+def test_mixed_qtb_pimd_single_step_matches_oracle_step(qtb, oracle, filter_prec):
+    # one QTB-PIMD step (P = 8, kappa_P taps) of the mixed form from the GPU's own
+    # state, against the oracle's FP64 step from the same state.  FP32 filter:
+    # positions within 1e-5 A, velocities within 1e-5 norm-wise.  BF16
+    # tensor-core filter: the noise itself differs from the FP64 convolution by
+    # up to RMS 4 * 2^-8 of RMS(eta) (the filter's bound, tests/test_gpu_filter_tc.py),
+    # which the O step passes on as sqrt((1 - c1^2)/m) times that; the velocity
+    # error may use that much on top of the 1e-5 of the deterministic part.
+    P, L, dt, T, gamma, wmax = 8, 257, 0.25, 50.0, 1e-2, 0.6
+    s, pot = W.lih_system(2, T, gamma=gamma, n_beads=P)
+    s["box"] = np.array([8.16] * 3)
+    s["pos"] = s["pos"] + np.random.default_rng(12).normal(0, 0.01, s["pos"].shape)
+    N = len(s["types"])
+    ctx = gpu_ctx(qtb, [s], pot, dt, precision=1, filter_prec=filter_prec, seed=99)
+    try:
+        qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB_PIMD, L, wmax)
+        qtb.qtb_step_n(ctx, 37)
+        x0, v0 = qtb.qtb_get_state(ctx, 0, P, N)
+        h = S.taps(L, dt, T, wmax, P=P, sol=S.kappa_solve(P))
+        sim = oracle_sim(oracle, s, pot, dt, seed=99, taps=h)
+        sim.set_state(x0, v0, 37)
+        qtb.qtb_step_n(ctx, 1)
+        sim.step(1, record=False)
+        x1, v1 = qtb.qtb_get_state(ctx, 0, P, N)
+        xo, vo, _, _ = sim.state()
+        assert np.abs(minimg(x1 - xo, s["box"])).max() < 1e-5
+        if filter_prec == 1:
+            assert rel_inf(v1, vo) < 1e-5
+        else:
+            m = pot["mass"][s["types"]] * W.MVV2E
+            c1 = np.exp(-gamma * dt)
+            kick = np.sqrt((1.0 - c1 * c1) * (h[0] ** 2 + 2.0 * (h[1:] ** 2).sum()) / m)   # RMS noise kick per atom
+            kick_rms = np.sqrt((kick ** 2).mean())
+            err = np.sqrt(((v1 - vo) ** 2).mean())
+            assert err < 1e-5 * np.sqrt((vo ** 2).mean()) + 4 * 2.0 ** -8 * kick_rms, (err, kick_rms)
     finally:
         qtb.qtb_destroy(ctx)
 

@@ -1,7 +1,8 @@
 """The allocation-free kappa_P entry point (qtb_kappa_solve_noalloc).
 
-It is meant for callers that cannot allocate device memory (inside a stream
-capture, under a fully reserved memory pool, in latency-critical loops); its
+It is meant for callers that cannot allocate device memory: a process whose
+device memory is all reserved by another allocator (cudaMalloc would fail) or a
+latency-critical loop (an allocation can block and synchronise the device); its
 scratch is a static device array in the library.  Its output must match the
 allocating entry point qtb_kappa_solve within the kappa_P tolerance of the
 parity tests, on two calls in a row (the second call reuses the array that the
@@ -35,6 +36,22 @@ def test_noalloc_matches_allocating_solve_on_consecutive_calls(qtb):
         qtb.qtb_kappa_solve_noalloc(P, n, ymax, y0, out.data_ptr(), stream.cuda_stream)
         got = out.cpu().numpy()
         ref = qtb.qtb_kappa_solve(P, n=n, y_max=ymax, y0=y0)
+        assert np.all(np.isfinite(got))
+        assert np.allclose(got, ref, rtol=KAPPA_RTOL, atol=0)
+
+
+def test_noalloc_one_bead_returns_theta_after_synchronising(qtb):
+    # P = 1: kappa_1 = theta, no solve.  The call synchronises its stream before
+    # returning, so the result is read on another stream without waiting.
+    import torch
+    n, ymax, y0 = 300, 400.0, 1.0
+    stream = torch.cuda.Stream()
+    ref = qtb.qtb_kappa_solve(1, n=n, y_max=ymax, y0=y0)
+    for _ in range(2):
+        out = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        qtb.qtb_kappa_solve_noalloc(1, n, ymax, y0, out.data_ptr(), stream.cuda_stream)
+        got = out.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert np.allclose(got, ref, rtol=KAPPA_RTOL, atol=0)
 
