@@ -285,15 +285,18 @@ typedef struct {
  * layouts {1, 2}, and for several systems the rebuild scopes {0, 1} -- it creates a context for the given systems and parameters
  * (qtb_init), applies the filter (noise_mode, n_taps, omega_max; as
  * qtb_set_filter on every system), runs n_blocks 256-step warm-up blocks and
- * then times n_blocks >= 1 blocks (so the list-rebuild rate of a system that has
- * left its initial configuration is in the timing), and writes
- * into *best a copy of *p with the fastest skin, nm_layout, list_lanes and
- * rebuild_scope.  The
+ * then times n_blocks >= 1 blocks, and writes into *best a copy of *p with the
+ * fastest skin, nm_layout, list_lanes and rebuild_scope.  equil_blocks >= 0:
+ * first the systems are advanced equil_blocks 256-step blocks with the default
+ * parameters, and every candidate (the defaults included) starts from the
+ * configuration reached, its lists built on it, so that the timing sees the list
+ * lengths and the rebuild rate of a long run rather than those of the initial
+ * configuration (0: every candidate starts from the given positions).  The
  * candidates change the summation order and the rebuild schedule only, not the
  * dynamics.  Pair potentials only (QTB_ERR_ARG otherwise).  stream: as qtb_init.
  * Allocates and frees one context at a time; synchronises. */
 int qtb_autotune(const qtb_system *sys, int n_sys, const qtb_params *p, void *stream, int noise_mode, int n_taps,
-                 double omega_max, int n_blocks, qtb_params *best, qtb_tuning *result);
+                 double omega_max, int n_blocks, int equil_blocks, qtb_params *best, qtb_tuning *result);
 
 /* Current step index (number of steps taken). */
 int qtb_get_step(qtb_ctx *c, long long *step);

@@ -87,7 +87,7 @@ def lib():
             "qtb_rebuild_lists": ([vp], i),
             "qtb_wait_selftest": ([vp, C.POINTER(i), C.POINTER(d)], i),
             "qtb_set_generator": ([vp, i, i], i),
-            "qtb_autotune": ([vp, i, vp, vp, i, i, d, i, vp, vp], i),
+            "qtb_autotune": ([vp, i, vp, vp, i, i, d, i, i, vp, vp], i),
             "qtb_set_profiling": ([vp, i], i),
             "qtb_kernel_times": ([vp, vp, vp, i], i),
             "qtb_kappa_solve": ([i, i, d, d, vp], i),
@@ -222,15 +222,16 @@ class qtb_tuning(C.Structure):
                 ("default_ms_per_step", C.c_double), ("n_tried", C.c_int)]
 
 
-def qtb_autotune(systems, params, mode=0, n_taps=1, omega_max=0.0, n_blocks=2, stream=None):
+def qtb_autotune(systems, params, mode=0, n_taps=1, omega_max=0.0, n_blocks=2, equil_blocks=0, stream=None):
     """Times the candidate skins, lane counts, integrator layouts and rebuild
-    scopes on these systems (see qtb.h) and returns (params with the fastest
+    scopes on these systems (see qtb.h), each from the state reached after
+    equil_blocks blocks with the defaults, and returns (params with the fastest
     choice, tuning dict)."""
     arr, p, stream, keep = _c_args(systems, params, stream)
     best = qtb_params()
     res = qtb_tuning()
     _check(lib().qtb_autotune(C.cast(arr, C.c_void_p), len(systems), C.addressof(p), stream, int(mode), int(n_taps),
-                              float(omega_max), int(n_blocks), C.addressof(best), C.byref(res)))
+                              float(omega_max), int(n_blocks), int(equil_blocks), C.addressof(best), C.byref(res)))
     tuned = dict(params, skin=best.skin, nm_layout=best.nm_layout, list_lanes=best.list_lanes,
                  rebuild_scope=best.rebuild_scope)
     info = {k: getattr(res, k) for k, _ in qtb_tuning._fields_}

@@ -158,7 +158,8 @@ def test_autotune_picks_a_valid_configuration(qtb, oracle):
     from helpers import gpu_params
     s, pot = W.mgo_system(4, 300.0)
     params = gpu_params(pot, 1.0, precision=1, filter_prec=1, seed=5)
-    tuned, info = qtb.qtb_autotune([s], params, qtb.NOISE_QTB, 513, 0.3, n_blocks=1)
+    # candidates timed from the state reached after two blocks (lists built on it)
+    tuned, info = qtb.qtb_autotune([s], params, qtb.NOISE_QTB, 513, 0.3, n_blocks=1, equil_blocks=2)
     print("autotune:", info)
     assert info["n_tried"] == 1 + 4 * 3
     assert 0 < info["ms_per_step"] <= info["default_ms_per_step"]
