@@ -8,6 +8,8 @@
 // sqrt(S(w_j)) on the grid w_j = 2 pi j/(L dt), S = theta W or kappa_P W.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "qtb_dev.cuh"
 #include "qtb_kernels.cuh"
 
@@ -213,7 +215,7 @@ __global__ void k_taps(const DSpec *spec, const double *S, double *h64, float *h
 
 // ---------------------------------------------------------------------------
 // kappa_P solve (Eq. 10), FP64: dense collocation rows, normal equations,
-// Cholesky (one CTA), triangular solves (one CTA).
+// blocked Cholesky (many CTAs), triangular solves (one CTA), one refinement step.
 
 // rows m < 2n-1; A is (2n-1) x n row-major, zeroed by the caller
 __global__ void k_kappa_rows(int P, int n, double ymax, double y0, double *A, double *b)
@@ -282,29 +284,95 @@ __global__ void k_kappa_normal(int rows, int n, const double *A, const double *b
     }
 }
 
-// In-place Cholesky of the lower triangle of M (n x n); one CTA.
-__global__ void k_kappa_chol(int n, double *M, unsigned *err)
+// Blocked right-looking Cholesky of the lower triangle of M (n x n, row-major),
+// panels of kCholNb columns: for each panel k0 the diagonal block is factored
+// by one CTA (k_chol_diag), the rows below it are solved against that factor
+// (k_chol_panel, L21 = A21 L11^-T, one CTA per kCholNb rows), and the trailing
+// lower triangle is updated, A22 -= L21 L21^T, by one CTA per kCholNb x
+// kCholNb tile (k_chol_update).  Same arithmetic as the unblocked
+// factorisation up to the order of the sums; a non-positive pivot sets
+// ERR_SOLVE (the solve then continues on a placeholder pivot).
+constexpr int kCholNb = 32;
+
+__global__ void k_chol_diag(int n, int k0, double *M, unsigned *err)
 {
-    __shared__ double dj;
-    for (int j = 0; j < n; ++j) {
-        if (threadIdx.x == 0) {
-            double v = M[(size_t)j * n + j];
+    __shared__ double a[kCholNb][kCholNb + 1];
+    const int nb = min(kCholNb, n - k0);
+    const int r = threadIdx.x / kCholNb, c = threadIdx.x % kCholNb;
+    const bool in = r < nb && c < nb && c <= r;
+    if (in) a[r][c] = M[(size_t)(k0 + r) * n + k0 + c];
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        if (r == j && c == j) {
+            double v = a[j][j];
             if (!(v > 0.0)) { atomicOr(err, (unsigned)ERR_SOLVE); v = 1e-300; }
-            dj = sqrt(v);
-            M[(size_t)j * n + j] = dj;
+            a[j][j] = sqrt(v);
         }
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) M[(size_t)i * n + j] /= dj;
+        if (in && c == j && r > j) a[r][j] /= a[j][j];
         __syncthreads();
-        // trailing update of the lower triangle: rows i > j, columns j < k <= i
-        {
-            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-            for (int i = j + 1 + warp; i < n; i += nw) {
-                const double lij = M[(size_t)i * n + j];
-                for (int k = j + 1 + lane; k <= i; k += 32) M[(size_t)i * n + k] -= lij * M[(size_t)k * n + j];
-            }
-        }
+        if (in && c > j) a[r][c] -= a[r][j] * a[c][j];
         __syncthreads();
+    }
+    if (in) M[(size_t)(k0 + r) * n + k0 + c] = a[r][c];
+}
+
+// rows r0 = k0 + nb + blockIdx.x kCholNb .. (+kCholNb) of the panel: X L11^T = A21
+__global__ void k_chol_panel(int n, int k0, double *M)
+{
+    __shared__ double L[kCholNb][kCholNb + 1], X[kCholNb][kCholNb + 1];
+    const int nb = min(kCholNb, n - k0);
+    const int r0 = k0 + nb + blockIdx.x * kCholNb;
+    const int r = threadIdx.x / kCholNb, c = threadIdx.x % kCholNb;
+    const bool row_in = r0 + r < n && c < nb;
+    L[r][c] = (r < nb && c <= r) ? M[(size_t)(k0 + r) * n + k0 + c] : 0.0;
+    X[r][c] = row_in ? M[(size_t)(r0 + r) * n + k0 + c] : 0.0;
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        if (c == j) X[r][j] /= L[j][j];
+        __syncthreads();
+        if (c > j && c < nb) X[r][c] -= X[r][j] * L[c][j];
+        __syncthreads();
+    }
+    if (row_in) M[(size_t)(r0 + r) * n + k0 + c] = X[r][c];
+}
+
+// trailing update of the lower triangle below the panel; blockIdx.x enumerates the
+// tiles (ti >= tj) of the (n - k0 - nb)^2 trailing matrix in kCholNb blocks
+__global__ void k_chol_update(int n, int k0, double *M)
+{
+    __shared__ double Li[kCholNb][kCholNb + 1], Lj[kCholNb][kCholNb + 1];
+    const int nb = min(kCholNb, n - k0);
+    const int t0 = k0 + nb;
+    int t = blockIdx.x, ti = 0;
+    while (t > ti) { t -= ti + 1; ++ti; }  // tile (ti, tj = t), tj <= ti
+    const int tj = t;
+    const int ri0 = t0 + ti * kCholNb, rj0 = t0 + tj * kCholNb;
+    for (int e = threadIdx.x; e < kCholNb * kCholNb; e += blockDim.x) {
+        const int a = e / kCholNb, q = e % kCholNb;
+        Li[a][q] = (ri0 + a < n && q < nb) ? M[(size_t)(ri0 + a) * n + k0 + q] : 0.0;
+        Lj[a][q] = (rj0 + a < n && q < nb) ? M[(size_t)(rj0 + a) * n + k0 + q] : 0.0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kCholNb * kCholNb; e += blockDim.x) {
+        const int a = e / kCholNb, b = e % kCholNb;
+        const int row = ri0 + a, col = rj0 + b;
+        if (row >= n || col > row) continue;
+        double acc = 0.0;
+        for (int q = 0; q < nb; ++q) acc += Li[a][q] * Lj[b][q];
+        M[(size_t)row * n + col] -= acc;
+    }
+}
+
+static void chol_blocked(int n, double *M, unsigned *err, cudaStream_t st)
+{
+    for (int k0 = 0; k0 < n; k0 += kCholNb) {
+        const int nb = std::min(kCholNb, n - k0), rest = n - k0 - nb;
+        k_chol_diag<<<1, kCholNb * kCholNb, 0, st>>>(n, k0, M, err);
+        if (rest <= 0) break;
+        const int nt = (rest + kCholNb - 1) / kCholNb;
+        k_chol_panel<<<nt, kCholNb * kCholNb, 0, st>>>(n, k0, M);
+        k_chol_update<<<nt * (nt + 1) / 2, 256, 0, st>>>(n, k0, M);
     }
 }
 
@@ -523,7 +591,7 @@ void launch_kappa_solve(int P, int n, double ymax, double y0, double *A, double 
     cudaMemsetAsync(A, 0, sizeof(double) * (size_t)rows * n, st);
     k_kappa_rows<<<(rows + 127) / 128, 128, 0, st>>>(P, n, ymax, y0, A, b);
     k_kappa_normal<<<dim3((n + 31) / 32, (n + 31) / 32), 256, 0, st>>>(rows, n, A, b, M, r);
-    k_kappa_chol<<<1, 1024, 0, st>>>(n, M, err);
+    chol_blocked(n, M, err, st);
     k_kappa_trsv<<<1, 1024, 0, st>>>(n, M, r);
     double *s = work, *g = work + rows;
     for (int it = 0; it < kKappaRefine; ++it) {

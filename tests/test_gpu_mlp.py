@@ -133,3 +133,112 @@ def test_model_taps_reproduce_eq10_on_oscillators(qtb, oracle, model):
     target = S.theta(w0, T) / (m * 103.64269652680505 * w0 ** 2)
     # friction correction at gamma/w0 = 0.1 is a few per cent (see the solver-tap test)
     assert x2.mean() == pytest.approx(target, rel=0.06)
+
+
+def _block_sigma(x, nb=16):
+    """Standard error of the mean of a correlated series by block averaging."""
+    x = np.asarray(x, np.float64)
+    m = len(x) // nb
+    b = x[:m * nb].reshape(nb, m).mean(1)
+    return b.std(ddof=1) / np.sqrt(nb)
+
+
+def _model_dev(qtb, model, P):
+    """The solver-judged largest deviation of the model's kappa_P/theta for P."""
+    info = qtb.qtb_kappa_model_info(model)
+    return dict(zip(info["P"], info["err"]))[P]
+
+
+def _bound(sig, dev, ref):
+    # statistics (2 sigma of the difference of the two runs' means) plus the
+    # model's accepted error: its random-force spectrum differs from the
+    # solver's by at most `dev` relative, so an average that responds linearly
+    # to the spectrum moves by at most that much (1.5x margin for the
+    # anharmonic response)
+    return 2.0 * sig + 1.5 * dev * abs(ref)
+
+
+@pytest.mark.parametrize("P", [4, 8])
+def test_model_double_wells_match_solver_taps(qtb, model, P):
+    # the learned kappa_P in the double-well study of zero-point-energy leakage
+    # (32769 quartic wells, V0 = 0.1 eV, a = 0.5 A, m = 1.008 u, 100 K, dt 0.5 fs,
+    # 2049 taps): bead-averaged <x^2> and <V> under QTB_NOISE_QTB_PIMD_MLP against
+    # the same run with the solver's taps (Eq. 10), same seed: within 2 sigma
+    # (block averages) plus the model's solver-judged deviation
+    V0, a, m, T, dt, nat = 0.1, 0.5, 1.008, 100.0, 0.5, 10923
+    out = {}
+    for mode in ("solver", "model"):
+        s, pot = W.oscillators(nat, T, 0.004, n_beads=P, x0=a, spread=0.05, mass=m)
+        ctx = gpu_ctx(qtb, [s], pot, dt, precision=1, filter_prec=1, seed=11, potential=qtb.POT_DOUBLEWELL,
+                      ext={"V0": V0, "a": a}, obs_stride=8, max_records=4096)
+        try:
+            if mode == "model":
+                qtb.qtb_set_kappa_model(ctx, model)
+                qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB_PIMD_MLP, 2049, 0.6)
+                assert qtb.qtb_filter_source(ctx, 0) == 2
+            else:
+                qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB_PIMD, 2049, 0.6)
+            qtb.qtb_step_n(ctx, 8192)
+            qtb.qtb_step_n(ctx, 16384)
+            ser = qtb.qtb_get_series(ctx, 0, 2048)
+        finally:
+            qtb.qtb_destroy(ctx)
+        out[mode] = ser / (3 * nat)
+    dev = _model_dev(qtb, model, P)
+    for k, name in ((17, "<x^2>"), (2, "<V>")):
+        a_, b_ = out["solver"][:, k], out["model"][:, k]
+        sig = np.hypot(_block_sigma(a_), _block_sigma(b_))
+        diff = b_.mean() - a_.mean()
+        print(f"P={P} {name}: solver {a_.mean():.6g} model {b_.mean():.6g}: diff {diff / abs(a_.mean()):+.2e} "
+              f"relative ({diff / sig:+.2f} sigma), model deviation {dev:.2e}")
+        assert abs(diff) < _bound(sig, dev, a_.mean())
+
+
+def test_model_lih_qtb_pimd_p4(qtb, oracle, model):
+    # LiH 6x6x6 (1728 ions) x 4 beads, QTB-PIMD at 50 K, dt 0.25 fs, 2049 taps, mixed
+    # form: under the learned kappa_P the per-bead forces on the run's own
+    # configuration match the oracle (FP32 criterion), and K, V, E_prim (Eq. 5) and
+    # the virial trace agree with the run with the solver's taps within 2 sigma
+    # plus the model's solver-judged deviation
+    from tolerances import F32_INF, F32_L2
+    from helpers import rel_inf, rel_l2
+    P = 4
+    rec = {}
+    for mode in ("solver", "model"):
+        s, pot = W.lih_system(6, 50.0, gamma=1e-3, n_beads=P)
+        N = len(s["types"])
+        ctx = gpu_ctx(qtb, [s], pot, 0.25, precision=1, filter_prec=1, seed=21, obs_stride=8, max_records=4096)
+        try:
+            if mode == "model":
+                qtb.qtb_set_kappa_model(ctx, model)
+                qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB_PIMD_MLP, 2049, 0.6)
+                assert qtb.qtb_filter_source(ctx, 0) == 2
+            else:
+                qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB_PIMD, 2049, 0.6)
+            qtb.qtb_step_n(ctx, 8192)
+            qtb.qtb_step_n(ctx, 16384)
+            rec[mode] = qtb.qtb_get_series(ctx, 0, 2048)
+            if mode == "model":
+                x, _ = qtb.qtb_get_state(ctx, 0, P, N)
+                f = qtb.qtb_get_forces(ctx, 0, P, N)
+                for b in (0, P - 1):
+                    fo, _, _ = oracle.pair_forces(x[b], s["types"], s["box"], pot,
+                                                  sel=np.arange(0, N, 27))
+                    fo = fo / P    # Eq. 4: each bead feels (1/P) grad V
+                    fb = f[b][np.arange(0, N, 27)]
+                    assert rel_l2(fb, fo) < F32_L2 and rel_inf(fb, fo) < F32_INF
+        finally:
+            qtb.qtb_destroy(ctx)
+    dev = _model_dev(qtb, model, P)
+    for k, name in ((1, "K"), (2, "V"), (4, "E_prim"), (None, "virial trace")):
+        get = (lambda r: r[:, 5] + r[:, 9] + r[:, 13]) if k is None else (lambda r, k=k: r[:, k])
+        a_, b_ = get(rec["solver"]), get(rec["model"])
+        sig = np.hypot(_block_sigma(a_), _block_sigma(b_))
+        diff = b_.mean() - a_.mean()
+        print(f"LiH P=4 {name}: solver {a_.mean():.6g} model {b_.mean():.6g} ({diff / sig:+.2f} sigma), "
+              f"model deviation {dev:.2e}")
+        # V, E_prim and the virial are dominated by the static lattice sums
+        # (~1e4 eV), which the random force does not set: the spectrum's error
+        # scales the thermal (zero-point) part, whose size is that of K
+        scale = rec["solver"][:, 1].mean()
+        assert abs(diff) < _bound(sig, dev, scale)
