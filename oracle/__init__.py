@@ -27,7 +27,7 @@ from . import spectra  # noqa: F401
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qtb_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libqtb_oracle.so")
-NREC = 20
+NREC = 21
 
 POT_PAIR, POT_HARMONIC, POT_DOUBLEWELL = 0, 1, 2
 
@@ -69,6 +69,7 @@ def lib():
         L.ora_sim_observe.argtypes = [C.c_void_p, dp]
         L.ora_sim_get.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]
         L.ora_sim_set.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
+        L.ora_sim_cell.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -136,18 +137,22 @@ class _Params(C.Structure):
                 ("ext_V0", C.c_double), ("ext_a", C.c_double), ("seed", C.c_uint64), ("sys", C.c_uint32),
                 ("pad0", C.c_int32), ("mass", C.c_void_p), ("charge", C.c_void_p), ("bA", C.c_void_p),
                 ("brho", C.c_void_p), ("bC", C.c_void_p), ("type", C.c_void_p), ("x0", C.c_void_p),
-                ("v0", C.c_void_p), ("K", C.c_int), ("pad1", C.c_int32), ("h", C.c_void_p)]
+                ("v0", C.c_void_p), ("K", C.c_int), ("pad1", C.c_int32), ("h", C.c_void_p),
+                ("npt", C.c_int), ("pad2", C.c_int32), ("pext", C.c_double), ("wmass", C.c_double),
+                ("gamma_e", C.c_double)]
 
 
 class Sim:
     """One system (N atoms x P beads) advanced by the oracle's BAOAB integrator.
 
     ``pos``/``vel`` are [P, N, 3]; ``taps`` (h_0..h_K) selects coloured noise,
-    ``None`` white Langevin noise at temperature T.
+    ``None`` white Langevin noise at temperature T.  ``npt`` = dict(pressure
+    (eV/A^3), mass (eV fs^2), gamma (1/fs)) makes the run isothermal-isobaric
+    (one bead, pair potential; see qtb_oracle.c).
     """
 
     def __init__(self, pos, vel, types, pot, box, T, gamma, dt, seed, sys=0, taps=None,
-                 potential=POT_PAIR, ext=None):
+                 potential=POT_PAIR, ext=None, npt=None):
         pos = np.ascontiguousarray(pos, np.float64)
         P, N = pos.shape[0], pos.shape[1]
         vel = np.zeros_like(pos) if vel is None else np.ascontiguousarray(vel, np.float64)
@@ -182,6 +187,10 @@ class Sim:
         if taps is not None:
             p.K = len(taps) - 1
             p.h = keep["h"].ctypes.data
+        if npt is not None:
+            assert P == 1 and potential == POT_PAIR
+            p.npt = 1
+            p.pext, p.wmass, p.gamma_e = float(npt["pressure"]), float(npt["mass"]), float(npt["gamma"])
         self.N, self.P = N, P
         self._p = p
         self._s = lib().ora_sim_create(C.byref(p))
@@ -207,6 +216,13 @@ class Sim:
         st = C.c_int64(0)
         lib().ora_sim_get(self._s, x.ctypes.data, v.ctypes.data, f.ctypes.data, C.byref(st))
         return x, v, f, st.value
+
+    def cell(self):
+        """(cell edges [3] in A, cell momentum p_e in eV fs)."""
+        box = np.zeros(3)
+        pe = C.c_double(0.0)
+        lib().ora_sim_cell(self._s, box.ctypes.data, C.byref(pe))
+        return box, pe.value
 
     def set_state(self, x, v, step):
         x = np.ascontiguousarray(x, np.float64)

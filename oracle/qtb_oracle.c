@@ -31,7 +31,18 @@
  *     A(dt/2) in normal-mode space (exact free ring-polymer rotation), force,
  *     B(dt/2);  O: v <- c1 v + sqrt((1-c1^2)/m) eta, c1 = exp(-gamma dt);
  *   - pair potential: energy-shifted Buckingham + damped shifted force
- *     Coulomb (Fennell & Gezelter 2006), all periodic images within r_c.
+ *     Coulomb (Fennell & Gezelter 2006), all periodic images within r_c;
+ *   - isothermal-isobaric runs (Sec. 2.1: the paper uses Quigley and Probert's
+ *     Langevin extension to constant pressure, refs [11, 12], and prints no
+ *     equations): isotropic Martyna-Tobias-Klein equations with Langevin
+ *     friction and noise on the particles and on the cell,
+ *       dr/dt = v + v_e r,   m dv/dt = F - alpha m v_e v - gamma m v + R,
+ *       dV/dt = 3 V v_e,     dp_e/dt = G - gamma_e p_e + R_e,  v_e = p_e / W,
+ *       G = 2 alpha K + Wvir - 3 V P_ext,  alpha = 1 + 3/N_f,  N_f = 3N,
+ *     Wvir = sum over pairs of r_ij . F_ij; split as B_e(dt/2) B(dt/2) A(dt/2)
+ *     O(dt) A(dt/2) force B(dt/2) B_e(dt/2), each B and A the exact solution of
+ *     its linear equation; the cell's random force is Philox stream 1, dof 0
+ *     (one bead only).  Stationary law: P(V) ~ V^N exp(-(U + P_ext V)/k_B T).
  *
  * Units: A, fs, eV, u, e, K.
  */
@@ -46,7 +57,7 @@
 #define ORA_KE 14.3996454784            /* e^2/(4 pi eps0) in eV A         */
 #define ORA_PI 3.14159265358979323846
 
-#define ORA_NREC 20
+#define ORA_NREC 21
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10, from its published definition: 10 rounds of
@@ -268,6 +279,11 @@ typedef struct {
     int K;
     int32_t pad1;
     const double *h;
+    /* isothermal-isobaric cell (npt = 1; one bead): external pressure P_ext
+     * (eV/A^3), cell mass W (eV fs^2), cell friction gamma_e (1/fs) */
+    int npt;
+    int32_t pad2;
+    double pext, wmass, gamma_e;
 } ora_params;
 
 typedef struct {
@@ -283,6 +299,10 @@ typedef struct {
     int wsz;
     double *win;
     int64_t gen_upto; /* quads generated for steps < gen_upto (multiple of 4) */
+    /* isothermal-isobaric cell: momentum p_e of the log-volume / 3 and whether
+     * the closing half kick of the previous step is still to be applied */
+    double peps;
+    int pending;
 } ora_sim;
 
 static double *dup(const double *a, size_t n)
@@ -429,6 +449,7 @@ static void observe(ora_sim *s, double *rec)
     for (int a = 0; a < 9; ++a) rec[5 + a] = s->vir[a];
     for (int c = 0; c < 3; ++c) rec[14 + c] = mom[c];
     rec[17] = x2 / P;
+    rec[20] = (s->p.potential == 0) ? s->p.box[0] * s->p.box[1] * s->p.box[2] : 0.0; /* cell volume */
     /* Centroid-virial kinetic estimators.  With the bead forces f_s = -(1/P)
      * grad V(r_s) of Eq. 4 and the centroid rbar = (1/P) sum_s r_s of each atom,
      *   K_cv   = 3N k_B T/2 - 1/2 sum_i sum_s (r_i,s - rbar_i) . f_i,s
@@ -464,9 +485,99 @@ static void observe(ora_sim *s, double *rec)
     rec[19] = K0 - 0.5 * cv;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Isothermal-isobaric step (one bead, pair potential): the equations and the
+ * splitting are in the header comment.  Positions are physical (A); the cell
+ * edges scale by exp(v_e t).                                                   */
+static double kinetic(const ora_sim *s)
+{
+    double K = 0.0;
+    for (int i = 0; i < s->p.N; ++i)
+        for (int c = 0; c < 3; ++c) {
+            double v = s->v[(size_t)i * 3 + c];
+            K += 0.5 * s->mass_t[s->type[i]] * ORA_MVV2E * v * v;
+        }
+    return K;
+}
+
+/* dG: the cell's generalised force 2 alpha K + Wvir - 3 V P_ext */
+static double cell_force(const ora_sim *s, double alpha)
+{
+    double V = s->p.box[0] * s->p.box[1] * s->p.box[2];
+    double wvir = s->vir[0] + s->vir[4] + s->vir[8];
+    return 2.0 * alpha * kinetic(s) + wvir - 3.0 * V * s->p.pext;
+}
+
+/* B(dt/2): exact solution of dv/dt = F/m - alpha v_e v */
+static void kick_npt(ora_sim *s, double alpha, double ve, double h)
+{
+    double x = alpha * ve * h;
+    double e = exp(-x);
+    double g = (x != 0.0) ? -expm1(-x) / x : 1.0; /* (1 - e^{-x}) / x */
+    for (int i = 0; i < s->p.N; ++i) {
+        double m = s->mass_t[s->type[i]] * ORA_MVV2E;
+        for (int c = 0; c < 3; ++c) {
+            size_t k = (size_t)i * 3 + c;
+            s->v[k] = s->v[k] * e + h * s->f[k] / m * g;
+        }
+    }
+}
+
+/* A(dt/2): exact solution of dr/dt = v + v_e r, the cell edges scaled alike */
+static void drift_npt(ora_sim *s, double ve, double h)
+{
+    double x = ve * h;
+    double e = exp(x);
+    double g = (x != 0.0) ? expm1(x) / x : 1.0; /* (e^{x} - 1) / x */
+    for (size_t k = 0; k < (size_t)s->p.N * 3; ++k) s->x[k] = s->x[k] * e + s->v[k] * h * g;
+    for (int c = 0; c < 3; ++c) s->p.box[c] *= e;
+}
+
+static void step_npt(ora_sim *s, double *rec1)
+{
+    int N = s->p.N, D = 3 * N;
+    double dt = s->p.dt, h = 0.5 * dt;
+    double c1 = exp(-s->p.gamma * dt), ce = exp(-s->p.gamma_e * dt);
+    double alpha = 1.0 + 3.0 / (3.0 * N);
+    double W = s->p.wmass;
+    double *eta = dup(NULL, (size_t)D);
+    int64_t n = s->step;
+    noise_at(s, n, eta);
+    /* B_e(dt/2): the closing half of the previous step (if any), then this one */
+    double G = cell_force(s, alpha);
+    if (s->pending) s->peps += h * G;
+    s->peps += h * G;
+    double ve = s->peps / W;
+    kick_npt(s, alpha, ve, h);  /* B */
+    drift_npt(s, ve, h);        /* A */
+    for (int i = 0; i < N; ++i) { /* O, particles */
+        double m = s->mass_t[s->type[i]] * ORA_MVV2E;
+        double sig = sqrt((1.0 - c1 * c1) / m);
+        for (int c = 0; c < 3; ++c) {
+            size_t k = (size_t)i * 3 + c;
+            s->v[k] = c1 * s->v[k] + sig * eta[(size_t)c * N + i];
+        }
+    }
+    /* O, cell: white noise at k_B T, Philox stream 1, dof 0 */
+    double xi = ora_white(s->p.seed, s->p.sys, 0u, 1u, n);
+    s->peps = ce * s->peps + sqrt((1.0 - ce * ce) * W * ORA_KB * s->p.T) * xi;
+    ve = s->peps / W;
+    drift_npt(s, ve, h);        /* A */
+    compute_forces(s);
+    kick_npt(s, alpha, ve, h);  /* B; B_e(dt/2) closes at the next step */
+    s->pending = 1;
+    s->step += 1;
+    if (rec1) observe(s, rec1);
+    free(eta);
+}
+
 /* Advance nsteps BAOAB steps; if rec != NULL write one record per step. */
 void ora_sim_step(ora_sim *s, int64_t nsteps, double *rec)
 {
+    if (s->p.npt) {
+        for (int64_t it = 0; it < nsteps; ++it) step_npt(s, rec ? rec + (size_t)it * ORA_NREC : NULL);
+        return;
+    }
     int N = s->p.N, P = s->p.P, D = 3 * N * P;
     double dt = s->p.dt;
     double c1 = exp(-s->p.gamma * dt);
@@ -563,3 +674,10 @@ void ora_sim_set(ora_sim *s, const double *x, const double *v, int64_t step)
 }
 
 int ora_nrec(void) { return ORA_NREC; }
+
+/* Cell edges (A) and cell momentum p_e of an isothermal-isobaric run. */
+void ora_sim_cell(const ora_sim *s, double *box, double *peps)
+{
+    if (box) memcpy(box, s->p.box, sizeof(double) * 3);
+    if (peps) *peps = s->peps;
+}
