@@ -124,6 +124,23 @@ typedef struct {
                               bit for bit as it would alone); 1 every system of the
                               context (fewer, larger rebuilds for batches of hot and
                               cold systems; results change at the rounding level). */
+    /* Isothermal-isobaric runs (Sec. 2.1: the paper's constant-pressure
+     * simulations use Quigley and Probert's Langevin extension, refs [11, 12];
+     * it prints no equations).  npt = 1: every system's cell is an isotropic
+     * Langevin barostat, the isotropic Martyna-Tobias-Klein equations with
+     * friction and noise on the particles and on the cell:
+     *   dr/dt = v + v_e r,  m dv/dt = F - (1 + 3/N_f) m v_e v - gamma m v + R,
+     *   dV/dt = 3 V v_e,    dp_e/dt = 2 (1 + 3/N_f) K + W_vir - 3 V P_ext
+     *                                 - cell_gamma p_e + R_e,   v_e = p_e / cell_mass,
+     * N_f = 3N, W_vir the pair virial; R the particle random force of the chosen
+     * noise (QTB: Eq. 7), R_e white at k_B T.  Stationary law:
+     * P(V) ~ V^N exp(-(U + P_ext V)/k_B T) for the white bath.  One bead and the
+     * pair potential only; the cell may shrink to 0.9 of its initial edges
+     * (QTB_ERR_STATE below that: the cell lists keep that margin). */
+    int npt;               /* 0: constant volume; 1: isotropic Langevin barostat        */
+    double pressure;       /* P_ext, eV/A^3 (1 GPa = 6.241509e-3 eV/A^3)                */
+    double cell_mass;      /* W, eV fs^2 (> 0)                                          */
+    double cell_gamma;     /* friction of the cell, 1/fs (>= 0)                          */
 } qtb_params;
 
 /* Observable record (FP64), one per recorded step and system:
@@ -138,8 +155,9 @@ typedef struct {
  *   [19] K_cv,0: the same with 3N k_B T/2 replaced by the centroid-mode kinetic
  *        energy sum_i m_i P |vbar_i|^2/2 (a bath that does not hold the centroid
  *        at k_B T: QTB-PIMD).  The paper prints neither (only Eq. 5).  One
- *        bead: [18] = 3N k_B T/2, [19] = K. */
-#define QTB_NREC 20
+ *        bead: [18] = 3N k_B T/2, [19] = K.
+ *   [20] cell volume (A^3; constant unless npt; 0 for external potentials) */
+#define QTB_NREC 21
 
 /* Create a context for n_sys independent systems sharing one parameter set.
  * Copies the host arrays, allocates device state, computes the first forces.
@@ -300,6 +318,11 @@ int qtb_autotune(const qtb_system *sys, int n_sys, const qtb_params *p, void *st
 
 /* Current step index (number of steps taken). */
 int qtb_get_step(qtb_ctx *c, long long *step);
+
+/* Cell of system sys: edges box[3] (A) and, for an isothermal-isobaric run,
+ * the cell momentum p_e (eV fs; 0 otherwise).  Either pointer may be NULL.
+ * Synchronises. */
+int qtb_get_cell(qtb_ctx *c, int sys, double *box, double *p_e);
 
 /* kappa_P / (k_B T) = F_P(y), y = beta hbar w, solved in FP64 on the GPU on the
  * collocation grid y_i = y0 sinh(i t), t = asinh(y_max/y0)/(n-1), i < n:

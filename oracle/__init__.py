@@ -70,6 +70,7 @@ def lib():
         L.ora_sim_get.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]
         L.ora_sim_set.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
         L.ora_sim_cell.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.ora_sim_set_cell.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_int]
         _lib = L
     return _lib
 
@@ -223,6 +224,10 @@ class Sim:
         pe = C.c_double(0.0)
         lib().ora_sim_cell(self._s, box.ctypes.data, C.byref(pe))
         return box, pe.value
+
+    def set_cell(self, box, peps, pending=1):
+        box = np.ascontiguousarray(box, np.float64)
+        lib().ora_sim_set_cell(self._s, box.ctypes.data, float(peps), int(pending))
 
     def set_state(self, x, v, step):
         x = np.ascontiguousarray(x, np.float64)

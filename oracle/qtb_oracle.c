@@ -675,6 +675,16 @@ void ora_sim_set(ora_sim *s, const double *x, const double *v, int64_t step)
 
 int ora_nrec(void) { return ORA_NREC; }
 
+/* Replace the cell of an isothermal-isobaric run (edges, momentum, whether the
+ * previous step's closing half kick is due) and recompute the forces. */
+void ora_sim_set_cell(ora_sim *s, const double *box, double peps, int pending)
+{
+    memcpy(s->p.box, box, sizeof(double) * 3);
+    s->peps = peps;
+    s->pending = pending;
+    compute_forces(s);
+}
+
 /* Cell edges (A) and cell momentum p_e of an isothermal-isobaric run. */
 void ora_sim_cell(const ora_sim *s, double *box, double *peps)
 {

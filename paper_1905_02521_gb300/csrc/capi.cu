@@ -222,6 +222,9 @@ int check_err_word(qtb_ctx *c)
     if (e & ERR_SOLVE) return fail(QTB_ERR_SOLVE, "kappa_P solve: non-positive pivot");
     if (e & ERR_TIMEOUT_TC) return fail(QTB_ERR_TIMEOUT, "tensor-core filter: a bounded barrier wait gave up");
     if (e & ERR_TIMEOUT_BAR) return fail(QTB_ERR_TIMEOUT, "step kernel: a bounded grid-barrier wait gave up");
+    if (e & ERR_CELL)
+        return fail(QTB_ERR_STATE, "npt: the cell shrank below %.2f of its initial edges (the margin of its cell lists)",
+                    kCellMinScale);
     return QTB_OK;
 }
 
@@ -472,15 +475,18 @@ int run_steps(qtb_ctx *c, int j0, int count, bool graph)
         const int j = j0 + t, cur = j & 1;
         const bool keep = c->capturing;
         if (j % 64 != 0) c->capturing = false;
+        if (c->p.npt) launch_cell(c->d, j, cur, c->p.r_cut + c->skin, c->skin, c->st);  // isothermal-isobaric cells
         if (!m.fused || t == 0) {
             ProfMark pm(c, KC_INTEGRATE);
             launch_integrate(c->d, m, j, cur, c->st);
         }
         const int adv = (m.fused && t < count - 1) ? 1 : 0;
-        // may this step be recorded? (inside the graph the block index is only known on the device)
+        // may this step be recorded? (inside the graph the block index is only known on the device);
+        // the cells need every step's kinetic energy and virial
         int rec;
         if (graph) rec = (kBlockSteps % obs == 0) ? ((j + 1) % obs == 0) : 1;
         else rec = ((c->step + t + 1) % obs == 0) ? 1 : 0;
+        if (c->p.npt) rec = 1;
         {
             ProfMark pm(c, KC_FORCE);
             CUDA_TRY(launch_force(c->d, m, c->tabf, c->tab, 1, j, cur, adv, rec, c->st));
@@ -706,6 +712,14 @@ int validate(const qtb_system *sys, int n_sys, const qtb_params *p)
     if (p->list_lanes != 0 && p->list_lanes != 8 && p->list_lanes != 16 && p->list_lanes != 32)
         return fail(QTB_ERR_ARG, "list_lanes must be 0, 8, 16 or 32");
     if (p->rebuild_scope != 0 && p->rebuild_scope != 1) return fail(QTB_ERR_ARG, "rebuild_scope must be 0 or 1");
+    if (p->npt != 0 && p->npt != 1) return fail(QTB_ERR_ARG, "npt must be 0 or 1");
+    if (p->npt) {
+        if (p->potential != QTB_POT_PAIR) return fail(QTB_ERR_ARG, "npt: pair potential only");
+        if (!(p->cell_mass > 0) || !(p->cell_gamma >= 0)) return fail(QTB_ERR_ARG, "npt: cell_mass > 0, cell_gamma >= 0");
+        if (!std::isfinite(p->pressure)) return fail(QTB_ERR_ARG, "npt: pressure must be finite");
+        for (int s = 0; s < n_sys; ++s)
+            if (sys[s].n_beads != 1) return fail(QTB_ERR_ARG, "npt: one bead per atom only (system %d)", s);
+    }
     if (p->potential == QTB_POT_PAIR) {
         if (!p->charge || !p->buck_A || !p->buck_rho || !p->buck_C) return fail(QTB_ERR_ARG, "pair tables missing");
         if (!(p->r_cut > 0)) return fail(QTB_ERR_ARG, "r_cut must be > 0");
@@ -848,7 +862,10 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         int cp = (int)roundup((long long)std::ceil(1.25 * e + 4.0 * std::sqrt(e) + 8.0), 8);
         return std::min(cp, (int)roundup(q.n_atoms, 8));
     };
-    const double cell_edge = 0.5 * r_list;
+    // an isothermal-isobaric cell may shrink to kCellMinScale of its edges: the
+    // cells (in the reference cell) and the lists keep that margin
+    const double cell_edge = 0.5 * r_list / (p->npt ? kCellMinScale : 1.0);
+    const double dens_margin = p->npt ? 1.0 / (kCellMinScale * kCellMinScale * kCellMinScale) : 1.0;
     int stage_cap = 0, maxnb = 32;
     if (c->pair) {
         double ecell = 0.0;
@@ -859,7 +876,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
             ecell = std::max(ecell, (double)sys[s].n_atoms / (nc[0] * nc[1] * nc[2]));
             // list capacity: 1.5 x the mean population of the list sphere plus a margin
             const double rho = sys[s].n_atoms / (sys[s].box[0] * sys[s].box[1] * sys[s].box[2]);
-            maxnb = std::max(maxnb, (int)roundup((long long)std::ceil(1.5 * rho * vlist + 64.0), 32));
+            maxnb = std::max(maxnb, (int)roundup((long long)std::ceil(1.5 * rho * dens_margin * vlist + 64.0), 32));
         }
         // staging chunk of the list build: 1.5 x the mean stencil population plus a
         // margin, between 512 entries (the sort keys share the buffer) and 1024
@@ -1019,7 +1036,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         }
     }
     m.nm_big = nm_big;
-    m.fused = c->pair ? 1 : 0;
+    m.fused = (c->pair && !p->npt) ? 1 : 0;  // the cell needs each step's reduced virial between steps
     for (int s = 0; s < n_sys; ++s)
         if (c->hs[s].P != 1) m.fused = 0;
     if (integrate_prepare(m) != cudaSuccess)
@@ -1123,6 +1140,28 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     d.done = (unsigned *)c->alloc(sizeof(unsigned) * n_sys);
     if (!d.done) return bail(fail(QTB_ERR_OOM, "device allocation failed"));
     cudaMemsetAsync(d.done, 0, sizeof(unsigned) * n_sys, c->st);
+    d.npt = nullptr;
+    if (p->npt) {
+        std::vector<DNpt> cells((size_t)n_sys);
+        for (int s = 0; s < n_sys; ++s) {
+            DNpt &C = cells[s];
+            memset(&C, 0, sizeof C);
+            C.lam = C.lam_rb = 1.0;
+            C.W = p->cell_mass;
+            C.pext = p->pressure;
+            C.ce = std::exp(-p->cell_gamma * p->dt);
+            C.sige = std::sqrt((1.0 - C.ce * C.ce) * C.W * kBoltz * sys[s].T);
+            C.alpha = 1.0 + 1.0 / sys[s].n_atoms;  // 1 + 3/N_f, N_f = 3N
+            C.V0 = sys[s].box[0] * sys[s].box[1] * sys[s].box[2];
+            C.e1 = C.g1 = C.e2 = C.g2 = 1.0;
+            C.a1 = C.a2 = 0.5 * p->dt;
+            C.e1f = C.g1f = C.e2f = C.g2f = C.lamf = 1.0f;
+            C.a1f = C.a2f = (float)(0.5 * p->dt);
+            C.on = 1;
+        }
+        d.npt = upload(c, cells);
+        if (!d.npt) return bail(fail(QTB_ERR_OOM, "device allocation failed"));
+    }
     if (ccta) {
         d.cpart = (double *)c->alloc(sizeof(double) * 2 * (size_t)ccta);
         d.cdone = (unsigned *)c->alloc(sizeof(unsigned) * n_sys);
@@ -1483,6 +1522,27 @@ int qtb_get_step(qtb_ctx *c, long long *step)
 {
     if (!c || !step) return fail(QTB_ERR_ARG, "null argument");
     *step = c->step;
+    return QTB_OK;
+}
+
+int qtb_get_cell(qtb_ctx *c, int sys, double *box, double *p_e)
+{
+    if (!c) return fail(QTB_ERR_ARG, "null context");
+    if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
+    if (int rc0 = ensure_fresh(c)) return rc0;
+    int rc = check_err_word(c);
+    if (rc) return rc;
+    double lam = 1.0, pe = 0.0;
+    if (c->d.npt) {
+        DNpt C;
+        CUDA_TRY(cudaMemcpyAsync(&C, c->d.npt + sys, sizeof C, cudaMemcpyDeviceToHost, c->st));
+        CUDA_TRY(cudaStreamSynchronize(c->st));
+        lam = C.lam;
+        pe = C.peps;
+    }
+    if (box)
+        for (int k = 0; k < 3; ++k) box[k] = c->hs[sys].box[k] * lam;
+    if (p_e) *p_e = pe;
     return QTB_OK;
 }
 

@@ -244,7 +244,9 @@ __global__ void k_load_state(Dev d, int s, const double *pos, const double *vel,
         const int comp = (int)(t - 3 * a);
         const size_t o = (size_t)comp * G + S.g0 + a;
         if (pos) {
-            const double x = pos[t], L = S.box[comp];
+            // isothermal-isobaric cell: the state is kept in the reference cell
+            const double lam = (d.npt && d.npt[s].on) ? d.npt[s].lam : 1.0;
+            const double x = pos[t] / lam, L = S.box[comp];
             // near_ref (the lists exist): between rebuilds a position moves on without
             // wrapping, so that the periodic images of the lists stay valid; the
             // uploaded position is stored as its periodic copy nearest the reference
@@ -315,6 +317,7 @@ __global__ void k_store_state(Dev d, int s, int which, double *out)
             const void *src = (which == 0) ? d.x : (which == 1) ? d.v : d.f;
             x = (double)reinterpret_cast<const R *>(src)[o];
         }
+        if (which == 0 && PM != PM_FREE && d.npt && d.npt[s].on) x *= d.npt[s].lam;  // physical position
         out[t] = x;
     }
 }
@@ -346,7 +349,11 @@ __global__ void k_refresh_check(Dev d, int cur)
     for (int s = 0; s < d.nsys; ++s) {
         const DSys &S = d.sys[s];
         const long long gn = (long long)S.N * S.P;
-        const R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
+        R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
+        if (d.npt && d.npt[s].on) {  // as the integrator: physical displacement against (3/8 skin)^2
+            const R l = (R)d.npt[s].lam;
+            lim = lim * R(0.5625) / (l * l);
+        }
         bool moved = false;
         for (long long l = ((tid - S.g0) % nth + nth) % nth; l < gn; l += nth) {
             const size_t g = (size_t)(S.g0 + l);
@@ -375,6 +382,83 @@ void launch_refresh_check(const Dev &d, const MdLaunch &m, int cur, cudaStream_t
     const int grid = (int)std::min<long long>(((long long)d.G + 255) / 256, 4096);
     if (m.mixed) k_refresh_check<PM_FIX, float><<<grid, 256, 0, st>>>(d, cur);
     else k_refresh_check<PM_BOX64, double><<<grid, 256, 0, st>>>(d, cur);
+}
+
+// ---------------------------------------------------------------------------
+// Isothermal-isobaric cells (Sec. 2.1, refs [11, 12]; the equations are those of
+// qtb_params::npt): one thread per system, at the start of step j (block clock
+// b, absolute step n = 256 b + j), from the kinetic energy and virial that the
+// previous step's force launch reduced into the latest record:
+//   B_e(dt/2) (the previous step's closing half, when due) and B_e(dt/2):
+//       p_e += dt/2 (2 alpha K + W_vir - 3 V P_ext), twice;
+//   the particles' first B(dt/2) factors for v_e = p_e / W: e1 = exp(-x),
+//       g1 = (1 - e^{-x})/x, x = alpha v_e dt/2;
+//   A(dt/2): lam <- lam e^{y}, y = v_e dt/2; the particles' drift in the
+//       reference cell a1 = dt/2 (e^y - 1)/y / lam_new;
+//   O(dt) of the cell: p_e <- ce p_e + sqrt((1 - ce^2) W k_B T) xi,
+//       xi from Philox stream 1, dof 0, step n;
+//   A(dt/2) with the new v_e (a2, lam), and the closing B(dt/2) factors e2, g2.
+// A list rebuild is requested for this step's force launch when the cell scale
+// has moved by more than skin/4 over the list radius since the system's last
+// rebuild; a cell below kCellMinScale raises ERR_CELL.
+__device__ __forceinline__ double xm1_over_x(double x) { return x != 0.0 ? expm1(x) / x : 1.0; }
+
+__global__ void k_cell(Dev d, int j, int cur, double r_list, double skin)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.nsys || !d.npt) return;
+    DNpt C = d.npt[s];
+    if (!C.on) return;
+    const DSys &S = d.sys[s];
+    const double *rec = d.latest + (size_t)s * QTB_NREC;
+    const double K = rec[1], Wv = rec[5] + rec[9] + rec[13];
+    const double V = S.box[0] * S.box[1] * S.box[2] * C.lam * C.lam * C.lam;
+    const double G = 2.0 * C.alpha * K + Wv - 3.0 * V * C.pext;
+    const double h = 0.5 * d.dt;
+    if (C.pending) C.peps += h * G;
+    C.peps += h * G;
+    double ve = C.peps / C.W;
+    double x = C.alpha * ve * h;
+    C.e1 = exp(-x);
+    C.g1 = xm1_over_x(-x);
+    double y = ve * h;
+    double lam = C.lam * exp(y);
+    C.a1 = h * xm1_over_x(y) / lam;
+    // the cell's random force: Philox stream 1, dof 0, step n
+    const long long n = d.clock[0] * kBlockSteps + j;
+    const long long q = (n >= 0) ? n / 4 : -((-n + 3) / 4);
+    const unsigned long long uq = (unsigned long long)q;
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)uq, 0u, 1u, (uint32_t)(uq >> 32)), (uint32_t)d.seed,
+                                  (uint32_t)(d.seed >> 32) ^ (uint32_t)s);
+    const int e = (int)(n - 4 * q);
+    const uint32_t wa = (e < 2) ? w.x : w.z, wb = (e < 2) ? w.y : w.w;
+    const double u1 = ((double)wa + 1.0) * 2.3283064365386963e-10, u2 = (double)wb * 2.3283064365386963e-10;
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    const double xi = sqrt(-2.0 * log(u1)) * ((e & 1) ? sn : cs);
+    C.peps = C.ce * C.peps + C.sige * xi;
+    ve = C.peps / C.W;
+    y = ve * h;
+    lam = lam * exp(y);
+    C.a2 = h * xm1_over_x(y) / lam;
+    x = C.alpha * ve * h;
+    C.e2 = exp(-x);
+    C.g2 = xm1_over_x(-x);
+    C.lam = lam;
+    C.pending = 1;
+    C.e1f = (float)C.e1; C.g1f = (float)C.g1; C.a1f = (float)C.a1; C.a2f = (float)C.a2;
+    C.e2f = (float)C.e2; C.g2f = (float)C.g2; C.lamf = (float)C.lam;
+    d.npt[s] = C;
+    if (!(lam >= kCellMinScale) || !isfinite(lam)) atomicOr(d.err, (unsigned)ERR_CELL);
+    if (fabs(lam / C.lam_rb - 1.0) * r_list > 0.25 * skin) {
+        atomicOr(&d.rflag[cur * d.nsys + s], 1u);
+        atomicOr(&d.flag[cur], 1u);
+    }
+}
+
+void launch_cell(const Dev &d, int j, int cur, double r_list, double skin, cudaStream_t st)
+{
+    k_cell<<<(d.nsys + 127) / 128, 128, 0, st>>>(d, j, cur, r_list, skin);
 }
 
 // Self-test of the bounded waits: one thread waits on words[0], which nothing

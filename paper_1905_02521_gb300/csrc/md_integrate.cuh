@@ -41,6 +41,8 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
     const size_t G = (size_t)d.G;
     const size_t base = act ? (size_t)c * G + S.g0 + i : 0;
     const float fsc = S.fix_scale[c], finv = S.fix_inv[c];
+    // isothermal-isobaric cell (one bead): this step's coefficients from the cell kernel
+    const DNpt *NC = (P == 1 && d.npt && d.npt[s].on) ? d.npt + s : nullptr;
     PS x0{};
     R a[P], a0[P];  // bead positions relative to bead 0: new, old
     if (act) {
@@ -66,8 +68,13 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
             q[k] = u;
         }
         // B: half kick with the current forces, bead velocities -> modes
+        if (NC) {  // with the cell's friction: v e1 + (hdt/m) F g1
+            const R e1 = sizeof(R) == 4 ? (R)NC->e1f : (R)NC->e1, g1 = sizeof(R) == 4 ? (R)NC->g1f : (R)NC->g1;
+            a[0] = fma(V[base], e1, (hdtm * F[base]) * g1);
+        } else {
 #pragma unroll(UN)
-        for (int b = 0; b < P; ++b) a[b] = fma(hdtm, F[base + (size_t)b * N], V[base + (size_t)b * N]);
+            for (int b = 0; b < P; ++b) a[b] = fma(hdtm, F[base + (size_t)b * N], V[base + (size_t)b * N]);
+        }
         R p[P];
 #pragma unroll(UN)
         for (int k = 0; k < P; ++k) {
@@ -79,9 +86,22 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
         const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
         const R *eta = reinterpret_cast<const R *>(d.eta) + eta_row(d, j) * d.Dtot + S.dof0;
         const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
+        if (NC) {
+            // one bead in a changing cell: A(dt/2) O(dt) A(dt/2) as displacements in the
+            // reference cell (x_ref += v a1, then v' a2: the exact drift of
+            // dr/dt = v + v_e r with the cell scaled alike)
+            const R a1 = sizeof(R) == 4 ? (R)NC->a1f : (R)NC->a1, a2 = sizeof(R) == 4 ? (R)NC->a2f : (R)NC->a2;
+            R pk = p[0];
+            R disp = pk * a1;
+            pk = fma(c1, pk, sig * eta[(size_t)c * N + i]);
+            disp = fma(pk, a2, disp);
+            q[0] = q[0] + disp;
+            p[0] = pk;
+        } else {
 #pragma unroll(UN)
-        for (int k = 0; k < P; ++k)
-            mode_aoa(q[k], p[k], rot[3 * k], rot[3 * k + 1], rot[3 * k + 2], c1, sig * eta[(size_t)(k * 3 + c) * N + i]);
+            for (int k = 0; k < P; ++k)
+                mode_aoa(q[k], p[k], rot[3 * k], rot[3 * k + 1], rot[3 * k + 2], c1, sig * eta[(size_t)(k * 3 + c) * N + i]);
+        }
         // modes -> beads
 #pragma unroll(UN)
         for (int b = 0; b < P; ++b) {
@@ -128,7 +148,14 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
         if (PM != PM_FREE) {
             const R tot = __shfl_sync(0xffffffffu, dd, l0 & 31) + __shfl_sync(0xffffffffu, dd, (l0 + 1) & 31) +
                           __shfl_sync(0xffffffffu, dd, (l0 + 2) & 31);
-            const R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
+            R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
+            if (NC) {
+                // physical displacement (lam times the reference one) against (3/8 skin)^2:
+                // the other quarter of the skin is the cell kernel's margin for the
+                // change of lam since the rebuild
+                const R l = sizeof(R) == 4 ? (R)NC->lamf : (R)NC->lam;
+                lim = lim * R(0.5625) / (l * l);
+            }
             moved |= act && c == 0 && tot > lim;
         }
     }

@@ -428,7 +428,9 @@ __device__ void build_cell(const Dev &d, R rc2, R rl2, int cell, void *stage_mem
     const int total = soff[kStencil];
     const int CH = d.stage_cap;
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) scount[t] = 0;
-    const R sx = (R)RP.fix_scale[0], sy = (R)RP.fix_scale[1], sz = (R)RP.fix_scale[2];
+    // physical distances (isothermal-isobaric: the reference cell scaled by lam)
+    const R lam = (d.npt && d.npt[RP.sys].on) ? (R)d.npt[RP.sys].lam : R(1);
+    const R sx = (R)RP.fix_scale[0] * lam, sy = (R)RP.fix_scale[1] * lam, sz = (R)RP.fix_scale[2] * lam;
     const unsigned lt = (1u << lane) - 1u;
     const int maxnb = d.maxnb;
     // pass 0 lists the entries within r_cut, pass 1 those of the skin shell, so
@@ -501,9 +503,9 @@ __device__ void build_cell(const Dev &d, R rc2, R rl2, int cell, void *stage_mem
                     dy = (R)(int)((unsigned)pj.y - (unsigned)hp.y) * sy;
                     dz = (R)(int)((unsigned)pj.z - (unsigned)hp.z) * sz;
                 } else {
-                    dx = (R)(pj.x - hp.x);
-                    dy = (R)(pj.y - hp.y);
-                    dz = (R)(pj.z - hp.z);
+                    dx = (R)(pj.x - hp.x) * lam;
+                    dy = (R)(pj.y - hp.y) * lam;
+                    dz = (R)(pj.z - hp.z) * lam;
                 }
                 const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
                 // the home bead-atom itself (r2 == 0) and the sentinels fail
@@ -656,6 +658,10 @@ static __device__ void reduce_system(const Dev &d, int s, long long step, int re
         for (int a = 0; a < 9; ++a) rec[5 + a] = tot[Q_VIR + map[a]] * invP;
         for (int c = 0; c < 3; ++c) rec[14 + c] = tot[Q_MOM + c];
         rec[17] = tot[Q_X2] * invP;
+        {  // cell volume: the reference cell scaled by lam^3 in an isothermal-isobaric run
+            const double l = (d.npt && d.npt[s].on) ? d.npt[s].lam : 1.0;
+            rec[20] = S.box[0] * S.box[1] * S.box[2] * l * l * l;
+        }
         // centroid-virial estimators: for one bead 3N k_B T/2 and K; ring
         // polymers get them from the centroid kernel that follows
         if (S.P == 1) {
@@ -699,7 +705,8 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
     const int i = (u - RP.fcta0) * list_atoms(LPA) + warp * APW + grp;
     const bool act = i < RP.N;
     const long long step = d.clock[0] * kBlockSteps + j + 1;
-    const bool rec = REC && ((kick == 0) || (step % d.obs_stride == 0));
+    // (isothermal-isobaric runs reduce K and the virial every step: the cell needs them)
+    const bool rec = REC && ((kick == 0) || (step % d.obs_stride == 0) || d.npt != nullptr);
     const DSys &S = d.sys[RP.sys];
     const size_t G = (size_t)d.G;
     const long long gi = RP.g0 + (act ? i : 0);
@@ -710,7 +717,10 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
     if (PM == PM_FIX) ti = hp.w; else ti = (int)hp.w;
     const int n = act ? min(d.nnb[gi], d.maxnb) : 0;
     const unsigned *row = d.nbr + (size_t)gi * d.maxnb;
-    const R sx = (R)RP.fix_scale[0], sy = (R)RP.fix_scale[1], sz = (R)RP.fix_scale[2];
+    // physical distances: the reference cell's, scaled by lam in an isothermal-isobaric run
+    const DNpt *NC = (d.npt && d.npt[RP.sys].on) ? d.npt + RP.sys : nullptr;
+    const R lam = NC ? (sizeof(R) == 4 ? (R)NC->lamf : (R)NC->lam) : R(1);
+    const R sx = (R)RP.fix_scale[0] * lam, sy = (R)RP.fix_scale[1] * lam, sz = (R)RP.fix_scale[2] * lam;
     const R rc2 = T.rc2;
     ACC fx{}, fy{}, fz{};
     R en = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
@@ -737,7 +747,7 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
             for (int c = 0; c < 3; ++c) {
                 const int code = (int)((e >> (26 + 2 * c)) & 3u);
                 const int m = (code == 3) ? -1 : (code == 2) ? (pd[c] > 0.0 ? -2 : 2) : code;
-                dv[c] = (R)(pd[c] + m * RP.box[c]);
+                dv[c] = (R)(pd[c] + m * RP.box[c]) * lam;
             }
             g.dx = dv[0]; g.dy = dv[1]; g.dz = dv[2];
             g.tj = (int)pj.w;
@@ -826,7 +836,14 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
         Fo[o] = fc;
         const R hdtm = T.hdt_m[ti];
         R v = V[o];
-        if (kick) v = fma(hdtm, fc, v);
+        if (kick) {
+            if (NC) {  // B(dt/2) with the cell's friction: v e2 + (hdt/m) F g2
+                const R e2 = sizeof(R) == 4 ? (R)NC->e2f : (R)NC->e2, g2 = sizeof(R) == 4 ? (R)NC->g2f : (R)NC->g2;
+                v = fma(v, e2, (hdtm * fc) * g2);
+            } else {
+                v = fma(hdtm, fc, v);
+            }
+        }
         if (REC && rec) {
             acc[Q_K] += 0.5 * T.mass_mvv[ti] * (double)v * (double)v;
             acc[Q_MOM + c] += T.mass[ti] * (double)v;
@@ -922,9 +939,14 @@ __global__ void __launch_bounds__(32 * kListWarps, sizeof(R) == 4 ? 7 : 4) k_ste
         }
         grid_barrier(d);
         // the per-system requests were read by every phase: consumed now (their
-        // next producer, of step s + 2, runs in a later launch)
+        // next producer, of step s + 2, runs in a later launch); an isothermal-
+        // isobaric cell remembers the scale its lists were built at
         if (blockIdx.x == 0)
-            for (int t = threadIdx.x; t < d.nsys; t += blockDim.x) d.rflag[cur * d.nsys + t] = 0u;
+            for (int t = threadIdx.x; t < d.nsys; t += blockDim.x) {
+                if (d.npt && d.npt[t].on && (d.rebuild_all || d.rflag[cur * d.nsys + t] != 0u))
+                    d.npt[t].lam_rb = d.npt[t].lam;
+                d.rflag[cur * d.nsys + t] = 0u;
+            }
     }
     release_next_step();
     for (int u = blockIdx.x; u < d.nunits; u += gridDim.x)

@@ -33,7 +33,26 @@ enum { Q_K = 0, Q_V = 1, Q_SPRING = 2, Q_VIR = 3 /* 6 slots: xx yy zz xy xz yz *
 enum { PM_BOX64 = 0, PM_FIX = 1, PM_FREE = 2 };
 
 // device error word bits
-enum { ERR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_SOLVE = 4, ERR_TIMEOUT_TC = 8, ERR_NBR_OVERFLOW = 16, ERR_TIMEOUT_BAR = 32 };
+enum { ERR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_SOLVE = 4, ERR_TIMEOUT_TC = 8, ERR_NBR_OVERFLOW = 16, ERR_TIMEOUT_BAR = 32,
+       ERR_CELL = 64 };
+
+// Isothermal-isobaric cell (isotropic Langevin barostat) of one system.  The
+// stored positions stay in the reference cell (edges DSys::box, fixed point per
+// reference edge in the mixed form); physical positions are lam times them, so a
+// change of the cell rescales every distance without touching the state.  The
+// cell kernel updates the cell at the start of each step and leaves there the
+// step's coefficients for the integrator and the step kernel.
+constexpr double kCellMinScale = 0.9;  // smallest lam the cell lists are sized for
+struct DNpt {
+    double lam, lam_rb, peps;  // cell scale, its value at the system's last list rebuild, cell momentum (eV fs)
+    double W, pext, ce, sige, alpha, V0;  // mass, P_ext, exp(-gamma_e dt), sqrt((1 - ce^2) W kT), 1 + 3/N_f, V at lam 1
+    // this step: first B  v <- v e1 + (hdt/m) F g1;  A  x_ref += v a1, then v' a2;
+    // closing B  v <- v e2 + (hdt/m) F g2
+    double e1, g1, a1, a2, e2, g2;
+    float e1f, g1f, a1f, a2f, e2f, g2f, lamf, pad;
+    int on, pending;  // barostat on; the previous step's closing half kick of the cell is due
+    int pad2[2];
+};
 
 // Neighbour-list entry (32 bits): replica-local index j in bits 0..25, the
 // periodic image m of the entry (per component m mod 4, two bits each: x at
@@ -158,6 +177,7 @@ struct Dev {
     // reductions
     double *part;         // [CTAs][kNQ]
     double *ipart;        // [integrator CTAs][kNQ]
+    DNpt *npt;            // [nsys] isothermal-isobaric cells (null: constant volume)
     double *latest;       // [nsys][QTB_NREC]
     double *series;       // [max_records][nsys][QTB_NREC]
     long long *clock;     // [0] = current noise block

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import build as _build
 
-NREC = 20
+NREC = 21
 TC_FILTER = True        # the BF16 tcgen05 Toeplitz-GEMM filter is available (QTB_FILTER_BF16)
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NONFINITE, ERR_SOLVE, ERR_OVERFLOW, ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
@@ -51,7 +51,8 @@ class qtb_params(C.Structure):
                 ("filter_prec", C.c_int), ("seed", C.c_ulonglong), ("obs_stride", C.c_int),
                 ("max_records", C.c_int), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_user", C.c_void_p), ("skin", C.c_double), ("nm_layout", C.c_int),
-                ("list_lanes", C.c_int), ("rebuild_scope", C.c_int)]
+                ("list_lanes", C.c_int), ("rebuild_scope", C.c_int), ("npt", C.c_int), ("pressure", C.c_double),
+                ("cell_mass", C.c_double), ("cell_gamma", C.c_double)]
 
 
 _lib = None
@@ -83,6 +84,7 @@ def lib():
             "qtb_get_taps": ([vp, i, vp, i, C.POINTER(i)], i),
             "qtb_get_noise": ([vp, i, vp, C.POINTER(ll)], i),
             "qtb_get_step": ([vp, C.POINTER(ll)], i),
+            "qtb_get_cell": ([vp, i, vp, C.POINTER(d)], i),
             "qtb_list_rebuilds": ([vp, C.POINTER(ll)], i),
             "qtb_rebuild_lists": ([vp], i),
             "qtb_wait_selftest": ([vp, C.POINTER(i), C.POINTER(d)], i),
@@ -198,6 +200,10 @@ def _c_args(systems, params, stream):
     p.nm_layout = int(params.get("nm_layout", 0))
     p.list_lanes = int(params.get("list_lanes", 0))
     p.rebuild_scope = int(params.get("rebuild_scope", 0))
+    p.npt = int(params.get("npt", 0))
+    p.pressure = float(params.get("pressure", 0.0))
+    p.cell_mass = float(params.get("cell_mass", 0.0))
+    p.cell_gamma = float(params.get("cell_gamma", 0.0))
     if params.get("torch_alloc", True):
         a, f = _torch_allocator()
         p.dev_alloc, p.dev_free = a, f
@@ -335,6 +341,14 @@ def qtb_get_step(ctx):
 
 
 KERNEL_CLASSES = ("white", "filter", "integrate", "rebuild", "force", "reduce")
+
+
+def qtb_get_cell(ctx, sys):
+    """(cell edges [3] in A, cell momentum p_e in eV fs) of system sys."""
+    box = np.zeros(3)
+    pe = C.c_double(0.0)
+    _check(lib().qtb_get_cell(ctx, sys, box.ctypes.data, C.byref(pe)))
+    return box, pe.value
 
 
 def qtb_set_profiling(ctx, enable=True):

@@ -4,11 +4,13 @@ import numpy as np
 
 
 def gpu_params(pot, dt, precision=0, filter_prec=1, seed=12345, potential=0, ext=None, obs_stride=1,
-               max_records=4096, skin=0.0, nm_layout=0, list_lanes=0, rebuild_scope=0):
+               max_records=4096, skin=0.0, nm_layout=0, list_lanes=0, rebuild_scope=0, npt=None):
     p = {k: pot[k] for k in ("mass", "charge", "buck_A", "buck_rho", "buck_C")}
     p.update(dsf_alpha=pot["dsf_alpha"], r_cut=pot["r_cut"], dt=dt, precision=precision, filter_prec=filter_prec,
              seed=seed, potential=potential, obs_stride=obs_stride, max_records=max_records, skin=skin,
              nm_layout=nm_layout, list_lanes=list_lanes, rebuild_scope=rebuild_scope)
+    if npt is not None:   # isothermal-isobaric cell: dict(pressure, mass, gamma), as the oracle's
+        p.update(npt=1, pressure=npt["pressure"], cell_mass=npt["mass"], cell_gamma=npt["gamma"])
     ext = ext or {}
     p["ext_omega"] = ext.get("omega", 0.0)
     p["ext_V0"] = ext.get("V0", 0.0)
@@ -20,9 +22,9 @@ def gpu_ctx(qtb, systems, pot, dt, **kw):
     return qtb.qtb_init(systems, gpu_params(pot, dt, **kw))
 
 
-def oracle_sim(oracle, s, pot, dt, seed=12345, sys=0, taps=None, potential=0, ext=None):
+def oracle_sim(oracle, s, pot, dt, seed=12345, sys=0, taps=None, potential=0, ext=None, npt=None):
     return oracle.Sim(s["pos"], s["vel"], s["types"], pot, s["box"] if potential == 0 else None, s["T"], s["gamma"],
-                      dt, seed=seed, sys=sys, taps=taps, potential=potential, ext=ext)
+                      dt, seed=seed, sys=sys, taps=taps, potential=potential, ext=ext, npt=npt)
 
 
 def minimg(d, box):

@@ -1,0 +1,180 @@
+"""Isothermal-isobaric runs on the GPU (the Langevin barostat of qtb_params.npt;
+Sec. 2.1 of the paper, refs [11, 12]) against the FP64 oracle and the
+isothermal-isobaric law.
+
+* FP64 form: positions, velocities, forces and cell after every one of the
+  first 100 steps equal the oracle's (1e-11), with a QTB bath and a cell that
+  contracts visibly over those steps;
+* mixed form: one step from the GPU's own state and cell against the oracle's
+  FP64 step (positions and cell 1e-5, velocities 1e-5 norm-wise);
+* the ideal gas samples P(V) ~ V^N exp(-P V / k_B T): <V> = (N + 1) k_B T / P;
+* LiH / LiD under QTB-MD and classical Langevin at zero pressure: the lattice
+  parameter against temperature (Figs. 2 and 6 of the paper, with the synthetic
+  potential): classically the two isotopes share one curve that grows with T;
+  with the quantum bath the zero-point motion expands the lighter crystal more
+  (LiH above LiD) and both lie above the classical curve at low T.
+"""
+import numpy as np
+import pytest
+
+from helpers import gpu_ctx, minimg, oracle_sim, rel_inf
+
+from oracle import spectra as S
+from paper_1905_02521_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+KB = 8.617333262e-5
+
+
+@pytest.fixture(scope="module")
+def qtb():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1905_02521_gb300 import build
+    build.build()
+    from paper_1905_02521_gb300 import qtb as q
+    return q
+
+
+def _cell_mass(B, V, period):
+    """Cell mass giving a volume oscillation of the given period (fs) for bulk modulus B."""
+    return 9.0 * B * V / (2 * np.pi / period) ** 2
+
+
+# static bulk modulus of the MgO model at its E(V) minimum (tests/test_oracle_npt.py): ~2.56 eV/A^3
+B_MGO = 2.56
+
+
+def test_fp64_npt_trajectory_matches_oracle(qtb, oracle):
+    # 64-ion MgO at 300 K from the 4.21 A lattice, zero pressure: the model's static
+    # minimum is at 4.128 A, so the cell contracts over the first steps; QTB bath,
+    # 513 taps; cell period ~200 fs
+    s, pot = W.mgo_system(2, 300.0, gamma=2e-3)
+    N = len(s["types"])
+    V = np.prod(s["box"])
+    npt = {"pressure": 0.0, "mass": _cell_mass(B_MGO, V, 200.0), "gamma": 5e-3}
+    taps = S.taps(513, 1.0, 300.0, 0.3)
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=0, seed=4321, npt=npt)
+    try:
+        qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB, 513, 0.3)
+        sim = oracle_sim(oracle, s, pot, 1.0, seed=4321, taps=taps, npt=npt)
+        for step in range(1, 101):
+            qtb.qtb_step_n(ctx, 1)
+            sim.step(1, record=False)
+            box_g, pe_g = qtb.qtb_get_cell(ctx, 0)
+            box_o, pe_o = sim.cell()
+            assert np.abs(box_g / box_o - 1).max() < 1e-12, (step, box_g, box_o)
+            assert pe_g == pytest.approx(pe_o, rel=1e-10, abs=1e-10 * abs(pe_o) + 1e-12)
+            xg, vg = qtb.qtb_get_state(ctx, 0, 1, N)
+            fg = qtb.qtb_get_forces(ctx, 0, 1, N)
+            xo, vo, fo, _ = sim.state()
+            assert np.abs(minimg(xg - xo, box_o)).max() < 1e-10
+            assert rel_inf(vg, vo) < 1e-11 and rel_inf(fg, fo) < 1e-11
+        assert box_o[0] < 0.995 * s["box"][0]        # the cell did move
+        obs = qtb.qtb_observables(ctx, 0)
+        assert obs[20] == pytest.approx(np.prod(box_o), rel=1e-12)
+    finally:
+        qtb.qtb_destroy(ctx)
+
+
+def test_mixed_npt_single_step_matches_oracle_step(qtb, oracle):
+    s, pot = W.mgo_system(2, 300.0, gamma=2e-3)
+    N = len(s["types"])
+    V = np.prod(s["box"])
+    npt = {"pressure": 0.0, "mass": _cell_mass(B_MGO, V, 200.0), "gamma": 5e-3}
+    taps = S.taps(513, 1.0, 300.0, 0.3)
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=1, filter_prec=1, seed=99, npt=npt)
+    try:
+        qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB, 513, 0.3)
+        qtb.qtb_step_n(ctx, 37)
+        x0, v0 = qtb.qtb_get_state(ctx, 0, 1, N)
+        box0, pe0 = qtb.qtb_get_cell(ctx, 0)
+        sim = oracle_sim(oracle, s, pot, 1.0, seed=99, taps=taps, npt=npt)
+        sim.set_cell(box0, pe0, 1)
+        sim.set_state(x0, v0, 37)
+        qtb.qtb_step_n(ctx, 1)
+        sim.step(1, record=False)
+        x1, v1 = qtb.qtb_get_state(ctx, 0, 1, N)
+        box1, _ = qtb.qtb_get_cell(ctx, 0)
+        xo, vo, _, _ = sim.state()
+        boxo, _ = sim.cell()
+        assert np.abs(box1 / boxo - 1).max() < 1e-5
+        assert np.abs(minimg(x1 - xo, boxo)).max() < 1e-5
+        assert rel_inf(v1, vo) < 1e-5
+    finally:
+        qtb.qtb_destroy(ctx)
+
+
+def test_ideal_gas_volume_on_gpu(qtb):
+    # 512 non-interacting particles (zero pair tables) at 300 K: <V> = (N + 1) k_B T / P
+    # (volume fluctuations of 4 %: the cell stays far above 0.9 of its edges)
+    N, T, m = 512, 300.0, 40.0
+    kT = KB * T
+    V_exact = 20000.0
+    P = (N + 1) * kT / V_exact
+    pot = {"mass": np.array([m]), "charge": np.zeros(1), "buck_A": np.zeros((1, 1)),
+           "buck_rho": np.ones((1, 1)), "buck_C": np.zeros((1, 1)), "dsf_alpha": 0.2, "r_cut": 1.0}
+    rng = np.random.default_rng(8)
+    L = V_exact ** (1 / 3)
+    s = {"pos": rng.uniform(0, L, (1, N, 3)), "vel": rng.normal(0, np.sqrt(kT / (m * W.MVV2E)), (1, N, 3)),
+         "types": np.zeros(N, np.int32), "box": np.array([L] * 3), "T": T, "gamma": 0.01}
+    npt = {"pressure": P, "mass": 9 * (N + 1) * kT / (2 * np.pi / 400.0) ** 2, "gamma": 0.005}
+    ctx = gpu_ctx(qtb, [s], pot, 2.0, precision=1, seed=17, npt=npt, obs_stride=16, max_records=16384)
+    try:
+        qtb.qtb_step_n(ctx, 8192)
+        qtb.qtb_step_n(ctx, 16 * 12288)
+        V = qtb.qtb_get_series(ctx, 0, 12288)[:, 20]
+    finally:
+        qtb.qtb_destroy(ctx)
+    nb = 24
+    sem = V[: len(V) // nb * nb].reshape(nb, -1).mean(1).std(ddof=1) / np.sqrt(nb)
+    print(f"ideal gas: <V> {V.mean():.1f} +- {sem:.1f}, exact {V_exact:.1f}; var/<V>^2 {V.var() / V.mean()**2:.5f} "
+          f"exact {1 / (N + 1):.5f}")
+    assert abs(V.mean() - V_exact) < 3 * sem + 1e-3 * V_exact
+    assert V.var() / V.mean() ** 2 == pytest.approx(1 / (N + 1), rel=0.15)
+
+
+def _lattice_parameter(qtb, isotope, T, quantum, ncell=3, steps=24576, neq=8192):
+    s, pot = W.lih_system(ncell, T, gamma=2e-3, isotope=isotope, seed=31)
+    V = np.prod(s["box"])
+    npt = {"pressure": 0.0, "mass": _cell_mass(1.0, V, 300.0), "gamma": 4e-3}
+    ctx = gpu_ctx(qtb, [s], pot, 0.25, precision=1, filter_prec=1, seed=23, npt=npt, obs_stride=16,
+                  max_records=4096)
+    try:
+        if quantum:
+            qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB, 2049, 0.6)
+        qtb.qtb_step_n(ctx, neq)
+        qtb.qtb_step_n(ctx, steps)
+        V = qtb.qtb_get_series(ctx, 0, steps // 16)[:, 20]
+    finally:
+        qtb.qtb_destroy(ctx)
+    a = (V / ncell ** 3) ** (1 / 3)
+    nb = 16
+    sem = a[: len(a) // nb * nb].reshape(nb, -1).mean(1).std(ddof=1) / np.sqrt(nb)
+    return a.mean(), sem
+
+
+def test_lih_lid_lattice_parameter_against_temperature(qtb):
+    res = {}
+    for T in (20.0, 150.0, 300.0):
+        for iso in ("H", "D"):
+            for q in (False, True):
+                res[(T, iso, q)] = _lattice_parameter(qtb, iso, T, q)
+    for T in (20.0, 150.0, 300.0):
+        print("T %5.0f K: classical LiH %.5f(%.0e) LiD %.5f(%.0e) | QTB LiH %.5f(%.0e) LiD %.5f(%.0e)" % (
+            T, *res[(T, "H", False)], *res[(T, "D", False)], *res[(T, "H", True)], *res[(T, "D", True)]))
+    sig = lambda *k: np.sqrt(sum(res[x][1] ** 2 for x in k))  # noqa: E731
+    # classical: no isotope effect; thermal expansion
+    for T in (20.0, 150.0, 300.0):
+        d = res[(T, "H", False)][0] - res[(T, "D", False)][0]
+        assert abs(d) < 4 * sig((T, "H", False), (T, "D", False)) + 2e-5
+    assert res[(300.0, "H", False)][0] > res[(20.0, "H", False)][0]
+    # quantum bath: zero-point expansion, larger for the lighter isotope
+    for T in (20.0, 150.0):
+        assert res[(T, "H", True)][0] - res[(T, "D", True)][0] > 4 * sig((T, "H", True), (T, "D", True))
+        assert res[(T, "D", True)][0] - res[(T, "D", False)][0] > 4 * sig((T, "D", True), (T, "D", False))
+    # at low T the quantum lattice parameter saturates: it moves less from 20 to 150 K
+    # than the classical one does
+    dq = res[(150.0, "H", True)][0] - res[(20.0, "H", True)][0]
+    dc = res[(150.0, "H", False)][0] - res[(20.0, "H", False)][0]
+    assert dq < dc
