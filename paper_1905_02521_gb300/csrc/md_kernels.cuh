@@ -718,7 +718,8 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
     const int n = act ? min(d.nnb[gi], d.maxnb) : 0;
     const unsigned *row = d.nbr + (size_t)gi * d.maxnb;
     // physical distances: the reference cell's, scaled by lam in an isothermal-isobaric run
-    const DNpt *NC = (d.npt && d.npt[RP.sys].on) ? d.npt + RP.sys : nullptr;
+    // (such runs launch the recording variants only: the others carry no cell code)
+    const DNpt *NC = (REC && d.npt && d.npt[RP.sys].on) ? d.npt + RP.sys : nullptr;
     const R lam = NC ? (sizeof(R) == 4 ? (R)NC->lamf : (R)NC->lam) : R(1);
     const R sx = (R)RP.fix_scale[0] * lam, sy = (R)RP.fix_scale[1] * lam, sz = (R)RP.fix_scale[2] * lam;
     const R rc2 = T.rc2;
