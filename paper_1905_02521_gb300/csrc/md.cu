@@ -479,11 +479,29 @@ bool md_supported_P(int P) { return (P >= 1 && P <= 6) || P == 8 || P == 16 || P
 
 int integrate_atoms_per_cta(int P, int big) { return P == 1 ? kIntAtomsPerCta : nm_atoms(P, big); }
 
+// integrator launches carry the programmatic-stream-serialisation attribute (the
+// kernels wait for the previous launch before reading the state)
+template <class K>
+static void pdl_launch(K kernel, int grid, int threads, size_t smem, cudaStream_t st, const Dev &d, int j, int cur)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, d, j, cur);
+}
+
 template <int P, int PM, class R>
 static void nm_launch(const Dev &d, const MdLaunch &m, int j, int cur, cudaStream_t st)
 {
-    if (m.nm_big) k_integrate_nm<P, PM, R, 1><<<m.n_icta, nm_threads(P, 1), nm_smem<P, PM, R>(1), st>>>(d, j, cur);
-    else k_integrate_nm<P, PM, R, 0><<<m.n_icta, nm_threads(P, 0), nm_smem<P, PM, R>(0), st>>>(d, j, cur);
+    if (m.nm_big) pdl_launch(k_integrate_nm<P, PM, R, 1>, m.n_icta, nm_threads(P, 1), nm_smem<P, PM, R>(1), st, d, j, cur);
+    else pdl_launch(k_integrate_nm<P, PM, R, 0>, m.n_icta, nm_threads(P, 0), nm_smem<P, PM, R>(0), st, d, j, cur);
 }
 
 template <int P, int PM, class R>
@@ -520,7 +538,7 @@ static void integrate_all(const Dev &d, const MdLaunch &m, int j, int cur, cudaS
 {
     for (int u = 0; u < m.nP; ++u) {
         switch (m.Pvals[u]) {
-            case 1: k_integrate<1, PM, R><<<m.n_icta, 128, 0, st>>>(d, j, cur); break;
+            case 1: pdl_launch(k_integrate<1, PM, R>, m.n_icta, 128, 0, st, d, j, cur); break;
 #define QTB_P(PP) case PP: nm_launch<PP, PM, R>(d, m, j, cur, st); break;
             QTB_P(2) QTB_P(3) QTB_P(4) QTB_P(5) QTB_P(6) QTB_P(8) QTB_P(16) QTB_P(32)
 #undef QTB_P

@@ -29,6 +29,8 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
     if (mine)
         for (int t = threadIdx.x; t < P * P; t += blockDim.x) Cs[t] = reinterpret_cast<const R *>(d.nmC)[S.nm0 + t];
     __syncthreads();
+    wait_previous_step();  // as k_integrate_nm
+    release_next_step();
     const int N = S.N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int aw = lane / 3, c = lane - 3 * aw;
@@ -244,6 +246,10 @@ __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int 
         Cs[t] = Cg[t];
         if (MT > 1) CsT[t] = Cg[(t % P) * P + t / P];  // CsT[k P + b] = C[b][k] (contiguous stores)
     }
+    // programmatic dependent launch: the mode matrix above is static; the state is
+    // the previous step's (see wait_previous_step)
+    wait_previous_step();
+    release_next_step();
     const int N = S.N;
     const int i0 = (cta - S.icta0) * A;
     const size_t G = (size_t)d.G;

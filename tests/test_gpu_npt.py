@@ -178,3 +178,47 @@ def test_lih_lid_lattice_parameter_against_temperature(qtb):
     dq = res[(150.0, "H", True)][0] - res[(20.0, "H", True)][0]
     dc = res[(150.0, "H", False)][0] - res[(20.0, "H", False)][0]
     assert dq < dc
+
+
+def test_constant_volume_cell_and_volume_slot(qtb):
+    # without the barostat the cell is the given one, its momentum 0, and record
+    # slot 20 the constant volume
+    s, pot = W.mgo_system(2, 300.0)
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=1)
+    try:
+        qtb.qtb_step_n(ctx, 10)
+        box, pe = qtb.qtb_get_cell(ctx, 0)
+        assert np.array_equal(box, s["box"]) and pe == 0.0
+        assert qtb.qtb_observables(ctx, 0)[20] == pytest.approx(np.prod(s["box"]), rel=1e-15)
+    finally:
+        qtb.qtb_destroy(ctx)
+
+
+def test_collapsing_cell_is_reported(qtb):
+    # a pressure far beyond the crystal's bulk modulus drives the cell below 0.9 of
+    # its edges, the margin its cell lists are built for: the run must stop with an
+    # error (the cell bit, or the overflow or non-finite check it triggers), not go
+    # on with missing pairs
+    s, pot = W.mgo_system(2, 300.0, gamma=2e-3)
+    V = np.prod(s["box"])
+    npt = {"pressure": 50.0, "mass": _cell_mass(B_MGO, V, 100.0), "gamma": 1e-3}
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=1, npt=npt)
+    try:
+        with pytest.raises(qtb.QtbError) as e:
+            for _ in range(40):
+                qtb.qtb_step_n(ctx, 50)
+                qtb.qtb_sync(ctx)
+        assert e.value.code in (qtb.ERR_STATE, qtb.ERR_OVERFLOW, qtb.ERR_NONFINITE)
+    finally:
+        qtb.qtb_destroy(ctx)
+
+
+def test_npt_arguments_are_checked(qtb):
+    s, pot = W.mgo_system(2, 300.0, n_beads=2)
+    with pytest.raises(qtb.QtbError) as e:   # one bead per atom only
+        gpu_ctx(qtb, [s], pot, 1.0, npt={"pressure": 0.0, "mass": 1e6, "gamma": 1e-3})
+    assert e.value.code == qtb.ERR_ARG
+    s1, _ = W.mgo_system(2, 300.0)
+    with pytest.raises(qtb.QtbError) as e:   # the cell needs a mass
+        gpu_ctx(qtb, [s1], pot, 1.0, npt={"pressure": 0.0, "mass": 0.0, "gamma": 1e-3})
+    assert e.value.code == qtb.ERR_ARG
