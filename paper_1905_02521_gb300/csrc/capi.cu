@@ -984,6 +984,13 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         for (int t = c->ds[s].ccta0; t < c->ds[s].ccta1; ++t) c->ccta_sys.push_back(s);
     c->ml.mixed = c->mixed;
     c->ml.lanes = lanes;
+    // minimum image suffices for the list entries when every edge exceeds twice the
+    // largest separation an entry can reach before a rebuild (r_cut + skin, plus skin/2
+    // of motion for each of the two atoms); not with a changing cell
+    c->ml.minimg = (c->pair && c->mixed && !p->npt) ? 1 : 0;
+    for (int s = 0; s < n_sys && c->ml.minimg; ++s)
+        for (int k = 0; k < 3; ++k)
+            if (!(sys[s].box[k] > 2.0 * (p->r_cut + 2.0 * c->skin))) c->ml.minimg = 0;
     if (c->pair && step_prepare(c->ml, stage_cap) != cudaSuccess)
         return bail(fail(QTB_ERR_CUDA, "cannot prepare the cooperative step kernel (shared memory, occupancy)"));
     int ext_gx = 0;

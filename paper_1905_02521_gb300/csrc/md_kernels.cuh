@@ -690,7 +690,7 @@ static __device__ void reduce_system(const Dev &d, int s, long long step, int re
 // coloured noise, written to x and pos[cur ^ 1], and the rebuild test for the
 // next step.  Recorded steps: the last CTA of a system reduces its partials.
 
-template <int PM, class R, int ADV, int REC, int LPA>
+template <int PM, class R, int ADV, int REC, int LPA, int MI>
 __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, const PairRow<R> *ptab, int kick,
                                            int j, int cur, int u, double (*red)[kNQ], double (*rsh)[kNQ + 1],
                                            int &s_last)
@@ -735,9 +735,19 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
         Geo g;
         if (PM == PM_FIX) {
             // exact in wrapping 32-bit arithmetic
-            g.dx = (R)(int)((unsigned)pj.x + ((e << 4) & 0xC0000000u) - (unsigned)hp.x) * sx;
-            g.dy = (R)(int)((unsigned)pj.y + ((e << 2) & 0xC0000000u) - (unsigned)hp.y) * sy;
-            g.dz = (R)(int)((unsigned)pj.z + (e & 0xC0000000u) - (unsigned)hp.z) * sz;
+            if constexpr (MI) {
+                // MI: every cell exceeds twice the largest separation a list entry can
+                // reach, so the difference modulo the 30-bit edge, sign-extended, is the
+                // entry's image (4 x the difference, exact in float, times scale/4: the
+                // same value as below, without decoding the image bits)
+                g.dx = (R)(int)(((unsigned)pj.x - (unsigned)hp.x) << 2) * (sx * R(0.25));
+                g.dy = (R)(int)(((unsigned)pj.y - (unsigned)hp.y) << 2) * (sy * R(0.25));
+                g.dz = (R)(int)(((unsigned)pj.z - (unsigned)hp.z) << 2) * (sz * R(0.25));
+            } else {
+                g.dx = (R)(int)((unsigned)pj.x + ((e << 4) & 0xC0000000u) - (unsigned)hp.x) * sx;
+                g.dy = (R)(int)((unsigned)pj.y + ((e << 2) & 0xC0000000u) - (unsigned)hp.y) * sy;
+                g.dz = (R)(int)((unsigned)pj.z + (e & 0xC0000000u) - (unsigned)hp.z) * sz;
+            }
             g.tj = pj.w;
         } else {
             // image from m mod 4: code 2 is +2 or -2, told apart by the sign of
@@ -909,7 +919,7 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
 // (72 registers, no spills; 1064 resident CTAs hold the 1000 units of an
 // 8000-ion crystal in one wave): 5 % faster there than 8 CTAs at 64 registers,
 // no slower on larger systems; six or eight entries in flight per lane spill.
-template <int PM, class R, int ADV, int REC, int LPA>
+template <int PM, class R, int ADV, int REC, int LPA, int MI>
 __global__ void __launch_bounds__(32 * kListWarps, sizeof(R) == 4 ? 7 : 4) k_step(Dev d, PairTabT<R> T, int kick, int j, int cur)
 {
     extern __shared__ __align__(32) unsigned char fsm[];
@@ -951,16 +961,16 @@ __global__ void __launch_bounds__(32 * kListWarps, sizeof(R) == 4 ? 7 : 4) k_ste
     }
     release_next_step();
     for (int u = blockIdx.x; u < d.nunits; u += gridDim.x)
-        force_unit<PM, R, ADV, REC, LPA>(d, T, ptab, kick, j, cur, u, red, rsh, s_last);
+        force_unit<PM, R, ADV, REC, LPA, MI>(d, T, ptab, kick, j, cur, u, red, rsh, s_last);
 }
 
-template <int PM, class R, int ADV, int REC, int LPA>
+template <int PM, class R, int ADV, int REC, int LPA, int MI>
 static cudaError_t step_prepare_one(size_t smem, int nsm, int &grid)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_step<PM, R, ADV, REC, LPA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_step<PM, R, ADV, REC, LPA, MI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<PM, R, ADV, REC, LPA>, 32 * kListWarps, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<PM, R, ADV, REC, LPA, MI>, 32 * kListWarps, smem);
     grid = per_sm * nsm;
     return e;
 }
@@ -973,22 +983,27 @@ static cudaError_t step_prepare_lanes(MdLaunch &m, int stage_entries)
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     m.step_smem = (size_t)stage_entries * (m.mixed ? sizeof(int4) : sizeof(D4));
-    if (m.mixed) {
-        if ((e = step_prepare_one<PM_FIX, float, 0, 0, LPA>(m.step_smem, nsm, m.step_grid[0])) != cudaSuccess) return e;
-        if ((e = step_prepare_one<PM_FIX, float, 0, 1, LPA>(m.step_smem, nsm, m.step_grid[1])) != cudaSuccess) return e;
-        if ((e = step_prepare_one<PM_FIX, float, 1, 0, LPA>(m.step_smem, nsm, m.step_grid[2])) != cudaSuccess) return e;
-        e = step_prepare_one<PM_FIX, float, 1, 1, LPA>(m.step_smem, nsm, m.step_grid[3]);
+    if (m.mixed && m.minimg) {
+        if ((e = step_prepare_one<PM_FIX, float, 0, 0, LPA, 1>(m.step_smem, nsm, m.step_grid[0])) != cudaSuccess) return e;
+        if ((e = step_prepare_one<PM_FIX, float, 0, 1, LPA, 1>(m.step_smem, nsm, m.step_grid[1])) != cudaSuccess) return e;
+        if ((e = step_prepare_one<PM_FIX, float, 1, 0, LPA, 1>(m.step_smem, nsm, m.step_grid[2])) != cudaSuccess) return e;
+        e = step_prepare_one<PM_FIX, float, 1, 1, LPA, 1>(m.step_smem, nsm, m.step_grid[3]);
+    } else if (m.mixed) {
+        if ((e = step_prepare_one<PM_FIX, float, 0, 0, LPA, 0>(m.step_smem, nsm, m.step_grid[0])) != cudaSuccess) return e;
+        if ((e = step_prepare_one<PM_FIX, float, 0, 1, LPA, 0>(m.step_smem, nsm, m.step_grid[1])) != cudaSuccess) return e;
+        if ((e = step_prepare_one<PM_FIX, float, 1, 0, LPA, 0>(m.step_smem, nsm, m.step_grid[2])) != cudaSuccess) return e;
+        e = step_prepare_one<PM_FIX, float, 1, 1, LPA, 0>(m.step_smem, nsm, m.step_grid[3]);
     } else {
-        if ((e = step_prepare_one<PM_BOX64, double, 0, 0, LPA>(m.step_smem, nsm, m.step_grid[0])) != cudaSuccess) return e;
-        if ((e = step_prepare_one<PM_BOX64, double, 0, 1, LPA>(m.step_smem, nsm, m.step_grid[1])) != cudaSuccess) return e;
-        if ((e = step_prepare_one<PM_BOX64, double, 1, 0, LPA>(m.step_smem, nsm, m.step_grid[2])) != cudaSuccess) return e;
-        e = step_prepare_one<PM_BOX64, double, 1, 1, LPA>(m.step_smem, nsm, m.step_grid[3]);
+        if ((e = step_prepare_one<PM_BOX64, double, 0, 0, LPA, 0>(m.step_smem, nsm, m.step_grid[0])) != cudaSuccess) return e;
+        if ((e = step_prepare_one<PM_BOX64, double, 0, 1, LPA, 0>(m.step_smem, nsm, m.step_grid[1])) != cudaSuccess) return e;
+        if ((e = step_prepare_one<PM_BOX64, double, 1, 0, LPA, 0>(m.step_smem, nsm, m.step_grid[2])) != cudaSuccess) return e;
+        e = step_prepare_one<PM_BOX64, double, 1, 1, LPA, 0>(m.step_smem, nsm, m.step_grid[3]);
     }
     return e;
 }
 
 // cooperative launch: all CTAs resident at once (the grid barriers need it)
-template <int PM, class R, int ADV, int REC, int LPA>
+template <int PM, class R, int ADV, int REC, int LPA, int MI>
 static cudaError_t step_launch(const Dev &d, const MdLaunch &m, const PairTabT<R> &T, int kick, int j, int cur,
                                cudaStream_t st)
 {
@@ -1006,17 +1021,17 @@ static cudaError_t step_launch(const Dev &d, const MdLaunch &m, const PairTabT<R
     at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 2;
-    return cudaLaunchKernelEx(&cfg, k_step<PM, R, ADV, REC, LPA>, d, T, kick, j, cur);
+    return cudaLaunchKernelEx(&cfg, k_step<PM, R, ADV, REC, LPA, MI>, d, T, kick, j, cur);
 }
 
-template <int PM, class R, int LPA>
+template <int PM, class R, int LPA, int MI>
 static cudaError_t step_any(const Dev &d, const MdLaunch &m, const PairTabT<R> &T, int kick, int j, int cur, int adv,
                             int rec, cudaStream_t st)
 {
-    if (adv && rec) return step_launch<PM, R, 1, 1, LPA>(d, m, T, kick, j, cur, st);
-    if (adv) return step_launch<PM, R, 1, 0, LPA>(d, m, T, kick, j, cur, st);
-    if (rec) return step_launch<PM, R, 0, 1, LPA>(d, m, T, kick, j, cur, st);
-    return step_launch<PM, R, 0, 0, LPA>(d, m, T, kick, j, cur, st);
+    if (adv && rec) return step_launch<PM, R, 1, 1, LPA, MI>(d, m, T, kick, j, cur, st);
+    if (adv) return step_launch<PM, R, 1, 0, LPA, MI>(d, m, T, kick, j, cur, st);
+    if (rec) return step_launch<PM, R, 0, 1, LPA, MI>(d, m, T, kick, j, cur, st);
+    return step_launch<PM, R, 0, 0, LPA, MI>(d, m, T, kick, j, cur, st);
 }
 
 // the step kernel of one lane count (one translation unit per count)
@@ -1025,8 +1040,9 @@ static cudaError_t step_force_lanes(const Dev &d, const MdLaunch &m, const PairT
                                     const PairTabT<double> &Td, int kick, int j, int cur, int adv, int rec,
                                     cudaStream_t st)
 {
-    if (m.mixed) return step_any<PM_FIX, float, LPA>(d, m, Tf, kick, j, cur, adv, rec, st);
-    return step_any<PM_BOX64, double, LPA>(d, m, Td, kick, j, cur, adv, rec, st);
+    if (m.mixed && m.minimg) return step_any<PM_FIX, float, LPA, 1>(d, m, Tf, kick, j, cur, adv, rec, st);
+    if (m.mixed) return step_any<PM_FIX, float, LPA, 0>(d, m, Tf, kick, j, cur, adv, rec, st);
+    return step_any<PM_BOX64, double, LPA, 0>(d, m, Td, kick, j, cur, adv, rec, st);
 }
 
 }  // namespace qtb

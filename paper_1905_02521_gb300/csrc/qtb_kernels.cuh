@@ -60,6 +60,8 @@ struct MdLaunch {
     int nm_big;           // ring-polymer integrator with 32 atoms per CTA (large contexts)
     int lanes;            // lanes per bead-atom of the step kernel (8, 16, 32)
     int step_grid[4];     // resident CTAs of the step kernel, by (adv, rec)
+    int minimg;           // mixed form, fixed cells all larger than 2 (r_cut + 2 skin): the step
+                          // kernel variant that takes list displacements by minimum image
     size_t step_smem;     // its dynamic shared memory (list build staging chunk)
 };
 constexpr int kIntAtomsPerWarp = 10;                   // integrator: lanes 3a + c, a < 10

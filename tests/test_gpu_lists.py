@@ -269,3 +269,24 @@ def test_uploaded_states_rebuild_only_when_needed(qtb, oracle, precision):
                 assert rel_l2(f, fo) < F32_L2 and rel_inf(f, fo) < F32_INF
     finally:
         qtb.qtb_destroy(ctx)
+
+
+def test_minimum_image_variant_is_bit_identical(qtb):
+    # a crystal whose cell exceeds twice (r_cut + 2 skin) runs alone on the step-kernel
+    # variant that takes list displacements by minimum image; batched with a small cell
+    # (which needs the image bits) the context uses the image-bit variant.  Each system
+    # rebuilds on its own schedule, so the big crystal's trajectory must agree bit for bit
+    s_big, pot = W.mgo_system(5, 300.0, seed=41)          # 21.05 A > 2 (8 + 1.6) A
+    s_small, _ = W.mgo_system(2, 300.0, seed=42)          # 8.42 A
+    N = len(s_big["types"])
+    out = []
+    for systems in ([s_big], [s_big, s_small]):
+        ctx = gpu_ctx(qtb, systems, pot, 1.0, precision=1, filter_prec=1, seed=7)
+        try:
+            qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB, 513, 0.3)
+            qtb.qtb_step_n(ctx, 300)
+            out.append(qtb.qtb_get_state(ctx, 0, 1, N) + (qtb.qtb_list_rebuilds(ctx),))
+        finally:
+            qtb.qtb_destroy(ctx)
+    (xa, va, _), (xb, vb, _) = out
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
