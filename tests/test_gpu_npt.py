@@ -222,3 +222,33 @@ def test_npt_arguments_are_checked(qtb):
     with pytest.raises(qtb.QtbError) as e:   # the cell needs a mass
         gpu_ctx(qtb, [s1], pot, 1.0, npt={"pressure": 0.0, "mass": 0.0, "gamma": 1e-3})
     assert e.value.code == qtb.ERR_ARG
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_cells_match_single_runs(qtb, precision):
+    # two crystals of different size and temperature in one isothermal-isobaric
+    # context: each has its own cell (and its own rebuild schedule), so each runs bit
+    # for bit as alone, where system k of a batch uses Philox key (seed, k)
+    sa, pot = W.mgo_system(2, 150.0, gamma=2e-3, seed=51)
+    sb, _ = W.mgo_system(3, 600.0, gamma=2e-3, seed=52)
+    npt = {"pressure": 0.003, "mass": _cell_mass(B_MGO, np.prod(sb["box"]), 200.0), "gamma": 5e-3}
+    ctx = gpu_ctx(qtb, [sa, sb], pot, 1.0, precision=precision, seed=5, npt=npt)
+    try:
+        qtb.qtb_set_filter(ctx, 1, qtb.NOISE_QTB, 513, 0.3)
+        qtb.qtb_step_n(ctx, 300)
+        batched = [(qtb.qtb_get_state(ctx, k, 1, len(s["types"]))[0], qtb.qtb_get_cell(ctx, k))
+                   for k, s in enumerate((sa, sb))]
+    finally:
+        qtb.qtb_destroy(ctx)
+    for k, s in enumerate((sa, sb)):
+        c1 = gpu_ctx(qtb, [s], pot, 1.0, precision=precision, seed=5 ^ (k << 32), npt=npt)
+        try:
+            if k == 1:
+                qtb.qtb_set_filter(c1, 0, qtb.NOISE_QTB, 513, 0.3)
+            qtb.qtb_step_n(c1, 300)
+            x = qtb.qtb_get_state(c1, 0, 1, len(s["types"]))[0]
+            box, pe = qtb.qtb_get_cell(c1, 0)
+            assert np.array_equal(x, batched[k][0])
+            assert np.array_equal(box, batched[k][1][0]) and pe == batched[k][1][1]
+        finally:
+            qtb.qtb_destroy(c1)
