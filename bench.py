@@ -154,7 +154,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-WORKLOADS = ("mgo8000", "lih_qtbpimd_p8", "lih_pimd_p32", "sweep64", "lih_pimd_p32_big")
+WORKLOADS = ("mgo8000", "lih_qtbpimd_p8", "lih_pimd_p32", "sweep64", "lih_pimd_p32_big", "lih_qtb_npt")
 
 # algorithmic bytes per bead-atom of one launch of the ring-polymer integrator
 # (k_integrate_nm): read x, v, f, xref and the coloured noise, write x, v and the
@@ -174,6 +174,8 @@ def workload(name, ncell, precision, filt):
         integrator's stream (~200 MB per step) exceeds the 129 MB L2.
     sweep64: 64 MgO systems of 3..8 cells per side (216-4096 ions) at T_i = 10 150^(i/63) K,
         QTB-MD, one context (batched), dt 1 fs, 2049 taps, w_max 0.3 rad/fs.
+    lih_qtb_npt: LiH 6^3 cells (1728 ions), QTB-MD 50 K at zero pressure with the isotropic
+        Langevin cell (cell period ~300 fs, friction 4e-3/fs), dt 0.25 fs, 2049 taps, w_max 0.6 rad/fs.
     """
     from paper_1905_02521_gb300 import qtb, workloads as W
     prec = qtb.MIXED if precision == "mixed" else qtb.FP64
@@ -197,6 +199,13 @@ def workload(name, ncell, precision, filt):
         else:
             desc = (f"LiH rock salt {nc}x{nc}x{nc} cells ({len(s['types'])} ions) x 32 beads, PIMD with white "
                     f"Langevin bath 50 K, dt 0.25 fs")
+    elif name == "lih_qtb_npt":
+        s, pot = W.lih_system(6, 50.0, gamma=1e-3)
+        systems = [s]
+        dt = 0.25
+        setup = (qtb.NOISE_QTB, 2049, 0.6)
+        desc = (f"LiH rock salt 6x6x6 cells (1728 ions), QTB-MD 50 K at zero pressure, isotropic Langevin cell, "
+                f"dt 0.25 fs, 2049-tap {filt} filter")
     elif name == "sweep64":
         systems, pot = W.sweep_systems(64, gamma=1e-3)
         setup = (qtb.NOISE_QTB, 2049, 0.3)
@@ -208,6 +217,9 @@ def workload(name, ncell, precision, filt):
     params = {k: pot[k] for k in ("mass", "charge", "buck_A", "buck_rho", "buck_C")}
     params.update(dsf_alpha=pot["dsf_alpha"], r_cut=pot["r_cut"], dt=dt, precision=prec, filter_prec=fp,
                   seed=12345, obs_stride=BLOCK, max_records=64)
+    if name == "lih_qtb_npt":   # cell mass for a ~300 fs volume period at a bulk modulus of ~1 eV/A^3
+        V = float(np.prod(systems[0]["box"]))
+        params.update(npt=1, pressure=0.0, cell_mass=9.0 * 1.0 * V / (2 * np.pi / 300.0) ** 2, cell_gamma=4e-3)
     return systems, pot, params, setup, desc
 
 
@@ -319,12 +331,15 @@ def run_ours(args):
     # roofline of the dominant kernel (pair force): algorithmic flops / mean launch time
     pairs = 0
     states = []
+    npt = bool(params.get("npt"))
+    cells = [qtb.qtb_get_cell(ctx, k) if npt else None for k in range(len(sizes))]   # (edges, momentum)
     for k, (n, p) in enumerate(sizes):
         x, v = qtb.qtb_get_state(ctx, k, p, n)
         states.append((pinned(torch, x), pinned(torch, v)))   # the end-to-end leg uploads from pinned memory
         # every bead of small systems; 4 evenly spaced beads of large ones, scaled to P
         beads = range(p) if n * p <= 100000 else range(0, p, max(1, p // 4))
-        pairs += int(round(sum(count_pairs(x[b], systems[k]["box"], pot["r_cut"]) for b in beads) * p / len(beads)))
+        box = cells[k][0] if npt else systems[k]["box"]
+        pairs += int(round(sum(count_pairs(x[b], box, pot["r_cut"]) for b in beads) * p / len(beads)))
     sampled = {k: kernel_ms[k] / kernel_n[k] for k in kernel_ms if kernel_n[k]}
     launch_ms = in_graph_launch_ms(sampled, kernel_n, np.mean(step_ms), args.steps, sizes)
     force_ms = launch_ms.get("force", 0.0)
@@ -345,11 +360,15 @@ def run_ours(args):
         t0 = time.perf_counter()
         for k, (xt, vt) in enumerate(states):
             x, v = xt.numpy(), vt.numpy()
+            if npt:     # the cell first: positions are taken in the cell current at the upload
+                qtb.qtb_set_cell(ctx, k, *cells[k])
             qtb.qtb_set_state(ctx, k, x, v)
         qtb.qtb_step_n(ctx, BLOCK)
         for k, (n, p) in enumerate(sizes):
             qtb.qtb_observables(ctx, k)
             qtb.qtb_get_state_into(ctx, k, outs[k][0].numpy(), outs[k][1].numpy())
+            if npt:
+                qtb.qtb_get_cell(ctx, k)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_value = ws * units * BLOCK * args.steps / (np.sum(e2e_ms) / 1e3)
     rebuilds_e2e = (qtb.qtb_list_rebuilds(ctx) - rebuilds_e2e0) / args.steps
@@ -386,10 +405,11 @@ def run_ours(args):
         "roofline_integrator": integrator_roofline(launch_ms, units, sizes, args.precision, args.workload),
         "kernel_ms_per_bench_step": step_breakdown,
         "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * units * 3 * 8),
-                "d2h_bytes_per_step": int(len(systems) * qtb.NREC * 8 + 2 * units * 3 * 8),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * units * 3 * 8 + npt * len(systems) * 32),
+                "d2h_bytes_per_step": int(len(systems) * (qtb.NREC * 8 + npt * 32) + 2 * units * 3 * 8),
                 "list_rebuilds_per_step": rebuilds_e2e,
-                "per_step": "state uploaded from pinned host memory, 256 steps, observables and state read back"},
+                "per_step": "state (and cell, at constant pressure) uploaded from pinned host memory, 256 steps, "
+                            "observables, state and cell read back"},
         # per block: white, filter, the integrator (once for one-bead systems, else every
         # step per distinct bead count), 256 step launches (a list rebuild runs inside the
         # step launch that needs it), the centroid estimators of the recorded step (ring
@@ -404,11 +424,11 @@ def run_ours(args):
     if args.precision == "mixed" and setup is not None and args.fp64_blocks > 0:
         # the metric compares the mixed form with the FP64 form at matched error:
         # the FP64 form of the same workload, timed from the same steady state
-        fp64 = fp64_form_leg(qtb, torch, systems, params, setup, states, units, args.fp64_blocks)
+        fp64 = fp64_form_leg(qtb, torch, systems, params, setup, states, units, args.fp64_blocks, cells)
         fp64["mixed_over_fp64"] = value / fp64["value"]
         line["fp64_form"] = fp64
     if args.precision == "mixed" and setup is not None and args.matched_blocks > 0 and len(systems) == 1:
-        line["matched_error"] = matched_error(qtb, systems, params, setup, states[0], args.matched_blocks)
+        line["matched_error"] = matched_error(qtb, systems, params, setup, states[0], args.matched_blocks, cells[0])
     if ws == 1 and not args.no_cpu_baseline:   # the host baseline belongs to the one-GPU line only
         line["cpu_baseline"] = cpu_baseline(args.workload, sample_atoms=64)
     if ws > 1:
@@ -417,7 +437,7 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
-def fp64_form_leg(qtb, torch, systems, params, setup, states, units, n_blocks):
+def fp64_form_leg(qtb, torch, systems, params, setup, states, units, n_blocks, cells):
     """The FP64 form (every step in FP64, FP64 filter) of the same workload: the
     mixed form's steady state uploaded, lists rebuilt on it, one warm-up block,
     then n_blocks device-timed 256-step blocks with an L2 flush between them."""
@@ -428,6 +448,8 @@ def fp64_form_leg(qtb, torch, systems, params, setup, states, units, n_blocks):
     try:
         qtb.qtb_set_filter(ctx, -1, *setup)
         for k, (xt, vt) in enumerate(states):
+            if cells[k] is not None:
+                qtb.qtb_set_cell(ctx, k, *cells[k])
             qtb.qtb_set_state(ctx, k, xt.numpy(), vt.numpy())
         qtb.qtb_rebuild_lists(ctx)
         qtb.qtb_step_n(ctx, BLOCK)
@@ -464,7 +486,7 @@ def block_sigma(x, n_blocks=16):
     return float(b.std(ddof=1) / np.sqrt(n_blocks))
 
 
-def matched_error(qtb, systems, params, setup, state, n_blocks, stride=4):
+def matched_error(qtb, systems, params, setup, state, n_blocks, cell, stride=4):
     """Error of the mixed form against the FP64 form at the bench's own size.
 
     Both forms start from the same steady state (the mixed form's, uploaded to
@@ -482,6 +504,8 @@ def matched_error(qtb, systems, params, setup, state, n_blocks, stride=4):
         ctx = qtb.qtb_init(systems, p)
         try:
             qtb.qtb_set_filter(ctx, -1, *setup)
+            if cell is not None:
+                qtb.qtb_set_cell(ctx, 0, *cell)
             qtb.qtb_set_state(ctx, 0, x, v)
             qtb.qtb_step_n(ctx, n_blocks * BLOCK)
             series[form] = qtb.qtb_get_series(ctx, 0, nrec)
@@ -490,7 +514,8 @@ def matched_error(qtb, systems, params, setup, state, n_blocks, stride=4):
     out = {"steps": n_blocks * BLOCK, "record_stride": stride, "reference": "FP64 GPU form (parity-pinned to the "
            "FP64 oracle at 1e-12)", "sigma": "block average, 16 blocks", "observables": {}}
     worst = 0.0
-    for name, get in MATCHED_OBS:
+    obs = MATCHED_OBS + ((("volume_A3", lambda r: r[:, 20]),) if cell is not None else ())
+    for name, get in obs:
         a, b = get(series["fp64"]), get(series["mixed"])
         sig = block_sigma(a)
         dev = (b.mean() - a.mean()) / sig if sig > 0 else 0.0

@@ -324,6 +324,19 @@ int qtb_get_step(qtb_ctx *c, long long *step);
  * Synchronises. */
 int qtb_get_cell(qtb_ctx *c, int sys, double *box, double *p_e);
 
+/* Set the cell of system sys of an isothermal-isobaric context: edges box[3]
+ * (A; the initial edges times one scale lam >= 0.9, since the cell is isotropic
+ * and its lists are sized for that) and cell momentum p_e (eV fs), in the form
+ * qtb_get_cell reports them (after a step, before the closing half kick of the
+ * cell momentum that the next step applies; whether that half kick is due is
+ * left as it is).  Positions are stored relative to the cell and scale with it,
+ * so a state is restored by setting the cell first and then the positions
+ * (qtb_set_state takes them in the cell current at the upload).  Every list is
+ * rebuilt, and the forces and the record of the current step evaluated again,
+ * at the next call that needs them.  QTB_ERR_ARG for a constant-volume context,
+ * an anisotropic or too small cell, or a non-finite value.  Synchronises. */
+int qtb_set_cell(qtb_ctx *c, int sys, const double *box, double p_e);
+
 /* kappa_P / (k_B T) = F_P(y), y = beta hbar w, solved in FP64 on the GPU on the
  * collocation grid y_i = y0 sinh(i t), t = asinh(y_max/y0)/(n-1), i < n:
  * least squares of Eq. 10 imposed at the nodes and midpoints with linear

@@ -475,7 +475,7 @@ int run_steps(qtb_ctx *c, int j0, int count, bool graph)
         const int j = j0 + t, cur = j & 1;
         const bool keep = c->capturing;
         if (j % 64 != 0) c->capturing = false;
-        if (c->p.npt) launch_cell(c->d, j, cur, c->p.r_cut + c->skin, c->skin, c->st);  // isothermal-isobaric cells
+        if (c->p.npt) launch_cell(c->d, j, cur, c->p.r_cut + c->skin, c->skin, c->mixed, c->st);  // isothermal-isobaric cells
         if (!m.fused || t == 0) {
             ProfMark pm(c, KC_INTEGRATE);
             launch_integrate(c->d, m, j, cur, c->st);
@@ -788,6 +788,9 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     for (int a = 0; a < nt; ++a) {
         T.mass[a] = p->mass[a];
         T.mass_mvv[a] = p->mass[a] * kMvv2e;
+        const float mh = (float)p->mass[a], kh = (float)(0.5 * p->mass[a] * kMvv2e);
+        T.mass_ff[a] = make_float2(mh, (float)(p->mass[a] - (double)mh));
+        T.half_mvv_ff[a] = make_float2(kh, (float)(0.5 * p->mass[a] * kMvv2e - (double)kh));
         T.hdt_m[a] = 0.5 * p->dt / (p->mass[a] * kMvv2e);
         T.ext_k[a] = p->mass[a] * kMvv2e * p->ext_omega * p->ext_omega;
     }
@@ -829,6 +832,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         for (int a = 0; a < kMaxTypes; ++a) {
             F.hdt_m[a] = (float)T.hdt_m[a]; F.ext_k[a] = (float)T.ext_k[a];
             F.mass[a] = T.mass[a]; F.mass_mvv[a] = T.mass_mvv[a];
+            F.mass_ff[a] = T.mass_ff[a]; F.half_mvv_ff[a] = T.half_mvv_ff[a];
         }
         F.ext_V0 = (float)T.ext_V0; F.ext_ia2 = (float)T.ext_ia2;
         F.ntypes = T.ntypes; F.potential = T.potential;
@@ -1164,6 +1168,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
             C.a1 = C.a2 = 0.5 * p->dt;
             C.e1f = C.g1f = C.e2f = C.g2f = C.lamf = 1.0f;
             C.a1f = C.a2f = (float)(0.5 * p->dt);
+            C.inv_wf = (float)(1.0 / p->cell_mass);
             C.on = 1;
         }
         d.npt = upload(c, cells);
@@ -1550,6 +1555,36 @@ int qtb_get_cell(qtb_ctx *c, int sys, double *box, double *p_e)
     if (box)
         for (int k = 0; k < 3; ++k) box[k] = c->hs[sys].box[k] * lam;
     if (p_e) *p_e = pe;
+    return QTB_OK;
+}
+
+int qtb_set_cell(qtb_ctx *c, int sys, const double *box, double p_e)
+{
+    if (!c || !box) return fail(QTB_ERR_ARG, "null argument");
+    if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
+    if (!c->d.npt) return fail(QTB_ERR_ARG, "qtb_set_cell: not an isothermal-isobaric context");
+    const double *ref = c->hs[sys].box;
+    const double lam = box[0] / ref[0];
+    for (int k = 0; k < 3; ++k)
+        if (!(std::fabs(box[k] / ref[k] - lam) <= 1e-12 * lam))
+            return fail(QTB_ERR_ARG, "qtb_set_cell: the cell is isotropic (edges proportional to the initial ones)");
+    if (!std::isfinite(lam) || !(lam >= kCellMinScale) || !std::isfinite(p_e))
+        return fail(QTB_ERR_ARG, "qtb_set_cell: edges below %.2f of the initial ones or not finite", kCellMinScale);
+    if (int rc0 = ensure_fresh(c)) return rc0;
+    if (int rc = check_err_word(c)) return rc;
+    DNpt C;
+    CUDA_TRY(cudaMemcpyAsync(&C, c->d.npt + sys, sizeof C, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+    C.lam = lam;
+    C.lamf = (float)lam;
+    C.peps = p_e;  // whether the closing half kick is due stays as it is
+    CUDA_TRY(cudaMemcpyAsync(c->d.npt + sys, &C, sizeof C, cudaMemcpyHostToDevice, c->st));
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+    // positions are stored relative to the cell and scale with it; every list is
+    // rebuilt and the forces and record evaluated again at the next call that
+    // needs them
+    if (c->pair) c->lists_built = false;
+    c->stale = true;
     return QTB_OK;
 }
 

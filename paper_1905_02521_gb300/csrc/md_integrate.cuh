@@ -39,6 +39,8 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
     double acc[kNQ];
     for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
     double spring = 0.0;
+    // the spring energy enters the record of recorded steps only (FP64 is scarce)
+    const bool recs = (d.clock[0] * kBlockSteps + j + 1) % d.obs_stride == 0;
     PS *X = reinterpret_cast<PS *>(d.x);
     const size_t G = (size_t)d.G;
     const size_t base = act ? (size_t)c * G + S.g0 + i : 0;
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
             a[b] = u;
             V[base + (size_t)b * N] = w;
         }
-        if (P > 1) {
+        if (P > 1 && recs) {
             R sp = 0;
 #pragma unroll(UN)
             for (int b = 0; b < P; ++b) {
@@ -165,9 +167,11 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
         atomicOr(&d.rflag[cur * d.nsys + s], 1u);
         atomicOr(&d.flag[cur], 1u);
     }
-    spring = warp_sum(spring);
-    acc[Q_SPRING] = spring;
-    if (mine) cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
+    if (P > 1 && recs) {
+        spring = warp_sum(spring);
+        acc[Q_SPRING] = spring;
+        if (mine) cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
+    }
 }
 
 // Ring-polymer integrator for P >= 2 with the normal-mode transforms in shared
@@ -416,6 +420,7 @@ __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int 
     __syncthreads();
     // phase 4: spring energy; packed positions and displacement test per bead-atom
     double spring = 0.0;
+    const bool recs = (d.clock[0] * kBlockSteps + j + 1) % d.obs_stride == 0;  // spring only where recorded
     bool moved = false;
     const R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
 #pragma unroll
@@ -429,7 +434,7 @@ __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int 
         for (int m = 0; m < MT; ++m) {
             const int b = g * MT + m;
             const R dx = xs[b * COLS + col] - xs[((b + 1) % P) * COLS + col];
-            spring += 0.5 * d.mass_mvv[tt[u]] * S.wP * S.wP * (double)(dx * dx);
+            if (recs) spring += 0.5 * d.mass_mvv[tt[u]] * S.wP * S.wP * (double)(dx * dx);
             if (PM != PM_FREE && c == 0) {
                 const size_t gg = S.g0 + (size_t)b * N + i;
                 const PS *XR = reinterpret_cast<const PS *>(d.xref);
@@ -456,10 +461,12 @@ __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int 
         atomicOr(&d.rflag[cur * d.nsys + s], 1u);
         atomicOr(&d.flag[cur], 1u);
     }
-    double acc[kNQ];
-    for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
-    acc[Q_SPRING] = warp_sum(spring);
-    cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
+    if (recs) {
+        double acc[kNQ];
+        for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+        acc[Q_SPRING] = warp_sum(spring);
+        cta_store_partials(acc, red, d.ipart + (size_t)cta * kNQ);
+    }
 }
 
 }  // namespace qtb

@@ -134,6 +134,22 @@ struct FF {
         }
     }
     __device__ float value() const { return __fadd_rn(hi, lo); }
+    // add another float-float value (bh + bl)
+    __device__ void add_ff(float bh, float bl)
+    {
+        float s, e;
+        two_sum(hi, bh, s, e);
+        hi = s;
+        lo = __fadd_rn(__fadd_rn(lo, bl), e);
+    }
+    // sum over the lanes l, l ^ W, l ^ 2W, ... (W a power of two <= 16): lane l < W
+    // ends with the sum over its residue class mod W
+    template <int W> __device__ void across_groups()
+    {
+#pragma unroll
+        for (int o = 16; o >= W; o >>= 1)
+            add_ff(__shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
+    }
 };
 
 // plain accumulator with the same interface (FP64 form)
@@ -167,6 +183,53 @@ static __device__ void cta_store_partials(const double *acc, double (*red)[kNQ],
         double s = 0.0;
         for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
         out[threadIdx.x] = s;
+    }
+}
+
+// FP32 form of the above for the list force kernel: the float-float sums of a
+// CTA's bead-atoms, stored as (hi, lo) pairs in out[0..kNQ).  The potential
+// energy and virial halves (en, w*) count on the lanes `lead` (one per
+// bead-atom), the kinetic energy kc + kl and momentum mc + ml of component c on
+// lane c of each LPA-lane group.  red is the CTA's [warps][kNQ] scratch (8 bytes
+// an entry).
+template <int LPA>
+static __device__ void cta_store_partials_ff(bool lead, float en, float w0, float w1, float w2, float w3, float w4,
+                                             float w5, float kc, float kl, float mc, float ml, double (*red)[kNQ],
+                                             float2 *out)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    static_assert(kNQ == 16 && Q_X2 == 12 && Q_MOM + 2 < 13, "slots 13 and 14 must be free");
+    float2 (*rf)[kNQ] = reinterpret_cast<float2 (*)[kNQ]>(red);
+    const float h[7] = {en, w0, w1, w2, w3, w4, w5};
+    constexpr int slot[7] = {Q_V, Q_VIR + 0, Q_VIR + 1, Q_VIR + 2, Q_VIR + 3, Q_VIR + 4, Q_VIR + 5};
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        FF a{lead ? 0.5f * h[k] : 0.f, 0.f};  // pairs are counted from both ends
+        a.template across_groups<LPA>();
+        if (lane == 0) rf[warp][slot[k]] = make_float2(a.hi, a.lo);
+    }
+    FF K{kc, kl}, M{mc, ml};
+    K.template across_groups<LPA>();
+    M.template across_groups<LPA>();
+    // component c of the warp's kinetic energy goes to slot Q_K (c = 0) or to the
+    // free slots 13 and 14, joined below
+    if (lane < 3) {
+        rf[warp][lane == 0 ? Q_K : 12 + lane] = make_float2(K.hi, K.lo);
+        rf[warp][Q_MOM + lane] = make_float2(M.hi, M.lo);
+    }
+    if (lane == 0) rf[warp][Q_SPRING] = rf[warp][Q_X2] = rf[warp][15] = make_float2(0.f, 0.f);
+    __syncthreads();
+    if (threadIdx.x < kNQ) {
+        const int q = threadIdx.x;
+        FF t{0.f, 0.f};
+        if (q != 13 && q != 14)
+            for (int w = 0; w < nw; ++w) t.add_ff(rf[w][q].x, rf[w][q].y);
+        if (q == Q_K)
+            for (int w = 0; w < nw; ++w) {
+                t.add_ff(rf[w][13].x, rf[w][13].y);
+                t.add_ff(rf[w][14].x, rf[w][14].y);
+            }
+        out[q] = make_float2(t.hi, t.lo);
     }
 }
 
@@ -625,55 +688,97 @@ __device__ __forceinline__ void pair_eval(const PairTabT<R> &T, const PairRow<R>
 }
 
 // Per-system reduction of the CTA partials into the observable record
-// (fixed summation order, FP64).  Executed by one CTA; sh holds one row per warp.
+// (fixed summation order).  Executed by one CTA; sh holds one row per warp.
+// FFP: the partials are float-float (hi, lo) pairs (FP32 list force kernel),
+// summed on the FP32 pipe; otherwise FP64.  The record's entries are then
+// formed in FP64, one per thread.
+template <bool FFP>
 static __device__ void reduce_system(const Dev &d, int s, long long step, int record, double (*sh)[kNQ + 1])
 {
+    __shared__ double tot[kNQ + 1];
     const DSys S = d.sys[s];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    double acc[kNQ + 1];
-    for (int q = 0; q <= kNQ; ++q) acc[q] = 0.0;
-    for (int c = S.fcta0 + (int)threadIdx.x; c < S.fcta1; c += blockDim.x)
-        for (int q = 0; q < kNQ; ++q) acc[q] += d.part[(size_t)c * kNQ + q];
-    for (int c = S.icta0 + (int)threadIdx.x; c < S.icta1; c += blockDim.x) acc[kNQ] += d.ipart[(size_t)c * kNQ + Q_SPRING];
-    for (int q = 0; q <= kNQ; ++q) acc[q] = warp_sum(acc[q]);
-    if (lane == 0)
-        for (int q = 0; q <= kNQ; ++q) sh[warp][q] = acc[q];
+    // the integrators' spring partials (ring polymers only: zero for one bead)
+    double sp = 0.0;
+    if (S.P > 1)
+        for (int c = S.icta0 + (int)threadIdx.x; c < S.icta1; c += blockDim.x) sp += d.ipart[(size_t)c * kNQ + Q_SPRING];
+    if (S.P > 1) sp = warp_sum(sp);
+    if constexpr (FFP) {
+        const float2 *P2 = reinterpret_cast<const float2 *>(d.part);
+        FF acc[kNQ];
+#pragma unroll
+        for (int q = 0; q < kNQ; ++q) acc[q] = FF{0.f, 0.f};
+        for (int c = S.fcta0 + (int)threadIdx.x; c < S.fcta1; c += blockDim.x)
+#pragma unroll
+            for (int q = 0; q < kNQ; ++q) {
+                const float2 v = P2[(size_t)c * kNQ + q];
+                acc[q].add_ff(v.x, v.y);
+            }
+        float2 (*sf)[kNQ + 1] = reinterpret_cast<float2 (*)[kNQ + 1]>(sh);
+#pragma unroll
+        for (int q = 0; q < kNQ; ++q) {
+            acc[q].warp_reduce();
+            if (lane == 0) sf[warp][q] = make_float2(acc[q].hi, acc[q].lo);
+        }
+        if (lane == 0) sh[warp][kNQ] = sp;  // the row's last entry (sf[warp][q] overlays sh[warp][q])
+        __syncthreads();
+        if (threadIdx.x < kNQ) {
+            FF t{0.f, 0.f};
+            for (int w = 0; w < nw; ++w) t.add_ff(sf[w][threadIdx.x].x, sf[w][threadIdx.x].y);
+            tot[threadIdx.x] = (double)t.hi + (double)t.lo;
+        } else if (threadIdx.x == kNQ) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += sh[w][kNQ];
+            tot[kNQ] = t;
+        }
+    } else {
+        double acc[kNQ];
+        for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+        for (int c = S.fcta0 + (int)threadIdx.x; c < S.fcta1; c += blockDim.x)
+            for (int q = 0; q < kNQ; ++q) acc[q] += d.part[(size_t)c * kNQ + q];
+        for (int q = 0; q < kNQ; ++q) acc[q] = warp_sum(acc[q]);
+        if (lane == 0) {
+            for (int q = 0; q < kNQ; ++q) sh[warp][q] = acc[q];
+            sh[warp][kNQ] = sp;
+        }
+        __syncthreads();
+        if (threadIdx.x <= kNQ) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += sh[w][threadIdx.x];
+            tot[threadIdx.x] = t;
+        }
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double tot[kNQ + 1];
-        for (int q = 0; q <= kNQ; ++q) {
-            tot[q] = 0.0;
-            for (int w = 0; w < nw; ++w) tot[q] += sh[w][q];
-        }
+    const int q = threadIdx.x;
+    if (q < QTB_NREC) {
         const double invP = S.invP;
-        double rec[QTB_NREC];
-        for (int q = 0; q < QTB_NREC; ++q) rec[q] = 0.0;
-        const double K = tot[Q_K], V = tot[Q_V] * invP, sp = tot[kNQ];
-        rec[0] = (double)step;
-        rec[1] = K;
-        rec[2] = V;
-        rec[3] = sp;
-        rec[4] = K - sp + V;
-        const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};  // xx xy xz / yx yy yz / zx zy zz
-        for (int a = 0; a < 9; ++a) rec[5 + a] = tot[Q_VIR + map[a]] * invP;
-        for (int c = 0; c < 3; ++c) rec[14 + c] = tot[Q_MOM + c];
-        rec[17] = tot[Q_X2] * invP;
-        {  // cell volume: the reference cell scaled by lam^3 in an isothermal-isobaric run
+        const double K = tot[Q_K], V = tot[Q_V] * invP, spr = tot[kNQ];
+        double r = 0.0;
+        if (q == 0) r = (double)step;
+        else if (q == 1) r = K;
+        else if (q == 2) r = V;
+        else if (q == 3) r = spr;
+        else if (q == 4) r = K - spr + V;
+        else if (q < 14) {
+            const int a = q - 5;  // xx xy xz / yx yy yz / zx zy zz
+            const int m = (a == 0) ? 0 : (a == 4) ? 1 : (a == 8) ? 2 : (a == 1 || a == 3) ? 3 : (a == 2 || a == 6) ? 4 : 5;
+            r = tot[Q_VIR + m] * invP;
+        } else if (q < 17) r = tot[Q_MOM + q - 14];
+        else if (q == 17) r = tot[Q_X2] * invP;
+        else if (q == 20) {  // cell volume: the reference cell scaled by lam^3 in an isothermal-isobaric run
             const double l = (d.npt && d.npt[s].on) ? d.npt[s].lam : 1.0;
-            rec[20] = S.box[0] * S.box[1] * S.box[2] * l * l * l;
+            r = S.box[0] * S.box[1] * S.box[2] * l * l * l;
+        } else if (S.P == 1) {
+            // centroid-virial estimators: for one bead 3N k_B T/2 and K; ring
+            // polymers get them from the centroid kernel that follows
+            r = (q == 18) ? 1.5 * S.N * kBoltz * S.T : K;
         }
-        // centroid-virial estimators: for one bead 3N k_B T/2 and K; ring
-        // polymers get them from the centroid kernel that follows
-        if (S.P == 1) {
-            rec[18] = 1.5 * S.N * kBoltz * S.T;
-            rec[19] = K;
-        }
-        if (!isfinite(K) || !isfinite(V)) atomicOr(d.err, (unsigned)ERR_NONFINITE);
-        for (int q = 0; q < QTB_NREC; ++q) d.latest[(size_t)s * QTB_NREC + q] = rec[q];
+        if (q == 0 && (!isfinite(K) || !isfinite(V))) atomicOr(d.err, (unsigned)ERR_NONFINITE);
+        d.latest[(size_t)s * QTB_NREC + q] = r;
         if (record >= 0 && step % d.obs_stride == 0) {
-            long long r = step / d.obs_stride - 1;
-            int slot = (int)(r % d.max_records);
-            for (int q = 0; q < QTB_NREC; ++q) d.series[((size_t)slot * d.nsys + s) * QTB_NREC + q] = rec[q];
+            const long long rr = step / d.obs_stride - 1;
+            const int slot = (int)(rr % d.max_records);
+            d.series[((size_t)slot * d.nsys + s) * QTB_NREC + q] = r;
         }
     }
 }
@@ -822,14 +927,19 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
         }
     }
     fx.template group_reduce<LPA>(); fy.template group_reduce<LPA>(); fz.template group_reduce<LPA>();
+    // recorded steps: the FP64 form sums its partials in FP64; the FP32 form in
+    // float-float on the FP32 pipe (this GPU's FP64 rate is a small fraction of
+    // its FP32 rate), kc and mc being a component lane's kinetic energy and momentum
+    constexpr bool kFF = sizeof(R) == 4;
     double acc[kNQ];
 #pragma unroll
     for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+    float kc = 0.f, kl = 0.f, mc = 0.f, ml = 0.f;  // float-float (hi, lo)
     if (REC && rec) {
         en = group_sum<LPA>(en);
         w0 = group_sum<LPA>(w0); w1 = group_sum<LPA>(w1); w2 = group_sum<LPA>(w2);
         w3 = group_sum<LPA>(w3); w4 = group_sum<LPA>(w4); w5 = group_sum<LPA>(w5);
-        if (act && sub == 0) {
+        if (!kFF && act && sub == 0) {
             acc[Q_V] = 0.5 * (double)en;
             acc[Q_VIR + 0] = 0.5 * (double)w0; acc[Q_VIR + 1] = 0.5 * (double)w1;
             acc[Q_VIR + 2] = 0.5 * (double)w2; acc[Q_VIR + 3] = 0.5 * (double)w3;
@@ -856,8 +966,18 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
             }
         }
         if (REC && rec) {
-            acc[Q_K] += 0.5 * T.mass_mvv[ti] * (double)v * (double)v;
-            acc[Q_MOM + c] += T.mass[ti] * (double)v;
+            if constexpr (kFF) {
+                // m v^2 / 2 and m v to ~1e-14: v^2 = p + pe exactly, the masses float-float
+                const float vf = (float)v, p = vf * vf, pe = fmaf(vf, vf, -p);
+                const float2 hm = T.half_mvv_ff[ti], mm = T.mass_ff[ti];
+                kc = hm.x * p;
+                kl = fmaf(hm.x, p, -kc) + fmaf(hm.x, pe, hm.y * p);
+                mc = mm.x * vf;
+                ml = fmaf(mm.x, vf, -mc) + mm.y * vf;
+            } else {
+                acc[Q_K] += 0.5 * T.mass_mvv[ti] * (double)v * (double)v;
+                acc[Q_MOM + c] += T.mass[ti] * (double)v;
+            }
         }
         if (ADV) {
             // next step, one bead (the mode is the bead): B(dt/2), A(dt/2) O(dt) A(dt/2)
@@ -891,9 +1011,14 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
         }
     }
     if (REC && rec) {
+        if constexpr (kFF) {
+            cta_store_partials_ff<LPA>(act && sub == 0, en, w0, w1, w2, w3, w4, w5, kc, kl, mc, ml, red,
+                                       reinterpret_cast<float2 *>(d.part) + (size_t)u * kNQ);
+        } else {
 #pragma unroll
-        for (int q = 0; q < kNQ; ++q) acc[q] = warp_sum(acc[q]);
-        cta_store_partials(acc, red, d.part + (size_t)u * kNQ);
+            for (int q = 0; q < kNQ; ++q) acc[q] = warp_sum(acc[q]);
+            cta_store_partials(acc, red, d.part + (size_t)u * kNQ);
+        }
         // the CTA with the system's last unit reduces (partials made visible first)
         __threadfence();
         __syncthreads();
@@ -904,7 +1029,7 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
         __syncthreads();
         if (s_last) {
             __threadfence();
-            reduce_system(d, RP.sys, step, kick ? 1 : -1, rsh);
+            reduce_system<kFF>(d, RP.sys, step, kick ? 1 : -1, rsh);
             if (threadIdx.x == 0) d.done[RP.sys] = 0u;
         }
     }

@@ -49,7 +49,7 @@ struct DNpt {
     // this step: first B  v <- v e1 + (hdt/m) F g1;  A  x_ref += v a1, then v' a2;
     // closing B  v <- v e2 + (hdt/m) F g2
     double e1, g1, a1, a2, e2, g2;
-    float e1f, g1f, a1f, a2f, e2f, g2f, lamf, pad;
+    float e1f, g1f, a1f, a2f, e2f, g2f, lamf, inv_wf;  // the FP32 form's coefficients, 1/W
     int on, pending;  // barostat on; the previous step's closing half kick of the cell is due
     int pad2[2];
 };
@@ -121,6 +121,7 @@ template <class R> struct PairTabT {
     R ext_V0, ext_ia2;                // DOUBLEWELL: V0, 1/a^2
     double mass[kMaxTypes];           // u (momentum)
     double mass_mvv[kMaxTypes];       // m mvv2e (kinetic energy, FP64 accumulation)
+    float2 mass_ff[kMaxTypes], half_mvv_ff[kMaxTypes];  // m, m mvv2e / 2 as float-float (hi, lo)
     int ntypes, potential;
 };
 typedef PairTabT<double> PairTab;

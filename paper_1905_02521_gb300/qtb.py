@@ -85,6 +85,7 @@ def lib():
             "qtb_get_noise": ([vp, i, vp, C.POINTER(ll)], i),
             "qtb_get_step": ([vp, C.POINTER(ll)], i),
             "qtb_get_cell": ([vp, i, vp, C.POINTER(d)], i),
+            "qtb_set_cell": ([vp, i, vp, d], i),
             "qtb_list_rebuilds": ([vp, C.POINTER(ll)], i),
             "qtb_rebuild_lists": ([vp], i),
             "qtb_wait_selftest": ([vp, C.POINTER(i), C.POINTER(d)], i),
@@ -349,6 +350,12 @@ def qtb_get_cell(ctx, sys):
     pe = C.c_double(0.0)
     _check(lib().qtb_get_cell(ctx, sys, box.ctypes.data, C.byref(pe)))
     return box, pe.value
+
+
+def qtb_set_cell(ctx, sys, box, p_e):
+    """Set the cell edges [3] (A, isotropic scale of the initial edges) and cell momentum (eV fs)."""
+    box = np.ascontiguousarray(box, np.float64)
+    _check(lib().qtb_set_cell(ctx, sys, box.ctypes.data, float(p_e)))
 
 
 def qtb_set_profiling(ctx, enable=True):

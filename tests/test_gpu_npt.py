@@ -224,6 +224,73 @@ def test_npt_arguments_are_checked(qtb):
     assert e.value.code == qtb.ERR_ARG
 
 
+def test_set_cell_then_state_continues_like_the_oracle(qtb, oracle):
+    # a cell and state set mid-run (edges 0.4 % larger, another cell momentum): the
+    # positions scale with the cell, and the FP64 run from there follows the oracle
+    # started from the same cell, state and step for 40 steps
+    s, pot = W.mgo_system(2, 300.0, gamma=2e-3)
+    N = len(s["types"])
+    npt = {"pressure": 0.002, "mass": _cell_mass(B_MGO, np.prod(s["box"]), 200.0), "gamma": 5e-3}
+    taps = S.taps(513, 1.0, 300.0, 0.3)
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=0, seed=77, npt=npt)
+    try:
+        qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB, 513, 0.3)
+        qtb.qtb_step_n(ctx, 30)
+        x0, v0 = qtb.qtb_get_state(ctx, 0, 1, N)
+        box0, pe0 = qtb.qtb_get_cell(ctx, 0)
+        box1, pe1 = box0 * 1.004, -0.5 * pe0 + 0.01
+        qtb.qtb_set_cell(ctx, 0, box1, pe1)
+        box_g, pe_g = qtb.qtb_get_cell(ctx, 0)
+        assert np.abs(box_g / box1 - 1).max() < 1e-15 and pe_g == pe1
+        xs, vs = qtb.qtb_get_state(ctx, 0, 1, N)
+        assert np.abs(minimg(xs - x0 * 1.004, box1)).max() < 1e-12 and np.array_equal(vs, v0)
+        x1 = x0 * 1.004 + 0.01 * np.sin(np.arange(3 * N)).reshape(1, N, 3)
+        qtb.qtb_set_state(ctx, 0, x1, v0)
+        sim = oracle_sim(oracle, s, pot, 1.0, seed=77, taps=taps, npt=npt)
+        sim.set_cell(box1, pe1, 1)
+        sim.set_state(x1, v0, 30)
+        for step in range(40):
+            qtb.qtb_step_n(ctx, 1)
+            sim.step(1, record=False)
+            box_g, pe_g = qtb.qtb_get_cell(ctx, 0)
+            box_o, pe_o = sim.cell()
+            assert np.abs(box_g / box_o - 1).max() < 1e-12, (step, box_g, box_o)
+            assert pe_g == pytest.approx(pe_o, rel=1e-10, abs=1e-12)
+            xg, vg = qtb.qtb_get_state(ctx, 0, 1, N)
+            xo, vo, _, _ = sim.state()
+            assert np.abs(minimg(xg - xo, box_o)).max() < 1e-10 and rel_inf(vg, vo) < 1e-10
+    finally:
+        qtb.qtb_destroy(ctx)
+
+
+def test_set_cell_arguments_are_checked(qtb):
+    s, pot = W.mgo_system(2, 300.0)
+    npt = {"pressure": 0.0, "mass": _cell_mass(B_MGO, np.prod(s["box"]), 200.0), "gamma": 5e-3}
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=1, npt=npt)
+    try:
+        box = np.asarray(s["box"], np.float64)
+        for bad_box, bad_pe in ((box * [1.0, 1.0, 1.01], 0.0),   # anisotropic
+                                (box * 0.85, 0.0),                # below the lists' margin
+                                (box * np.nan, 0.0), (box, np.inf)):
+            with pytest.raises(qtb.QtbError) as e:
+                qtb.qtb_set_cell(ctx, 0, bad_box, bad_pe)
+            assert e.value.code == qtb.ERR_ARG
+        with pytest.raises(qtb.QtbError) as e:
+            qtb.qtb_set_cell(ctx, 1, box, 0.0)
+        assert e.value.code == qtb.ERR_ARG
+        qtb.qtb_step_n(ctx, 5)    # the context is still usable
+        qtb.qtb_sync(ctx)
+    finally:
+        qtb.qtb_destroy(ctx)
+    c2 = gpu_ctx(qtb, [s], pot, 1.0, precision=1)
+    try:
+        with pytest.raises(qtb.QtbError) as e:   # constant volume
+            qtb.qtb_set_cell(c2, 0, s["box"], 0.0)
+        assert e.value.code == qtb.ERR_ARG
+    finally:
+        qtb.qtb_destroy(c2)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_batched_cells_match_single_runs(qtb, precision):
     # two crystals of different size and temperature in one isothermal-isobaric
