@@ -475,7 +475,10 @@ int run_steps(qtb_ctx *c, int j0, int count, bool graph)
         const int j = j0 + t, cur = j & 1;
         const bool keep = c->capturing;
         if (j % 64 != 0) c->capturing = false;
-        if (c->p.npt) launch_cell(c->d, j, cur, c->p.r_cut + c->skin, c->skin, c->mixed, c->st);  // isothermal-isobaric cells
+        // isothermal-isobaric cells: updated here before the first step of the call
+        // (fused) or of every step; in fused steps the step kernel updates them for
+        // the next step
+        if (c->p.npt && (!m.fused || t == 0)) launch_cell(c->d, j, c->mixed, c->st);
         if (!m.fused || t == 0) {
             ProfMark pm(c, KC_INTEGRATE);
             launch_integrate(c->d, m, j, cur, c->st);
@@ -1047,7 +1050,9 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         }
     }
     m.nm_big = nm_big;
-    m.fused = (c->pair && !p->npt) ? 1 : 0;  // the cell needs each step's reduced virial between steps
+    // one-bead pair systems fuse the next step's first half into the step kernel
+    // (with cells, behind a grid barrier after the cells' updates)
+    m.fused = c->pair ? 1 : 0;
     for (int s = 0; s < n_sys; ++s)
         if (c->hs[s].P != 1) m.fused = 0;
     if (integrate_prepare(m) != cudaSuccess)
@@ -1169,6 +1174,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
             C.e1f = C.g1f = C.e2f = C.g2f = C.lamf = 1.0f;
             C.a1f = C.a2f = (float)(0.5 * p->dt);
             C.inv_wf = (float)(1.0 / p->cell_mass);
+            C.rb_tol = 0.25 * c->skin / (p->r_cut + c->skin);
             C.on = 1;
         }
         d.npt = upload(c, cells);

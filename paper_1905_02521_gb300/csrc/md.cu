@@ -385,116 +385,24 @@ void launch_refresh_check(const Dev &d, const MdLaunch &m, int cur, cudaStream_t
 }
 
 // ---------------------------------------------------------------------------
-// Isothermal-isobaric cells (Sec. 2.1, refs [11, 12]; the equations are those of
-// qtb_params::npt): one thread per system, at the start of step j (block clock
-// b, absolute step n = 256 b + j), from the kinetic energy and virial that the
-// previous step's force launch reduced into the latest record:
-//   B_e(dt/2) (the previous step's closing half, when due) and B_e(dt/2):
-//       p_e += dt/2 (2 alpha K + W_vir - 3 V P_ext), twice;
-//   the particles' first B(dt/2) factors for v_e = p_e / W: e1 = exp(-x),
-//       g1 = (1 - e^{-x})/x, x = alpha v_e dt/2;
-//   A(dt/2): lam <- lam e^{y}, y = v_e dt/2; the particles' drift in the
-//       reference cell a1 = dt/2 (e^y - 1)/y / lam_new;
-//   O(dt) of the cell: p_e <- ce p_e + sqrt((1 - ce^2) W k_B T) xi,
-//       xi from Philox stream 1, dof 0, step n;
-//   A(dt/2) with the new v_e (a2, lam), and the closing B(dt/2) factors e2, g2.
-// A list rebuild is requested for this step's force launch when the cell scale
-// has moved by more than skin/4 over the list radius since the system's last
-// rebuild; a cell below kCellMinScale raises ERR_CELL.
-// FP32 form: the transcendental factors in FP32 (this GPU's FP64 rate is a small
-// fraction of its FP32 rate and the kernel is one thread's dependent chain); the
-// cell momentum, G and lam stay FP64, lam advanced as lam + lam (e^y - 1).
-__device__ __forceinline__ double xm1_over_x(double x) { return x != 0.0 ? expm1(x) / x : 1.0; }
-__device__ __forceinline__ float xm1_over_xf(float x)
-{
-    // (e^x - 1)/x: Taylor to x^3 near 0 (the next term is below 1e-14 for |x| < 1e-3)
-    return fabsf(x) < 1e-3f ? fmaf(x, fmaf(x, fmaf(x, 1.0f / 24.0f, 1.0f / 6.0f), 0.5f), 1.0f) : expm1f(x) / x;
-}
-
+// Isothermal-isobaric cells: the update of each system's cell at the start of
+// step j (cell_update), one thread per system.  Launched before the first step
+// of each call; the steps after it get theirs from the step kernel that
+// precedes them.
 template <bool F32>
-__global__ void k_cell(Dev d, int j, int cur, double r_list, double skin)
+__global__ void k_cell(Dev d, int j)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= d.nsys || !d.npt) return;
-    DNpt C = d.npt[s];
-    if (!C.on) return;
-    const DSys &S = d.sys[s];
-    const double *rec = d.latest + (size_t)s * QTB_NREC;
-    const double K = rec[1], Wv = rec[5] + rec[9] + rec[13];
-    const double V = S.box[0] * S.box[1] * S.box[2] * C.lam * C.lam * C.lam;
-    const double G = 2.0 * C.alpha * K + Wv - 3.0 * V * C.pext;
-    const double h = 0.5 * d.dt;
-    if (C.pending) C.peps += h * G;
-    C.peps += h * G;
-    // the cell's random force: Philox stream 1, dof 0, step n
-    const long long n = d.clock[0] * kBlockSteps + j;
-    const long long q = (n >= 0) ? n / 4 : -((-n + 3) / 4);
-    const unsigned long long uq = (unsigned long long)q;
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)uq, 0u, 1u, (uint32_t)(uq >> 32)), (uint32_t)d.seed,
-                                  (uint32_t)(d.seed >> 32) ^ (uint32_t)s);
-    const int e = (int)(n - 4 * q);
-    const uint32_t wa = (e < 2) ? w.x : w.z, wb = (e < 2) ? w.y : w.w;
-    double lam;
-    if constexpr (F32) {
-        const float hf = (float)h, af = (float)C.alpha;
-        float ve = (float)C.peps * C.inv_wf;
-        float x = af * ve * hf, y = ve * hf;
-        C.e1f = expf(-x);
-        C.g1f = xm1_over_xf(-x);
-        lam = fma(C.lam, (double)expm1f(y), C.lam);
-        C.a1f = hf * xm1_over_xf(y) / (float)lam;
-        const float u1 = ((float)wa + 1.0f) * 2.3283064365386963e-10f, u2 = (float)wb * 2.3283064365386963e-10f;
-        float sn, cs;
-        sincospif(2.0f * u2, &sn, &cs);
-        const float xi = sqrtf(-2.0f * logf(u1)) * ((e & 1) ? sn : cs);
-        C.peps = fma(C.ce, C.peps, C.sige * (double)xi);
-        ve = (float)C.peps * C.inv_wf;
-        x = af * ve * hf;
-        y = ve * hf;
-        lam = fma(lam, (double)expm1f(y), lam);
-        C.a2f = hf * xm1_over_xf(y) / (float)lam;
-        C.e2f = expf(-x);
-        C.g2f = xm1_over_xf(-x);
-        C.lamf = (float)lam;  // (the FP32 kernels read only the float coefficients)
-    } else {
-        double ve = C.peps / C.W;
-        double x = C.alpha * ve * h;
-        C.e1 = exp(-x);
-        C.g1 = xm1_over_x(-x);
-        double y = ve * h;
-        lam = C.lam * exp(y);
-        C.a1 = h * xm1_over_x(y) / lam;
-        const double u1 = ((double)wa + 1.0) * 2.3283064365386963e-10, u2 = (double)wb * 2.3283064365386963e-10;
-        double sn, cs;
-        sincospi(2.0 * u2, &sn, &cs);
-        const double xi = sqrt(-2.0 * log(u1)) * ((e & 1) ? sn : cs);
-        C.peps = C.ce * C.peps + C.sige * xi;
-        ve = C.peps / C.W;
-        y = ve * h;
-        lam = lam * exp(y);
-        C.a2 = h * xm1_over_x(y) / lam;
-        x = C.alpha * ve * h;
-        C.e2 = exp(-x);
-        C.g2 = xm1_over_x(-x);
-        C.e1f = (float)C.e1; C.g1f = (float)C.g1; C.a1f = (float)C.a1; C.a2f = (float)C.a2;
-        C.e2f = (float)C.e2; C.g2f = (float)C.g2; C.lamf = (float)lam;
-    }
-    C.lam = lam;
-    C.pending = 1;
-    d.npt[s] = C;
-    if (!(lam >= kCellMinScale) || !isfinite(lam)) atomicOr(d.err, (unsigned)ERR_CELL);
-    if (fabs(lam - C.lam_rb) * r_list > 0.25 * skin * C.lam_rb) {
-        atomicOr(&d.rflag[cur * d.nsys + s], 1u);
-        atomicOr(&d.flag[cur], 1u);
-    }
+    if (s >= d.nsys || !d.npt || !d.npt[s].on) return;
+    cell_update<F32>(d, s, d.clock[0] * kBlockSteps + j, j & 1);
 }
 
-void launch_cell(const Dev &d, int j, int cur, double r_list, double skin, bool fp32, cudaStream_t st)
+void launch_cell(const Dev &d, int j, bool fp32, cudaStream_t st)
 {
     if (fp32)
-        k_cell<true><<<(d.nsys + 127) / 128, 128, 0, st>>>(d, j, cur, r_list, skin);
+        k_cell<true><<<(d.nsys + 127) / 128, 128, 0, st>>>(d, j);
     else
-        k_cell<false><<<(d.nsys + 127) / 128, 128, 0, st>>>(d, j, cur, r_list, skin);
+        k_cell<false><<<(d.nsys + 127) / 128, 128, 0, st>>>(d, j);
 }
 
 // Self-test of the bounded waits: one thread waits on words[0], which nothing

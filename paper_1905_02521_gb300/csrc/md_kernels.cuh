@@ -783,6 +783,107 @@ static __device__ void reduce_system(const Dev &d, int s, long long step, int re
     }
 }
 
+// Isothermal-isobaric cells (Sec. 2.1, refs [11, 12]; the equations are those of
+// qtb_params::npt): the update of system s's cell at the start of absolute step
+// n (step j = n mod 256 of its block, positions in pos[cur], cur = j & 1), by one
+// thread, from the kinetic energy and virial that the previous step's force
+// launch reduced into the latest record:
+//   B_e(dt/2) (the previous step's closing half, when due) and B_e(dt/2):
+//       p_e += dt/2 (2 alpha K + W_vir - 3 V P_ext), twice;
+//   the particles' first B(dt/2) factors for v_e = p_e / W: e1 = exp(-x),
+//       g1 = (1 - e^{-x})/x, x = alpha v_e dt/2;
+//   A(dt/2): lam <- lam e^{y}, y = v_e dt/2; the particles' drift in the
+//       reference cell a1 = dt/2 (e^y - 1)/y / lam_new;
+//   O(dt) of the cell: p_e <- ce p_e + sqrt((1 - ce^2) W k_B T) xi,
+//       xi from Philox stream 1, dof 0, step n;
+//   A(dt/2) with the new v_e (a2, lam), and the closing B(dt/2) factors e2, g2.
+// A list rebuild is requested for this step's force launch when the cell scale
+// has moved by more than skin/4 over the list radius since the system's last
+// rebuild; a cell below kCellMinScale raises ERR_CELL.
+// FP32 form: the transcendental factors in FP32 (this GPU's FP64 rate is a small
+// fraction of its FP32 rate and the kernel is one thread's dependent chain); the
+// cell momentum, G and lam stay FP64, lam advanced as lam + lam (e^y - 1).
+__device__ __forceinline__ double xm1_over_x(double x) { return x != 0.0 ? expm1(x) / x : 1.0; }
+__device__ __forceinline__ float xm1_over_xf(float x)
+{
+    // (e^x - 1)/x: Taylor to x^3 near 0 (the next term is below 1e-14 for |x| < 1e-3)
+    return fabsf(x) < 1e-3f ? fmaf(x, fmaf(x, fmaf(x, 1.0f / 24.0f, 1.0f / 6.0f), 0.5f), 1.0f) : expm1f(x) / x;
+}
+
+template <bool F32>
+__device__ void cell_update(const Dev &d, int s, long long n, int cur)
+{
+    DNpt C = d.npt[s];
+    const DSys &S = d.sys[s];
+    const double *rec = d.latest + (size_t)s * QTB_NREC;
+    const double K = rec[1], Wv = rec[5] + rec[9] + rec[13];
+    const double V = S.box[0] * S.box[1] * S.box[2] * C.lam * C.lam * C.lam;
+    const double G = 2.0 * C.alpha * K + Wv - 3.0 * V * C.pext;
+    const double h = 0.5 * d.dt;
+    if (C.pending) C.peps += h * G;
+    C.peps += h * G;
+    // the cell's random force: Philox stream 1, dof 0, step n
+    const long long q = (n >= 0) ? n / 4 : -((-n + 3) / 4);
+    const unsigned long long uq = (unsigned long long)q;
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)uq, 0u, 1u, (uint32_t)(uq >> 32)), (uint32_t)d.seed,
+                                  (uint32_t)(d.seed >> 32) ^ (uint32_t)s);
+    const int e = (int)(n - 4 * q);
+    const uint32_t wa = (e < 2) ? w.x : w.z, wb = (e < 2) ? w.y : w.w;
+    double lam;
+    if constexpr (F32) {
+        const float hf = (float)h, af = (float)C.alpha;
+        float ve = (float)C.peps * C.inv_wf;
+        float x = af * ve * hf, y = ve * hf;
+        C.e1f = expf(-x);
+        C.g1f = xm1_over_xf(-x);
+        lam = fma(C.lam, (double)expm1f(y), C.lam);
+        C.a1f = hf * xm1_over_xf(y) / (float)lam;
+        const float u1 = ((float)wa + 1.0f) * 2.3283064365386963e-10f, u2 = (float)wb * 2.3283064365386963e-10f;
+        float sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        const float xi = sqrtf(-2.0f * logf(u1)) * ((e & 1) ? sn : cs);
+        C.peps = fma(C.ce, C.peps, C.sige * (double)xi);
+        ve = (float)C.peps * C.inv_wf;
+        x = af * ve * hf;
+        y = ve * hf;
+        lam = fma(lam, (double)expm1f(y), lam);
+        C.a2f = hf * xm1_over_xf(y) / (float)lam;
+        C.e2f = expf(-x);
+        C.g2f = xm1_over_xf(-x);
+        C.lamf = (float)lam;  // (the FP32 kernels read only the float coefficients)
+    } else {
+        double ve = C.peps / C.W;
+        double x = C.alpha * ve * h;
+        C.e1 = exp(-x);
+        C.g1 = xm1_over_x(-x);
+        double y = ve * h;
+        lam = C.lam * exp(y);
+        C.a1 = h * xm1_over_x(y) / lam;
+        const double u1 = ((double)wa + 1.0) * 2.3283064365386963e-10, u2 = (double)wb * 2.3283064365386963e-10;
+        double sn, cs;
+        sincospi(2.0 * u2, &sn, &cs);
+        const double xi = sqrt(-2.0 * log(u1)) * ((e & 1) ? sn : cs);
+        C.peps = C.ce * C.peps + C.sige * xi;
+        ve = C.peps / C.W;
+        y = ve * h;
+        lam = lam * exp(y);
+        C.a2 = h * xm1_over_x(y) / lam;
+        x = C.alpha * ve * h;
+        C.e2 = exp(-x);
+        C.g2 = xm1_over_x(-x);
+        C.e1f = (float)C.e1; C.g1f = (float)C.g1; C.a1f = (float)C.a1; C.a2f = (float)C.a2;
+        C.e2f = (float)C.e2; C.g2f = (float)C.g2; C.lamf = (float)lam;
+    }
+    C.lam = lam;
+    C.pending = 1;
+    d.npt[s] = C;
+    if (!(lam >= kCellMinScale) || !isfinite(lam)) atomicOr(d.err, (unsigned)ERR_CELL);
+    if (fabs(lam - C.lam_rb) > C.rb_tol * C.lam_rb) {
+        atomicOr(&d.rflag[cur * d.nsys + s], 1u);
+        atomicOr(&d.flag[cur], 1u);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Pair force from the neighbour lists: LPA lanes per home bead-atom
 // (32 / LPA bead-atoms per warp), each lane strides through the list with two
@@ -979,8 +1080,9 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
                 acc[Q_MOM + c] += T.mass[ti] * (double)v;
             }
         }
-        if (ADV) {
+        if (ADV && !NC) {
             // next step, one bead (the mode is the bead): B(dt/2), A(dt/2) O(dt) A(dt/2)
+            // (with a cell, after the cell's update: npt_next_half)
             const R *rot = reinterpret_cast<const R *>(d.rot) + 3 * S.rot0;
             const R cs = rot[0], sw = rot[1], ws = rot[2];
             const R sig = reinterpret_cast<const R *>(d.osig)[RP.sys * kMaxTypes + ti];
@@ -1031,6 +1133,75 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
             __threadfence();
             reduce_system<kFF>(d, RP.sys, step, kick ? 1 : -1, rsh);
             if (threadIdx.x == 0) d.done[RP.sys] = 0u;
+            if (ADV && NC && kick) {
+                // the cell's update for the next step, from the record just formed
+                __syncthreads();
+                if (threadIdx.x == 0) cell_update<kFF>(d, RP.sys, step, cur ^ 1);
+            }
+        }
+    }
+}
+
+// Isothermal-isobaric runs (one bead per atom), fused steps: the first half of
+// the next step, B(dt/2) A(dt/2) O(dt) A(dt/2) with the coefficients of the
+// cell's update, for the bead-atoms of this CTA's force units, after the grid
+// barrier that follows that update.  The arithmetic is the one-bead cell branch
+// of k_integrate's, operation for operation, so that a fused step gives the
+// same bits as an integrator launch would.  j1 is the next step (its noise row),
+// nxt its position buffer.
+template <int PM, class R, int LPA>
+__device__ void npt_next_half(const Dev &d, int j1, int nxt)
+{
+    typedef typename PosT<PM, R>::S PS;
+    constexpr int NA = list_atoms(LPA);
+    __shared__ R sdd[3 * NA];
+    const size_t G = (size_t)d.G;
+    for (int u = blockIdx.x; u < d.nunits; u += gridDim.x) {
+        const DRep RP = d.rep[d.lcta_rep[u]];
+        const int s = RP.sys;
+        const DSys &S = d.sys[s];
+        const DNpt *NC = d.npt + s;
+        const int t = threadIdx.x, k = t / 3, c = t - 3 * k;
+        const int i = (u - RP.fcta0) * NA + k;
+        const bool act = t < 3 * NA && i < RP.N;
+        R dd = 0;
+        if (act) {
+            const size_t gi = RP.g0 + i, o = (size_t)c * G + gi;
+            R *V = reinterpret_cast<R *>(d.v);
+            const R *F = reinterpret_cast<const R *>(d.f);
+            PS *X = reinterpret_cast<PS *>(d.x);
+            const int ty = d.typ[S.g0 + i];
+            const R hdtm = reinterpret_cast<const R *>(d.hdt_m)[ty];
+            const R sig = reinterpret_cast<const R *>(d.osig)[s * kMaxTypes + ty];
+            const R c1 = sizeof(R) == 4 ? (R)S.c1_f : (R)S.c1;
+            const R e1 = sizeof(R) == 4 ? (R)NC->e1f : (R)NC->e1, g1 = sizeof(R) == 4 ? (R)NC->g1f : (R)NC->g1;
+            const R a1 = sizeof(R) == 4 ? (R)NC->a1f : (R)NC->a1, a2 = sizeof(R) == 4 ? (R)NC->a2f : (R)NC->a2;
+            const R eta = reinterpret_cast<const R *>(d.eta)[eta_row(d, j1) * d.Dtot + S.dof0 + (size_t)c * S.N + i];
+            R pk = fma(V[o], e1, (hdtm * F[o]) * g1);
+            R disp = pk * a1;
+            pk = fma(c1, pk, sig * eta);
+            disp = fma(pk, a2, disp);
+            V[o] = pk;
+            const float fsc = S.fix_scale[c];
+            const PS xn = PosT<PM, R>::add(X[o], disp, S.box[c], fsc, S.fix_inv[c]);
+            X[o] = xn;
+            reinterpret_cast<PS *>(d.pos[nxt])[4 * gi + c] = xn;
+            const R dc = PosT<PM, R>::diff(xn, reinterpret_cast<const PS *>(d.xref)[o], fsc);
+            dd = dc * dc;
+        }
+        if (t < 3 * NA) sdd[t] = dd;
+        __syncthreads();
+        // the physical displacement (lam times the reference one) against (3/8 skin)^2
+        bool moved = false;
+        if (act && c == 0) {
+            const R tot = sdd[t] + sdd[t + 1] + sdd[t + 2];
+            const R l = sizeof(R) == 4 ? (R)NC->lamf : (R)NC->lam;
+            const R lim = (sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2) * R(0.5625) / (l * l);
+            moved = tot > lim;
+        }
+        if (__syncthreads_or(moved) && threadIdx.x == 0) {
+            atomicOr(&d.rflag[nxt * d.nsys + s], 1u);
+            atomicOr(&d.flag[nxt], 1u);
         }
     }
 }
@@ -1044,8 +1215,12 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
 // (72 registers, no spills; 1064 resident CTAs hold the 1000 units of an
 // 8000-ion crystal in one wave): 5 % faster there than 8 CTAs at 64 registers,
 // no slower on larger systems; six or eight entries in flight per lane spill.
+// The recording variants (energy and virial as well) take 4 CTAs per SM and
+// spill nothing: 10 % faster per step on an isothermal-isobaric run, which
+// records every step, and no slower on the 8000-ion crystal's recorded step.
 template <int PM, class R, int ADV, int REC, int LPA, int MI>
-__global__ void __launch_bounds__(32 * kListWarps, sizeof(R) == 4 ? 7 : 4) k_step(Dev d, PairTabT<R> T, int kick, int j, int cur)
+__global__ void __launch_bounds__(32 * kListWarps, sizeof(R) == 4 ? (REC ? 4 : 7) : 4)
+    k_step(Dev d, PairTabT<R> T, int kick, int j, int cur)
 {
     extern __shared__ __align__(32) unsigned char fsm[];
     __shared__ BuildSmem B;
@@ -1087,6 +1262,14 @@ __global__ void __launch_bounds__(32 * kListWarps, sizeof(R) == 4 ? 7 : 4) k_ste
     release_next_step();
     for (int u = blockIdx.x; u < d.nunits; u += gridDim.x)
         force_unit<PM, R, ADV, REC, LPA, MI>(d, T, ptab, kick, j, cur, u, red, rsh, s_last);
+    if constexpr (ADV && REC) {
+        // isothermal-isobaric cells: the next step's first half waits for the
+        // cells' updates (made by each system's last CTA) behind a grid barrier
+        if (d.npt && kick) {
+            grid_barrier(d);
+            npt_next_half<PM, R, LPA>(d, j + 1, cur ^ 1);
+        }
+    }
 }
 
 template <int PM, class R, int ADV, int REC, int LPA, int MI>

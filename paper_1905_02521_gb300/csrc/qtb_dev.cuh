@@ -52,6 +52,7 @@ struct DNpt {
     float e1f, g1f, a1f, a2f, e2f, g2f, lamf, inv_wf;  // the FP32 form's coefficients, 1/W
     int on, pending;  // barostat on; the previous step's closing half kick of the cell is due
     int pad2[2];
+    double rb_tol;    // list rebuild when |lam - lam_rb| > rb_tol lam_rb (skin/4 over the list radius)
 };
 
 // Neighbour-list entry (32 bits): replica-local index j in bits 0..25, the

@@ -110,7 +110,7 @@ void launch_store_state(const Dev &d, const MdLaunch &m, int s, long long n3, in
 // systems with a bead-atom more than skin/2 from its position at the last rebuild
 void launch_refresh_check(const Dev &d, const MdLaunch &m, int cur, cudaStream_t st);
 // isothermal-isobaric cells: update at the start of step j (see md.cu)
-void launch_cell(const Dev &d, int j, int cur, double r_list, double skin, bool fp32, cudaStream_t st);
+void launch_cell(const Dev &d, int j, bool fp32, cudaStream_t st);
 // words[0]: a flag nothing sets; words[1]: set to 1 when the bounded wait gives up
 void launch_wait_selftest(unsigned *words, cudaStream_t st);
 void launch_tick(const Dev &d, cudaStream_t st);

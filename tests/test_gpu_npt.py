@@ -77,6 +77,57 @@ def test_fp64_npt_trajectory_matches_oracle(qtb, oracle):
         qtb.qtb_destroy(ctx)
 
 
+def test_fp64_npt_fused_steps_match_oracle(qtb, oracle):
+    # 300 steps in one call (a CUDA-graph block of 256 and 44 direct steps): every
+    # step but the last of a call updates the cell inside the step kernel and
+    # runs the next step's first half there; the oracle steps one at a time
+    s, pot = W.mgo_system(2, 300.0, gamma=2e-3)
+    N = len(s["types"])
+    npt = {"pressure": 0.001, "mass": _cell_mass(B_MGO, np.prod(s["box"]), 200.0), "gamma": 5e-3}
+    taps = S.taps(513, 1.0, 300.0, 0.3)
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=0, seed=4242, npt=npt)
+    try:
+        qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB, 513, 0.3)
+        sim = oracle_sim(oracle, s, pot, 1.0, seed=4242, taps=taps, npt=npt)
+        qtb.qtb_step_n(ctx, 300)
+        sim.step(300, record=False)
+        box_g, pe_g = qtb.qtb_get_cell(ctx, 0)
+        box_o, pe_o = sim.cell()
+        assert np.abs(box_g / box_o - 1).max() < 1e-11
+        assert pe_g == pytest.approx(pe_o, rel=1e-9, abs=1e-12)
+        xg, vg = qtb.qtb_get_state(ctx, 0, 1, N)
+        xo, vo, _, _ = sim.state()
+        assert np.abs(minimg(xg - xo, box_o)).max() < 1e-9 and rel_inf(vg, vo) < 1e-9
+        assert abs(box_o[0] / s["box"][0] - 1) > 2e-3   # the cell did move
+    finally:
+        qtb.qtb_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fused_npt_steps_equal_single_steps(qtb, precision):
+    # the fused step (cell update and the next step's first half in the step
+    # kernel) does the arithmetic of the cell kernel and integrator launches that
+    # single-step calls make: the two runs agree bit for bit, lists rebuilt alike
+    s, pot = W.lih_system(3, 50.0, gamma=1e-3)
+    N = len(s["types"])
+    npt = {"pressure": 0.0, "mass": _cell_mass(1.0, np.prod(s["box"]), 300.0), "gamma": 4e-3}
+    out = []
+    for calls in ([300], [1] * 300):
+        ctx = gpu_ctx(qtb, [s], pot, 0.25, precision=precision, filter_prec=1, seed=8, npt=npt)
+        try:
+            qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB, 1025, 0.6)
+            for n in calls:
+                qtb.qtb_step_n(ctx, n)
+            out.append((qtb.qtb_get_state(ctx, 0, 1, N), qtb.qtb_get_cell(ctx, 0), qtb.qtb_list_rebuilds(ctx)))
+        finally:
+            qtb.qtb_destroy(ctx)
+    (xa, va), (ba, pa), ra = out[0]
+    (xb, vb), (bb, pb), rb = out[1]
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert np.array_equal(ba, bb) and pa == pb
+    assert ra == rb and ra > 0
+
+
 def test_mixed_npt_single_step_matches_oracle_step(qtb, oracle):
     s, pot = W.mgo_system(2, 300.0, gamma=2e-3)
     N = len(s["types"])
