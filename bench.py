@@ -414,7 +414,8 @@ def run_ours(args):
         # step per distinct bead count), 256 step launches (a list rebuild runs inside the
         # step launch that needs it), the centroid estimators of the recorded step (ring
         # polymers), the block clock
-        "gpu_launches": 2 + integ + BLOCK + cen + 1,
+        # (+ the cell kernel before each block's first step at constant pressure)
+        "gpu_launches": 2 + integ + BLOCK + cen + 1 + (1 if npt else 0),
         "list_rebuilds_per_bench_step": rebuilds,
         "wall_s": wall,
         "observables": {"K_eV": float(obs[1]), "V_eV": float(obs[2]), "step": int(obs[0])},
