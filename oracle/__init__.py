@@ -27,7 +27,7 @@ from . import spectra  # noqa: F401
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qtb_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libqtb_oracle.so")
-NREC = 21
+NREC = 23
 
 POT_PAIR, POT_HARMONIC, POT_DOUBLEWELL = 0, 1, 2
 
@@ -149,7 +149,7 @@ class Sim:
     ``pos``/``vel`` are [P, N, 3]; ``taps`` (h_0..h_K) selects coloured noise,
     ``None`` white Langevin noise at temperature T.  ``npt`` = dict(pressure
     (eV/A^3), mass (eV fs^2), gamma (1/fs)) makes the run isothermal-isobaric
-    (one bead, pair potential; see qtb_oracle.c).
+    (pair potential; ring polymers through their centroids; see qtb_oracle.c).
     """
 
     def __init__(self, pos, vel, types, pot, box, T, gamma, dt, seed, sys=0, taps=None,
@@ -189,7 +189,7 @@ class Sim:
             p.K = len(taps) - 1
             p.h = keep["h"].ctypes.data
         if npt is not None:
-            assert P == 1 and potential == POT_PAIR
+            assert potential == POT_PAIR
             p.npt = 1
             p.pext, p.wmass, p.gamma_e = float(npt["pressure"]), float(npt["mass"]), float(npt["gamma"])
         self.N, self.P = N, P

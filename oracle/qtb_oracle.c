@@ -41,8 +41,19 @@
  *       G = 2 alpha K + Wvir - 3 V P_ext,  alpha = 1 + 3/N_f,  N_f = 3N,
  *     Wvir = sum over pairs of r_ij . F_ij; split as B_e(dt/2) B(dt/2) A(dt/2)
  *     O(dt) A(dt/2) force B(dt/2) B_e(dt/2), each B and A the exact solution of
- *     its linear equation; the cell's random force is Philox stream 1, dof 0
- *     (one bead only).  Stationary law: P(V) ~ V^N exp(-(U + P_ext V)/k_B T).
+ *     its linear equation; the cell's random force is Philox stream 1, dof 0.
+ *     Stationary law: P(V) ~ V^N exp(-(U + P_ext V)/k_B T).
+ *     Ring polymers (P > 1): the cell acts on each atom's centroid mode only
+ *     (the internal modes, physical bead offsets from the centroid, do not
+ *     scale with it), so the equations above hold for the centroid modes
+ *     Q_0 = sqrt(P) rbar with K -> K_0, the centroid modes' kinetic energy, and
+ *     Wvir -> W_cv = sum_i rbar_i . F_i = (1/P) sum_s Wvir_s - sum_i sum_s
+ *     (r_i,s - rbar_i) . f_i,s (f = -(1/P) grad V, Eq. 4), the virial of a
+ *     scaling of the centroids at fixed offsets; N_f = 3N.  B and the O of the
+ *     modes as in the constant-volume step, the centroid's B and A with the
+ *     cell's friction and drift factors.  Stationary law: the ring polymer's
+ *     isothermal-isobaric distribution (for an ideal gas again V^N
+ *     exp(-P_ext V / k_B T)).
  *
  * Units: A, fs, eV, u, e, K.
  */
@@ -57,7 +68,7 @@
 #define ORA_KE 14.3996454784            /* e^2/(4 pi eps0) in eV A         */
 #define ORA_PI 3.14159265358979323846
 
-#define ORA_NREC 21
+#define ORA_NREC 23
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10, from its published definition: 10 rounds of
@@ -483,10 +494,15 @@ static void observe(ora_sim *s, double *rec)
     }
     rec[18] = 1.5 * N * ORA_KB * s->p.T - 0.5 * cv;
     rec[19] = K0 - 0.5 * cv;
+    /* the centroid modes' kinetic energy and the centroid virial (trace): the
+     * cell's generalised force of an isothermal-isobaric run (for one bead K
+     * and the virial trace) */
+    rec[21] = K0;
+    rec[22] = (s->vir[0] + s->vir[4] + s->vir[8]) - cv;
 }
 
 /* ------------------------------------------------------------------------ */
-/* Isothermal-isobaric step (one bead, pair potential): the equations and the
+/* Isothermal-isobaric step (one bead, pair potential; ring polymers below): the equations and the
  * splitting are in the header comment.  Positions are physical (A); the cell
  * edges scale by exp(v_e t).                                                   */
 static double kinetic(const ora_sim *s)
@@ -571,11 +587,149 @@ static void step_npt(ora_sim *s, double *rec1)
     free(eta);
 }
 
+/* Ring polymers at constant pressure: K_0 and sum_i sum_s (r_i,s - rbar_i) .
+ * f_i,s, bead offsets by minimum image about bead 0 (as in observe). */
+static void centroid_terms(const ora_sim *s, double *K0_out, double *cv_out)
+{
+    int N = s->p.N, P = s->p.P;
+    double cv = 0.0, K0 = 0.0;
+    for (int i = 0; i < N; ++i) {
+        double m = s->mass_t[s->type[i]];
+        for (int c = 0; c < 3; ++c) {
+            double L = s->p.box[c];
+            double x0 = s->x[(size_t)i * 3 + c];
+            double dbar = 0.0, vs = 0.0;
+            for (int b = 0; b < P; ++b) {
+                double d = s->x[((size_t)b * N + i) * 3 + c] - x0;
+                d -= L * round(d / L);
+                dbar += d;
+                vs += s->v[((size_t)b * N + i) * 3 + c];
+            }
+            dbar /= P;
+            for (int b = 0; b < P; ++b) {
+                double d = s->x[((size_t)b * N + i) * 3 + c] - x0;
+                d -= L * round(d / L);
+                cv += (d - dbar) * s->f[((size_t)b * N + i) * 3 + c];
+            }
+            K0 += 0.5 * m * ORA_MVV2E * vs * vs / P;
+        }
+    }
+    *K0_out = K0;
+    *cv_out = cv;
+}
+
+/* modes of one atom-component: out[k] = sum_b C[b][k] a[b, i, c] */
+static void to_modes(const ora_sim *s, const double *a, int i, int c, double *out)
+{
+    int N = s->p.N, P = s->p.P;
+    for (int k = 0; k < P; ++k) {
+        double acc = 0.0;
+        for (int b = 0; b < P; ++b) acc += s->C[b * P + k] * a[((size_t)b * N + i) * 3 + c];
+        out[k] = acc;
+    }
+}
+
+static void to_beads(const ora_sim *s, const double *m, int i, int c, double *a)
+{
+    int N = s->p.N, P = s->p.P;
+    for (int b = 0; b < P; ++b) {
+        double acc = 0.0;
+        for (int k = 0; k < P; ++k) acc += s->C[b * P + k] * m[k];
+        a[((size_t)b * N + i) * 3 + c] = acc;
+    }
+}
+
+/* The ring-polymer isothermal-isobaric step (P > 1; equations in the header
+ * comment).  Positions are physical and unwrapped; the centroid mode Q_0 drifts
+ * as dQ_0/dt = p_0 + v_e Q_0, the internal modes rotate freely. */
+static void step_npt_rp(ora_sim *s, double *rec1)
+{
+    int N = s->p.N, P = s->p.P, D = 3 * N * P;
+    double dt = s->p.dt, h = 0.5 * dt;
+    double c1 = exp(-s->p.gamma * dt), ce = exp(-s->p.gamma_e * dt);
+    double alpha = 1.0 + 3.0 / (3.0 * N);
+    double W = s->p.wmass;
+    double *eta = dup(NULL, (size_t)D), *q = dup(NULL, (size_t)P), *pm = dup(NULL, (size_t)P),
+           *fk = dup(NULL, (size_t)P);
+    int64_t n = s->step;
+    noise_at(s, n, eta);
+    /* B_e(dt/2) twice (the first closes the previous step), from K_0 and W_cv */
+    double K0, cv;
+    centroid_terms(s, &K0, &cv);
+    double Vol = s->p.box[0] * s->p.box[1] * s->p.box[2];
+    double G = 2.0 * alpha * K0 + ((s->vir[0] + s->vir[4] + s->vir[8]) - cv) - 3.0 * Vol * s->p.pext;
+    if (s->pending) s->peps += h * G;
+    s->peps += h * G;
+    double ve1 = s->peps / W;
+    /* O of the cell (between the two A halves; independent of the particles) */
+    double xi = ora_white(s->p.seed, s->p.sys, 0u, 1u, n);
+    double peps2 = ce * s->peps + sqrt((1.0 - ce * ce) * W * ORA_KB * s->p.T) * xi;
+    double ve2 = peps2 / W;
+    double x1 = alpha * ve1 * h, e1 = exp(-x1), g1 = (x1 != 0.0) ? -expm1(-x1) / x1 : 1.0;
+    double y1 = ve1 * h, ey1 = exp(y1), gy1 = (y1 != 0.0) ? expm1(y1) / y1 : 1.0;
+    double y2 = ve2 * h, ey2 = exp(y2), gy2 = (y2 != 0.0) ? expm1(y2) / y2 : 1.0;
+    for (int i = 0; i < N; ++i) {
+        double m = s->mass_t[s->type[i]] * ORA_MVV2E;
+        double sig = sqrt((1.0 - c1 * c1) / m);
+        for (int c = 0; c < 3; ++c) {
+            to_modes(s, s->x, i, c, q);
+            to_modes(s, s->v, i, c, pm);
+            to_modes(s, s->f, i, c, fk);
+            /* B(dt/2): the centroid with the cell's friction */
+            pm[0] = pm[0] * e1 + h * fk[0] / m * g1;
+            for (int k = 1; k < P; ++k) pm[k] += h * fk[k] / m;
+            for (int half = 0; half < 2; ++half) {
+                /* A(dt/2): centroid drift with the cell, internal modes rotate */
+                double ey = half ? ey2 : ey1, gy = half ? gy2 : gy1;
+                q[0] = q[0] * ey + pm[0] * h * gy;
+                for (int k = 1; k < P; ++k) {
+                    double w = s->wk[k];
+                    double cs = cos(h * w), sn = sin(h * w);
+                    double qn = q[k] * cs + pm[k] / w * sn;
+                    double pn = -q[k] * w * sn + pm[k] * cs;
+                    q[k] = qn;
+                    pm[k] = pn;
+                }
+                if (half == 0) /* O(dt), every mode */
+                    for (int k = 0; k < P; ++k) pm[k] = c1 * pm[k] + sig * eta[(size_t)(k * 3 + c) * N + i];
+            }
+            to_beads(s, q, i, c, s->x);
+            to_beads(s, pm, i, c, s->v);
+        }
+    }
+    for (int c = 0; c < 3; ++c) {
+        s->p.box[c] *= ey1;
+        s->p.box[c] *= ey2;
+    }
+    s->peps = peps2;
+    compute_forces(s);
+    /* closing B(dt/2) with the new v_e */
+    double x2 = alpha * ve2 * h, e2 = exp(-x2), g2 = (x2 != 0.0) ? -expm1(-x2) / x2 : 1.0;
+    for (int i = 0; i < N; ++i) {
+        double m = s->mass_t[s->type[i]] * ORA_MVV2E;
+        for (int c = 0; c < 3; ++c) {
+            to_modes(s, s->v, i, c, pm);
+            to_modes(s, s->f, i, c, fk);
+            pm[0] = pm[0] * e2 + h * fk[0] / m * g2;
+            for (int k = 1; k < P; ++k) pm[k] += h * fk[k] / m;
+            to_beads(s, pm, i, c, s->v);
+        }
+    }
+    s->pending = 1;
+    s->step += 1;
+    if (rec1) observe(s, rec1);
+    free(eta); free(q); free(pm); free(fk);
+}
+
 /* Advance nsteps BAOAB steps; if rec != NULL write one record per step. */
 void ora_sim_step(ora_sim *s, int64_t nsteps, double *rec)
 {
     if (s->p.npt) {
-        for (int64_t it = 0; it < nsteps; ++it) step_npt(s, rec ? rec + (size_t)it * ORA_NREC : NULL);
+        for (int64_t it = 0; it < nsteps; ++it) {
+            double *r1 = rec ? rec + (size_t)it * ORA_NREC : NULL;
+            if (s->p.P == 1) step_npt(s, r1);
+            else step_npt_rp(s, r1);
+        }
         return;
     }
     int N = s->p.N, P = s->p.P, D = 3 * N * P;
