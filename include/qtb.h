@@ -134,9 +134,13 @@ typedef struct {
      *                                 - cell_gamma p_e + R_e,   v_e = p_e / cell_mass,
      * N_f = 3N, W_vir the pair virial; R the particle random force of the chosen
      * noise (QTB: Eq. 7), R_e white at k_B T.  Stationary law:
-     * P(V) ~ V^N exp(-(U + P_ext V)/k_B T) for the white bath.  One bead and the
-     * pair potential only; the cell may shrink to 0.9 of its initial edges
-     * (QTB_ERR_STATE below that: the cell lists keep that margin). */
+     * P(V) ~ V^N exp(-(U + P_ext V)/k_B T) for the white bath.  Ring polymers
+     * (P > 1): the cell acts on each atom's centroid mode (sqrt(P) rbar) only,
+     * the bead offsets from the centroid are physical and do not scale with it;
+     * K and W_vir above become the centroid modes' kinetic energy K_0 and the
+     * centroid virial W_cv (record slots 21 and 22).  Pair potential only; the
+     * cell may shrink to 0.9 of its initial edges (QTB_ERR_STATE below that: the
+     * cell lists keep that margin). */
     int npt;               /* 0: constant volume; 1: isotropic Langevin barostat        */
     double pressure;       /* P_ext, eV/A^3 (1 GPa = 6.241509e-3 eV/A^3)                */
     double cell_mass;      /* W, eV fs^2 (> 0)                                          */
@@ -156,8 +160,14 @@ typedef struct {
  *        energy sum_i m_i P |vbar_i|^2/2 (a bath that does not hold the centroid
  *        at k_B T: QTB-PIMD).  The paper prints neither (only Eq. 5).  One
  *        bead: [18] = 3N k_B T/2, [19] = K.
- *   [20] cell volume (A^3; constant unless npt; 0 for external potentials) */
-#define QTB_NREC 21
+ *   [20] cell volume (A^3; constant unless npt; 0 for external potentials)
+ *   [21] K_0 = sum_i m_i P |vbar_i|^2/2, the centroid modes' kinetic energy
+ *   [22] W_cv = (1/P) sum_s W_vir,s - sum_s sum_i (r_i^(s) - rbar_i) . f_i^(s),
+ *        the centroid virial (trace): the virial of a scaling of the centroids
+ *        at fixed bead offsets.  One bead: [21] = K, [22] = the virial trace.
+ *        [21] and [22] of ring polymers, like [18] and [19], are formed on
+ *        recorded steps (every step at constant pressure). */
+#define QTB_NREC 23
 
 /* Create a context for n_sys independent systems sharing one parameter set.
  * Copies the host arrays, allocates device state, computes the first forces.

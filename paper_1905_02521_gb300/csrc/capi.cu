@@ -307,7 +307,7 @@ int refresh_forces(qtb_ctx *c)
     launch_spring(c->d, c->ml, c->st);  // the record's spring term (no integrator ran)
     CUDA_TRY(launch_force(c->d, c->ml, c->tabf, c->tab, 0, j, cur, 0, 1, c->st));
     if (!c->pair) launch_reduce(c->d, c->ml, j, -1, c->st);  // the list force kernel reduces itself
-    launch_centroid(c->d, c->ml, j, -1, c->st);
+    launch_centroid(c->d, c->ml, j, -1, 0, c->st);
     CUDA_TRY(cudaGetLastError());
     return QTB_OK;
 }
@@ -497,7 +497,7 @@ int run_steps(qtb_ctx *c, int j0, int count, bool graph)
         if (!m.pair || (rec && m.n_ccta)) {
             ProfMark pm(c, KC_REDUCE);
             if (!m.pair) launch_reduce(c->d, m, j, 1, c->st);
-            if (rec) launch_centroid(c->d, m, j, 1, c->st);
+            if (rec) launch_centroid(c->d, m, j, 1, 1, c->st);
         }
         c->capturing = keep;
     }
@@ -720,8 +720,6 @@ int validate(const qtb_system *sys, int n_sys, const qtb_params *p)
         if (p->potential != QTB_POT_PAIR) return fail(QTB_ERR_ARG, "npt: pair potential only");
         if (!(p->cell_mass > 0) || !(p->cell_gamma >= 0)) return fail(QTB_ERR_ARG, "npt: cell_mass > 0, cell_gamma >= 0");
         if (!std::isfinite(p->pressure)) return fail(QTB_ERR_ARG, "npt: pressure must be finite");
-        for (int s = 0; s < n_sys; ++s)
-            if (sys[s].n_beads != 1) return fail(QTB_ERR_ARG, "npt: one bead per atom only (system %d)", s);
     }
     if (p->potential == QTB_POT_PAIR) {
         if (!p->charge || !p->buck_A || !p->buck_rho || !p->buck_C) return fail(QTB_ERR_ARG, "pair tables missing");
@@ -1175,13 +1173,15 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
             C.a1f = C.a2f = (float)(0.5 * p->dt);
             C.inv_wf = (float)(1.0 / p->cell_mass);
             C.rb_tol = 0.25 * c->skin / (p->r_cut + c->skin);
+            C.lam_old = C.inv_lam = 1.0;
+            C.lam_oldf = C.inv_lamf = 1.0f;
             C.on = 1;
         }
         d.npt = upload(c, cells);
         if (!d.npt) return bail(fail(QTB_ERR_OOM, "device allocation failed"));
     }
     if (ccta) {
-        d.cpart = (double *)c->alloc(sizeof(double) * 2 * (size_t)ccta);
+        d.cpart = (double *)c->alloc(sizeof(double) * 6 * (size_t)ccta);  // kCenQ per CTA
         d.cdone = (unsigned *)c->alloc(sizeof(unsigned) * n_sys);
         if (!d.cpart || !d.cdone || !d.ccta_sys) return bail(fail(QTB_ERR_OOM, "device allocation failed"));
         cudaMemsetAsync(d.cdone, 0, sizeof(unsigned) * n_sys, c->st);

@@ -82,18 +82,26 @@ __global__ void k_reduce(Dev d, int j, int record)
 // component, with d_b the offset of bead b from bead 0 (minimum image), the
 // sums over beads of d_b f_b, d_b, f_b and v_b give
 //   sum_b (d_b - dbar) f_b = sum d_b f_b - (sum d_b)(sum f_b)/P,
-// FP64.  The last CTA of a system completes the record (fixed order).
+// FP64.  The last CTA of a system completes the record (fixed order); slots 21
+// and 22 are K_0 and the centroid virial (1/P) sum_s W_s - sum (r - rbar) . f.
+// In an isothermal-isobaric cell (every step, kick = 1) this kernel also ends
+// the step's closing B(dt/2) of each centroid with the cell's friction (the
+// force kernel gave the plain kick) and adds the change to the record's K,
+// E_prim and momentum; bead offsets are physical (lam times the stored ones).
 constexpr int kCenWarps = 8;
+constexpr int kCenQ = 6;  // per-CTA partials: virial term, K_0, and the cell kick's dK and momentum
 
 template <int PM, class R>
-__global__ void __launch_bounds__(32 * kCenWarps) k_centroid(Dev d, int j, int record)
+__global__ void __launch_bounds__(32 * kCenWarps) k_centroid(Dev d, int j, int record, int kick)
 {
     typedef typename PosT<PM, R>::S PS;
     __shared__ double sh[kCenWarps][12][kCenAtoms];
-    __shared__ double fin[kCenWarps][2];
+    __shared__ double dlt[3][kCenAtoms];
+    __shared__ double fin[kCenWarps][kCenQ];
     __shared__ int last;
     const long long step = d.clock[0] * kBlockSteps + j + 1;  // steps completed
-    if (record >= 0 && step % d.obs_stride != 0) return;
+    // (isothermal-isobaric cells need K_0 and W_cv on every step)
+    if (record >= 0 && step % d.obs_stride != 0 && !d.npt) return;
     const int cta = blockIdx.x, s = d.ccta_sys[cta];
     const DSys S = d.sys[s];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -102,7 +110,10 @@ __global__ void __launch_bounds__(32 * kCenWarps) k_centroid(Dev d, int j, int r
     const size_t G = (size_t)d.G;
     const PS *X = reinterpret_cast<const PS *>(d.x);
     const R *F = reinterpret_cast<const R *>(d.f);
-    const R *V = reinterpret_cast<const R *>(d.v);
+    R *V = reinterpret_cast<R *>(d.v);
+    // stored positions are the physical ones over lam in a cell
+    const DNpt *NC = (d.npt && d.npt[s].on) ? d.npt + s : nullptr;
+    const double lam = NC ? NC->lam : 1.0;
     double a[12];
 #pragma unroll
     for (int q = 0; q < 12; ++q) a[q] = 0.0;
@@ -114,7 +125,7 @@ __global__ void __launch_bounds__(32 * kCenWarps) k_centroid(Dev d, int j, int r
             double sdf = 0.0, sd = 0.0, sf = 0.0, sv = 0.0;
             for (int b = warp; b < P; b += kCenWarps) {
                 const size_t o = o0 + (size_t)b * N;
-                const double dd = (double)PosT<PM, R>::rel(X[o], x0, S.box[c], S.fix_scale[c], S.fix_inv[c]);
+                const double dd = (double)PosT<PM, R>::rel(X[o], x0, S.box[c], S.fix_scale[c], S.fix_inv[c]) * lam;
                 const double f = (double)F[o];
                 sdf = fma(dd, f, sdf);
                 sd += dd;
@@ -127,9 +138,12 @@ __global__ void __launch_bounds__(32 * kCenWarps) k_centroid(Dev d, int j, int r
 #pragma unroll
     for (int q = 0; q < 12; ++q) sh[warp][q][lane] = a[q];
     __syncthreads();
+    const bool cellkick = NC && kick;
     if (warp == 0) {
-        double cv = 0.0, k0 = 0.0;
+        double cv = 0.0, k0 = 0.0, dk = 0.0, dm[3] = {0.0, 0.0, 0.0};
         if (i < N) {
+            const int ty = d.typ[S.g0 + i];
+            const double mv = d.mass_mvv[ty];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 double sdf = 0.0, sd = 0.0, sf = 0.0, sv = 0.0;
@@ -140,16 +154,47 @@ __global__ void __launch_bounds__(32 * kCenWarps) k_centroid(Dev d, int j, int r
                     sv += sh[w][4 * c + 3][lane];
                 }
                 cv += sdf - sd * sf / P;
+                if (cellkick) {
+                    // the closing B(dt/2) of the centroid with the cell's friction: the
+                    // force kernel gave every bead the plain kick hdt f / m; the centroid
+                    // velocity becomes vbar e2 + (hdt/m) fbar g2 (vbar before the kick)
+                    const bool f32 = sizeof(R) == 4;
+                    const double e2 = f32 ? (double)NC->e2f : NC->e2, g2 = f32 ? (double)NC->g2f : NC->g2;
+                    const double hd = (double)reinterpret_cast<const R *>(d.hdt_m)[ty];
+                    const double vb = sv / P, fb = hd * (sf / P);
+                    const double vn = (vb - fb) * e2 + fb * g2;
+                    const double del = vn - vb;
+                    dlt[c][lane] = del;
+                    dk += 0.5 * mv * P * (vn * vn - vb * vb);
+                    dm[c] = mv / kMvv2e * P * del;  // momentum in u A/fs
+                    sv = P * vn;
+                }
                 k0 += sv * sv;
             }
-            k0 *= 0.5 * d.mass_mvv[d.typ[S.g0 + i]] / P;
+            k0 *= 0.5 * mv / P;
         }
         cv = warp_sum(cv);
         k0 = warp_sum(k0);
-        if (lane == 0) {
-            d.cpart[2 * (size_t)cta] = cv;
-            d.cpart[2 * (size_t)cta + 1] = k0;
+        double *out = d.cpart + kCenQ * (size_t)cta;
+        if (cellkick) {
+            dk = warp_sum(dk);
+            for (int c = 0; c < 3; ++c) dm[c] = warp_sum(dm[c]);
         }
+        if (lane == 0) {
+            out[0] = cv;
+            out[1] = k0;
+            out[2] = dk;
+            out[3] = dm[0]; out[4] = dm[1]; out[5] = dm[2];
+        }
+    }
+    if (cellkick) {
+        __syncthreads();
+        if (i < N)
+            for (int c = 0; c < 3; ++c) {
+                const size_t o0 = (size_t)c * G + S.g0 + i;
+                const R del = (R)dlt[c][lane];
+                for (int b = warp; b < P; b += kCenWarps) V[o0 + (size_t)b * N] += del;
+            }
     }
     // the CTA that finishes a system last completes its record
     __threadfence();
@@ -158,33 +203,41 @@ __global__ void __launch_bounds__(32 * kCenWarps) k_centroid(Dev d, int j, int r
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double cv = 0.0, k0 = 0.0;
-    for (int c = S.ccta0 + (int)threadIdx.x; c < S.ccta1; c += blockDim.x) {
-        cv += __ldcg(d.cpart + 2 * (size_t)c);
-        k0 += __ldcg(d.cpart + 2 * (size_t)c + 1);
-    }
-    cv = warp_sum(cv);
-    k0 = warp_sum(k0);
-    if (lane == 0) {
-        fin[warp][0] = cv;
-        fin[warp][1] = k0;
+    double t[kCenQ];
+#pragma unroll
+    for (int q = 0; q < kCenQ; ++q) t[q] = 0.0;
+    for (int c = S.ccta0 + (int)threadIdx.x; c < S.ccta1; c += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < kCenQ; ++q) t[q] += __ldcg(d.cpart + kCenQ * (size_t)c + q);
+#pragma unroll
+    for (int q = 0; q < kCenQ; ++q) {
+        t[q] = warp_sum(t[q]);
+        if (lane == 0) fin[warp][q] = t[q];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        cv = 0.0;
-        k0 = 0.0;
-        for (int w = 0; w < kCenWarps; ++w) {
-            cv += fin[w][0];
-            k0 += fin[w][1];
+        double tot[kCenQ];
+        for (int q = 0; q < kCenQ; ++q) {
+            tot[q] = 0.0;
+            for (int w = 0; w < kCenWarps; ++w) tot[q] += fin[w][q];
         }
-        const double r18 = 1.5 * N * kBoltz * S.T - 0.5 * cv, r19 = k0 - 0.5 * cv;
-        d.latest[(size_t)s * QTB_NREC + 18] = r18;
-        d.latest[(size_t)s * QTB_NREC + 19] = r19;
-        if (record >= 0) {
+        const double cv = tot[0], k0 = tot[1];
+        double *L = d.latest + (size_t)s * QTB_NREC;
+        if (cellkick) {  // the record of the force kernel had the plain kick
+            L[1] += tot[2];
+            L[4] += tot[2];
+            for (int c = 0; c < 3; ++c) L[14 + c] += tot[3 + c];
+        }
+        L[18] = 1.5 * N * kBoltz * S.T - 0.5 * cv;
+        L[19] = k0 - 0.5 * cv;
+        L[21] = k0;
+        L[22] = (L[5] + L[9]) + L[13] - cv;
+        if (record >= 0 && step % d.obs_stride == 0) {
             const long long r = step / d.obs_stride - 1;
             const int slot = (int)(r % d.max_records);
-            d.series[((size_t)slot * d.nsys + s) * QTB_NREC + 18] = r18;
-            d.series[((size_t)slot * d.nsys + s) * QTB_NREC + 19] = r19;
+            double *Sr = d.series + ((size_t)slot * d.nsys + s) * QTB_NREC;
+            const int upd[9] = {1, 4, 14, 15, 16, 18, 19, 21, 22};
+            for (int u = 0; u < 9; ++u) Sr[upd[u]] = L[upd[u]];
         }
         d.cdone[s] = 0u;
     }
@@ -208,6 +261,8 @@ __global__ void __launch_bounds__(128) k_spring(Dev d)
     const size_t G = (size_t)d.G;
     const PS *X = reinterpret_cast<const PS *>(d.x);
     double spring = 0.0;
+    // a cell's stored offsets are the physical ones over lam
+    const double l2 = (d.npt && d.npt[s].on) ? d.npt[s].lam * d.npt[s].lam : 1.0;
     if (S.P > 1)
         for (int t = threadIdx.x; t < 3 * na; t += blockDim.x) {
             const int c = t / na, i = a0 + (t - c * na);
@@ -221,7 +276,7 @@ __global__ void __launch_bounds__(128) k_spring(Dev d)
                 prev = xr;
             }
             sp = fma(prev, prev, sp);  // bead P-1 to bead 0 (the origin)
-            spring += 0.5 * d.mass_mvv[d.typ[S.g0 + i]] * S.wP * S.wP * (double)sp;
+            spring += 0.5 * d.mass_mvv[d.typ[S.g0 + i]] * S.wP * S.wP * (double)sp * l2;
         }
     double acc[kNQ];
     for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
@@ -528,16 +583,16 @@ void launch_reduce(const Dev &d, const MdLaunch &, int j, int record, cudaStream
     k_reduce<<<d.nsys, 128, 0, st>>>(d, j, record);
 }
 
-void launch_centroid(const Dev &d, const MdLaunch &m, int j, int record, cudaStream_t st)
+void launch_centroid(const Dev &d, const MdLaunch &m, int j, int record, int kick, cudaStream_t st)
 {
     if (m.n_ccta == 0) return;
     const int g = m.n_ccta, nt = 32 * kCenWarps;
     if (!m.pair) {
-        if (m.mixed) k_centroid<PM_FREE, float><<<g, nt, 0, st>>>(d, j, record);
-        else k_centroid<PM_FREE, double><<<g, nt, 0, st>>>(d, j, record);
+        if (m.mixed) k_centroid<PM_FREE, float><<<g, nt, 0, st>>>(d, j, record, kick);
+        else k_centroid<PM_FREE, double><<<g, nt, 0, st>>>(d, j, record, kick);
     } else {
-        if (m.mixed) k_centroid<PM_FIX, float><<<g, nt, 0, st>>>(d, j, record);
-        else k_centroid<PM_BOX64, double><<<g, nt, 0, st>>>(d, j, record);
+        if (m.mixed) k_centroid<PM_FIX, float><<<g, nt, 0, st>>>(d, j, record, kick);
+        else k_centroid<PM_BOX64, double><<<g, nt, 0, st>>>(d, j, record, kick);
     }
 }
 

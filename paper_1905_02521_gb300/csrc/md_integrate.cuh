@@ -261,6 +261,14 @@ __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int 
     R *V = reinterpret_cast<R *>(d.v);
     const R *F = reinterpret_cast<const R *>(d.f);
     const R *hdt = reinterpret_cast<const R *>(d.hdt_m);
+    // isothermal-isobaric cell: it acts on the centroid mode only (the B with its
+    // friction needs the velocity and force modes apart: the kicks hdt F / m go to
+    // fs, the new-position area, unused until phase 3); stored positions are the
+    // physical ones over lam, so the internal modes are taken to physical length
+    // with this step's old lam and back with its new one
+    const DNpt *NC = (d.npt && d.npt[s].on) ? d.npt + s : nullptr;
+    static_assert(sizeof(PS) == sizeof(R), "fs overlays xn_s");
+    R *fs = reinterpret_cast<R *>(xn_s);
     // phase 1: loads, then relative positions and B(dt/2) velocities, bead space
     PS xold[PER][MT], x0v[PER];
     R vv[PER][MT], fv[PER][MT], xrel[PER][MT];
@@ -303,7 +311,12 @@ __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int 
             const R xr = (b == 0) ? R(0) : PosT<PM, R>::rel(xold[u][m], x0v[u], S.box[c], S.fix_scale[c], S.fix_inv[c]);
             xrel[u][m] = xr;
             xs[b * COLS + col] = xr;
-            ps[b * COLS + col] = fma(hd, fv[u][m], vv[u][m]);
+            if (NC) {
+                ps[b * COLS + col] = vv[u][m];
+                fs[b * COLS + col] = hd * fv[u][m];
+            } else {
+                ps[b * COLS + col] = fma(hd, fv[u][m], vv[u][m]);
+            }
         }
     }
     __syncthreads();
@@ -328,7 +341,7 @@ __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int 
         R q[MT], p[MT];
 #pragma unroll
         for (int m = 0; m < MT; ++m) q[m] = p[m] = R(0);
-        if (idx < NTASK) {
+        if (idx < NTASK && !NC) {
 #pragma unroll 8
             for (int b = 0; b < P; ++b) {
                 const R xv = xs[b * COLS + col], pv = ps[b * COLS + col];
@@ -344,6 +357,45 @@ __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int 
             for (int m = 0; m < MT; ++m) {
                 const int k = g * MT + m;
                 mode_aoa(q[m], p[m], rot[3 * k], rot[3 * k + 1], rot[3 * k + 2], c1, noise[m]);
+            }
+        } else if (idx < NTASK) {
+            R pf[MT];
+#pragma unroll
+            for (int m = 0; m < MT; ++m) pf[m] = R(0);
+#pragma unroll 8
+            for (int b = 0; b < P; ++b) {
+                const R xv = xs[b * COLS + col], pv = ps[b * COLS + col], fb = fs[b * COLS + col];
+                R cf[MT];
+                nm_row<MT>(Cs + b * P + g * MT, cf);
+#pragma unroll
+                for (int m = 0; m < MT; ++m) {
+                    q[m] = fma(cf[m], xv, q[m]);
+                    p[m] = fma(cf[m], pv, p[m]);
+                    pf[m] = fma(cf[m], fb, pf[m]);
+                }
+            }
+            const bool f32 = sizeof(R) == 4;
+            const R e1 = f32 ? (R)NC->e1f : (R)NC->e1, g1 = f32 ? (R)NC->g1f : (R)NC->g1;
+            const R a1 = f32 ? (R)NC->a1f : (R)NC->a1, a2 = f32 ? (R)NC->a2f : (R)NC->a2;
+            const R lo = f32 ? (R)NC->lam_oldf : (R)NC->lam_old, il = f32 ? (R)NC->inv_lamf : (R)NC->inv_lam;
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                const int k = g * MT + m;
+                if (k == 0) {
+                    // centroid: B with the cell's friction, then A O A as a drift in the
+                    // reference cell (the one-bead integrator's factors)
+                    R pk = fma(p[m], e1, pf[m] * g1);
+                    R disp = pk * a1;
+                    pk = fma(c1, pk, noise[m]);
+                    disp = fma(pk, a2, disp);
+                    q[m] = q[m] + disp;
+                    p[m] = pk;
+                } else {
+                    R qk = q[m] * lo;
+                    p[m] = p[m] + pf[m];
+                    mode_aoa(qk, p[m], rot[3 * k], rot[3 * k + 1], rot[3 * k + 2], c1, noise[m]);
+                    q[m] = qk * il;
+                }
             }
         }
 #pragma unroll
@@ -422,7 +474,14 @@ __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int 
     double spring = 0.0;
     const bool recs = (d.clock[0] * kBlockSteps + j + 1) % d.obs_stride == 0;  // spring only where recorded
     bool moved = false;
-    const R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
+    R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
+    double l2 = 1.0;  // physical length squared over stored (cell)
+    if (NC) {
+        // physical displacement against (3/8 skin)^2 (see k_integrate)
+        const R l = sizeof(R) == 4 ? (R)NC->lamf : (R)NC->lam;
+        lim = lim * R(0.5625) / (l * l);
+        l2 = NC->lam * NC->lam;
+    }
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int idx = threadIdx.x + u * NT;
@@ -434,7 +493,7 @@ __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int 
         for (int m = 0; m < MT; ++m) {
             const int b = g * MT + m;
             const R dx = xs[b * COLS + col] - xs[((b + 1) % P) * COLS + col];
-            if (recs) spring += 0.5 * d.mass_mvv[tt[u]] * S.wP * S.wP * (double)(dx * dx);
+            if (recs) spring += 0.5 * d.mass_mvv[tt[u]] * S.wP * S.wP * (double)(dx * dx) * l2;
             if (PM != PM_FREE && c == 0) {
                 const size_t gg = S.g0 + (size_t)b * N + i;
                 const PS *XR = reinterpret_cast<const PS *>(d.xref);

@@ -769,9 +769,12 @@ static __device__ void reduce_system(const Dev &d, int s, long long step, int re
             const double l = (d.npt && d.npt[s].on) ? d.npt[s].lam : 1.0;
             r = S.box[0] * S.box[1] * S.box[2] * l * l * l;
         } else if (S.P == 1) {
-            // centroid-virial estimators: for one bead 3N k_B T/2 and K; ring
-            // polymers get them from the centroid kernel that follows
-            r = (q == 18) ? 1.5 * S.N * kBoltz * S.T : K;
+            // centroid-virial estimators: for one bead 3N k_B T/2 and K, the
+            // centroid kinetic energy K and virial trace; ring polymers get them
+            // from the centroid kernel that follows
+            if (q == 18) r = 1.5 * S.N * kBoltz * S.T;
+            else if (q == 19 || q == 21) r = K;
+            else r = (tot[Q_VIR + 0] * invP + tot[Q_VIR + 1] * invP) + tot[Q_VIR + 2] * invP;  // q == 22
         }
         if (q == 0 && (!isfinite(K) || !isfinite(V))) atomicOr(d.err, (unsigned)ERR_NONFINITE);
         d.latest[(size_t)s * QTB_NREC + q] = r;
@@ -816,7 +819,7 @@ __device__ void cell_update(const Dev &d, int s, long long n, int cur)
     DNpt C = d.npt[s];
     const DSys &S = d.sys[s];
     const double *rec = d.latest + (size_t)s * QTB_NREC;
-    const double K = rec[1], Wv = rec[5] + rec[9] + rec[13];
+    const double K = rec[21], Wv = rec[22];  // centroid kinetic energy and virial (one bead: K, W)
     const double V = S.box[0] * S.box[1] * S.box[2] * C.lam * C.lam * C.lam;
     const double G = 2.0 * C.alpha * K + Wv - 3.0 * V * C.pext;
     const double h = 0.5 * d.dt;
@@ -873,6 +876,14 @@ __device__ void cell_update(const Dev &d, int s, long long n, int cur)
         C.g2 = xm1_over_x(-x);
         C.e1f = (float)C.e1; C.g1f = (float)C.g1; C.a1f = (float)C.a1; C.a2f = (float)C.a2;
         C.e2f = (float)C.e2; C.g2f = (float)C.g2; C.lamf = (float)lam;
+    }
+    // ring polymers: the bead offsets keep their physical length across the update
+    if constexpr (F32) {
+        C.lam_oldf = (float)C.lam;
+        C.inv_lamf = 1.0f / (float)lam;
+    } else {
+        C.lam_old = C.lam;
+        C.inv_lam = 1.0 / lam;
     }
     C.lam = lam;
     C.pending = 1;
@@ -1059,7 +1070,8 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
         const R hdtm = T.hdt_m[ti];
         R v = V[o];
         if (kick) {
-            if (NC) {  // B(dt/2) with the cell's friction: v e2 + (hdt/m) F g2
+            if (NC && S.P == 1) {  // B(dt/2) with the cell's friction: v e2 + (hdt/m) F g2
+                // (ring polymers: the plain kick here, the centroid's friction in k_centroid)
                 const R e2 = sizeof(R) == 4 ? (R)NC->e2f : (R)NC->e2, g2 = sizeof(R) == 4 ? (R)NC->g2f : (R)NC->g2;
                 v = fma(v, e2, (hdtm * fc) * g2);
             } else {

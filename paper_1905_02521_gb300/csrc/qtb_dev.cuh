@@ -53,6 +53,8 @@ struct DNpt {
     int on, pending;  // barostat on; the previous step's closing half kick of the cell is due
     int pad2[2];
     double rb_tol;    // list rebuild when |lam - lam_rb| > rb_tol lam_rb (skin/4 over the list radius)
+    double lam_old, inv_lam;  // this step's lam before the update and 1/lam after (ring polymers)
+    float lam_oldf, inv_lamf;
 };
 
 // Neighbour-list entry (32 bits): replica-local index j in bits 0..25, the

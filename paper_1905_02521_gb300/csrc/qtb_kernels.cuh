@@ -92,7 +92,7 @@ void launch_reduce(const Dev &d, const MdLaunch &m, int j, int record, cudaStrea
 // centroid-virial estimators of the ring-polymer systems (record slots 18, 19),
 // after the force launch of a step that may be recorded (record < 0: latest only)
 constexpr int kCenAtoms = 32;  // atoms per CTA of the centroid estimator
-void launch_centroid(const Dev &d, const MdLaunch &m, int j, int record, cudaStream_t st);
+void launch_centroid(const Dev &d, const MdLaunch &m, int j, int record, int kick, cudaStream_t st);
 // spring energy of the current positions into the integrator partials (the
 // record of a refreshed step, which no integrator produced)
 void launch_spring(const Dev &d, const MdLaunch &m, cudaStream_t st);

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import build as _build
 
-NREC = 21
+NREC = 23
 TC_FILTER = True        # the BF16 tcgen05 Toeplitz-GEMM filter is available (QTB_FILTER_BF16)
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NONFINITE, ERR_SOLVE, ERR_OVERFLOW, ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
