@@ -154,7 +154,8 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-WORKLOADS = ("mgo8000", "lih_qtbpimd_p8", "lih_pimd_p32", "sweep64", "lih_pimd_p32_big", "lih_qtb_npt")
+WORKLOADS = ("mgo8000", "lih_qtbpimd_p8", "lih_pimd_p32", "sweep64", "lih_pimd_p32_big", "lih_qtb_npt",
+             "lih_qtbpimd_p8_npt")
 
 # algorithmic bytes per bead-atom of one launch of the ring-polymer integrator
 # (k_integrate_nm): read x, v, f, xref and the coloured noise, write x, v and the
@@ -176,6 +177,7 @@ def workload(name, ncell, precision, filt):
         QTB-MD, one context (batched), dt 1 fs, 2049 taps, w_max 0.3 rad/fs.
     lih_qtb_npt: LiH 6^3 cells (1728 ions), QTB-MD 50 K at zero pressure with the isotropic
         Langevin cell (cell period ~300 fs, friction 4e-3/fs), dt 0.25 fs, 2049 taps, w_max 0.6 rad/fs.
+    lih_qtbpimd_p8_npt: lih_qtbpimd_p8 at zero pressure, the same cell acting on the centroids.
     """
     from paper_1905_02521_gb300 import qtb, workloads as W
     prec = qtb.MIXED if precision == "mixed" else qtb.FP64
@@ -187,8 +189,8 @@ def workload(name, ncell, precision, filt):
         setup = (qtb.NOISE_QTB, 2049, 0.3)
         desc = (f"MgO rock salt {ncell}x{ncell}x{ncell} cells ({len(s['types'])} ions), QTB-MD 100 K, dt 1 fs, "
                 f"2049-tap {filt} noise filter, 256-step blocks")
-    elif name in ("lih_qtbpimd_p8", "lih_pimd_p32", "lih_pimd_p32_big"):
-        P = 8 if name == "lih_qtbpimd_p8" else 32
+    elif name in ("lih_qtbpimd_p8", "lih_pimd_p32", "lih_pimd_p32_big", "lih_qtbpimd_p8_npt"):
+        P = 8 if name.startswith("lih_qtbpimd_p8") else 32
         nc = 20 if name == "lih_pimd_p32_big" else 6
         s, pot = W.lih_system(nc, 50.0, gamma=1e-3, n_beads=P)
         systems = [s]
@@ -196,6 +198,8 @@ def workload(name, ncell, precision, filt):
         if P == 8:
             setup = (qtb.NOISE_QTB_PIMD, 2049, 0.6)
             desc = f"LiH rock salt 6x6x6 cells (1728 ions) x 8 beads, QTB-PIMD (kappa_P solver) 50 K, dt 0.25 fs, 2049-tap {filt} filter"
+            if name.endswith("_npt"):
+                desc += ", zero pressure, isotropic Langevin cell on the centroids"
         else:
             desc = (f"LiH rock salt {nc}x{nc}x{nc} cells ({len(s['types'])} ions) x 32 beads, PIMD with white "
                     f"Langevin bath 50 K, dt 0.25 fs")
@@ -217,7 +221,7 @@ def workload(name, ncell, precision, filt):
     params = {k: pot[k] for k in ("mass", "charge", "buck_A", "buck_rho", "buck_C")}
     params.update(dsf_alpha=pot["dsf_alpha"], r_cut=pot["r_cut"], dt=dt, precision=prec, filter_prec=fp,
                   seed=12345, obs_stride=BLOCK, max_records=64)
-    if name == "lih_qtb_npt":   # cell mass for a ~300 fs volume period at a bulk modulus of ~1 eV/A^3
+    if name.endswith("_npt"):   # cell mass for a ~300 fs volume period at a bulk modulus of ~1 eV/A^3
         V = float(np.prod(systems[0]["box"]))
         params.update(npt=1, pressure=0.0, cell_mass=9.0 * 1.0 * V / (2 * np.pi / 300.0) ** 2, cell_gamma=4e-3)
     return systems, pot, params, setup, desc
@@ -373,7 +377,9 @@ def run_ours(args):
     e2e_value = ws * units * BLOCK * args.steps / (np.sum(e2e_ms) / 1e3)
     rebuilds_e2e = (qtb.qtb_list_rebuilds(ctx) - rebuilds_e2e0) / args.steps
     integ = 1 if fused else BLOCK * len({p for _, p in sizes})
-    cen = 1 if any(p > 1 for _, p in sizes) else 0  # centroid estimators, recorded step only
+    # centroid estimators: recorded step only, every step at constant pressure
+    cen = (BLOCK if npt else 1) if any(p > 1 for _, p in sizes) else 0
+    cell_launches = (1 if fused else BLOCK) if npt else 0
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -414,8 +420,9 @@ def run_ours(args):
         # step per distinct bead count), 256 step launches (a list rebuild runs inside the
         # step launch that needs it), the centroid estimators of the recorded step (ring
         # polymers), the block clock
-        # (+ the cell kernel before each block's first step at constant pressure)
-        "gpu_launches": 2 + integ + BLOCK + cen + 1 + (1 if npt else 0),
+        # (+ the cell kernel: before each block's first step at constant pressure, every
+        # step for ring polymers)
+        "gpu_launches": 2 + integ + BLOCK + cen + 1 + cell_launches,
         "list_rebuilds_per_bench_step": rebuilds,
         "wall_s": wall,
         "observables": {"K_eV": float(obs[1]), "V_eV": float(obs[2]), "step": int(obs[0])},

@@ -290,15 +290,15 @@ def test_ideal_gas_volume_on_gpu(qtb):
     assert V.var() / V.mean() ** 2 == pytest.approx(1 / (N + 1), rel=0.15)
 
 
-def _lattice_parameter(qtb, isotope, T, quantum, ncell=3, steps=24576, neq=8192):
-    s, pot = W.lih_system(ncell, T, gamma=2e-3, isotope=isotope, seed=31)
+def _lattice_parameter(qtb, isotope, T, quantum, ncell=3, steps=24576, neq=8192, P=1):
+    s, pot = W.lih_system(ncell, T, gamma=2e-3, isotope=isotope, seed=31, n_beads=P)
     V = np.prod(s["box"])
     npt = {"pressure": 0.0, "mass": _cell_mass(1.0, V, 300.0), "gamma": 4e-3}
     ctx = gpu_ctx(qtb, [s], pot, 0.25, precision=1, filter_prec=1, seed=23, npt=npt, obs_stride=16,
                   max_records=4096)
     try:
         if quantum:
-            qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB, 2049, 0.6)
+            qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB if P == 1 else qtb.NOISE_QTB_PIMD, 2049, 0.6)
         qtb.qtb_step_n(ctx, neq)
         qtb.qtb_step_n(ctx, steps)
         V = qtb.qtb_get_series(ctx, 0, steps // 16)[:, 20]
@@ -334,6 +334,31 @@ def test_lih_lid_lattice_parameter_against_temperature(qtb):
     dq = res[(150.0, "H", True)][0] - res[(20.0, "H", True)][0]
     dc = res[(150.0, "H", False)][0] - res[(20.0, "H", False)][0]
     assert dq < dc
+
+
+def test_lih_lattice_parameter_qtb_pimd_converges_faster_than_pimd(qtb):
+    # LiH 3^3 at zero pressure (the comparison of Figs. 2 and 6 of the paper,
+    # with the synthetic potential): PIMD with 32 beads is the converged
+    # quantum lattice parameter at 150 and 300 K; QTB-PIMD with 8 beads lands
+    # on it where PIMD with 8 beads has not yet converged (150 K), and QTB-MD
+    # alone overestimates the expansion (zero-point energy leaking into the
+    # anharmonic modes)
+    res = {}
+    for T in (150.0, 300.0):
+        for key, P, q in (("qtb_md", 1, True), ("qtb_pimd8", 8, True), ("pimd8", 8, False), ("pimd32", 32, False)):
+            res[(T, key)] = _lattice_parameter(qtb, "H", T, q, P=P)
+    res[(150.0, "pimd32_D")] = _lattice_parameter(qtb, "D", 150.0, False, P=32)
+    for k, (a, e) in sorted(res.items()):
+        print(f"T {k[0]:5.0f} K {k[1]:10s} a = {a:.5f} +- {e:.5f}")
+    sig = lambda *k: np.sqrt(sum(res[x][1] ** 2 for x in k))  # noqa: E731
+    for T in (150.0, 300.0):
+        ref = res[(T, "pimd32")][0]
+        assert abs(res[(T, "qtb_pimd8")][0] - ref) < 4 * sig((T, "qtb_pimd8"), (T, "pimd32"))
+        assert res[(T, "qtb_md")][0] - ref > 4 * sig((T, "qtb_md"), (T, "pimd32"))
+    assert abs(res[(300.0, "pimd8")][0] - res[(300.0, "pimd32")][0]) < 4 * sig((300.0, "pimd8"), (300.0, "pimd32"))
+    assert abs(res[(150.0, "qtb_pimd8")][0] - res[(150.0, "pimd32")][0]) < \
+        abs(res[(150.0, "pimd8")][0] - res[(150.0, "pimd32")][0])
+    assert res[(150.0, "pimd32")][0] - res[(150.0, "pimd32_D")][0] > 4 * sig((150.0, "pimd32"), (150.0, "pimd32_D"))
 
 
 def test_constant_volume_cell_and_volume_slot(qtb):
