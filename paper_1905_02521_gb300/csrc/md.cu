@@ -79,10 +79,11 @@ __global__ void k_reduce(Dev d, int j, int record)
 // |vbar_i|^2 / 2 the kinetic energy of the centroid mode (the form for a bath
 // that does not hold the centroid at k_B T, QTB-PIMD).  A CTA takes kCenAtoms
 // atoms (lane = atom, coalesced rows); its 8 warps split the beads.  Per atom and
-// component, with d_b the offset of bead b from bead 0 (minimum image), the
-// sums over beads of d_b f_b, d_b, f_b and v_b give
-//   sum_b (d_b - dbar) f_b = sum d_b f_b - (sum d_b)(sum f_b)/P,
-// FP64.  The last CTA of a system completes the record (fixed order); slots 21
+// component, with d_b the offset of bead b from bead 0 (minimum image), two
+// passes over the beads give dbar, then sum_b (d_b - dbar) f_b, in the
+// arithmetic of the form (FP32 form: sums over atoms in float-float; the FP64
+// pipe of this GPU is slow).  The last CTA of a system completes the record
+// (fixed order, FP64); slots 21
 // and 22 are K_0 and the centroid virial (1/P) sum_s W_s - sum (r - rbar) . f.
 // In an isothermal-isobaric cell (every step, kick = 1) this kernel also ends
 // the step's closing B(dt/2) of each centroid with the cell's friction (the
@@ -95,8 +96,10 @@ template <int PM, class R>
 __global__ void __launch_bounds__(32 * kCenWarps) k_centroid(Dev d, int j, int record, int kick)
 {
     typedef typename PosT<PM, R>::S PS;
-    __shared__ double sh[kCenWarps][12][kCenAtoms];
-    __shared__ double dlt[3][kCenAtoms];
+    constexpr bool kF32 = sizeof(R) == 4;
+    constexpr int NB = (32 + kCenWarps - 1) / kCenWarps;  // beads per warp (P <= 32)
+    __shared__ R sh[kCenWarps][9][kCenAtoms];
+    __shared__ R scv[kCenWarps][kCenAtoms];
     __shared__ double fin[kCenWarps][kCenQ];
     __shared__ int last;
     const long long step = d.clock[0] * kBlockSteps + j + 1;  // steps completed
@@ -113,88 +116,119 @@ __global__ void __launch_bounds__(32 * kCenWarps) k_centroid(Dev d, int j, int r
     R *V = reinterpret_cast<R *>(d.v);
     // stored positions are the physical ones over lam in a cell
     const DNpt *NC = (d.npt && d.npt[s].on) ? d.npt + s : nullptr;
-    const double lam = NC ? NC->lam : 1.0;
-    double a[12];
+    const R lam = NC ? (kF32 ? (R)NC->lamf : (R)NC->lam) : R(1);
+    const R invP = kF32 ? (R)S.invP_f : (R)S.invP;
+    const bool cellkick = NC && kick;
+    // pass 1: this warp's beads (b = warp, warp + 8, ...): offsets from bead 0,
+    // forces, and their sums with the velocities'
+    R dv[3][NB], fv[3][NB], sd[3], sf[3], sv[3];
 #pragma unroll
-    for (int q = 0; q < 12; ++q) a[q] = 0.0;
-    if (i < N) {
+    for (int c = 0; c < 3; ++c) {
+        sd[c] = sf[c] = sv[c] = R(0);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
+        for (int k = 0; k < NB; ++k) dv[c][k] = fv[c][k] = R(0);
+        if (i < N) {
             const size_t o0 = (size_t)c * G + S.g0 + i;
             const PS x0 = X[o0];
-            double sdf = 0.0, sd = 0.0, sf = 0.0, sv = 0.0;
-            for (int b = warp; b < P; b += kCenWarps) {
-                const size_t o = o0 + (size_t)b * N;
-                const double dd = (double)PosT<PM, R>::rel(X[o], x0, S.box[c], S.fix_scale[c], S.fix_inv[c]) * lam;
-                const double f = (double)F[o];
-                sdf = fma(dd, f, sdf);
-                sd += dd;
-                sf += f;
-                sv += (double)V[o];
-            }
-            a[4 * c] = sdf; a[4 * c + 1] = sd; a[4 * c + 2] = sf; a[4 * c + 3] = sv;
-        }
-    }
 #pragma unroll
-    for (int q = 0; q < 12; ++q) sh[warp][q][lane] = a[q];
+            for (int k = 0; k < NB; ++k) {
+                const int b = warp + k * kCenWarps;
+                if (b < P) {
+                    const size_t o = o0 + (size_t)b * N;
+                    const R dd = PosT<PM, R>::rel(X[o], x0, S.box[c], S.fix_scale[c], S.fix_inv[c]) * lam;
+                    const R f = F[o];
+                    dv[c][k] = dd;
+                    fv[c][k] = f;
+                    sd[c] += dd;
+                    sf[c] += f;
+                    sv[c] += V[o];
+                }
+            }
+        }
+        sh[warp][c][lane] = sd[c];
+        sh[warp][3 + c][lane] = sf[c];
+        sh[warp][6 + c][lane] = sv[c];
+    }
     __syncthreads();
-    const bool cellkick = NC && kick;
-    if (warp == 0) {
-        double cv = 0.0, k0 = 0.0, dk = 0.0, dm[3] = {0.0, 0.0, 0.0};
-        if (i < N) {
-            const int ty = d.typ[S.g0 + i];
-            const double mv = d.mass_mvv[ty];
+    // the atom's bead sums (every warp forms them alike, in warp order)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                double sdf = 0.0, sd = 0.0, sf = 0.0, sv = 0.0;
-                for (int w = 0; w < kCenWarps; ++w) {
-                    sdf += sh[w][4 * c][lane];
-                    sd += sh[w][4 * c + 1][lane];
-                    sf += sh[w][4 * c + 2][lane];
-                    sv += sh[w][4 * c + 3][lane];
-                }
-                cv += sdf - sd * sf / P;
-                if (cellkick) {
-                    // the closing B(dt/2) of the centroid with the cell's friction: the
-                    // force kernel gave every bead the plain kick hdt f / m; the centroid
-                    // velocity becomes vbar e2 + (hdt/m) fbar g2 (vbar before the kick)
-                    const bool f32 = sizeof(R) == 4;
-                    const double e2 = f32 ? (double)NC->e2f : NC->e2, g2 = f32 ? (double)NC->g2f : NC->g2;
-                    const double hd = (double)reinterpret_cast<const R *>(d.hdt_m)[ty];
-                    const double vb = sv / P, fb = hd * (sf / P);
-                    const double vn = (vb - fb) * e2 + fb * g2;
-                    const double del = vn - vb;
-                    dlt[c][lane] = del;
-                    dk += 0.5 * mv * P * (vn * vn - vb * vb);
-                    dm[c] = mv / kMvv2e * P * del;  // momentum in u A/fs
-                    sv = P * vn;
-                }
-                k0 += sv * sv;
-            }
-            k0 *= 0.5 * mv / P;
-        }
-        cv = warp_sum(cv);
-        k0 = warp_sum(k0);
-        double *out = d.cpart + kCenQ * (size_t)cta;
-        if (cellkick) {
-            dk = warp_sum(dk);
-            for (int c = 0; c < 3; ++c) dm[c] = warp_sum(dm[c]);
-        }
-        if (lane == 0) {
-            out[0] = cv;
-            out[1] = k0;
-            out[2] = dk;
-            out[3] = dm[0]; out[4] = dm[1]; out[5] = dm[2];
+    for (int c = 0; c < 3; ++c) {
+        sd[c] = sf[c] = sv[c] = R(0);
+        for (int w = 0; w < kCenWarps; ++w) {
+            sd[c] += sh[w][c][lane];
+            sf[c] += sh[w][3 + c][lane];
+            sv[c] += sh[w][6 + c][lane];
         }
     }
-    if (cellkick) {
-        __syncthreads();
-        if (i < N)
-            for (int c = 0; c < 3; ++c) {
+    // pass 2: the virial term sum_b (d_b - dbar) . f_b over this warp's beads and,
+    // in a cell, the closing B(dt/2) of the centroid with the cell's friction: the
+    // force kernel gave every bead the plain kick hdt f / m; the centroid velocity
+    // becomes vbar e2 + (hdt/m) fbar g2 (vbar before the kick)
+    R cvw = R(0), del[3] = {R(0), R(0), R(0)};
+    int ty = 0;
+    if (i < N) {
+        ty = d.typ[S.g0 + i];
+        R e2 = R(1), g2 = R(1), hd = R(0);
+        if (cellkick) {
+            e2 = kF32 ? (R)NC->e2f : (R)NC->e2;
+            g2 = kF32 ? (R)NC->g2f : (R)NC->g2;
+            hd = reinterpret_cast<const R *>(d.hdt_m)[ty];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const R dbar = sd[c] * invP;
+#pragma unroll
+            for (int k = 0; k < NB; ++k)
+                if (warp + k * kCenWarps < P) cvw = fma(dv[c][k] - dbar, fv[c][k], cvw);
+            if (cellkick) {
+                const R vb = sv[c] * invP, fb = hd * (sf[c] * invP);
+                del[c] = fma(vb - fb, e2, fb * g2) - vb;
                 const size_t o0 = (size_t)c * G + S.g0 + i;
-                const R del = (R)dlt[c][lane];
-                for (int b = warp; b < P; b += kCenWarps) V[o0 + (size_t)b * N] += del;
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                    const int b = warp + k * kCenWarps;
+                    if (b < P) V[o0 + (size_t)b * N] += del[c];
+                }
             }
+        }
+    }
+    scv[warp][lane] = cvw;
+    __syncthreads();
+    if (warp == 0) {
+        // per atom: the virial term, K_0 after the kick, and the kick's change of K
+        // and of the momentum; then the sums over the CTA's atoms (FP32 form in
+        // float-float, FP64 form in FP64)
+        R q[kCenQ];
+#pragma unroll
+        for (int u = 0; u < kCenQ; ++u) q[u] = R(0);
+        if (i < N) {
+            for (int w = 0; w < kCenWarps; ++w) q[0] += scv[w][lane];
+            const double mv = d.mass_mvv[ty];
+            const R hmP = (R)(0.5 * mv * P), mP = (R)(mv * (1.0 / kMvv2e) * P);
+            R k0 = R(0), dk = R(0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const R vb = sv[c] * invP, vn = vb + del[c];
+                k0 = fma(vn, vn, k0);
+                dk = fma(del[c], vn + vb, dk);
+                q[3 + c] = mP * del[c];
+            }
+            q[1] = hmP * k0;
+            q[2] = hmP * dk;
+        }
+        double out[kCenQ];
+#pragma unroll
+        for (int u = 0; u < kCenQ; ++u) {
+            if constexpr (kF32) {
+                FF a{(float)q[u], 0.f};
+                a.warp_reduce();
+                out[u] = (double)a.hi + (double)a.lo;
+            } else {
+                out[u] = warp_sum((double)q[u]);
+            }
+        }
+        if (lane == 0)
+            for (int u = 0; u < kCenQ; ++u) d.cpart[kCenQ * (size_t)cta + u] = out[u];
     }
     // the CTA that finishes a system last completes its record
     __threadfence();
@@ -205,21 +239,21 @@ __global__ void __launch_bounds__(32 * kCenWarps) k_centroid(Dev d, int j, int r
     __threadfence();
     double t[kCenQ];
 #pragma unroll
-    for (int q = 0; q < kCenQ; ++q) t[q] = 0.0;
+    for (int u = 0; u < kCenQ; ++u) t[u] = 0.0;
     for (int c = S.ccta0 + (int)threadIdx.x; c < S.ccta1; c += blockDim.x)
 #pragma unroll
-        for (int q = 0; q < kCenQ; ++q) t[q] += __ldcg(d.cpart + kCenQ * (size_t)c + q);
+        for (int u = 0; u < kCenQ; ++u) t[u] += __ldcg(d.cpart + kCenQ * (size_t)c + u);
 #pragma unroll
-    for (int q = 0; q < kCenQ; ++q) {
-        t[q] = warp_sum(t[q]);
-        if (lane == 0) fin[warp][q] = t[q];
+    for (int u = 0; u < kCenQ; ++u) {
+        t[u] = warp_sum(t[u]);
+        if (lane == 0) fin[warp][u] = t[u];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double tot[kCenQ];
-        for (int q = 0; q < kCenQ; ++q) {
-            tot[q] = 0.0;
-            for (int w = 0; w < kCenWarps; ++w) tot[q] += fin[w][q];
+        for (int u = 0; u < kCenQ; ++u) {
+            tot[u] = 0.0;
+            for (int w = 0; w < kCenWarps; ++w) tot[u] += fin[w][u];
         }
         const double cv = tot[0], k0 = tot[1];
         double *L = d.latest + (size_t)s * QTB_NREC;

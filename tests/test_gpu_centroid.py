@@ -65,7 +65,10 @@ def _check(obs, s, pot, oracle, x, v, step, potential, ext, tol):
         assert obs[18] == pytest.approx(1.5 * N * KB * s["T"], rel=1e-14)
         assert obs[19] == obs[1]
     assert abs(obs[18] - oo[18]) < tol * scale + 1e-13 * abs(oo[18])
-    assert abs(obs[19] - oo[19]) < tol * scale + 1e-12 * abs(oo[1])
+    # K_0 of slot 19: FP64 in the FP64 form; the FP32 form forms each atom's
+    # centroid kinetic energy in FP32 (float-float sums over atoms): ~1e-7 relative
+    k0_rel = 1e-12 if tol < 1e-6 else 1e-6
+    assert abs(obs[19] - oo[19]) < tol * scale + k0_rel * abs(oo[1])
     return oo
 
 
