@@ -1001,13 +1001,18 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     int ext_gx = 0;
     for (int s = 0; s < n_sys; ++s) ext_gx = std::max(ext_gx, (c->hs[s].N * c->hs[s].P + 127) / 128);
     long long nforce = 0;
+    int ngroups = 0;
     for (int s = 0; s < n_sys; ++s) {
         DSys &S = c->ds[s];
+        S.grp0 = S.ngrp = 0;
         if (c->pair) {
             // the system's replicas are consecutive, and so are their list force CTAs
             S.fcta0 = c->dr[S.rep0].fcta0;
             S.fcta1 = c->dr[S.rep0 + c->hs[s].P - 1].fcta0 + (c->hs[s].N + list_atoms(lanes) - 1) / list_atoms(lanes);
             nforce = S.fcta1;
+            S.grp0 = ngroups;
+            S.ngrp = (S.fcta1 - S.fcta0 + kRedGroup - 1) / kRedGroup;
+            ngroups += S.ngrp;
         } else {
             S.fcta0 = s * ext_gx;
             S.fcta1 = (s + 1) * ext_gx;
@@ -1146,6 +1151,10 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     d.eta = c->alloc(c->rsz * (size_t)kBlockSteps * (size_t)D);
     d.eta_blocks = 1;
     d.part = (double *)c->alloc(sizeof(double) * kNQ * (size_t)std::max(nforce, 1LL));
+    d.gpart = (double *)c->alloc(sizeof(double) * kNQ * (size_t)std::max(ngroups, 1));
+    d.gdone = (unsigned *)c->alloc(sizeof(unsigned) * (size_t)std::max(ngroups, 1));
+    if (!d.gpart || !d.gdone) return bail(fail(QTB_ERR_OOM, "device allocation failed"));
+    cudaMemsetAsync(d.gdone, 0, sizeof(unsigned) * (size_t)std::max(ngroups, 1), c->st);
     d.ipart = (double *)c->alloc(sizeof(double) * kNQ * (size_t)icta);
     d.latest = (double *)c->alloc(sizeof(double) * QTB_NREC * n_sys);
     d.series = (double *)c->alloc(sizeof(double) * QTB_NREC * (size_t)n_sys * p->max_records);

@@ -66,7 +66,7 @@ __global__ void k_reduce(Dev d, int j, int record)
     const long long step = d.clock[0] * kBlockSteps + j + 1;  // steps completed
     // during stepping only the recorded steps are reduced (record < 0: always)
     if (record >= 0 && step % d.obs_stride != 0) return;
-    reduce_system<false>(d, blockIdx.x, step, record, sh);
+    reduce_system<false>(d, blockIdx.x, step, record, sh, d.part, d.sys[blockIdx.x].fcta0, d.sys[blockIdx.x].fcta1);
 }
 
 // ---------------------------------------------------------------------------

@@ -687,13 +687,14 @@ __device__ __forceinline__ void pair_eval(const PairTabT<R> &T, const PairRow<R>
     e = en;
 }
 
-// Per-system reduction of the CTA partials into the observable record
+// Per-system reduction of the partials part[c0..c1) into the observable record
 // (fixed summation order).  Executed by one CTA; sh holds one row per warp.
 // FFP: the partials are float-float (hi, lo) pairs (FP32 list force kernel),
 // summed on the FP32 pipe; otherwise FP64.  The record's entries are then
 // formed in FP64, one per thread.
 template <bool FFP>
-static __device__ void reduce_system(const Dev &d, int s, long long step, int record, double (*sh)[kNQ + 1])
+static __device__ void reduce_system(const Dev &d, int s, long long step, int record, double (*sh)[kNQ + 1],
+                                     const double *part, int c0, int c1)
 {
     __shared__ double tot[kNQ + 1];
     const DSys S = d.sys[s];
@@ -704,11 +705,11 @@ static __device__ void reduce_system(const Dev &d, int s, long long step, int re
         for (int c = S.icta0 + (int)threadIdx.x; c < S.icta1; c += blockDim.x) sp += d.ipart[(size_t)c * kNQ + Q_SPRING];
     if (S.P > 1) sp = warp_sum(sp);
     if constexpr (FFP) {
-        const float2 *P2 = reinterpret_cast<const float2 *>(d.part);
+        const float2 *P2 = reinterpret_cast<const float2 *>(part);
         FF acc[kNQ];
 #pragma unroll
         for (int q = 0; q < kNQ; ++q) acc[q] = FF{0.f, 0.f};
-        for (int c = S.fcta0 + (int)threadIdx.x; c < S.fcta1; c += blockDim.x)
+        for (int c = c0 + (int)threadIdx.x; c < c1; c += blockDim.x)
 #pragma unroll
             for (int q = 0; q < kNQ; ++q) {
                 const float2 v = P2[(size_t)c * kNQ + q];
@@ -734,8 +735,8 @@ static __device__ void reduce_system(const Dev &d, int s, long long step, int re
     } else {
         double acc[kNQ];
         for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
-        for (int c = S.fcta0 + (int)threadIdx.x; c < S.fcta1; c += blockDim.x)
-            for (int q = 0; q < kNQ; ++q) acc[q] += d.part[(size_t)c * kNQ + q];
+        for (int c = c0 + (int)threadIdx.x; c < c1; c += blockDim.x)
+            for (int q = 0; q < kNQ; ++q) acc[q] += part[(size_t)c * kNQ + q];
         for (int q = 0; q < kNQ; ++q) acc[q] = warp_sum(acc[q]);
         if (lane == 0) {
             for (int q = 0; q < kNQ; ++q) sh[warp][q] = acc[q];
@@ -1133,22 +1134,62 @@ __device__ __forceinline__ void force_unit(const Dev &d, const PairTabT<R> &T, c
             for (int q = 0; q < kNQ; ++q) acc[q] = warp_sum(acc[q]);
             cta_store_partials(acc, red, d.part + (size_t)u * kNQ);
         }
-        // the CTA with the system's last unit reduces (partials made visible first)
+        // two levels, in fixed groups of kRedGroup consecutive units of the system:
+        // the CTA that finishes a group's last unit sums the group's partials (unit
+        // order), the one that finishes the system's last group forms the record
+        // from the group sums (group order); partials made visible first.  The
+        // order depends on the system's units only, so a system of a batch reduces
+        // as it would alone.
         __threadfence();
         __syncthreads();
+        const int g = (u - S.fcta0) / kRedGroup, gu0 = S.fcta0 + g * kRedGroup;
+        const int gn = min(kRedGroup, S.fcta1 - gu0);
         if (threadIdx.x == 0) {
-            const unsigned prev = atomicAdd(&d.done[RP.sys], 1u);
-            s_last = (prev == (unsigned)(S.fcta1 - S.fcta0 - 1)) ? 1 : 0;
+            const unsigned prev = atomicAdd(&d.gdone[S.grp0 + g], 1u);
+            s_last = (prev == (unsigned)(gn - 1)) ? 1 : 0;
         }
         __syncthreads();
         if (s_last) {
             __threadfence();
-            reduce_system<kFF>(d, RP.sys, step, kick ? 1 : -1, rsh);
-            if (threadIdx.x == 0) d.done[RP.sys] = 0u;
-            if (ADV && NC && kick) {
-                // the cell's update for the next step, from the record just formed
-                __syncthreads();
-                if (threadIdx.x == 0) cell_update<kFF>(d, RP.sys, step, cur ^ 1);
+            if (threadIdx.x < kNQ) {
+                const int q = threadIdx.x;
+                if constexpr (kFF) {
+                    const float2 *P2 = reinterpret_cast<const float2 *>(d.part);
+                    float2 v[kRedGroup];
+#pragma unroll
+                    for (int k = 0; k < kRedGroup; ++k)
+                        v[k] = (k < gn) ? __ldcg(P2 + (size_t)(gu0 + k) * kNQ + q) : make_float2(0.f, 0.f);
+                    FF t{0.f, 0.f};
+#pragma unroll
+                    for (int k = 0; k < kRedGroup; ++k) t.add_ff(v[k].x, v[k].y);
+                    reinterpret_cast<float2 *>(d.gpart)[(size_t)(S.grp0 + g) * kNQ + q] = make_float2(t.hi, t.lo);
+                } else {
+                    double v[kRedGroup];
+#pragma unroll
+                    for (int k = 0; k < kRedGroup; ++k) v[k] = (k < gn) ? __ldcg(d.part + (size_t)(gu0 + k) * kNQ + q) : 0.0;
+                    double t = 0.0;
+#pragma unroll
+                    for (int k = 0; k < kRedGroup; ++k) t += v[k];
+                    d.gpart[(size_t)(S.grp0 + g) * kNQ + q] = t;
+                }
+            }
+            if (threadIdx.x == 0) d.gdone[S.grp0 + g] = 0u;
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const unsigned prev = atomicAdd(&d.done[RP.sys], 1u);
+                s_last = (prev == (unsigned)(S.ngrp - 1)) ? 1 : 0;
+            }
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                reduce_system<kFF>(d, RP.sys, step, kick ? 1 : -1, rsh, d.gpart, S.grp0, S.grp0 + S.ngrp);
+                if (threadIdx.x == 0) d.done[RP.sys] = 0u;
+                if (ADV && NC && kick) {
+                    // the cell's update for the next step, from the record just formed
+                    __syncthreads();
+                    if (threadIdx.x == 0) cell_update<kFF>(d, RP.sys, step, cur ^ 1);
+                }
             }
         }
     }

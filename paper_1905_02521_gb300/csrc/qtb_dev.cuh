@@ -21,6 +21,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kBlockSteps = 256;     // noise block length (steps)
 constexpr int kDofPad = 128;         // per-system dof padding (tensor-core M tile)
 constexpr int kNQ = 16;              // partial sums per CTA (see Q_* below)
+constexpr int kRedGroup = 16;        // force units per group of the two-level record reduction
 constexpr int kFixBits = 30;         // fixed-point positions: box edge = 2^30 units
 constexpr int kMaxTypes = 4;
 constexpr int kWarpsPerForceCta = 8;  // warps of the list build kernel
@@ -78,6 +79,7 @@ struct DSys {
     int rep0;          // first replica (pair potential)
     int icta0, icta1;  // integrator CTA range
     int fcta0, fcta1;  // force CTA range
+    int grp0, ngrp;    // its groups of kRedGroup force units (two-level record reduction)
     int ccta0, ccta1;  // centroid-estimator CTA range (empty for one bead)
     int cell0, cell1;  // cells of all its replicas (pair potential)
     int rot0;          // offset of this system's mode rotation table
@@ -179,7 +181,9 @@ struct Dev {
     const void *hdt_m;    // [ntypes] dt / (2 m mvv2e) (R)
     const void *osig;     // [nsys * ntypes] sqrt((1 - c1^2)/(m mvv2e)) (R)
     // reductions
-    double *part;         // [CTAs][kNQ]
+    double *part;         // [CTAs][kNQ] (the FP32 list kernel: float-float pairs)
+    double *gpart;        // [groups][kNQ] sums of kRedGroup units' partials (list kernel)
+    unsigned *gdone;      // [groups] units finished, reset by the group's last one
     double *ipart;        // [integrator CTAs][kNQ]
     DNpt *npt;            // [nsys] isothermal-isobaric cells (null: constant volume)
     double *latest;       // [nsys][QTB_NREC]
@@ -187,7 +191,7 @@ struct Dev {
     long long *clock;     // [0] = current noise block
     unsigned *err;        // error word
     unsigned *done;       // [nsys] CTAs finished (last-CTA reduction), reset by the last one
-    double *cpart;        // [centroid CTAs][2] virial term, centroid kinetic energy
+    double *cpart;        // [centroid CTAs][kCenQ] virial term, K_0, the cell kick's dK and momentum
     const int *ccta_sys;  // [centroid CTAs] system of each CTA
     unsigned *cdone;      // [nsys] centroid CTAs finished, reset by the last one
     int stage_cap;        // staged neighbourhood entries per CTA of the list build kernel
