@@ -423,6 +423,14 @@ int qtb_filter_source(qtb_ctx *c, int sys, int *source);
  * overlap on the GPU, from different streams or threads, race. */
 int qtb_kappa_solve_noalloc(int P, int n, double y_max, double y0, double *F_dev, void *stream);
 
+/* Measured FP32 fused-multiply-add throughput of the current GPU (TFLOP/s), the
+ * denominator of the step kernel's roofline (no counterpart in the paper): every
+ * SM filled with threads running independent chains of dependent FMAs, the best
+ * of five timed launches of about 5 ms (*ms, may be NULL); FMA = 2 flops.  Runs on
+ * the default stream and synchronises; allocates and frees 1.2 MB of device
+ * memory.  QTB_ERR_ARG for a NULL tflops. */
+int qtb_fp32_peak(double *tflops, double *ms);
+
 void qtb_destroy(qtb_ctx *c);
 
 /* Message of the last failed call in this thread (never NULL). */

@@ -86,6 +86,7 @@ def lib():
             "qtb_get_step": ([vp, C.POINTER(ll)], i),
             "qtb_get_cell": ([vp, i, vp, C.POINTER(d)], i),
             "qtb_set_cell": ([vp, i, vp, d], i),
+            "qtb_fp32_peak": ([C.POINTER(d), C.POINTER(d)], i),
             "qtb_list_rebuilds": ([vp, C.POINTER(ll)], i),
             "qtb_rebuild_lists": ([vp], i),
             "qtb_wait_selftest": ([vp, C.POINTER(i), C.POINTER(d)], i),
@@ -356,6 +357,13 @@ def qtb_set_cell(ctx, sys, box, p_e):
     """Set the cell edges [3] (A, isotropic scale of the initial edges) and cell momentum (eV fs)."""
     box = np.ascontiguousarray(box, np.float64)
     _check(lib().qtb_set_cell(ctx, sys, box.ctypes.data, float(p_e)))
+
+
+def qtb_fp32_peak():
+    """(measured FP32 FMA throughput in TFLOP/s, best launch time in ms) of the current GPU."""
+    t, ms = C.c_double(0.0), C.c_double(0.0)
+    _check(lib().qtb_fp32_peak(C.byref(t), C.byref(ms)))
+    return t.value, ms.value
 
 
 def qtb_set_profiling(ctx, enable=True):

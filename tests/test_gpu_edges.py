@@ -148,3 +148,17 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable(qtb):
         assert obs[0] == 20 and np.all(np.isfinite(obs))
     finally:
         qtb.qtb_destroy(ctx)
+
+
+def test_fp32_peak_is_measured_and_plausible(qtb):
+    # the step kernel's roofline denominator: FMA chains filling every SM; between
+    # half and 1.05 of the nominal 152 SMs x 128 lanes x 2 flops at the highest SM
+    # clock this GPU reports
+    import torch
+    t, ms = qtb.qtb_fp32_peak()
+    mhz = torch.cuda.get_device_properties(0).clock_rate / 1e3 if hasattr(
+        torch.cuda.get_device_properties(0), "clock_rate") else 2070.0
+    nominal = 152 * 128 * 2 * max(mhz, 2070.0) * 1e6 / 1e12
+    print(f"FP32 FMA peak {t:.1f} TFLOP/s in {ms:.2f} ms (nominal {nominal:.1f})")
+    assert 0.5 * nominal < t < 1.05 * nominal
+    assert ms > 0.5
