@@ -208,7 +208,8 @@ int qtb_set_generator(qtb_ctx *c, int generator, int segment_blocks);
  * does not fix the integrator; the reading used is BAOAB: a half kick by the
  * forces (B), the exact free ring-polymer motion for dt/2 per normal mode (A),
  * the friction and random force over dt (O: v <- c1 v + sqrt((1 - c1^2)/m) eta,
- * c1 = exp(-gamma dt)), A, new forces, B.  Whole 256-step noise blocks run as
+ * c1 = exp(-gamma dt)), A, new forces, B.  With qtb_params.npt the cell's
+ * equations (given there) join every step.  Whole 256-step noise blocks run as
  * one CUDA-graph launch.  n_steps >= 0 (0: no-op). */
 int qtb_step_n(qtb_ctx *c, long long n_steps);
 
@@ -219,8 +220,9 @@ int qtb_sync(qtb_ctx *c);
  * above): the kinetic and potential energies and the primitive energy
  * estimator of Eq. 5 (E = K - spring + V, with the spring term of Eq. 3 and
  * V/P per replica of Eq. 4), the virial, the total momentum, the mean square
- * position and the centroid-virial kinetic estimators.  Synchronises; returns
- * a device-side error of an earlier step if one was raised. */
+ * position, the centroid-virial kinetic estimators, the cell volume and the
+ * centroid kinetic energy and virial.  Synchronises once; returns a device-side
+ * error of an earlier step if one was raised (out is then filled as it is). */
 int qtb_observables(qtb_ctx *c, int sys, double *out);
 
 /* All records kept for system sys, oldest first: out[max][QTB_NREC]; *n_out =

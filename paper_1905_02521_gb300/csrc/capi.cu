@@ -210,11 +210,18 @@ void fit_erfcx(double xmax, double c[12])
         for (int j = 0; j < n; ++j) c[j] += a[k] * Tm[k][j];
 }
 
+static int decode_err_word(qtb_ctx *c, unsigned e);
+
 int check_err_word(qtb_ctx *c)
 {
     unsigned e = 0;
     CUDA_TRY(cudaMemcpyAsync(&e, c->d.err, sizeof e, cudaMemcpyDeviceToHost, c->st));
     CUDA_TRY(cudaStreamSynchronize(c->st));
+    return decode_err_word(c, e);
+}
+
+static int decode_err_word(qtb_ctx *c, unsigned e)
+{
     if (e & ERR_OVERFLOW) return fail(QTB_ERR_OVERFLOW, "a cell-list cell exceeded its capacity (%d)", c->d.cap);
     if (e & ERR_NBR_OVERFLOW)
         return fail(QTB_ERR_OVERFLOW, "a neighbour list exceeded its capacity (%d entries)", c->d.maxnb);
@@ -1345,12 +1352,14 @@ int qtb_observables(qtb_ctx *c, int sys, double *out)
     if (!c || !out) return fail(QTB_ERR_ARG, "null argument");
     if (sys < 0 || sys >= (int)c->hs.size()) return fail(QTB_ERR_ARG, "system %d out of range", sys);
     if (int rc0 = ensure_fresh(c)) return rc0;
-    int rc = check_err_word(c);
-    if (rc) return rc;
+    // the error word and the record in one synchronisation (on an error the
+    // record is returned as it is, with the error code)
+    unsigned e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, c->d.err, sizeof e, cudaMemcpyDeviceToHost, c->st));
     CUDA_TRY(cudaMemcpyAsync(out, c->d.latest + (size_t)sys * QTB_NREC, sizeof(double) * QTB_NREC,
                              cudaMemcpyDeviceToHost, c->st));
     CUDA_TRY(cudaStreamSynchronize(c->st));
-    return QTB_OK;
+    return decode_err_word(c, e);
 }
 
 int qtb_get_series(qtb_ctx *c, int sys, double *out, int max, int *n_out)
