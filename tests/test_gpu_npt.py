@@ -496,3 +496,69 @@ def test_batched_cells_match_single_runs(qtb, precision):
             assert np.array_equal(box, batched[k][1][0]) and pe == batched[k][1][1]
         finally:
             qtb.qtb_destroy(c1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_ring_polymer_cells_match_single_runs(qtb, precision):
+    # two ring-polymer crystals (P = 4 and 2) in one isothermal-isobaric context:
+    # each system's record is reduced in groups of its own force units and its
+    # centroid kernel CTAs are its own, so each runs bit for bit as alone
+    sa, pot = W.mgo_system(2, 200.0, gamma=2e-3, seed=61, n_beads=4)
+    sb, _ = W.mgo_system(3, 500.0, gamma=2e-3, seed=62, n_beads=2)
+    npt = {"pressure": 0.002, "mass": _cell_mass(B_MGO, np.prod(sb["box"]), 200.0), "gamma": 5e-3}
+    ctx = gpu_ctx(qtb, [sa, sb], pot, 1.0, precision=precision, seed=7, npt=npt)
+    try:
+        qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB_PIMD, 513, 0.3)
+        qtb.qtb_step_n(ctx, 300)
+        batched = [(qtb.qtb_get_state(ctx, k, s["pos"].shape[0], len(s["types"])), qtb.qtb_get_cell(ctx, k))
+                   for k, s in enumerate((sa, sb))]
+    finally:
+        qtb.qtb_destroy(ctx)
+    for k, s in enumerate((sa, sb)):
+        c1 = gpu_ctx(qtb, [s], pot, 1.0, precision=precision, seed=7 ^ (k << 32), npt=npt)
+        try:
+            if k == 0:
+                qtb.qtb_set_filter(c1, 0, qtb.NOISE_QTB_PIMD, 513, 0.3)
+            qtb.qtb_step_n(c1, 300)
+            x, v = qtb.qtb_get_state(c1, 0, s["pos"].shape[0], len(s["types"]))
+            box, pe = qtb.qtb_get_cell(c1, 0)
+            assert np.array_equal(x, batched[k][0][0]) and np.array_equal(v, batched[k][0][1])
+            assert np.array_equal(box, batched[k][1][0]) and pe == batched[k][1][1]
+        finally:
+            qtb.qtb_destroy(c1)
+
+
+def test_ring_polymer_set_cell_then_state_continues_like_the_oracle(qtb, oracle):
+    # P = 4 FP64: a cell and state set mid-run, then 30 steps against the oracle
+    # started from the same cell, state and step (the internal modes rescale with
+    # the cell from the set scale on)
+    P = 4
+    s, pot = W.mgo_system(2, 300.0, gamma=2e-3, n_beads=P, seed=93)
+    N = len(s["types"])
+    npt = {"pressure": 0.001, "mass": _cell_mass(B_MGO, np.prod(s["box"]), 200.0), "gamma": 5e-3}
+    taps = S.taps(513, 1.0, 300.0, 0.3, P=P, sol=S.kappa_solve(P))
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=0, seed=31, npt=npt)
+    try:
+        qtb.qtb_set_filter(ctx, 0, qtb.NOISE_QTB_PIMD, 513, 0.3)
+        qtb.qtb_step_n(ctx, 20)
+        x0, v0 = qtb.qtb_get_state(ctx, 0, P, N)
+        box0, pe0 = qtb.qtb_get_cell(ctx, 0)
+        box1, pe1 = box0 * 0.997, 0.5 * pe0 - 0.02
+        x1 = _unwrap_beads(x0, box0) * 0.997
+        qtb.qtb_set_cell(ctx, 0, box1, pe1)
+        qtb.qtb_set_state(ctx, 0, x1, v0)
+        sim = oracle_sim(oracle, s, pot, 1.0, seed=31, taps=taps, npt=npt)
+        sim.set_cell(box1, pe1, 1)
+        sim.set_state(x1, v0, 20)
+        for step in range(30):
+            qtb.qtb_step_n(ctx, 1)
+            sim.step(1, record=False)
+            box_g, pe_g = qtb.qtb_get_cell(ctx, 0)
+            box_o, pe_o = sim.cell()
+            assert np.abs(box_g / box_o - 1).max() < 1e-12, (step, box_g, box_o)
+            assert pe_g == pytest.approx(pe_o, rel=1e-9, abs=1e-12)
+            xg, vg = qtb.qtb_get_state(ctx, 0, P, N)
+            xo, vo, _, _ = sim.state()
+            assert np.abs(minimg(xg - xo, box_o)).max() < 1e-10 and rel_inf(vg, vo) < 1e-10
+    finally:
+        qtb.qtb_destroy(ctx)
