@@ -1612,6 +1612,15 @@ int qtb_set_cell(qtb_ctx *c, int sys, const double *box, double p_e)
     return QTB_OK;
 }
 
+int qtb_fp32_peak(double *tflops, double *ms)
+{
+    if (!tflops) return fail(QTB_ERR_ARG, "qtb_fp32_peak: null tflops");
+    const int rc = measure_fp32_peak(tflops, ms);
+    if (rc == QTB_ERR_OOM) return fail(rc, "qtb_fp32_peak: device allocation failed");
+    if (rc != QTB_OK) return fail(rc, "qtb_fp32_peak: CUDA error %s", cudaGetErrorString(cudaGetLastError()));
+    return QTB_OK;
+}
+
 int qtb_kappa_solve(int P, int n, double y_max, double y0, double *F)
 {
     if (P < 1 || n < 8 || !(y_max > 0) || !(y0 > 0) || !F) return fail(QTB_ERR_ARG, "qtb_kappa_solve: bad arguments");

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "qtb.h"
+#include "qtb_kernels.cuh"
 
 namespace qtb {
 
@@ -34,12 +35,10 @@ __global__ void __launch_bounds__(kPeakThreads) k_fma_peak(float *out, int iters
     if (store) out[blockIdx.x * kPeakThreads + threadIdx.x] = s;
 }
 
-}  // namespace qtb
-
-extern "C" int qtb_fp32_peak(double *tflops, double *ms)
+// The measurement behind qtb_fp32_peak (which reports errors by name): QTB_OK,
+// QTB_ERR_CUDA or QTB_ERR_OOM.
+int measure_fp32_peak(double *tflops, double *ms)
 {
-    using namespace qtb;
-    if (!tflops) return QTB_ERR_ARG;
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return QTB_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QTB_ERR_CUDA;
@@ -79,3 +78,5 @@ extern "C" int qtb_fp32_peak(double *tflops, double *ms)
     if (ms) *ms = best;
     return QTB_OK;
 }
+
+}  // namespace qtb

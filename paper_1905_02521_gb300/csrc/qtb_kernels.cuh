@@ -111,6 +111,7 @@ void launch_store_state(const Dev &d, const MdLaunch &m, int s, long long n3, in
 void launch_refresh_check(const Dev &d, const MdLaunch &m, int cur, cudaStream_t st);
 // isothermal-isobaric cells: update at the start of step j (see md.cu)
 void launch_cell(const Dev &d, int j, bool fp32, cudaStream_t st);
+int measure_fp32_peak(double *tflops, double *ms);  // peak.cu
 // words[0]: a flag nothing sets; words[1]: set to 1 when the bounded wait gives up
 void launch_wait_selftest(unsigned *words, cudaStream_t st);
 void launch_tick(const Dev &d, cudaStream_t st);
