@@ -942,6 +942,12 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         S.c1_f = (float)S.c1;
         S.skin2 = 0.25 * c->skin * c->skin;
         S.skin2_f = (float)S.skin2;
+        {   // isothermal-isobaric: the particles' share of the skin (0.999: FP32 slack)
+            const double tol = kNptCellSkin * c->skin / (p->r_cut + c->skin);
+            const double D = 0.999 * 0.5 * (c->skin * (1.0 - tol) - tol * p->r_cut);
+            S.npt_d2 = D * D;
+            S.npt_d2_f = (float)S.npt_d2;
+        }
         for (int k = 0; k < 3; ++k) {
             S.fix_scale[k] = (float)(q.box[k] / (double)(1 << kFixBits));
             S.fix_inv[k] = (q.box[k] > 0) ? (float)((double)(1 << kFixBits) / q.box[k]) : 0.f;
@@ -1188,7 +1194,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
             C.e1f = C.g1f = C.e2f = C.g2f = C.lamf = 1.0f;
             C.a1f = C.a2f = (float)(0.5 * p->dt);
             C.inv_wf = (float)(1.0 / p->cell_mass);
-            C.rb_tol = 0.25 * c->skin / (p->r_cut + c->skin);
+            C.rb_tol = kNptCellSkin * c->skin / (p->r_cut + c->skin);
             C.lam_old = C.inv_lam = 1.0;
             C.lam_oldf = C.inv_lamf = 1.0f;
             C.on = 1;

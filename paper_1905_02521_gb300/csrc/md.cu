@@ -439,9 +439,9 @@ __global__ void k_refresh_check(Dev d, int cur)
         const DSys &S = d.sys[s];
         const long long gn = (long long)S.N * S.P;
         R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
-        if (d.npt && d.npt[s].on) {  // as the integrator: physical displacement against (3/8 skin)^2
+        if (d.npt && d.npt[s].on) {  // as the integrator: physical displacement against D^2
             const R l = (R)d.npt[s].lam;
-            lim = lim * R(0.5625) / (l * l);
+            lim = (sizeof(R) == 4 ? (R)S.npt_d2_f : (R)S.npt_d2) / (l * l);
         }
         bool moved = false;
         for (long long l = ((tid - S.g0) % nth + nth) % nth; l < gn; l += nth) {

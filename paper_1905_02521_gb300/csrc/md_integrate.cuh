@@ -154,11 +154,11 @@ __global__ void __launch_bounds__(128) k_integrate(Dev d, int j, int cur)
                           __shfl_sync(0xffffffffu, dd, (l0 + 2) & 31);
             R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
             if (NC) {
-                // physical displacement (lam times the reference one) against (3/8 skin)^2:
-                // the other quarter of the skin is the cell kernel's margin for the
-                // change of lam since the rebuild
+                // physical displacement (lam times the reference one) against D^2 (the
+                // rest of the skin is the cell kernel's margin for the change of lam
+                // since the rebuild; see kNptCellSkin)
                 const R l = sizeof(R) == 4 ? (R)NC->lamf : (R)NC->lam;
-                lim = lim * R(0.5625) / (l * l);
+                lim = (sizeof(R) == 4 ? (R)S.npt_d2_f : (R)S.npt_d2) / (l * l);
             }
             moved |= act && c == 0 && tot > lim;
         }
@@ -477,9 +477,9 @@ __global__ void __launch_bounds__(nm_threads(P, BIG)) k_integrate_nm(Dev d, int 
     R lim = sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2;
     double l2 = 1.0;  // physical length squared over stored (cell)
     if (NC) {
-        // physical displacement against (3/8 skin)^2 (see k_integrate)
+        // physical displacement against D^2 (see k_integrate)
         const R l = sizeof(R) == 4 ? (R)NC->lamf : (R)NC->lam;
-        lim = lim * R(0.5625) / (l * l);
+        lim = (sizeof(R) == 4 ? (R)S.npt_d2_f : (R)S.npt_d2) / (l * l);
         l2 = NC->lam * NC->lam;
     }
 #pragma unroll

@@ -802,7 +802,7 @@ static __device__ void reduce_system(const Dev &d, int s, long long step, int re
 //       xi from Philox stream 1, dof 0, step n;
 //   A(dt/2) with the new v_e (a2, lam), and the closing B(dt/2) factors e2, g2.
 // A list rebuild is requested for this step's force launch when the cell scale
-// has moved by more than skin/4 over the list radius since the system's last
+// has moved by more than kNptCellSkin skin over the list radius since the system's last
 // rebuild; a cell below kCellMinScale raises ERR_CELL.
 // FP32 form: the transcendental factors in FP32 (this GPU's FP64 rate is a small
 // fraction of its FP32 rate and the kernel is one thread's dependent chain); the
@@ -1244,12 +1244,12 @@ __device__ void npt_next_half(const Dev &d, int j1, int nxt)
         }
         if (t < 3 * NA) sdd[t] = dd;
         __syncthreads();
-        // the physical displacement (lam times the reference one) against (3/8 skin)^2
+        // the physical displacement (lam times the reference one) against D^2 (DSys::npt_d2)
         bool moved = false;
         if (act && c == 0) {
             const R tot = sdd[t] + sdd[t + 1] + sdd[t + 2];
             const R l = sizeof(R) == 4 ? (R)NC->lamf : (R)NC->lam;
-            const R lim = (sizeof(R) == 4 ? (R)S.skin2_f : (R)S.skin2) * R(0.5625) / (l * l);
+            const R lim = (sizeof(R) == 4 ? (R)S.npt_d2_f : (R)S.npt_d2) / (l * l);
             moved = tot > lim;
         }
         if (__syncthreads_or(moved) && threadIdx.x == 0) {

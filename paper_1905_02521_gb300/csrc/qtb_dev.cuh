@@ -44,6 +44,15 @@ enum { ERR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_SOLVE = 4, ERR_TIMEOUT_TC = 8, E
 // cell kernel updates the cell at the start of each step and leaves there the
 // step's coefficients for the integrator and the step kernel.
 constexpr double kCellMinScale = 0.9;  // smallest lam the cell lists are sized for
+// Isothermal-isobaric runs split the list skin between the cell and the
+// particles: a rebuild when lam has moved by more than tol lam_rb since the last
+// rebuild (tol = kNptCellSkin skin / r_list) or a bead-atom by more than D
+// (physical).  A pair within r_cut now was within (lam_rb/lam) r_cut + 2 lam_rb d
+// <= (r_cut tol + 2 D)/(1 - tol) of each other at the rebuild, which D = (skin
+// (1 - tol) - tol r_cut)/2 makes r_cut + skin: the lists hold it.  The cell's
+// volume fluctuates by a few tenths of a percent in lam, so an eighth of the skin
+// (over the list radius) leaves most of the skin to the particles.
+constexpr double kNptCellSkin = 0.125;
 struct DNpt {
     double lam, lam_rb, peps;  // cell scale, its value at the system's last list rebuild, cell momentum (eV fs)
     double W, pext, ce, sige, alpha, V0;  // mass, P_ext, exp(-gamma_e dt), sqrt((1 - ce^2) W kT), 1 + 3/N_f, V at lam 1
@@ -53,7 +62,7 @@ struct DNpt {
     float e1f, g1f, a1f, a2f, e2f, g2f, lamf, inv_wf;  // the FP32 form's coefficients, 1/W
     int on, pending;  // barostat on; the previous step's closing half kick of the cell is due
     int pad2[2];
-    double rb_tol;    // list rebuild when |lam - lam_rb| > rb_tol lam_rb (skin/4 over the list radius)
+    double rb_tol;    // list rebuild when |lam - lam_rb| > rb_tol lam_rb (kNptCellSkin skin over the list radius)
     double lam_old, inv_lam;  // this step's lam before the update and 1/lam after (ring polymers)
     float lam_oldf, inv_lamf;
 };
@@ -94,6 +103,11 @@ struct DSys {
     // rebuild; squared, in A^2
     double skin2;
     float skin2_f;
+    // isothermal-isobaric cells: the physical displacement D allowed since the
+    // last rebuild, squared (A^2), D = (skin (1 - tol) - tol r_cut)/2 with the
+    // cell's share tol = kNptCellSkin skin / (r_cut + skin) of the list radius
+    double npt_d2;
+    float npt_d2_f;
 };
 
 struct DRep {          // one replica (system, bead) of a pair-potential system
