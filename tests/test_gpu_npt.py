@@ -8,6 +8,7 @@ isothermal-isobaric law.
 * mixed form: one step from the GPU's own state and cell against the oracle's
   FP64 step (positions and cell 1e-5, velocities 1e-5 norm-wise);
 * the ideal gas samples P(V) ~ V^N exp(-P V / k_B T): <V> = (N + 1) k_B T / P;
+* a cold crystal's volume fluctuations give its bulk modulus: var(V) = k_B T V / B;
 * ring polymers (the cell on the centroid modes): the FP64 form against the
   oracle after each of 60 QTB-PIMD steps, one mixed step against the oracle's,
   the ideal gas's volume law with P = 4 beads;
@@ -359,6 +360,40 @@ def test_lih_lattice_parameter_qtb_pimd_converges_faster_than_pimd(qtb):
     assert abs(res[(150.0, "qtb_pimd8")][0] - res[(150.0, "pimd32")][0]) < \
         abs(res[(150.0, "pimd8")][0] - res[(150.0, "pimd32")][0])
     assert res[(150.0, "pimd32")][0] - res[(150.0, "pimd32_D")][0] > 4 * sig((150.0, "pimd32"), (150.0, "pimd32_D"))
+
+
+def test_crystal_volume_fluctuations_match_bulk_modulus_on_gpu(qtb, oracle):
+    # 216-ion MgO at 20 K (white bath, zero pressure, mixed form): the volume
+    # fluctuates about the static minimum with var(V) = k_B T V / B, B = V d^2E/dV^2
+    # of the perfect lattice from the oracle's own energies (the compressibility
+    # of the harmonic crystal, which the cell equations must reproduce)
+    from scipy.optimize import minimize_scalar
+    pot = W.mgo_potential()
+
+    def E(a):
+        p, t, b = W.rocksalt(1, a, sigma=0.0)
+        return oracle.pair_forces(p, t, b, pot)[1]
+    a0 = minimize_scalar(E, bracket=(4.1, 4.13, 4.16), tol=1e-10).x
+    h = 1e-3 * a0 ** 3
+    EV = lambda V: E(V ** (1.0 / 3.0))  # noqa: E731
+    B = a0 ** 3 * (EV(a0 ** 3 + h) - 2 * EV(a0 ** 3) + EV(a0 ** 3 - h)) / h ** 2
+    T = 20.0
+    s, _ = W.mgo_system(3, T, gamma=1e-2, sigma=0.0, seed=5)
+    s["pos"] = W.rocksalt(3, a0, sigma=0.0)[0][None]
+    s["box"] = np.array([3 * a0] * 3)
+    V0 = np.prod(s["box"])
+    npt = {"pressure": 0.0, "mass": _cell_mass(B, V0, 200.0), "gamma": 0.01}
+    ctx = gpu_ctx(qtb, [s], pot, 1.0, precision=1, seed=13, npt=npt, obs_stride=16, max_records=8192)
+    try:
+        qtb.qtb_step_n(ctx, 4096)
+        qtb.qtb_step_n(ctx, 16 * 6144)
+        V = qtb.qtb_get_series(ctx, 0, 6144)[:, 20]
+    finally:
+        qtb.qtb_destroy(ctx)
+    ratio = V.var() / (KB * T * V0 / B)
+    print(f"B = {B:.3f} eV/A^3, <V>/V0 - 1 = {V.mean() / V0 - 1:.2e}, var(V) / (k_B T V / B) = {ratio:.3f}")
+    assert V.mean() == pytest.approx(V0, rel=2e-3)
+    assert ratio == pytest.approx(1.0, abs=0.2)
 
 
 def test_constant_volume_cell_and_volume_slot(qtb):
