@@ -393,7 +393,7 @@ def run_ours(args):
         "config": {"workload": desc, "name": args.workload, "systems": len(systems),
                    "atom_beads_per_md_step": units, "md_steps_per_bench_step": BLOCK, "precision": args.precision,
                    "filter": filt if setup is not None else "none (white noise)", "parallelism": f"replicas x{ws}",
-                   "skin_A": params["skin"] if params["skin"] else "default",
+                   "skin_A": params["skin"] if params["skin"] else "default: per system min(r_cut/4, 0.8 max(1, sqrt(T/300 K)))",
                    "list_lanes": params.get("list_lanes") or "default (16)",
                    "rebuild_scope": "all systems" if params.get("rebuild_scope") else "requesting systems",
                    "autotune": tuning,

@@ -111,7 +111,9 @@ typedef struct {
     double skin;           /* PAIR: Verlet-list skin, A, < r_cut/2.  Lists hold every
                               pair within r_cut + skin and are rebuilt (on the device)
                               once some bead-atom has moved skin/2 since the last
-                              rebuild.  0 selects min(0.8, r_cut/4); < 0: no skin.
+                              rebuild.  0 selects, per system, min(r_cut/4,
+                              0.8 max(1, sqrt(T/300 K))) (hot systems move further
+                              between rebuilds); < 0: no skin.
                               Forces do not depend on it (up to summation order). */
     int nm_layout;         /* ring-polymer integrator (n_beads > 1): 0 auto, 1 compact
                               (8-32 atoms per CTA, more CTAs; small contexts), 2 wide (32

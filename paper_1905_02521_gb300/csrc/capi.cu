@@ -59,7 +59,8 @@ int qtb::set_last_error(int code, const char *msg)
 
 struct qtb_ctx {
     cudaStream_t st = nullptr;
-    double skin = 0.0;           // neighbour-list skin, A
+    double skin = 0.0;           // largest neighbour-list skin of the systems, A
+    std::vector<double> skins;   // each system's skin, A
     qtb_params p{};
     std::vector<double> mass, charge, bA, brho, bC;
     bool mixed = false, pair = true;
@@ -701,10 +702,13 @@ int rebuild_filters(qtb_ctx *c)
     return QTB_OK;
 }
 
-// skin of the neighbour lists: 0 selects min(0.8 A, r_cut/4), < 0 means none
-double effective_skin(const qtb_params *p)
+// skin of system s's neighbour lists: a given skin (> 0) for every system, none
+// (< 0), or (0) min(r_cut/4, 0.8 A max(1, sqrt(T/300 K))): the thermal
+// excursions that decide the rebuild rate grow as sqrt(T), and a hot system of a
+// batch would otherwise rebuild on almost every step
+double effective_skin(const qtb_params *p, double T)
 {
-    if (p->skin == 0.0) return std::min(0.8, 0.25 * p->r_cut);
+    if (p->skin == 0.0) return std::min(0.25 * p->r_cut, 0.8 * std::max(1.0, std::sqrt(T / 300.0)));
     return p->skin < 0.0 ? 0.0 : p->skin;
 }
 
@@ -731,7 +735,7 @@ int validate(const qtb_system *sys, int n_sys, const qtb_params *p)
     if (p->potential == QTB_POT_PAIR) {
         if (!p->charge || !p->buck_A || !p->buck_rho || !p->buck_C) return fail(QTB_ERR_ARG, "pair tables missing");
         if (!(p->r_cut > 0)) return fail(QTB_ERR_ARG, "r_cut must be > 0");
-        if (!(effective_skin(p) < 0.5 * p->r_cut)) return fail(QTB_ERR_ARG, "skin must be < r_cut/2");
+        if (!(effective_skin(p, 0.0) < 0.5 * p->r_cut)) return fail(QTB_ERR_ARG, "skin must be < r_cut/2");
     }
     for (int s = 0; s < n_sys; ++s) {
         const qtb_system &q = sys[s];
@@ -774,7 +778,12 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         c->own_stream = true;
     }
     c->p = *p;
-    c->skin = effective_skin(p);
+    c->skins.resize(n_sys);
+    c->skin = 0.0;  // the largest of the systems' skins
+    for (int s = 0; s < n_sys; ++s) {
+        c->skins[s] = effective_skin(p, sys[s].T);
+        c->skin = std::max(c->skin, c->skins[s]);
+    }
     const int nt = p->n_types;
     c->mass.assign(p->mass, p->mass + nt);
     c->mixed = (p->precision == QTB_MIXED);
@@ -866,7 +875,8 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     // Neighbour lists within r_list = r_cut + skin, built from cells >=
     // r_list/2 with a 5^3 stencil whose neighbourhood streams through shared
     // memory in chunks.
-    const double r_list = p->r_cut + c->skin;
+    // (each system's list radius r_cut + its skin; the pair table keeps the largest)
+    auto r_list_of = [&](int s) { return p->r_cut + c->skins[s]; };
     auto cell_cap = [&](const qtb_system &q, double edge) {
         int nc[3];
         for (int k = 0; k < 3; ++k) nc[k] = std::max(1, (int)std::floor(q.box[k] / edge));
@@ -876,13 +886,14 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     };
     // an isothermal-isobaric cell may shrink to kCellMinScale of its edges: the
     // cells (in the reference cell) and the lists keep that margin
-    const double cell_edge = 0.5 * r_list / (p->npt ? kCellMinScale : 1.0);
+    auto cell_edge_of = [&](int s) { return 0.5 * r_list_of(s) / (p->npt ? kCellMinScale : 1.0); };
     const double dens_margin = p->npt ? 1.0 / (kCellMinScale * kCellMinScale * kCellMinScale) : 1.0;
     int stage_cap = 0, maxnb = 32;
     if (c->pair) {
         double ecell = 0.0;
-        const double vlist = 4.0 / 3.0 * kPi * r_list * r_list * r_list;
         for (int s = 0; s < n_sys; ++s) {
+            const double r_list = r_list_of(s), cell_edge = cell_edge_of(s);
+            const double vlist = 4.0 / 3.0 * kPi * r_list * r_list * r_list;
             int nc[3];
             for (int k = 0; k < 3; ++k) nc[k] = std::max(1, (int)std::floor(sys[s].box[k] / cell_edge));
             ecell = std::max(ecell, (double)sys[s].n_atoms / (nc[0] * nc[1] * nc[2]));
@@ -940,11 +951,14 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         S.invP = 1.0 / h.P;
         S.invP_f = (float)S.invP;
         S.c1_f = (float)S.c1;
-        S.skin2 = 0.25 * c->skin * c->skin;
+        const double skin = c->skins[s];
+        S.skin2 = 0.25 * skin * skin;
         S.skin2_f = (float)S.skin2;
+        S.rl2 = (p->r_cut + skin) * (p->r_cut + skin);
+        S.rl2_f = (float)S.rl2;
         {   // isothermal-isobaric: the particles' share of the skin (0.999: FP32 slack)
-            const double tol = kNptCellSkin * c->skin / (p->r_cut + c->skin);
-            const double D = 0.999 * 0.5 * (c->skin * (1.0 - tol) - tol * p->r_cut);
+            const double tol = kNptCellSkin * skin / (p->r_cut + skin);
+            const double D = 0.999 * 0.5 * (skin * (1.0 - tol) - tol * p->r_cut);
             S.npt_d2 = D * D;
             S.npt_d2_f = (float)S.npt_d2;
         }
@@ -967,9 +981,9 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
         c->max_dofp = std::max(c->max_dofp, S.dofp);
         if (c->pair) {
             int nc[3];
-            for (int k = 0; k < 3; ++k) nc[k] = std::max(1, (int)std::floor(q.box[k] / cell_edge));
+            for (int k = 0; k < 3; ++k) nc[k] = std::max(1, (int)std::floor(q.box[k] / cell_edge_of(s)));
             const int cells = nc[0] * nc[1] * nc[2];
-            cap = std::max(cap, cell_cap(q, cell_edge));
+            cap = std::max(cap, cell_cap(q, cell_edge_of(s)));
             for (int b = 0; b < h.P; ++b) {
                 DRep R;
                 memset(&R, 0, sizeof R);
@@ -1008,7 +1022,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
     c->ml.minimg = (c->pair && c->mixed && !p->npt) ? 1 : 0;
     for (int s = 0; s < n_sys && c->ml.minimg; ++s)
         for (int k = 0; k < 3; ++k)
-            if (!(sys[s].box[k] > 2.0 * (p->r_cut + 2.0 * c->skin))) c->ml.minimg = 0;
+            if (!(sys[s].box[k] > 2.0 * (p->r_cut + 2.0 * c->skins[s]))) c->ml.minimg = 0;
     if (c->pair && step_prepare(c->ml, stage_cap) != cudaSuccess)
         return bail(fail(QTB_ERR_CUDA, "cannot prepare the cooperative step kernel (shared memory, occupancy)"));
     int ext_gx = 0;
@@ -1194,7 +1208,7 @@ int qtb_init(qtb_ctx **out, const qtb_system *sys, int n_sys, const qtb_params *
             C.e1f = C.g1f = C.e2f = C.g2f = C.lamf = 1.0f;
             C.a1f = C.a2f = (float)(0.5 * p->dt);
             C.inv_wf = (float)(1.0 / p->cell_mass);
-            C.rb_tol = kNptCellSkin * c->skin / (p->r_cut + c->skin);
+            C.rb_tol = kNptCellSkin * c->skins[s] / (p->r_cut + c->skins[s]);
             C.lam_old = C.inv_lam = 1.0;
             C.lam_oldf = C.inv_lamf = 1.0f;
             C.on = 1;

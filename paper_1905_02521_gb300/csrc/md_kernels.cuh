@@ -1299,7 +1299,7 @@ __global__ void __launch_bounds__(32 * kListWarps, sizeof(R) == 4 ? (REC ? 4 : 7
             if (!d.rebuild_all && d.rflag[cur * d.nsys + s] == 0u) continue;  // uniform over the grid
             const int c0 = d.sys[s].cell0, c1 = d.sys[s].cell1, nb = (int)gridDim.x;
             for (int cell = c0 + (((int)blockIdx.x - c0) % nb + nb) % nb; cell < c1; cell += nb)
-                build_cell<PM, R>(d, T.rc2, T.rl2, cell, fsm, B);
+                build_cell<PM, R>(d, T.rc2, sizeof(R) == 4 ? (R)d.sys[s].rl2_f : (R)d.sys[s].rl2, cell, fsm, B);
         }
         grid_barrier(d);
         // the per-system requests were read by every phase: consumed now (their

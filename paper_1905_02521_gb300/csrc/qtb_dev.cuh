@@ -103,6 +103,9 @@ struct DSys {
     // rebuild; squared, in A^2
     double skin2;
     float skin2_f;
+    // its list radius (r_cut + its skin), squared
+    double rl2;
+    float rl2_f;
     // isothermal-isobaric cells: the physical displacement D allowed since the
     // last rebuild, squared (A^2), D = (skin (1 - tol) - tol r_cut)/2 with the
     // cell's share tol = kNptCellSkin skin / (r_cut + skin) of the list radius
